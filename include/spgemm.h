@@ -1,0 +1,250 @@
+/*
+ * spgemm.h -- C ABI of the GB300 semiring SpGEMM library (libspgemm.so).
+ *
+ * Computes C = A*B over a semiring (Section 1: "the product of two sparse
+ * matrices (SpGEMM) over a semiring"), column by column (Gustavson's
+ * formulation, Section 2.1), including the hypersparse DCSC block products and
+ * stage-wise merges of 2D Sparse SUMMA (Sections 2.3, 3.2, 3.5) run as a
+ * virtual g x g block grid on one GPU.
+ *
+ * Conventions for every entry point
+ *   - Indices are 0-based.  Matrices are CSC: int64 column pointers (n+1),
+ *     int32 row indices sorted strictly ascending inside each column, values
+ *     of the semiring's element type (double / float / uint8 / int64).
+ *   - Every pointer passed in a matrix handle is a DEVICE pointer on the
+ *     context's GPU, unless an entry point says otherwise.
+ *   - All work is enqueued on the context's CUDA stream.  Only calls that must
+ *     return a device-computed number to the host (spgemm_symbolic's nnz,
+ *     spgemm_numeric's output size) synchronise that stream.
+ *   - Every function returns spgemm_status_t and never aborts; the message of
+ *     the last failure is available from spgemm_last_error(ctx).
+ *   - Results are structural: C(i,j) exists iff some k pairs a stored A(i,k)
+ *     with a stored B(k,j); entries whose value equals the semiring zero are
+ *     kept.  C's rows are sorted ascending within each column.  For the three
+ *     exact semirings the result is bit-identical whatever the options
+ *     (predictor on/off, batching, grid size g, tier thresholds).
+ *
+ * Ownership
+ *   - Input handles made by spgemm_mat_csc / spgemm_mat_csr BORROW the
+ *     caller's arrays and never free them; the caller keeps them alive until
+ *     the handle is destroyed.
+ *   - Handles returned by the library (products, conversions) OWN arrays
+ *     allocated through the context allocator; spgemm_mat_destroy frees them.
+ *   - Temporaries come from a per-context workspace that grows on demand and
+ *     is released by spgemm_ctx_destroy.
+ */
+#ifndef SPGEMM_H
+#define SPGEMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SPGEMM_OK = 0,
+    SPGEMM_ERR_INVALID_ARG = 1,    /* null pointer, negative size, bad enum value      */
+    SPGEMM_ERR_DIM_MISMATCH = 2,   /* inner dimensions of A and B differ               */
+    SPGEMM_ERR_BAD_FORMAT = 3,     /* colptr not monotone, row out of range/unsorted   */
+    SPGEMM_ERR_OOM = 4,            /* the allocator returned NULL                      */
+    SPGEMM_ERR_INDEX_OVERFLOW = 5, /* a row count or dimension beyond int32 rows       */
+    SPGEMM_ERR_TIMEOUT = 6,        /* a bounded device wait gave up                    */
+    SPGEMM_ERR_CUDA = 7,           /* a CUDA runtime call failed                       */
+    SPGEMM_ERR_UNSUPPORTED = 8,    /* combination not implemented                      */
+    SPGEMM_ERR_STATE = 9           /* call out of order (e.g. numeric before symbolic) */
+} spgemm_status_t;
+
+/* The four semirings (Section 1 names SpGEMM over an arbitrary semiring). */
+typedef enum {
+    SPGEMM_PLUS_TIMES_F64 = 0, /* (+, *, 0) on double                                  */
+    SPGEMM_MIN_PLUS_F32 = 1,   /* (min, +, +inf) on float; fl32(a+b), round to nearest  */
+    SPGEMM_OR_AND_BOOL = 2,    /* (or, and, false) on uint8, nonzero byte = true        */
+    SPGEMM_PLUS_TIMES_I64 = 3  /* (+, *, 0) on int64, two's-complement wraparound       */
+} spgemm_semiring_t;
+
+typedef enum {
+    SPGEMM_FMT_CSC = 0,  /* Section 2.2, Fig. 5                                          */
+    SPGEMM_FMT_CSR = 1,  /* rows compressed; stored as the CSC of the transpose          */
+    SPGEMM_FMT_DCSC = 2  /* Section 2.3: JC, CP, IR, NUM (+ AUX column index)            */
+} spgemm_format_t;
+
+typedef struct spgemm_ctx* spgemm_ctx_t;
+typedef struct spgemm_mat* spgemm_mat_t;
+typedef struct spgemm_plan* spgemm_plan_t;
+
+/* Device allocator callbacks: alloc(bytes, user) returns a device pointer or
+ * NULL; free(ptr, user).  Both are called on the host thread that makes the
+ * library call, in stream order of the context stream. */
+typedef void* (*spgemm_alloc_fn)(size_t bytes, void* user);
+typedef void (*spgemm_free_fn)(void* ptr, void* user);
+
+/* Options.  spgemm_opts_default fills the defaults; a NULL opts pointer means
+ * defaults everywhere. */
+typedef struct {
+    int use_predictor;        /* 1: size outputs from the learned nnz predictor and skip
+                                 the exact symbolic pass; overflowed columns are redone
+                                 exactly, so the result is unchanged.  Default 0.      */
+    int summa_fused;          /* spgemm_summa_blocked: 1 = accumulate all stages of a
+                                 block column in one accumulator, 0 = materialise each
+                                 stage's partial products and merge them.  Default 0.  */
+    int summa_merge_every;    /* staged mode: merge after this many stages (0 = after
+                                 the last stage, the paper's buffered triples).        */
+    int warp_max_flops;       /* columns with flops <= this use warp-wide hash tables  */
+    int block_max_flops;      /* columns with flops <= this use CTA-wide hash tables;
+                                 larger columns use row-chunked dense accumulators     */
+    int dense_part_flops;     /* target flops per CTA when a dense column is split     */
+    float predictor_margin;   /* capacity = (1 + margin) * prediction (+ slack)        */
+    int reserved[8];
+} spgemm_opts_t;
+
+void spgemm_opts_default(spgemm_opts_t* opts);
+
+/* ---------------------------------------------------------------- context */
+/* stream: a cudaStream_t (NULL = legacy default stream).  alloc/free may be NULL,
+ * in which case cudaMallocAsync/cudaFreeAsync on the stream are used. */
+spgemm_status_t spgemm_ctx_create(spgemm_ctx_t* ctx, void* cuda_stream, spgemm_alloc_fn alloc,
+                                  spgemm_free_fn free_fn, void* alloc_user);
+spgemm_status_t spgemm_ctx_destroy(spgemm_ctx_t ctx);
+spgemm_status_t spgemm_ctx_set_stream(spgemm_ctx_t ctx, void* cuda_stream);
+const char* spgemm_last_error(spgemm_ctx_t ctx);
+const char* spgemm_status_string(spgemm_status_t s);
+
+/* ---------------------------------------------------------------- matrices */
+/* Borrowing CSC handle over device arrays (Section 2.2, Fig. 5): colptr[n+1]
+ * int64, rowidx[nnz] int32, vals[nnz] of the semiring type (vals may be NULL
+ * for a pattern-only matrix, read as all-ones / all-true / zero for min-plus).
+ * No check is run here; see spgemm_mat_validate. */
+spgemm_status_t spgemm_mat_csc(spgemm_ctx_t ctx, spgemm_mat_t* out, int64_t m, int64_t n, int64_t nnz,
+                               const int64_t* colptr, const int32_t* rowidx, const void* vals,
+                               spgemm_semiring_t semiring);
+/* Borrowing CSR handle: rowptr[m+1], colidx[nnz] sorted within each row. */
+spgemm_status_t spgemm_mat_csr(spgemm_ctx_t ctx, spgemm_mat_t* out, int64_t m, int64_t n, int64_t nnz,
+                               const int64_t* rowptr, const int32_t* colidx, const void* vals,
+                               spgemm_semiring_t semiring);
+/* Checks the CSC/CSR invariants on the device: colptr[0] == 0, colptr
+ * monotone, colptr[n] == nnz, rows in [0, m) and strictly ascending per column.
+ * Returns SPGEMM_ERR_BAD_FORMAT on the first violation found (synchronises). */
+spgemm_status_t spgemm_mat_validate(spgemm_mat_t mat);
+/* CSC -> DCSC (Section 2.3): JC = ids of the nzc nonempty columns, CP = their
+ * pointers (nzc+1), IR/NUM shared with the source (the result borrows them, so
+ * the source must outlive it).  With build_aux, AUX is built over chunks of
+ * ceil(n/nzc) columns: AUX[t] = position in JC of the first nonzero column with
+ * id >= t*chunk, last entry nzc (the paper leaves empty chunks unspecified;
+ * this reading makes chunk t's columns JC[AUX[t] .. AUX[t+1])). */
+spgemm_status_t spgemm_mat_to_dcsc(spgemm_ctx_t ctx, spgemm_mat_t csc, int build_aux, spgemm_mat_t* out);
+/* Transpose (Section 2.4 transposes B once): CSC of A^T, rows sorted.  Owns its arrays. */
+spgemm_status_t spgemm_mat_transpose(spgemm_ctx_t ctx, spgemm_mat_t a, spgemm_mat_t* out);
+/* Read back a handle's shape and device arrays.  For DCSC, colptr is CP,
+ * jc/aux/nzc/chunk describe the compressed column index (NULL outputs are
+ * skipped).  Pointers stay owned by the handle. */
+spgemm_status_t spgemm_mat_export(spgemm_mat_t mat, int64_t* m, int64_t* n, int64_t* nnz,
+                                  const int64_t** colptr, const int32_t** rowidx, const void** vals);
+spgemm_status_t spgemm_mat_export_dcsc(spgemm_mat_t mat, int64_t* nzc, const int32_t** jc,
+                                       const int32_t** aux, int64_t* naux, int64_t* chunk);
+spgemm_status_t spgemm_mat_format(spgemm_mat_t mat, spgemm_format_t* fmt, spgemm_semiring_t* sr);
+spgemm_status_t spgemm_mat_destroy(spgemm_mat_t mat);
+
+/* ---------------------------------------------------------------- measurement */
+/* Phases timed with CUDA events on the context stream when timing is enabled. */
+#define SPGEMM_NPHASE 8
+typedef enum {
+    SPGEMM_PHASE_ANALYZE = 0,        /* flops per column, binning, dense work items     */
+    SPGEMM_PHASE_SYMBOLIC_HASH = 1,  /* symbolic pass, hash-table tiers                 */
+    SPGEMM_PHASE_SYMBOLIC_DENSE = 2, /* symbolic pass, row-chunked dense tier           */
+    SPGEMM_PHASE_SCAN = 3,           /* column pointers of C                            */
+    SPGEMM_PHASE_NUMERIC_HASH = 4,   /* numeric pass, hash-table tiers                  */
+    SPGEMM_PHASE_NUMERIC_DENSE = 5,  /* numeric pass, row-chunked dense tier            */
+    SPGEMM_PHASE_PREDICT = 6,        /* predictor inference + overflow repair           */
+    SPGEMM_PHASE_MERGE = 7           /* SUMMA stage merge                               */
+} spgemm_phase_t;
+/* Enable (1) / disable (0) phase timing; enabling resets the accumulators. */
+spgemm_status_t spgemm_ctx_timing(spgemm_ctx_t ctx, int enable);
+/* Accumulated milliseconds and counts per (semiring, phase) since timing was
+ * enabled (synchronises the stream).  ms and count each hold 4 * SPGEMM_NPHASE
+ * entries, indexed [semiring * SPGEMM_NPHASE + phase]. */
+spgemm_status_t spgemm_ctx_phase_ms(spgemm_ctx_t ctx, double* ms, int64_t* count);
+/* Number of kernels this library has launched in the process so far. */
+int64_t spgemm_launch_count(void);
+
+/* ---------------------------------------------------------------- flat product */
+/* Plan C = A*B (A: m x k, B: k x n; CSC, CSR or DCSC operands): per-column flops
+ * flops_j = sum over k in B(:,j) of nnz(A(:,k)) (Section 1's "flops"), predictor
+ * features when enabled, and the binning of columns into accumulator tiers.
+ * Errors: DIM_MISMATCH when A.n != B.m, INVALID_ARG for semiring mismatch. */
+spgemm_status_t spgemm_plan(spgemm_ctx_t ctx, spgemm_mat_t A, spgemm_mat_t B, spgemm_semiring_t semiring,
+                            const spgemm_opts_t* opts, spgemm_plan_t* plan);
+/* Exact symbolic pass: nnz(C(:,j)) = |union of the row sets of A(:,k), k in B(:,j)|
+ * and C's column pointers; writes the total to *nnz_C (synchronises).  With the
+ * predictor enabled this call is optional: spgemm_numeric then sizes C from the
+ * predictions and repairs mispredicted columns exactly. */
+spgemm_status_t spgemm_symbolic(spgemm_plan_t plan, int64_t* nnz_C);
+/* Numeric pass: C(:,j) = (+)_{k in B(:,j)} A(:,k) (x) B(k,j), rows sorted; C is
+ * a new owning CSC handle (m x n).  Runs the symbolic pass first if it has not
+ * run and the predictor is off. */
+spgemm_status_t spgemm_numeric(spgemm_plan_t plan, spgemm_mat_t* C);
+/* Plan statistics: total flops, nnz(C) (after numeric), columns per tier,
+ * predictor overflow count.  Any output pointer may be NULL. */
+spgemm_status_t spgemm_plan_stats(spgemm_plan_t plan, int64_t* flops, int64_t* nnz_C, int64_t* tier_cols4,
+                                  int64_t* overflow_cols);
+/* Per-tier totals of the plan: columns, flops, nnz(C) (after the symbolic pass,
+ * else -1) and nnz of the B columns, for tiers {empty, warp hash, CTA hash,
+ * dense}; any pointer may be NULL. */
+spgemm_status_t spgemm_plan_tier_stats(spgemm_plan_t plan, int64_t* cols4, int64_t* flops4, int64_t* nnz4,
+                                       int64_t* bnnz4);
+spgemm_status_t spgemm_plan_destroy(spgemm_plan_t plan);
+
+/* One-call product: plan + symbolic + numeric. */
+spgemm_status_t spgemm_multiply(spgemm_ctx_t ctx, spgemm_mat_t A, spgemm_mat_t B, spgemm_semiring_t semiring,
+                                const spgemm_opts_t* opts, spgemm_mat_t* C);
+
+/* ---------------------------------------------------------------- 2D Sparse SUMMA */
+/* C = A*B on a virtual g x g grid (Sections 3.2 and 3.5; single-processor
+ * simulation as in Section 5.3): A and B are split into g x g blocks of
+ * ceil(dim/g) rows/columns (the last block may be short or empty), each block
+ * stored as DCSC with AUX; stage s computes the hypersparse block products
+ * A_{I,s} * B_{s,J} for all I, J and the stage partials are merged into C_{IJ}
+ * (Section 6.1 buffers the partial triples and merges them later).  Returns
+ * the flat CSC C (m x n), identical in structure to spgemm_multiply.
+ * Errors as spgemm_plan; INVALID_ARG for g < 1. */
+spgemm_status_t spgemm_summa_blocked(spgemm_ctx_t ctx, spgemm_mat_t A, spgemm_mat_t B, int g,
+                                     spgemm_semiring_t semiring, const spgemm_opts_t* opts, spgemm_mat_t* C);
+/* Block statistics of the last summa call on this context: per-stage flops
+ * (g entries) and the number of nonempty block products.  Outputs may be NULL. */
+spgemm_status_t spgemm_summa_stats(spgemm_ctx_t ctx, int64_t* stage_flops, int g, int64_t* nonempty_products);
+
+/* ---------------------------------------------------------------- batching */
+/* count independent products C[i] = A[i]*B[i] (all over one semiring) in one
+ * plan: the columns of every product are binned together and each tier runs
+ * as one persistent launch over a shared work queue; with opts->use_predictor
+ * the symbolic pass is skipped as in spgemm_numeric.  C[i] are owning CSC
+ * handles (they share one allocation, freed with the last of them). */
+spgemm_status_t spgemm_batch(spgemm_ctx_t ctx, int count, const spgemm_mat_t* A, const spgemm_mat_t* B,
+                             spgemm_semiring_t semiring, const spgemm_opts_t* opts, spgemm_mat_t* C);
+
+/* ---------------------------------------------------------------- learned predictor */
+/* The nnz predictor is a small MLP (8 -> 32 -> 32 -> 1, ReLU, fp32) over per-column
+ * features; it has no counterpart in the paper (its Section 8 lists structure
+ * prediction as future work).  Parameters are held by the context. */
+#define SPGEMM_PREDICTOR_NPARAM 1377
+/* Copy NPARAM floats (host pointer) into the context's predictor. */
+spgemm_status_t spgemm_predictor_set(spgemm_ctx_t ctx, const float* params_host);
+spgemm_status_t spgemm_predictor_get(spgemm_ctx_t ctx, float* params_host);
+/* Per-column features of C = A*B (device output, n x 8 floats row-major) and,
+ * when nnz_out is non-NULL, the exact nnz per column from the symbolic pass
+ * (device, n int64) -- the training labels. */
+spgemm_status_t spgemm_predictor_features(spgemm_ctx_t ctx, spgemm_mat_t A, spgemm_mat_t B, float* features_dev,
+                                          int64_t* nnz_out_dev);
+/* One Adam step of the MSE loss on log1p(nnz) over a device batch
+ * (X: N x 8 floats, y: N floats = log1p(nnz)); writes the loss (host) and,
+ * if grad_host is non-NULL, the gradient before the step (host, NPARAM). */
+spgemm_status_t spgemm_predictor_train_step(spgemm_ctx_t ctx, const float* X_dev, const float* y_dev, int64_t N,
+                                            float lr, float* loss_host, float* grad_host);
+/* Forward pass: pred_dev[i] = network(X[i]) (log1p scale). */
+spgemm_status_t spgemm_predictor_forward(spgemm_ctx_t ctx, const float* X_dev, int64_t N, float* pred_dev);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPGEMM_H */

@@ -1,0 +1,190 @@
+// Shared device-side definitions of the SpGEMM library: semiring traits,
+// matrix views (CSC / DCSC with AUX), and thread-group primitives.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include "spgemm.h"
+
+namespace sg {
+
+// ------------------------------------------------------------------ semirings
+// Each semiring gives the stored element type T, the shared-memory
+// accumulator type Acc (wide enough for a native shared atomic), the additive
+// identity, (x), and an atomic (+) on a shared accumulator (Section 1: SpGEMM
+// over an arbitrary semiring).
+struct PT64 {
+    using T = double;
+    using Acc = double;
+    static constexpr int id = SPGEMM_PLUS_TIMES_F64;
+    __device__ static Acc zero() { return 0.0; }
+    __device__ static Acc one() { return 1.0; }
+    __device__ static Acc mul(T a, T b) { return __dmul_rn(a, b); }
+    __device__ static Acc add(Acc a, Acc b) { return __dadd_rn(a, b); }
+    __device__ static void atomic_add(Acc* p, Acc x) { atomicAdd(p, x); }
+    __device__ static T out(Acc a) { return a; }
+};
+
+struct MP32 {
+    using T = float;
+    using Acc = float;
+    static constexpr int id = SPGEMM_MIN_PLUS_F32;
+    __device__ static Acc zero() { return CUDART_INF_F; }
+    __device__ static Acc one() { return 0.0f; }
+    __device__ static Acc mul(T a, T b) { return __fadd_rn(a, b); }
+    __device__ static Acc add(Acc a, Acc b) { return b < a ? b : a; }
+    // min on floats through integer atomics: for x >= 0 the IEEE bit patterns
+    // order like signed ints; for x < 0 they order in reverse as unsigned ints.
+    __device__ static void atomic_add(Acc* p, Acc x) {
+        if (x >= 0.0f) atomicMin(reinterpret_cast<int*>(p), __float_as_int(x));
+        else atomicMax(reinterpret_cast<unsigned int*>(p), __float_as_uint(x));
+    }
+    __device__ static T out(Acc a) { return a; }
+};
+
+struct BOOL8 {
+    using T = uint8_t;
+    using Acc = unsigned int;
+    static constexpr int id = SPGEMM_OR_AND_BOOL;
+    __device__ static Acc zero() { return 0u; }
+    __device__ static Acc one() { return 1u; }
+    __device__ static Acc mul(T a, T b) { return (a != 0 && b != 0) ? 1u : 0u; }
+    __device__ static Acc add(Acc a, Acc b) { return a | b; }
+    __device__ static void atomic_add(Acc* p, Acc x) { if (x) atomicOr(p, x); }
+    __device__ static T out(Acc a) { return (T)(a != 0); }
+};
+
+struct PTI64 {
+    using T = int64_t;
+    using Acc = unsigned long long;
+    static constexpr int id = SPGEMM_PLUS_TIMES_I64;
+    __device__ static Acc zero() { return 0ull; }
+    __device__ static Acc one() { return 1ull; }
+    __device__ static Acc mul(T a, T b) { return (Acc)a * (Acc)b; }
+    __device__ static Acc add(Acc a, Acc b) { return a + b; }
+    __device__ static void atomic_add(Acc* p, Acc x) { atomicAdd(p, x); }
+    __device__ static T out(Acc a) { return (T)a; }
+};
+
+// ------------------------------------------------------------------ matrix view
+// CSC when jc == nullptr; DCSC (Section 2.3) otherwise: cp[p], jc[p] describe the
+// p-th nonempty column, aux indexes chunks of `chunk` columns.
+struct DMat {
+    int64_t m = 0, n = 0;     // rows, columns (full dimensions)
+    int64_t nzc = 0;          // stored columns (n for CSC)
+    int64_t nnz = 0;
+    const int64_t* cp = nullptr;
+    const int32_t* jc = nullptr;
+    const int32_t* aux = nullptr;
+    int64_t chunk = 1, naux = 0;
+    const int32_t* ir = nullptr;
+    const void* num = nullptr;  // nullptr: pattern only (values = semiring one)
+};
+
+template <class SR>
+__device__ __forceinline__ typename SR::T load_val(const DMat& M, int64_t idx) {
+    if (M.num == nullptr) return (typename SR::T)SR::one();
+    return __ldg(reinterpret_cast<const typename SR::T*>(M.num) + idx);
+}
+
+// Column k of A as a half-open range of positions; empty -> s == e.
+// DCSC: chunk t = k / chunk holds JC positions [aux[t], aux[t+1]) (AUX, Section 2.3).
+__device__ __forceinline__ void col_range(const DMat& A, int32_t k, int64_t& s, int64_t& e) {
+    if (k < 0 || (int64_t)k >= A.n) {   // malformed operand: treat as an empty column
+        s = e = 0;
+        return;
+    }
+    if (A.jc == nullptr) {
+        s = __ldg(A.cp + k);
+        e = __ldg(A.cp + k + 1);
+        return;
+    }
+    int64_t t = k / A.chunk;
+    int32_t p0 = __ldg(A.aux + t), p1 = __ldg(A.aux + t + 1);
+    for (int32_t p = p0; p < p1; ++p) {
+        int32_t c = __ldg(A.jc + p);
+        if (c == k) { s = __ldg(A.cp + p); e = __ldg(A.cp + p + 1); return; }
+        if (c > k) break;
+    }
+    s = e = 0;
+}
+
+__device__ __forceinline__ int64_t col_len(const DMat& A, int32_t k) {
+    int64_t s, e;
+    col_range(A, k, s, e);
+    return e - s;
+}
+
+// ------------------------------------------------------------------ group helpers
+// A "group" of GS threads cooperates on one output column: GS == 32 is a warp,
+// GS == blockDim.x is the whole CTA.
+template <int GS>
+struct Group {
+    static_assert(GS == 32 || GS % 32 == 0, "group size");
+    __device__ static int lane() { return threadIdx.x % GS; }
+    __device__ static int gid() { return threadIdx.x / GS; }
+    __device__ static void sync() {
+        if constexpr (GS == 32) __syncwarp();
+        else __syncthreads();
+    }
+};
+
+__device__ __forceinline__ int warp_incl_scan(int v) {
+    int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+__device__ __forceinline__ long long warp_incl_scan64(long long v) {
+    int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        long long t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Inclusive scan over a group of GS threads (GS a multiple of 32), through
+// `scratch` (GS/32 ints).  Also returns the group total.
+template <int GS>
+__device__ __forceinline__ int group_incl_scan(int v, int* scratch, int& total) {
+    int x = warp_incl_scan(v);
+    if constexpr (GS == 32) {
+        total = __shfl_sync(0xffffffffu, x, 31);
+        return x;
+    } else {
+        constexpr int NW = GS / 32;
+        int lane = threadIdx.x & 31, w = (threadIdx.x % GS) >> 5;
+        if (lane == 31) scratch[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            int s = lane < NW ? scratch[lane] : 0;
+            s = warp_incl_scan(s);
+            if (lane < NW) scratch[lane] = s;
+        }
+        __syncthreads();
+        int add = w > 0 ? scratch[w - 1] : 0;
+        total = scratch[NW - 1];
+        __syncthreads();
+        return x + add;
+    }
+}
+
+__host__ __device__ __forceinline__ int64_t ceil_div64(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+__device__ __forceinline__ uint32_t hash_row(int32_t r) { return (uint32_t)r * 0x9E3779B1u; }
+
+}  // namespace sg

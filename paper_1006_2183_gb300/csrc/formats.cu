@@ -1,0 +1,376 @@
+// Format conversions: transpose (Section 2.4 transposes B once as a
+// preprocessing step), CSC -> DCSC with the AUX column index (Section 2.3),
+// and device-side validation of the CSC invariants.
+#include <algorithm>
+
+#include "internal.cuh"
+
+using namespace sg;
+
+namespace {
+
+constexpr int RS_BLOCK = 256;
+constexpr int RS_ROUNDS = 8;
+constexpr int RS_TILE = RS_BLOCK * RS_ROUNDS;
+constexpr int RS_WARPS = RS_BLOCK / 32;
+
+// ---------------------------------------------------------------- stable LSD radix sort
+// (uint32 key, uint32 payload) pairs, 8-bit digits.  Tile order inside a CTA is
+// element e = round * 256 + tid, ranks are assigned in that order, so each pass is
+// stable and the passes compose into a stable sort.
+__global__ void __launch_bounds__(RS_BLOCK) k_rs_hist(const uint32_t* __restrict__ keys, int64_t n, int shift,
+                                                      int64_t ntiles, int64_t* __restrict__ hist) {
+    __shared__ int cnt[256];
+    cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t t0 = (int64_t)blockIdx.x * RS_TILE;
+    for (int r = 0; r < RS_ROUNDS; ++r) {
+        int64_t e = t0 + r * RS_BLOCK + threadIdx.x;
+        if (e < n) atomicAdd(&cnt[(keys[e] >> shift) & 255u], 1);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(RS_BLOCK) k_rs_scatter(const uint32_t* __restrict__ kin,
+                                                         const uint32_t* __restrict__ vin, int64_t n, int shift,
+                                                         int64_t ntiles, const int64_t* __restrict__ off,
+                                                         uint32_t* __restrict__ kout, uint32_t* __restrict__ vout) {
+    __shared__ int run[256];
+    __shared__ int wcnt[RS_WARPS][256];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    run[tid] = 0;
+    const int64_t t0 = (int64_t)blockIdx.x * RS_TILE;
+    for (int r = 0; r < RS_ROUNDS; ++r) {
+        const int64_t e = t0 + r * RS_BLOCK + tid;
+        const bool valid = e < n;
+        uint32_t key = valid ? kin[e] : 0u;
+        uint32_t val = valid ? vin[e] : 0u;
+        int d = valid ? (int)((key >> shift) & 255u) : 256;
+        unsigned mask = __match_any_sync(0xffffffffu, d);
+        int rank = __popc(mask & ((1u << lane) - 1u));
+        int leader = __ffs(mask) - 1;
+#pragma unroll
+        for (int ww = 0; ww < RS_WARPS; ++ww) wcnt[ww][tid] = 0;
+        __syncthreads();
+        if (valid && lane == leader) wcnt[w][d] = __popc(mask);
+        __syncthreads();
+        {
+            int acc = run[tid];
+#pragma unroll
+            for (int ww = 0; ww < RS_WARPS; ++ww) {
+                int c = wcnt[ww][tid];
+                wcnt[ww][tid] = acc;
+                acc += c;
+            }
+            run[tid] = acc;
+        }
+        __syncthreads();
+        if (valid) {
+            int64_t pos = off[(int64_t)d * ntiles + blockIdx.x] + wcnt[w][d] + rank;
+            kout[pos] = key;
+            vout[pos] = val;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_iota_u32(uint32_t* p, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = (uint32_t)i;
+}
+
+__global__ void k_expand_cols(const int64_t* __restrict__ cp, int64_t n, int32_t* __restrict__ col) {
+    int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+    int sub = threadIdx.x & 7;
+    if (j >= n) return;
+    for (int64_t t = cp[j] + sub; t < cp[j + 1]; t += 8) col[t] = (int32_t)j;
+}
+
+__global__ void k_row_hist(const int32_t* __restrict__ ir, int64_t nnz, int64_t m, int64_t* __restrict__ cnt) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += (int64_t)gridDim.x * blockDim.x)
+        if (ir[i] >= 0 && ir[i] < m) atomicAdd(reinterpret_cast<unsigned long long*>(cnt + ir[i]), 1ull);
+}
+
+template <int W>
+struct Word;
+template <>
+struct Word<1> { using T = uint8_t; };
+template <>
+struct Word<4> { using T = uint32_t; };
+template <>
+struct Word<8> { using T = uint64_t; };
+
+template <int W>
+__global__ void k_gather(const uint32_t* __restrict__ perm, const int32_t* __restrict__ colid,
+                         const void* __restrict__ vin, int64_t nnz, int32_t* __restrict__ ir_out,
+                         void* __restrict__ vout) {
+    using T = typename Word<W>::T;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t s = perm[i];
+        ir_out[i] = colid[s];
+        if (vin) reinterpret_cast<T*>(vout)[i] = reinterpret_cast<const T*>(vin)[s];
+    }
+}
+
+int grid_for(int64_t n, int block = 256) { return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div64(n, block), 152 * 32)); }
+
+// ---------------------------------------------------------------- DCSC
+__global__ void k_nonempty(const int64_t* __restrict__ cp, int64_t n, int64_t* __restrict__ flag) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+        flag[j] = cp[j + 1] > cp[j] ? 1 : 0;
+}
+
+__global__ void k_dcsc_scatter(const int64_t* __restrict__ cp, int64_t n, const int64_t* __restrict__ pos,
+                               int32_t* __restrict__ jc, int64_t* __restrict__ dcp) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        if (cp[j + 1] > cp[j]) {
+            jc[pos[j]] = (int32_t)j;
+            dcp[pos[j]] = cp[j];
+        }
+        if (j == n - 1) dcp[pos[n]] = cp[n];
+    }
+}
+
+// AUX[t] = first JC position whose column id >= t * chunk; AUX[naux] = nzc
+__global__ void k_aux(const int32_t* __restrict__ jc, int64_t nzc, int64_t chunk, int64_t naux,
+                      int32_t* __restrict__ aux) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t <= naux; t += (int64_t)gridDim.x * blockDim.x) {
+        if (t == naux) {
+            aux[t] = (int32_t)nzc;
+            continue;
+        }
+        int64_t v = t * chunk, lo = 0, hi = nzc;
+        while (lo < hi) {
+            int64_t mid = (lo + hi) >> 1;
+            if ((int64_t)jc[mid] < v) lo = mid + 1;
+            else hi = mid;
+        }
+        aux[t] = (int32_t)lo;
+    }
+}
+
+// ---------------------------------------------------------------- validation
+__global__ void k_validate(const int64_t* __restrict__ cp, const int32_t* __restrict__ ir, int64_t m, int64_t n,
+                           int64_t nnz, int* __restrict__ bad) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        int64_t s = cp[j], e = cp[j + 1];
+        if (j == 0 && s != 0) { atomicMax(bad, 1); continue; }
+        if (j == n - 1 && e != nnz) { atomicMax(bad, 2); continue; }
+        if (e < s || s < 0 || e > nnz) { atomicMax(bad, 3); continue; }
+        int32_t prev = -1;
+        for (int64_t t = s; t < e; ++t) {
+            int32_t r = ir[t];
+            if (r < 0 || r >= m) { atomicMax(bad, 4); break; }
+            if (r <= prev) { atomicMax(bad, 5); break; }
+            prev = r;
+        }
+    }
+}
+
+}  // namespace
+
+// CSC (m x n) -> CSC of the transpose (n x m), rows sorted.  `out` is filled in place.
+spgemm_status_t transpose_csc(spgemm_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const int64_t* cp,
+                              const int32_t* ir, const void* num, size_t w, spgemm_mat_t out) {
+    cudaStream_t st = ctx->stream;
+    if (nnz > (int64_t)UINT32_MAX) return set_err(ctx, SPGEMM_ERR_INDEX_OVERFLOW, "transpose: nnz beyond 2^32");
+    const int64_t ntiles = std::max<int64_t>(1, ceil_div64(nnz, RS_TILE));
+    auto cpb = ctx_buf(ctx, 8 * (m + 1));
+    auto irb = ctx_buf(ctx, 4 * std::max<int64_t>(nnz, 1));
+    auto vb = ctx_buf(ctx, w * std::max<int64_t>(nnz, 1));
+    size_t tmp_bytes = 4 * 4 * std::max<int64_t>(nnz, 1) + 4 * std::max<int64_t>(nnz, 1) +
+                       8 * (256 * ntiles + 1) * 2 + scan_tmp_bytes(std::max<int64_t>(256 * ntiles, m)) + 8 * (m + 1) +
+                       1024;
+    auto tmp = ctx_buf(ctx, tmp_bytes);
+    if (!cpb || !irb || !vb || !tmp) return set_err(ctx, SPGEMM_ERR_OOM, "transpose buffers");
+    char* t = (char*)tmp->p;
+    const int64_t nz1 = std::max<int64_t>(nnz, 1);
+    uint32_t* k0 = (uint32_t*)t; t += 4 * nz1;
+    uint32_t* k1 = (uint32_t*)t; t += 4 * nz1;
+    uint32_t* v0 = (uint32_t*)t; t += 4 * nz1;
+    uint32_t* v1 = (uint32_t*)t; t += 4 * nz1;
+    int32_t* colid = (int32_t*)t; t += 4 * nz1;
+    t = (char*)(((uintptr_t)t + 255) / 256 * 256);
+    int64_t* hist = (int64_t*)t; t += 8 * (256 * ntiles + 1);
+    int64_t* off = (int64_t*)t; t += 8 * (256 * ntiles + 1);
+    int64_t* rowcnt = (int64_t*)t; t += 8 * (m + 1);
+    void* stmp = t;
+    int64_t* tcp = (int64_t*)cpb->p;
+    if (nnz > 0) {
+        SG_CUDA(ctx, cudaMemcpyAsync(k0, ir, 4 * nnz, cudaMemcpyDeviceToDevice, st));
+        k_iota_u32<<<grid_for(nnz), 256, 0, st>>>(v0, nnz);
+        note_launch();
+        k_expand_cols<<<(int)ceil_div64(n * 8, 256) + 1, 256, 0, st>>>(cp, n, colid);
+        note_launch();
+        int bits = 0;
+        while (bits < 32 && (int64_t(1) << bits) < m) ++bits;
+        for (int shift = 0; shift < bits; shift += 8) {
+            k_rs_hist<<<(int)ntiles, RS_BLOCK, 0, st>>>(k0, nnz, shift, ntiles, hist);
+            note_launch();
+            launch_exclusive_scan(st, hist, 256 * ntiles, off, stmp);
+            k_rs_scatter<<<(int)ntiles, RS_BLOCK, 0, st>>>(k0, v0, nnz, shift, ntiles, off, k1, v1);
+            note_launch();
+            std::swap(k0, k1);
+            std::swap(v0, v1);
+        }
+        SG_CUDA(ctx, cudaMemsetAsync(rowcnt, 0, 8 * m, st));
+        k_row_hist<<<grid_for(nnz), 256, 0, st>>>(ir, nnz, m, rowcnt);
+        note_launch();
+        launch_exclusive_scan(st, rowcnt, m, tcp, stmp);
+        note_launch();
+        switch (w) {
+        case 1: k_gather<1><<<grid_for(nnz), 256, 0, st>>>(v0, colid, num, nnz, (int32_t*)irb->p, vb->p); break;
+        case 4: k_gather<4><<<grid_for(nnz), 256, 0, st>>>(v0, colid, num, nnz, (int32_t*)irb->p, vb->p); break;
+        default: k_gather<8><<<grid_for(nnz), 256, 0, st>>>(v0, colid, num, nnz, (int32_t*)irb->p, vb->p); break;
+        }
+    } else {
+        SG_CUDA(ctx, cudaMemsetAsync(tcp, 0, 8 * (m + 1), st));
+    }
+    SG_CUDA(ctx, cudaGetLastError());
+    out->ctx = ctx;
+    out->fmt = SPGEMM_FMT_CSC;
+    out->m = n;
+    out->n = m;
+    out->nnz = nnz;
+    out->nzc = m;
+    out->cp = tcp;
+    out->ir = (const int32_t*)irb->p;
+    out->num = num ? vb->p : nullptr;
+    out->owned = {cpb, irb, vb, tmp};
+    // the temporaries are released with the handle's first owner release; drop them now
+    out->owned.pop_back();
+    return SPGEMM_OK;
+}
+
+spgemm_status_t make_dcsc(spgemm_ctx* ctx, const spgemm_mat* M, bool with_aux, spgemm_mat* out) {
+    cudaStream_t st = ctx->stream;
+    const int64_t n = M->n;
+    auto tmp = ctx_buf(ctx, 8 * (n + 1) * 2 + scan_tmp_bytes(n));
+    if (!tmp) return set_err(ctx, SPGEMM_ERR_OOM, "dcsc temporaries");
+    int64_t* flag = (int64_t*)tmp->p;
+    int64_t* pos = flag + (n + 1);
+    void* stmp = pos + (n + 1);
+    int64_t nzc = 0;
+    if (n > 0) {
+        k_nonempty<<<grid_for(n), 256, 0, st>>>(M->cp, n, flag);
+        note_launch();
+        launch_exclusive_scan(st, flag, n, pos, stmp);
+        SG_CUDA(ctx, cudaMemcpyAsync(&nzc, pos + n, 8, cudaMemcpyDeviceToHost, st));
+        SG_TRY(sync_ctx(ctx));
+    }
+    const int64_t chunk = n == 0 ? 1 : (nzc > 0 ? ceil_div64(n, nzc) : n);
+    const int64_t naux = n == 0 ? 0 : ceil_div64(n, chunk);
+    auto jcb = ctx_buf(ctx, 4 * std::max<int64_t>(nzc, 1));
+    auto cpb = ctx_buf(ctx, 8 * (nzc + 1));
+    std::shared_ptr<DevBuf> auxb;
+    if (with_aux) auxb = ctx_buf(ctx, 4 * (naux + 1));
+    if (!jcb || !cpb || (with_aux && !auxb)) return set_err(ctx, SPGEMM_ERR_OOM, "dcsc arrays");
+    if (n > 0) {
+        k_dcsc_scatter<<<grid_for(n), 256, 0, st>>>(M->cp, n, pos, (int32_t*)jcb->p, (int64_t*)cpb->p);
+        note_launch();
+    } else {
+        SG_CUDA(ctx, cudaMemsetAsync(cpb->p, 0, 8, st));
+    }
+    if (with_aux) {
+        k_aux<<<grid_for(naux + 1), 256, 0, st>>>((int32_t*)jcb->p, nzc, chunk, naux, (int32_t*)auxb->p);
+        note_launch();
+    }
+    SG_CUDA(ctx, cudaGetLastError());
+    out->ctx = ctx;
+    out->fmt = SPGEMM_FMT_DCSC;
+    out->sr = M->sr;
+    out->m = M->m;
+    out->n = n;
+    out->nnz = M->nnz;
+    out->nzc = nzc;
+    out->cp = (const int64_t*)cpb->p;
+    out->jc = (const int32_t*)jcb->p;
+    out->aux = with_aux ? (const int32_t*)auxb->p : nullptr;
+    out->naux = with_aux ? naux : 0;
+    out->chunk = chunk;
+    out->ir = M->ir;
+    out->num = M->num;
+    out->owned = M->owned;   // share the source's arrays if it owns them
+    out->owned.push_back(jcb);
+    out->owned.push_back(cpb);
+    if (auxb) out->owned.push_back(auxb);
+    return SPGEMM_OK;
+}
+
+extern "C" {
+
+spgemm_status_t spgemm_mat_transpose(spgemm_ctx_t ctx, spgemm_mat_t a, spgemm_mat_t* out) {
+    if (!ctx || !a || !out) return SPGEMM_ERR_INVALID_ARG;
+    if (a->fmt == SPGEMM_FMT_DCSC) return set_err(ctx, SPGEMM_ERR_UNSUPPORTED, "transpose of a DCSC handle");
+    auto* T = new spgemm_mat();
+    spgemm_status_t s;
+    if (a->fmt == SPGEMM_FMT_CSR) {
+        // CSR(A) stores CSC(A^T): its arrays already are A^T in CSC; copy nothing, borrow
+        T->ctx = ctx;
+        T->fmt = SPGEMM_FMT_CSC;
+        T->m = a->n;
+        T->n = a->m;
+        T->nnz = a->nnz;
+        T->nzc = a->m;
+        T->cp = a->cp;
+        T->ir = a->ir;
+        T->num = a->num;
+        T->owned = a->owned;
+        s = SPGEMM_OK;
+    } else {
+        s = transpose_csc(ctx, a->m, a->n, a->nnz, a->cp, a->ir, a->num, sr_size(a->sr), T);
+    }
+    if (s != SPGEMM_OK) {
+        delete T;
+        return s;
+    }
+    T->sr = a->sr;
+    *out = T;
+    return SPGEMM_OK;
+}
+
+spgemm_status_t spgemm_mat_to_dcsc(spgemm_ctx_t ctx, spgemm_mat_t csc, int build_aux, spgemm_mat_t* out) {
+    if (!ctx || !csc || !out) return SPGEMM_ERR_INVALID_ARG;
+    if (csc->fmt != SPGEMM_FMT_CSC) return set_err(ctx, SPGEMM_ERR_INVALID_ARG, "to_dcsc expects a CSC handle");
+    auto* D = new spgemm_mat();
+    spgemm_status_t s = make_dcsc(ctx, csc, build_aux != 0, D);
+    if (s != SPGEMM_OK) {
+        delete D;
+        return s;
+    }
+    *out = D;
+    return SPGEMM_OK;
+}
+
+spgemm_status_t spgemm_mat_validate(spgemm_mat_t M) {
+    if (!M) return SPGEMM_ERR_INVALID_ARG;
+    spgemm_ctx* ctx = M->ctx;
+    if (M->fmt == SPGEMM_FMT_DCSC) return set_err(ctx, SPGEMM_ERR_UNSUPPORTED, "validate of DCSC");
+    // stored arrays: CSC with (rows = stored m) x (cols = stored n)
+    const int64_t sm = M->fmt == SPGEMM_FMT_CSR ? M->n : M->m;
+    const int64_t sn = M->fmt == SPGEMM_FMT_CSR ? M->m : M->n;
+    auto flag = ctx_buf(ctx, 16);
+    if (!flag) return set_err(ctx, SPGEMM_ERR_OOM, "validate flag");
+    SG_CUDA(ctx, cudaMemsetAsync(flag->p, 0, 4, ctx->stream));
+    int h = 0;
+    if (sn > 0) {
+        k_validate<<<grid_for(sn), 256, 0, ctx->stream>>>(M->cp, M->ir, sm, sn, M->nnz, (int*)flag->p);
+        note_launch();
+    } else {
+        int64_t c0 = -1;
+        SG_CUDA(ctx, cudaMemcpyAsync(&c0, M->cp, 8, cudaMemcpyDeviceToHost, ctx->stream));
+        SG_TRY(sync_ctx(ctx));
+        if (c0 != 0 || M->nnz != 0) h = 1;
+    }
+    if (sn > 0) {
+        SG_CUDA(ctx, cudaMemcpyAsync(&h, flag->p, 4, cudaMemcpyDeviceToHost, ctx->stream));
+        SG_TRY(sync_ctx(ctx));
+    }
+    static const char* why[] = {"", "colptr[0] != 0", "colptr[n] != nnz", "colptr not monotone",
+                                "row index out of range", "rows not strictly ascending in a column"};
+    if (h) return set_err(ctx, SPGEMM_ERR_BAD_FORMAT, "%s", why[h < 6 ? h : 0]);
+    return SPGEMM_OK;
+}
+
+}  // extern "C"

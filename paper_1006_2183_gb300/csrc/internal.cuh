@@ -1,0 +1,146 @@
+// Host-side internals shared by the C-ABI translation units.
+#pragma once
+#include <cstdarg>
+#include <cstdio>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+struct spgemm_ctx {
+    cudaStream_t stream = nullptr;
+    spgemm_alloc_fn alloc = nullptr;
+    spgemm_free_fn free_fn = nullptr;
+    void* user = nullptr;
+    int device = 0;
+    std::string err;
+    // learned predictor (device parameters + Adam moments)
+    float* pred = nullptr;      // NPARAM
+    float* adam_m = nullptr;
+    float* adam_v = nullptr;
+    float* grad = nullptr;      // NPARAM (device gradient buffer)
+    int adam_t = 0;
+    bool pred_ready = false;
+    // phase timing (CUDA events on the context stream)
+    bool timing = false;
+    struct Pending { int slot; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
+    double phase_ms[4 * SPGEMM_NPHASE] = {0};
+    int64_t phase_cnt[4 * SPGEMM_NPHASE] = {0};
+    // statistics of the last SUMMA call
+    std::vector<int64_t> summa_stage_flops;
+    int64_t summa_nonempty = 0;
+};
+
+// Shared ownership of an allocation (batch outputs share one buffer).
+struct DevBuf {
+    spgemm_ctx* ctx;
+    void* p;
+    DevBuf(spgemm_ctx* c, void* q) : ctx(c), p(q) {}
+    ~DevBuf();
+};
+
+struct spgemm_mat {
+    spgemm_ctx* ctx = nullptr;
+    spgemm_format_t fmt = SPGEMM_FMT_CSC;
+    spgemm_semiring_t sr = SPGEMM_PLUS_TIMES_F64;
+    int64_t m = 0, n = 0, nnz = 0;   // logical dimensions (CSR: rows x cols of the matrix)
+    // stored compressed arrays: CSC (and CSR as the CSC of the transpose)
+    const int64_t* cp = nullptr;
+    const int32_t* ir = nullptr;
+    const void* num = nullptr;
+    // DCSC extras
+    int64_t nzc = 0;
+    const int32_t* jc = nullptr;
+    const int32_t* aux = nullptr;
+    int64_t naux = 0, chunk = 1;
+    std::vector<std::shared_ptr<DevBuf>> owned;
+};
+
+struct spgemm_plan {
+    spgemm_ctx* ctx = nullptr;
+    spgemm_semiring_t sr;
+    spgemm_opts_t opts;
+    sg::DMat A, B;
+    spgemm_mat_t Aconv = nullptr, Bconv = nullptr;   // owned conversions (CSR inputs)
+    sg::TierCfg cfg;
+    int64_t m = 0, n = 0;          // output dimensions
+    int64_t G = 0;                 // dense chunks per column
+    std::vector<std::shared_ptr<DevBuf>> bufs;
+    int64_t* flops = nullptr;
+    uint8_t* bin = nullptr;
+    unsigned long long* ctr = nullptr;   // bin_count[NBIN], bin_cursor[NBIN], flops_total, nitems
+    int64_t* bin_off_dev = nullptr;
+    int32_t* list = nullptr;
+    int2* items = nullptr;
+    int8_t* nparts = nullptr;
+    int32_t* cursors = nullptr;
+    int32_t* part_count = nullptr;
+    int64_t* nnz_col = nullptr;
+    void* scan_tmp = nullptr;
+    float* feat = nullptr;
+    std::shared_ptr<DevBuf> Ccp_buf;
+    int64_t* Ccp = nullptr;
+    int64_t bin_cnt[sg::NBIN] = {0};
+    int64_t bin_off[sg::NBIN] = {0};
+    int64_t flops_total = 0;
+    int64_t nitems = 0;
+    int64_t nnzC = -1;
+    bool symbolic_done = false;
+    int64_t overflow_cols = 0;
+    // predictor path state
+    bool predicted = false;
+};
+
+spgemm_status_t set_err(spgemm_ctx* ctx, spgemm_status_t s, const char* fmt, ...);
+
+// Records CUDA events around a phase when the context has timing enabled.
+struct PhaseTimer {
+    spgemm_ctx* ctx;
+    int phase;
+    cudaEvent_t a = nullptr;
+    PhaseTimer(spgemm_ctx* c, int ph, int sr) : ctx(c), phase(sr * SPGEMM_NPHASE + ph) {
+        if (ctx->timing) {
+            cudaEventCreate(&a);
+            cudaEventRecord(a, ctx->stream);
+        }
+    }
+    ~PhaseTimer() {
+        if (a) {
+            cudaEvent_t b;
+            cudaEventCreate(&b);
+            cudaEventRecord(b, ctx->stream);
+            ctx->pending.push_back({phase, a, b});
+        }
+    }
+};
+void* ctx_alloc(spgemm_ctx* ctx, size_t bytes);
+void ctx_free(spgemm_ctx* ctx, void* p);
+std::shared_ptr<DevBuf> ctx_buf(spgemm_ctx* ctx, size_t bytes);
+size_t sr_size(spgemm_semiring_t sr);
+sg::DMat dmat_of(const spgemm_mat* M);
+spgemm_status_t check_cuda(spgemm_ctx* ctx, cudaError_t e, const char* what);
+spgemm_status_t sync_ctx(spgemm_ctx* ctx);
+
+// formats.cu
+spgemm_status_t transpose_csc(spgemm_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const int64_t* cp,
+                              const int32_t* ir, const void* num, size_t w, spgemm_mat_t out_handle);
+spgemm_status_t make_dcsc(spgemm_ctx* ctx, const spgemm_mat* csc, bool aux, spgemm_mat* out);
+
+// flat product pieces used by summa/batch
+spgemm_status_t plan_build(spgemm_ctx* ctx, const sg::DMat& A, const sg::DMat& B, spgemm_semiring_t sr,
+                           const spgemm_opts_t& opts, struct spgemm_plan* P);
+
+#define SG_CUDA(ctx, call)                                                  \
+    do {                                                                    \
+        cudaError_t e__ = (call);                                           \
+        if (e__ != cudaSuccess) return check_cuda((ctx), e__, #call);       \
+    } while (0)
+
+#define SG_TRY(call)                               \
+    do {                                           \
+        spgemm_status_t s__ = (call);              \
+        if (s__ != SPGEMM_OK) return s__;          \
+    } while (0)

@@ -1,0 +1,50 @@
+"""Helpers shared by the GPU parity tests (compare the CUDA path with the oracle)."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+from helpers import FP64_RTOL, PT_F64
+
+_lib_built = False
+
+
+def sp():
+    """The binding, with the library built first (on the box it is built from source)."""
+    global _lib_built
+    if not _lib_built:
+        from paper_1006_2183_gb300 import build
+        build.build()
+        _lib_built = True
+    from paper_1006_2183_gb300 import spgemm
+    return spgemm
+
+
+def assert_matches(C, R, sr, rtol=FP64_RTOL, what=""):
+    """C (binding HostCSC) vs R (oracle): structure bit-exact, values per the semiring contract."""
+    assert (C.m, C.n) == (R.m, R.n), what
+    np.testing.assert_array_equal(np.asarray(C.colptr), np.asarray(R.colptr), err_msg=f"colptr {what}")
+    np.testing.assert_array_equal(np.asarray(C.rowidx), np.asarray(R.rowidx), err_msg=f"rowidx {what}")
+    cv, rv = np.asarray(C.vals), np.asarray(R.vals)
+    if sr == PT_F64:
+        err = np.abs(cv - rv)
+        bad = err > rtol * np.abs(rv)
+        if bad.any():
+            i = int(np.nonzero(bad)[0][0])
+            raise AssertionError(f"{bad.sum()} values beyond rtol {rtol} {what}: first at {i}: {cv[i]} vs {rv[i]}")
+    else:
+        np.testing.assert_array_equal(cv, rv, err_msg=f"values {what}")
+
+
+def gpu_product(ctx, A, B, sr, opts=None):
+    s = sp()
+    dA = s.Matrix.from_host(ctx, A, sr)
+    dB = dA if B is A else s.Matrix.from_host(ctx, B, sr)
+    return s.spgemm_multiply(ctx, dA, dB, sr, opts).to_host()
+
+
+def check_product(ctx, A, B, sr, opts=None, what=""):
+    C = gpu_product(ctx, A, B, sr, opts)
+    R = oracle.spgemm(A, B, sr)
+    assert_matches(C, R, sr, what=what)
+    return C

@@ -1,0 +1,227 @@
+"""Parity of the flat CUDA product (plan -> symbolic -> numeric) with the CPU oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import assert_matches, check_product, gpu_product, sp
+from helpers import MP_F32, OR_BOOL, PT_F64, PT_I64
+from paper_1006_2183_gb300 import gen
+from paper_1006_2183_gb300.gen import CSC
+
+pytestmark = pytest.mark.gpu
+SEMIRINGS = [PT_F64, MP_F32, OR_BOOL, PT_I64]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    s = sp()
+    return s.Context()
+
+
+@pytest.mark.parametrize("sr", SEMIRINGS)
+def test_er_4096_eight_per_column(ctx, sr):
+    """C = A*A, A 4096 x 4096 ER with exactly 8 per column (full comparison)."""
+    A = gen.erdos_renyi(4096, 4096, 8, 0x1001, sr)
+    C = check_product(ctx, A, A, sr)
+    fl = oracle.flops_per_col(A, A)
+    assert int(fl.sum()) == 8 * 8 * 4096
+
+
+@pytest.mark.parametrize("sr", SEMIRINGS)
+def test_rectangular_random(ctx, sr):
+    for t, (m, k, n, dens) in enumerate([(37, 29, 41, 0.1), (300, 200, 150, 0.03), (1, 50, 70, 0.3),
+                                         (90, 1, 33, 0.5), (513, 257, 129, 0.02), (2000, 3000, 100, 0.01)]):
+        A = gen.random_csc(m, k, dens, 10 + t, sr)
+        B = gen.random_csc(k, n, dens, 20 + t, sr)
+        if sr == PT_F64:
+            A = A.with_vals(A.vals - 0.5)   # cancellation on the way
+        check_product(ctx, A, B, sr, what=f"shape {(m, k, n)}")
+
+
+@pytest.mark.parametrize("sr", SEMIRINGS)
+def test_rmat_all_tiers(ctx, sr):
+    """R-MAT scale 13: columns land in every tier (warp, CTA hash, dense chunks)."""
+    A = gen.rmat(13, 8, 0x1302, sr)
+    C = check_product(ctx, A, A, sr)
+    s = sp()
+    dA = s.Matrix.from_host(ctx, A, sr)
+    plan = s.spgemm_plan(ctx, dA, dA, sr)
+    st = plan.stats()
+    assert st["tiers"][1] > 0 and st["tiers"][2] > 0 and st["tiers"][3] > 0, st
+    assert st["flops"] == int(oracle.flops_per_col(A, A).sum())
+
+
+@pytest.mark.parametrize("sr", [PT_F64, PT_I64])
+def test_tier_choice_does_not_change_result(ctx, sr):
+    A = gen.rmat(12, 8, 0x1202, sr)
+    s = sp()
+    ref = oracle.spgemm(A, A, sr)
+    for kw in ({"warp_max_flops": 0, "block_max_flops": 0},      # everything dense
+               {"warp_max_flops": 512, "block_max_flops": 4096},
+               {"warp_max_flops": 0, "block_max_flops": 4096},    # CTA tables only
+               {"dense_part_flops": 1024}):                       # many dense parts
+        C = gpu_product(ctx, A, A, sr, s.default_opts(**kw))
+        assert_matches(C, ref, sr, what=str(kw))
+
+
+def test_dense_rows_multiple_chunks_and_ragged_tail(ctx):
+    # m not a multiple of the dense chunk (8192 rows for FP64): several chunks and a short tail
+    m = 3 * 8192 + 77
+    A = gen.erdos_renyi(m, 400, 60, 5)
+    B = gen.erdos_renyi(400, 50, 200, 6)
+    check_product(ctx, A, B, PT_F64, what="dense with tail")
+
+
+def test_edge_cases(ctx):
+    s = sp()
+    sr = PT_F64
+    # empty matrices
+    Z = CSC(5, 7, np.zeros(8, np.int64), np.zeros(0, np.int32), np.zeros(0))
+    Y = CSC(7, 3, np.zeros(4, np.int64), np.zeros(0, np.int32), np.zeros(0))
+    C = gpu_product(ctx, Z, Y, sr)
+    assert C.nnz == 0 and list(C.colptr) == [0, 0, 0, 0]
+    # 1 x 1
+    one = CSC(1, 1, np.array([0, 1]), np.array([0], np.int32), np.array([3.0]))
+    C = gpu_product(ctx, one, one, sr)
+    assert C.nnz == 1 and C.vals[0] == 9.0
+    # one dense column times a row of ones
+    m = 5000
+    D = CSC(m, 1, np.array([0, m]), np.arange(m, dtype=np.int32), np.linspace(0, 1, m))
+    Rw = CSC(1, 40, np.arange(41, dtype=np.int64), np.zeros(40, np.int32), np.arange(1.0, 41.0))
+    check_product(ctx, D, Rw, sr, what="outer product")
+    # columns exactly at the warp/CTA thresholds: flops 512 and 4096
+    for f in (32, 512, 513, 4096, 4097):
+        A = gen.erdos_renyi(20000, 64, 64, 7)
+        cnt = f // 64
+        B = gen.erdos_renyi(64, 3, max(cnt, 1), 8 + f)
+        check_product(ctx, A, B, sr, what=f"flops ~{f}")
+
+
+@pytest.mark.parametrize("sr", [PT_F64, OR_BOOL])
+def test_csr_and_dcsc_operands(ctx, sr):
+    s = sp()
+    A = gen.rmat(10, 8, 31, sr)
+    B = gen.random_csc(1024, 300, 0.004, 32, sr)
+    R = oracle.spgemm(A, B, sr)
+    dA = s.Matrix.from_host(ctx, A, sr)
+    dB = s.Matrix.from_host(ctx, B, sr)
+    # A given as CSR (its transpose's CSC arrays)
+    from oracle import formats as of
+    tcp, tir, tv = of.transpose(A.m, A.n, A.colptr, A.rowidx, A.vals)
+    import torch
+    dev = ctx.device
+    Acsr = s.Matrix.csr(ctx, A.m, A.n, torch.from_numpy(tcp).to(dev), torch.from_numpy(tir).to(dev),
+                        torch.from_numpy(np.ascontiguousarray(tv)).to(dev), sr)
+    assert_matches(s.spgemm_multiply(ctx, Acsr, dB, sr).to_host(), R, sr, what="A csr")
+    # B as DCSC (hypersparse: most of its columns are empty), A as DCSC with AUX
+    Bd = s.spgemm_mat_to_dcsc(ctx, dB, True)
+    assert_matches(s.spgemm_multiply(ctx, dA, Bd, sr).to_host(), R, sr, what="B dcsc")
+    Ad = s.spgemm_mat_to_dcsc(ctx, dA, True)
+    assert_matches(s.spgemm_multiply(ctx, Ad, Bd, sr).to_host(), R, sr, what="A,B dcsc")
+
+
+def test_transpose_and_dcsc_against_oracle(ctx):
+    from oracle import formats as of
+    s = sp()
+    for seed, (m, n, d) in enumerate([(300, 200, 0.02), (4000, 4096, 0.0005), (1, 9, 0.5), (9, 9, 0.05)]):
+        A = gen.random_csc(m, n, d, 40 + seed)
+        dA = s.Matrix.from_host(ctx, A, PT_F64)
+        T = s.spgemm_mat_transpose(ctx, dA).to_host()
+        tcp, tir, tv = of.transpose(A.m, A.n, A.colptr, A.rowidx, A.vals)
+        np.testing.assert_array_equal(T.colptr, tcp)
+        np.testing.assert_array_equal(T.rowidx, tir)
+        np.testing.assert_array_equal(T.vals, tv)
+        D = s.spgemm_mat_to_dcsc(ctx, dA, True)
+        nzc, jc, aux, chunk = D.export_dcsc()
+        ojc, ocp, oaux, ochunk = of.to_dcsc(A.n, A.colptr)
+        assert nzc == len(ojc) and chunk == ochunk
+        np.testing.assert_array_equal(jc.cpu().numpy(), ojc)
+        np.testing.assert_array_equal(aux.cpu().numpy(), oaux)
+        np.testing.assert_array_equal(D.export()[3].cpu().numpy(), ocp)
+
+
+def test_nine_by_nine_dcsc_example(ctx):
+    """The DCSC of the 9x9 example of Section 2.3 (JC, CP, AUX) from the device converter."""
+    s = sp()
+    cp, ir = gen.csc_from_coo(9, 9, np.array([5, 7, 3, 1]), np.array([0, 0, 6, 7]))
+    A = CSC(9, 9, cp, ir, np.array([0.1, 0.2, 0.3, 0.4]))
+    D = s.spgemm_mat_to_dcsc(ctx, s.Matrix.from_host(ctx, A, PT_F64), True)
+    nzc, jc, aux, chunk = D.export_dcsc()
+    assert list(jc.cpu().numpy() + 1) == [1, 7, 8]
+    assert list(D.export()[3].cpu().numpy() + 1) == [1, 3, 4, 5]
+    assert list(aux.cpu().numpy() + 1) == [1, 2, 2, 4]
+
+
+def test_errors_are_reported(ctx):
+    s = sp()
+    import torch
+    dev = ctx.device
+    A = gen.random_csc(10, 8, 0.3, 1)
+    B = gen.random_csc(9, 4, 0.3, 2)
+    dA, dB = s.Matrix.from_host(ctx, A, PT_F64), s.Matrix.from_host(ctx, B, PT_F64)
+    with pytest.raises(s.SpGEMMError) as e:
+        s.spgemm_multiply(ctx, dA, dB, PT_F64)
+    assert e.value.status == 2   # DIM_MISMATCH
+    with pytest.raises(s.SpGEMMError):
+        s.spgemm_multiply(ctx, dA, dA.__class__.from_host(ctx, gen.random_csc(8, 4, 0.3, 3), PT_I64), PT_F64)
+    # unsorted rows inside a column -> BAD_FORMAT from the validator
+    bad = s.Matrix.csc(ctx, 4, 1, torch.tensor([0, 2], dtype=torch.int64, device=dev),
+                       torch.tensor([3, 1], dtype=torch.int32, device=dev), torch.ones(2, dtype=torch.float64, device=dev),
+                       PT_F64)
+    with pytest.raises(s.SpGEMMError) as e:
+        bad.validate()
+    assert e.value.status == 3
+    oob = s.Matrix.csc(ctx, 4, 1, torch.tensor([0, 1], dtype=torch.int64, device=dev),
+                       torch.tensor([9], dtype=torch.int32, device=dev), torch.ones(1, dtype=torch.float64, device=dev),
+                       PT_F64)
+    with pytest.raises(s.SpGEMMError):
+        oob.validate()
+    dA.validate()
+
+
+def test_symbolic_matches_oracle_counts(ctx):
+    s = sp()
+    A = gen.rmat(12, 8, 0x77)
+    dA = s.Matrix.from_host(ctx, A, PT_F64)
+    plan = s.spgemm_plan(ctx, dA, dA, PT_F64)
+    nnz = s.spgemm_symbolic(plan)
+    ref = oracle.symbolic(A, A)
+    assert nnz == int(ref.sum())
+    C = s.spgemm_numeric(plan).to_host()
+    np.testing.assert_array_equal(np.diff(C.colptr), ref)
+
+
+@pytest.mark.parametrize("sr", [PT_F64, MP_F32])
+def test_rmat_scale18_sampled(ctx, sr):
+    """The benchmark workload (R-MAT scale 18, edge factor 8): sampled columns vs the oracle,
+    plus whole-matrix properties (nnz <= min(flops, m), rows sorted, nnz = oracle symbolic)."""
+    A = gen.rmat(18, 8, 0x1802, sr)
+    s = sp()
+    dA = s.Matrix.from_host(ctx, A, sr)
+    C = s.spgemm_multiply(ctx, dA, dA, sr).to_host()
+    nz = oracle.symbolic(A, A)
+    np.testing.assert_array_equal(np.diff(C.colptr), nz)
+    lens = np.diff(A.colptr)
+    rng = np.random.default_rng(1)
+    heavy = np.argsort(lens)[-20:]
+    cols = np.unique(np.concatenate([heavy, rng.choice(A.n, 300, replace=False), [0, A.n - 1]]))
+    R = oracle.spgemm_columns(A, A, sr, cols)
+    for t, j in enumerate(cols):
+        got_r = C.rowidx[C.colptr[j]:C.colptr[j + 1]]
+        np.testing.assert_array_equal(got_r, R.rowidx[R.colptr[t]:R.colptr[t + 1]])
+        got_v = C.vals[C.colptr[j]:C.colptr[j + 1]]
+        ref_v = R.vals[R.colptr[t]:R.colptr[t + 1]]
+        if sr == PT_F64:
+            assert np.all(np.abs(got_v - ref_v) <= 1e-13 * np.abs(ref_v)), j
+        else:
+            np.testing.assert_array_equal(got_v, ref_v)
+    col_of = np.repeat(np.arange(C.n), np.diff(C.colptr))
+    same = col_of[1:] == col_of[:-1]
+    assert np.all(np.diff(C.rowidx.astype(np.int64))[same] > 0)
+
+
+def test_repeatable_exact_semirings(ctx):
+    A = gen.rmat(12, 8, 0x99, PT_I64)
+    C1 = gpu_product(ctx, A, A, PT_I64)
+    C2 = gpu_product(ctx, A, A, PT_I64)
+    np.testing.assert_array_equal(C1.vals, C2.vals)
