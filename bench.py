@@ -1,0 +1,363 @@
+#!/usr/bin/env python
+"""SpGEMM benchmark on one or more GB300s (one process per GPU).
+
+Workload (default): C = A*A with A an R-MAT matrix of scale 18 (262,144
+vertices), edge factor 8, (a, b, c, d) = (0.57, 0.19, 0.19, 0.05), duplicates
+merged, self-loops kept, values uniform(0, 1).  One step runs every product
+of the workload once: the flat product in plus-times FP64 and in min-plus
+FP32, and the same two on a 16 x 16 virtual 2D Sparse SUMMA grid.
+Metric: GFLOPS = 2 * flops / time, flops = sum_j sum_{k in B(:,j)} nnz(A(:,k)).
+
+Multi-GPU: every rank computes its own copy of the workload (independent
+problems, no collective on the data path); value = all ranks' flops / the
+slowest rank's time ("weak" scaling).
+
+--impl reference times the CPU oracle (plain Gustavson, OpenMP over columns)
+on a bounded column sample of the same workload, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1006_2183_gb300 import gen  # noqa: E402
+
+METRIC = "SpGEMM GFLOPS (2*flops/s)"
+UNIT = "GFLOPS"
+SCALE, EF, SEED = 18, 8, 0x1802
+GRID = 16
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=int, default=SCALE)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--products", default="flat,summa",
+                    help="comma list of product kinds in a step: flat, summa")
+    return ap.parse_args()
+
+
+def flops_of(A) -> int:
+    lens = np.diff(A.colptr)
+    return int(lens[A.rowidx].sum())
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        rows = []
+        for ln in open(self.path):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        mx = max(r[1] for r in rows)
+        loaded = [r[0] for r in rows]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[2]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- reference arm (CPU oracle)
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    A = gen.rmat(args.scale, EF, SEED, gen.PLUS_TIMES_F64)
+    n = A.n
+    # bounded sample: every 16th output column of the flat plus-times FP64 product
+    cols = np.arange(0, n, 16)
+    lens = np.diff(A.colptr)
+    fl_cols = np.array([lens[A.rowidx[A.colptr[j]:A.colptr[j + 1]]].sum() for j in cols], np.int64)
+    flops = int(fl_cols.sum())
+    cores = oracle.max_threads()
+    times = []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.spgemm_columns(A, A, oracle.PT_F64, cols)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = 2.0 * flops * len(times) / tot / 1e9
+    sample = f"every 16th output column ({len(cols)} columns, {flops} flops) of the flat plus-times FP64 product"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"rmat{args.scale}_AxA", "scale": args.scale, "edge_factor": EF,
+                       "abcd": [0.57, 0.19, 0.19, 0.05], "seed": SEED},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    import torch.distributed as dist
+    from paper_1006_2183_gb300 import build as _build
+    if rank == 0 or world == 1:
+        _build.build()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+        dist.barrier()
+        _build.build()
+    torch.cuda.set_device(local)
+    from paper_1006_2183_gb300 import spgemm as sp
+
+    kinds = [k for k in args.products.split(",") if k]
+    A64 = gen.rmat(args.scale, EF, SEED, gen.PLUS_TIMES_F64)
+    A32 = A64.with_vals(A64.vals.astype(np.float32))
+    flops1 = flops_of(A64)
+    ctx = sp.Context()
+    dev = ctx.device
+    mats = {sp.PLUS_TIMES_F64: sp.Matrix.from_host(ctx, A64, sp.PLUS_TIMES_F64),
+            sp.MIN_PLUS_F32: sp.Matrix.from_host(ctx, A32, sp.MIN_PLUS_F32)}
+    products = []
+    for k in kinds:
+        for sr in (sp.PLUS_TIMES_F64, sp.MIN_PLUS_F32):
+            products.append((k, sr))
+
+    def run_product(kind, sr, M):
+        if kind == "flat":
+            plan = sp.spgemm_plan(ctx, M, M, sr)
+            C = sp.spgemm_numeric(plan)
+            return C, plan
+        C = sp.spgemm_summa_blocked(ctx, M, M, GRID, sr)
+        return C, None
+
+    # probe which product kinds the library supports (summa may be absent in a build)
+    ok_products = []
+    for kind, sr in products:
+        try:
+            C, plan = run_product(kind, sr, mats[sr])
+            ok_products.append((kind, sr))
+            del C, plan
+        except sp.SpGEMMError as e:
+            if e.status != 8:
+                raise
+    products = ok_products
+    flops_step = flops1 * len(products)
+
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        outs = []
+        for kind, sr in products:
+            outs.append(run_product(kind, sr, mats[sr]))
+        return outs
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    # timed region: per-step CUDA events on the context stream, L2 flushed between steps
+    st = ctx.stream
+    ctx.timing(True)
+    l0 = sp.launch_count()
+    times = []
+    nnz_seen = {}
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            outs = step()
+            e1.record(st)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            for (kind, sr), (C, plan) in zip(products, outs):
+                nnz_seen[(kind, sr)] = C.shape()[2]
+            del outs
+    torch.cuda.synchronize()
+    launches = sp.launch_count() - l0
+    phases = ctx.phase_ms()
+    ctx.timing(False)
+    clocks = clk.summary()
+    tot_ms = sum(times)
+    if world > 1:
+        t = torch.tensor([tot_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+        dist.barrier()
+    value = 2.0 * flops_step * args.steps * world / (tot_ms / 1e3) / 1e9
+
+    # dominant kernel: numeric dense tier of the flat plus-times FP64 product
+    hbm, peak_kind = peaks()
+    roof = None
+    if ("flat", sp.PLUS_TIMES_F64) in products:
+        plan = sp.spgemm_plan(ctx, mats[sp.PLUS_TIMES_F64], mats[sp.PLUS_TIMES_F64], sp.PLUS_TIMES_F64)
+        sp.spgemm_symbolic(plan)
+        ts = plan.tier_stats()
+        ms, cnt = phases[(sp.PLUS_TIMES_F64, "numeric_dense")]
+        if cnt:
+            nnz_d, bnnz_d, cols_d = ts["nnz"][3], ts["bnnz"][3], ts["cols"][3]
+            alg = nnz_d * 12 + bnnz_d * 12 + cols_d * 16 + A64.nnz * 12 + 8 * (A64.n + 1)
+            per_launch_ms = ms / cnt
+            ach = alg / (per_launch_ms / 1e3) / 1e9
+            roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                    "traffic": None, "kernel": "k_dense<PT64,numeric>", "peak_kind": peak_kind,
+                    "alg_bytes_per_launch": alg, "ms_per_launch": per_launch_ms}
+        del plan
+    # whole-product roofline on compulsory bytes (A read once, C written once)
+    pipe = {}
+    for (kind, sr) in products:
+        w = 8 if sr == sp.PLUS_TIMES_F64 else 4
+        byt = (A64.n + 1) * 8 + A64.nnz * (4 + w) + (A64.n + 1) * 8 + nnz_seen[(kind, sr)] * (4 + w)
+        pipe[f"{kind}_{'pt64' if w == 8 else 'mp32'}"] = {"compulsory_bytes": byt, "nnz_C": nnz_seen[(kind, sr)]}
+    phase_tab = {f"{'pt64' if s == 0 else 'mp32'}:{p}": round(v[0] / max(1, args.steps), 4)
+                 for (s, p), v in phases.items() if v[1]}
+    byt_step = sum(v["compulsory_bytes"] for v in pipe.values())
+    pipeline_frac = byt_step / (tot_ms / args.steps / 1e3) / 1e9 / hbm
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        import torch as _t
+        pinned = {}
+        for sr, H in ((sp.PLUS_TIMES_F64, A64), (sp.MIN_PLUS_F32, A32)):
+            pinned[sr] = (_t.from_numpy(H.colptr).pin_memory(), _t.from_numpy(H.rowidx).pin_memory(),
+                          _t.from_numpy(np.ascontiguousarray(H.vals)).pin_memory())
+        h2d = sum(sum(t.numel() * t.element_size() for t in pinned[sr]) for _, sr in products)
+        outbuf = {}
+        d2h = 0
+        for (kind, sr) in products:
+            nz = nnz_seen[(kind, sr)]
+            w = 8 if sr == sp.PLUS_TIMES_F64 else 4
+            outbuf[(kind, sr)] = (_t.empty(A64.n + 1, dtype=_t.int64).pin_memory(),
+                                  _t.empty(nz, dtype=_t.int32).pin_memory(),
+                                  _t.empty(nz, dtype=sp.TORCH_DTYPE[sr]).pin_memory())
+            d2h += (A64.n + 1) * 8 + nz * (4 + w)
+        et = []
+        for it in range(args.warmup + args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for (kind, sr) in products:
+                cp, ir, v = (x.to(dev, non_blocking=True) for x in pinned[sr])
+                M = sp.Matrix.csc(ctx, A64.m, A64.n, cp, ir, v, sr)
+                C, plan = run_product(kind, sr, M)
+                _, _, nz, ccp, cir, cv = C.export()
+                ob = outbuf[(kind, sr)]
+                ob[0].copy_(ccp, non_blocking=True)
+                ob[1][:nz].copy_(cir, non_blocking=True)
+                ob[2][:nz].copy_(cv, non_blocking=True)
+                st.synchronize()
+                del C, plan, M
+            dt = time.perf_counter() - t0
+            if it >= args.warmup:
+                et.append(dt)
+        e2e_val = 2.0 * flops_step * len(et) * world / sum(et) / 1e9
+        e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        cols = np.arange(0, A64.n, 16)
+        lens = np.diff(A64.colptr)
+        fl = int(sum(lens[A64.rowidx[A64.colptr[j]:A64.colptr[j + 1]]].sum() for j in cols))
+        t0 = time.perf_counter()
+        oracle.spgemm_columns(A64, A64, oracle.PT_F64, cols)
+        dt = time.perf_counter() - t0
+        cpu = {"value": 2.0 * fl / dt / 1e9, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+               "sample": f"every 16th output column ({len(cols)} columns, {fl} flops) of the flat "
+                         f"plus-times FP64 product, {dt:.2f} s"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"rmat{args.scale}_AxA", "scale": args.scale, "edge_factor": EF,
+                           "abcd": [0.57, 0.19, 0.19, 0.05], "seed": SEED, "grid": GRID,
+                           "products": [f"{k}_{'pt64' if s == 0 else 'mp32'}" for k, s in products],
+                           "flops_per_product": flops1, "nnz_A": A64.nnz, "l2": "flushed between steps (512 MiB write)",
+                           "pipeline_hbm_frac": pipeline_frac, "pipeline": pipe, "phase_ms_per_step": phase_tab},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -229,8 +229,38 @@ spgemm_status_t spgemm_mat_destroy(spgemm_mat_t M) {
 
 }  // extern "C"
 
-// ------------------------------------------------------------------ plan
-static spgemm_status_t to_csc_operand(spgemm_ctx* ctx, spgemm_mat_t M, spgemm_mat_t* conv, DMat* d) {
+// ------------------------------------------------------------------ engine
+DMat csc_view(int64_t m, int64_t n, int64_t nnz, const int64_t* cp, const int32_t* ir, const void* num) {
+    DMat d;
+    d.m = m;
+    d.n = n;
+    d.nzc = n;
+    d.nnz = nnz;
+    d.cp = cp;
+    d.ir = ir;
+    d.num = num;
+    return d;
+}
+
+spgemm_mat_t new_owned_csc(spgemm_ctx* ctx, spgemm_semiring_t sr, int64_t m, int64_t n, int64_t nnz,
+                           std::vector<std::shared_ptr<DevBuf>> owned, const int64_t* cp, const int32_t* ir,
+                           const void* num) {
+    auto* M = new spgemm_mat();
+    M->ctx = ctx;
+    M->fmt = SPGEMM_FMT_CSC;
+    M->sr = sr;
+    M->m = m;
+    M->n = n;
+    M->nzc = n;
+    M->nnz = nnz;
+    M->cp = cp;
+    M->ir = ir;
+    M->num = num;
+    M->owned = std::move(owned);
+    return M;
+}
+
+spgemm_status_t to_csc_operand(spgemm_ctx* ctx, spgemm_mat_t M, spgemm_mat_t* conv, DMat* d) {
     if (M->fmt == SPGEMM_FMT_CSR) {
         // stored arrays are the CSC of M^T (n x m); transposing them gives M's CSC
         spgemm_mat_t T = new spgemm_mat();
@@ -248,144 +278,242 @@ static spgemm_status_t to_csc_operand(spgemm_ctx* ctx, spgemm_mat_t M, spgemm_ma
     return SPGEMM_OK;
 }
 
-spgemm_status_t plan_build(spgemm_ctx* ctx, const DMat& A, const DMat& B, spgemm_semiring_t sr,
-                           const spgemm_opts_t& opts, struct spgemm_plan* P) {
-    P->ctx = ctx;
-    P->sr = sr;
-    P->opts = opts;
-    P->A = A;
-    P->B = B;
-    P->m = A.m;
-    P->n = B.n;
-    P->cfg.warp_max = std::max(0, std::min(opts.warp_max_flops, 512));
-    P->cfg.block_max = std::max(P->cfg.warp_max, std::min(opts.block_max_flops, 4096));
-    P->cfg.dense_rows = dense_rows_for(sr, 0);
-    P->cfg.part_flops = std::max(1024, opts.dense_part_flops);
+spgemm_status_t engine_setup(Engine* E, spgemm_ctx* ctx, spgemm_semiring_t sr, const spgemm_opts_t& opts,
+                             std::vector<Prod> prods, bool want_features) {
+    E->ctx = ctx;
+    E->sr = sr;
+    E->opts = opts;
+    E->cfg.warp_max = std::max(0, std::min(opts.warp_max_flops, 512));
+    E->cfg.block_max = std::max(E->cfg.warp_max, std::min(opts.block_max_flops, 4096));
+    int64_t mmax = 32;
+    for (auto& pr : prods) mmax = std::max<int64_t>(mmax, pr.A.m);
+    E->cfg.dense_rows = (int)std::min<int64_t>((mmax + 31) / 32 * 32, 1 << 20);
+    E->cfg.part_flops = std::max(1024, opts.dense_part_flops);
     cudaStream_t st = ctx->stream;
-    const int64_t nzcB = B.nzc;
-    // one arena for the per-column arrays of the plan
+    const int64_t np = (int64_t)prods.size();
+    E->hitem_base.assign(np + 1, 0);
+    int64_t bnz = 0, amax_n = 0;
+    for (int64_t i = 0; i < np; ++i) {
+        prods[i].item_base = E->hitem_base[i];
+        prods[i].bnz_base = bnz;
+        prods[i].G = (int32_t)ceil_div64(std::max<int64_t>(prods[i].A.m, 1), E->cfg.dense_rows);
+        E->hitem_base[i + 1] = E->hitem_base[i] + prods[i].B.nzc;
+        bnz += prods[i].B.nnz;
+        amax_n += prods[i].A.n;
+    }
+    E->hprods = std::move(prods);
+    const int64_t U = E->hitem_base[np];
     size_t off = 0;
     auto take = [&](size_t bytes) {
         size_t o = off;
         off += (bytes + 255) / 256 * 256;
         return o;
     };
-    size_t o_flops = take(8 * std::max<int64_t>(nzcB, 1));
-    size_t o_bin = take(std::max<int64_t>(nzcB, 1));
-    size_t o_ctr = take(8 * (2 * NBIN + 2));
+    const int64_t U1 = std::max<int64_t>(U, 1);
+    size_t o_prods = take(sizeof(Prod) * std::max<int64_t>(np, 1));
+    size_t o_base = take(8 * (np + 1));
+    size_t o_flops = take(8 * U1);
+    size_t o_bin = take(U1);
+    size_t o_iprod = take(4 * U1);
+    size_t o_ctr = take(8 * (2 * NBIN + 4));
     size_t o_binoff = take(8 * NBIN);
-    size_t o_list = take(4 * std::max<int64_t>(nzcB, 1));
-    size_t o_nnz = take(8 * std::max<int64_t>(B.n, 1));
-    size_t o_scan = take(scan_tmp_bytes(B.n));
-    size_t o_feat = opts.use_predictor ? take(32 * std::max<int64_t>(nzcB, 1)) : 0;
-    size_t o_sk = opts.use_predictor ? take(8 * std::max<int64_t>(A.n, 1)) : 0;
+    size_t o_list = take(sizeof(int2) * U1);
+    size_t o_nnz = take(8 * U1);
+    size_t o_scan = take(scan_tmp_bytes(U1));
+    size_t o_feat = want_features ? take(32 * U1) : 0;
+    size_t o_sk = want_features ? take(8 * std::max<int64_t>(amax_n, 1)) : 0;
+    size_t o_skb = want_features ? take(8 * (np + 1)) : 0;
     auto arena = ctx_buf(ctx, off);
-    if (!arena) return set_err(ctx, SPGEMM_ERR_OOM, "plan arena of %zu bytes", off);
-    P->bufs.push_back(arena);
+    if (!arena) return set_err(ctx, SPGEMM_ERR_OOM, "engine arena of %zu bytes", off);
+    E->bufs.push_back(arena);
     char* base = (char*)arena->p;
-    P->flops = (int64_t*)(base + o_flops);
-    P->bin = (uint8_t*)(base + o_bin);
-    P->ctr = (unsigned long long*)(base + o_ctr);
-    P->bin_off_dev = (int64_t*)(base + o_binoff);
-    P->list = (int32_t*)(base + o_list);
-    P->nnz_col = (int64_t*)(base + o_nnz);
-    P->scan_tmp = base + o_scan;
+    Prod* dprods = (Prod*)(base + o_prods);
+    int64_t* dbase = (int64_t*)(base + o_base);
+    E->flops = (int64_t*)(base + o_flops);
+    E->bin = (uint8_t*)(base + o_bin);
+    E->item_prod = (int32_t*)(base + o_iprod);
+    E->ctr = (unsigned long long*)(base + o_ctr);
+    E->bin_off_dev = (int64_t*)(base + o_binoff);
+    E->list = (int2*)(base + o_list);
+    E->nnz_item = (int64_t*)(base + o_nnz);
+    E->scan_tmp = base + o_scan;
+    SG_CUDA(ctx, cudaMemcpyAsync(dprods, E->hprods.data(), sizeof(Prod) * np, cudaMemcpyHostToDevice, st));
+    SG_CUDA(ctx, cudaMemcpyAsync(dbase, E->hitem_base.data(), 8 * (np + 1), cudaMemcpyHostToDevice, st));
+    E->it.prods = dprods;
+    E->it.item_base = dbase;
+    E->it.nprod = np;
+    E->it.nitems = U;
+    E->it.total_bnz = bnz;
     uint64_t* sketch = nullptr;
-    if (opts.use_predictor) {
-        P->feat = (float*)(base + o_feat);
-        sketch = (uint64_t*)(base + o_sk);
-        launch_row_sketch(st, A, sketch);
-    }
+    int64_t* skbase = nullptr;
     PhaseTimer t_an(ctx, SPGEMM_PHASE_ANALYZE, sr);
-    SG_CUDA(ctx, cudaMemsetAsync(P->ctr, 0, 8 * (2 * NBIN + 2), st));
-    launch_analyze(st, A, B, P->cfg, P->flops, P->bin, P->ctr, P->ctr + 2 * NBIN, sketch, P->feat);
+    if (want_features) {
+        E->feat = (float*)(base + o_feat);
+        sketch = (uint64_t*)(base + o_sk);
+        skbase = (int64_t*)(base + o_skb);
+        std::vector<int64_t> hb(np + 1, 0);
+        for (int64_t i = 0; i < np; ++i) {
+            hb[i + 1] = hb[i] + E->hprods[i].A.n;
+            launch_row_sketch(st, E->hprods[i].A, sketch + hb[i]);
+        }
+        SG_CUDA(ctx, cudaMemcpyAsync(skbase, hb.data(), 8 * (np + 1), cudaMemcpyHostToDevice, st));
+    }
+    SG_CUDA(ctx, cudaMemsetAsync(E->ctr, 0, 8 * (2 * NBIN + 4), st));
+    launch_analyze(st, E->it, E->cfg, E->flops, E->bin, E->item_prod, E->ctr, E->ctr + 2 * NBIN, sketch, skbase,
+                   E->feat);
     unsigned long long hc[NBIN + 1];
-    SG_CUDA(ctx, cudaMemcpyAsync(hc, P->ctr, sizeof(unsigned long long) * NBIN, cudaMemcpyDeviceToHost, st));
-    SG_CUDA(ctx, cudaMemcpyAsync(hc + NBIN, P->ctr + 2 * NBIN, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    SG_CUDA(ctx, cudaMemcpyAsync(hc, E->ctr, sizeof(unsigned long long) * NBIN, cudaMemcpyDeviceToHost, st));
+    SG_CUDA(ctx, cudaMemcpyAsync(hc + NBIN, E->ctr + 2 * NBIN, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     SG_TRY(sync_ctx(ctx));
     int64_t acc = 0;
     for (int b = 0; b < NBIN; ++b) {
-        P->bin_cnt[b] = (int64_t)hc[b];
-        P->bin_off[b] = acc;
-        acc += P->bin_cnt[b];
+        E->bin_cnt[b] = (int64_t)hc[b];
+        E->bin_off[b] = acc;
+        acc += E->bin_cnt[b];
     }
-    P->flops_total = (int64_t)hc[NBIN];
-    SG_CUDA(ctx, cudaMemcpyAsync(P->bin_off_dev, P->bin_off, sizeof(int64_t) * NBIN, cudaMemcpyHostToDevice, st));
-    launch_bin_scatter(st, nzcB, P->bin, P->bin_off_dev, P->ctr + NBIN, P->list);
-    const int64_t nd = P->bin_cnt[BIN_DENSE];
+    E->flops_total = (int64_t)hc[NBIN];
+    SG_CUDA(ctx, cudaMemcpyAsync(E->bin_off_dev, E->bin_off, sizeof(int64_t) * NBIN, cudaMemcpyHostToDevice, st));
+    launch_bin_scatter(st, E->it, E->bin, E->item_prod, E->bin_off_dev, E->ctr + NBIN, E->list);
+    const int64_t nd = E->bin_cnt[BIN_DENSE];
+    E->dw = DenseWork();
     if (nd > 0) {
-        P->G = ceil_div64(A.m, P->cfg.dense_rows);
-        const int64_t maxp = std::min<int64_t>(P->G, MAX_PARTS);
-        size_t o2 = 0;
+        // slabs of the long columns, then the range buffers sized from their count
         off = 0;
-        size_t o_items = take(sizeof(int2) * nd * maxp);
+        size_t o_items = take(sizeof(int2) * nd * MAX_PARTS);
         size_t o_np = take(nd);
-        size_t o_pc = take(4 * nd * maxp);
-        size_t o_cur = take(4 * std::max<int64_t>(B.nnz, 1) * maxp);
-        (void)o2;
+        size_t o_pc = take(4 * nd * MAX_PARTS);
+        size_t o_pb = take(8 * nd * MAX_PARTS);
+        size_t o_pn = take(4 * nd * MAX_PARTS);
+        size_t o_cur = take(4 * std::max<int64_t>(bnz, 1) * MAX_PARTS);
         auto dbuf = ctx_buf(ctx, off);
-        if (!dbuf) return set_err(ctx, SPGEMM_ERR_OOM, "dense-tier arena of %zu bytes", off);
-        P->bufs.push_back(dbuf);
+        if (!dbuf) return set_err(ctx, SPGEMM_ERR_OOM, "range-tier arena of %zu bytes", off);
+        E->bufs.push_back(dbuf);
         char* db = (char*)dbuf->p;
-        P->items = (int2*)(db + o_items);
-        P->nparts = (int8_t*)(db + o_np);
-        P->part_count = (int32_t*)(db + o_pc);
-        P->cursors = (int32_t*)(db + o_cur);
-        launch_dense_items(st, P->list + P->bin_off[BIN_DENSE], nd, P->flops, (int)P->G, P->cfg.part_flops, P->items,
-                           P->ctr + 2 * NBIN + 1, P->nparts);
+        E->ditems = (int2*)(db + o_items);
+        E->nparts = (int8_t*)(db + o_np);
+        E->part_count = (int32_t*)(db + o_pc);
+        E->cursors = (int32_t*)(db + o_cur);
+        DenseWork& dw = E->dw;
+        dw.dlist = E->list + E->bin_off[BIN_DENSE];
+        dw.ndense = nd;
+        dw.items = E->ditems;
+        dw.nitems = E->ctr + 2 * NBIN + 1;
+        dw.nparts = E->nparts;
+        dw.cursors = E->cursors;
+        dw.part_count = E->part_count;
+        dw.parts_ctr = E->ctr + 2 * NBIN + 2;
+        dw.err = (int*)(E->ctr + 2 * NBIN + 3);
+        dw.pbase = (int64_t*)(db + o_pb);
+        dw.pcnt = (int32_t*)(db + o_pn);
+        dw.RB = E->cfg.dense_rows;
+        launch_dense_items(st, E->it, dw.dlist, nd, E->flops, E->cfg.part_flops, dw.RB, E->ditems,
+                           E->ctr + 2 * NBIN + 1, E->nparts);
+        unsigned long long nslabs = 0;
+        SG_CUDA(ctx, cudaMemcpyAsync(&nslabs, E->ctr + 2 * NBIN + 1, 8, cudaMemcpyDeviceToHost, st));
+        SG_TRY(sync_ctx(ctx));
+        dw.parts_cap = ceil_div64(E->flops_total, dw.H) + (int64_t)nslabs * (ceil_div64(dw.RB, RANGE_W) + 2) + 16;
+        auto pbuf = ctx_buf(ctx, sizeof(RangePart) * dw.parts_cap);
+        if (!pbuf) return set_err(ctx, SPGEMM_ERR_OOM, "range list of %lld entries", (long long)dw.parts_cap);
+        E->bufs.push_back(pbuf);
+        dw.parts = (RangePart*)pbuf->p;
     }
     SG_CUDA(ctx, cudaGetLastError());
     return SPGEMM_OK;
 }
 
 template <class SR>
-static void dispatch_symbolic(struct spgemm_plan* P) {
-    const int64_t nd = P->bin_cnt[BIN_DENSE];
+static void dispatch_symbolic(Engine* E) {
     for (int which = 1; which <= 2; ++which) {
-        PhaseTimer t(P->ctx, which == 1 ? SPGEMM_PHASE_SYMBOLIC_HASH : SPGEMM_PHASE_SYMBOLIC_DENSE, P->sr);
-        launch_symbolic<SR>(P->ctx->stream, P->A, P->B, P->cfg, P->list, P->bin_off, P->bin_cnt, P->items,
-                            P->ctr + 2 * NBIN + 1, nd * std::min<int64_t>(std::max<int64_t>(P->G, 1), MAX_PARTS),
-                            P->nparts, P->cursors, P->part_count, P->nnz_col, which);
+        PhaseTimer t(E->ctx, which == 1 ? SPGEMM_PHASE_SYMBOLIC_HASH : SPGEMM_PHASE_SYMBOLIC_DENSE, E->sr);
+        launch_symbolic<SR>(E->ctx->stream, E->it, E->cfg, E->list, E->bin_off, E->bin_cnt, E->dw, E->nnz_item,
+                            which);
     }
 }
 
 template <class SR>
-static void dispatch_numeric(struct spgemm_plan* P, int32_t* Cir, void* Cv) {
-    const int64_t nd = P->bin_cnt[BIN_DENSE];
+static void dispatch_numeric(Engine* E, int32_t* Cir, void* Cv) {
     for (int which = 1; which <= 2; ++which) {
-        PhaseTimer t(P->ctx, which == 1 ? SPGEMM_PHASE_NUMERIC_HASH : SPGEMM_PHASE_NUMERIC_DENSE, P->sr);
-        launch_numeric<SR>(P->ctx->stream, P->A, P->B, P->cfg, P->list, P->bin_off, P->bin_cnt, P->items,
-                           P->ctr + 2 * NBIN + 1, nd * std::min<int64_t>(std::max<int64_t>(P->G, 1), MAX_PARTS),
-                           P->cursors, P->part_count, P->nparts, P->Ccp, Cir, (typename SR::T*)Cv, which);
+        PhaseTimer t(E->ctx, which == 1 ? SPGEMM_PHASE_NUMERIC_HASH : SPGEMM_PHASE_NUMERIC_DENSE, E->sr);
+        launch_numeric<SR>(E->ctx->stream, E->it, E->cfg, E->list, E->bin_off, E->bin_cnt, E->dw, E->Coff, Cir,
+                           (typename SR::T*)Cv, which);
     }
 }
 
-static void run_symbolic_kernels(struct spgemm_plan* P) {
-    cudaStream_t st = P->ctx->stream;
-    cudaMemsetAsync(P->nnz_col, 0, 8 * std::max<int64_t>(P->n, 1), st);
-    switch (P->sr) {
-    case SPGEMM_PLUS_TIMES_F64: dispatch_symbolic<PT64>(P); break;
-    case SPGEMM_MIN_PLUS_F32: dispatch_symbolic<MP32>(P); break;
-    case SPGEMM_OR_AND_BOOL: dispatch_symbolic<BOOL8>(P); break;
-    case SPGEMM_PLUS_TIMES_I64: dispatch_symbolic<PTI64>(P); break;
+spgemm_status_t engine_symbolic(Engine* E) {
+    if (E->symbolic_done) return SPGEMM_OK;
+    spgemm_ctx* ctx = E->ctx;
+    cudaStream_t st = ctx->stream;
+    const int64_t U = E->it.nitems;
+    SG_CUDA(ctx, cudaMemsetAsync(E->nnz_item, 0, 8 * std::max<int64_t>(U, 1), st));
+    switch (E->sr) {
+    case SPGEMM_PLUS_TIMES_F64: dispatch_symbolic<PT64>(E); break;
+    case SPGEMM_MIN_PLUS_F32: dispatch_symbolic<MP32>(E); break;
+    case SPGEMM_OR_AND_BOOL: dispatch_symbolic<BOOL8>(E); break;
+    case SPGEMM_PLUS_TIMES_I64: dispatch_symbolic<PTI64>(E); break;
     }
-    launch_sum_parts(st, P->list + P->bin_off[BIN_DENSE], P->bin_cnt[BIN_DENSE], P->nparts, P->part_count, P->nnz_col,
-                     P->B.jc);
-}
-
-static spgemm_status_t finish_colptr(struct spgemm_plan* P) {
-    spgemm_ctx* ctx = P->ctx;
-    P->Ccp_buf = ctx_buf(ctx, 8 * (P->n + 1));
-    if (!P->Ccp_buf) return set_err(ctx, SPGEMM_ERR_OOM, "colptr of C");
-    P->Ccp = (int64_t*)P->Ccp_buf->p;
+    launch_sum_parts(st, E->it, E->list + E->bin_off[BIN_DENSE], E->bin_cnt[BIN_DENSE], E->nparts, E->part_count,
+                     E->nnz_item);
+    E->Coff_buf = ctx_buf(ctx, 8 * (U + 1));
+    if (!E->Coff_buf) return set_err(ctx, SPGEMM_ERR_OOM, "item offsets");
+    E->Coff = (int64_t*)E->Coff_buf->p;
     {
-        PhaseTimer t(ctx, SPGEMM_PHASE_SCAN, P->sr);
-        launch_exclusive_scan(ctx->stream, P->nnz_col, P->n, P->Ccp, P->scan_tmp);
+        PhaseTimer t(ctx, SPGEMM_PHASE_SCAN, E->sr);
+        launch_exclusive_scan(st, E->nnz_item, U, E->Coff, E->scan_tmp);
     }
     int64_t nnz = 0;
-    SG_CUDA(ctx, cudaMemcpyAsync(&nnz, P->Ccp + P->n, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+    int err = 0;
+    SG_CUDA(ctx, cudaMemcpyAsync(&nnz, E->Coff + U, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    SG_CUDA(ctx, cudaMemcpyAsync(&err, E->ctr + 2 * NBIN + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
     SG_TRY(sync_ctx(ctx));
-    P->nnzC = nnz;
+    if (err) return set_err(ctx, SPGEMM_ERR_INDEX_OVERFLOW, "range tier capacity exceeded (code %d)", err);
+    E->nnz_total = nnz;
+    E->symbolic_done = true;
+    return SPGEMM_OK;
+}
+
+spgemm_status_t engine_alloc_out(Engine* E, std::shared_ptr<DevBuf>* rbuf, std::shared_ptr<DevBuf>* vbuf) {
+    const size_t w = sr_size(E->sr);
+    *rbuf = ctx_buf(E->ctx, 4 * (size_t)std::max<int64_t>(E->nnz_total, 1));
+    *vbuf = ctx_buf(E->ctx, w * (size_t)std::max<int64_t>(E->nnz_total, 1));
+    if (!*rbuf || !*vbuf) return set_err(E->ctx, SPGEMM_ERR_OOM, "output arrays for nnz %lld", (long long)E->nnz_total);
+    return SPGEMM_OK;
+}
+
+spgemm_status_t engine_numeric(Engine* E, int32_t* Cir, void* Cv) {
+    if (!E->symbolic_done) SG_TRY(engine_symbolic(E));
+    switch (E->sr) {
+    case SPGEMM_PLUS_TIMES_F64: dispatch_numeric<PT64>(E, Cir, Cv); break;
+    case SPGEMM_MIN_PLUS_F32: dispatch_numeric<MP32>(E, Cir, Cv); break;
+    case SPGEMM_OR_AND_BOOL: dispatch_numeric<BOOL8>(E, Cir, Cv); break;
+    case SPGEMM_PLUS_TIMES_I64: dispatch_numeric<PTI64>(E, Cir, Cv); break;
+    }
+    SG_CUDA(E->ctx, cudaGetLastError());
+    return SPGEMM_OK;
+}
+
+// C's column pointers for product 0 of E (n = B.n columns): the item offsets
+// themselves when B is CSC, else a scatter over JC.
+static spgemm_status_t product_colptr(Engine* E, std::shared_ptr<DevBuf>* cpbuf, const int64_t** cp) {
+    const Prod& pr = E->hprods[0];
+    if (pr.B.jc == nullptr && E->hprods.size() == 1) {
+        *cpbuf = E->Coff_buf;
+        *cp = E->Coff;
+        return SPGEMM_OK;
+    }
+    const int64_t n = pr.B.n;
+    auto buf = ctx_buf(E->ctx, 8 * (n + 1) + 16);
+    if (!buf) return set_err(E->ctx, SPGEMM_ERR_OOM, "colptr");
+    int64_t* cb = (int64_t*)buf->p;
+    int64_t hb[2] = {0, n + 1};
+    auto bb = ctx_buf(E->ctx, 16);
+    if (!bb) return set_err(E->ctx, SPGEMM_ERR_OOM, "colptr base");
+    SG_CUDA(E->ctx, cudaMemcpyAsync(bb->p, hb, 16, cudaMemcpyHostToDevice, E->ctx->stream));
+    Items one = E->it;
+    one.nprod = 1;
+    launch_colptrs(E->ctx->stream, one, (const int64_t*)bb->p, n + 1, E->Coff, cb);
+    SG_TRY(sync_ctx(E->ctx));   // keeps hb alive until the copy has run
+    *cpbuf = buf;
+    *cp = cb;
     return SPGEMM_OK;
 }
 
@@ -403,10 +531,15 @@ spgemm_status_t spgemm_plan(spgemm_ctx_t ctx, spgemm_mat_t A, spgemm_mat_t B, sp
     spgemm_opts_default(&o);
     if (opts) o = *opts;
     auto* P = new struct spgemm_plan();
-    DMat dA, dB;
-    spgemm_status_t s = to_csc_operand(ctx, A, &P->Aconv, &dA);
-    if (s == SPGEMM_OK) s = to_csc_operand(ctx, B, &P->Bconv, &dB);
-    if (s == SPGEMM_OK) s = plan_build(ctx, dA, dB, sr, o, P);
+    P->ctx = ctx;
+    P->sr = sr;
+    P->opts = o;
+    P->m = A->m;
+    P->n = B->n;
+    Prod pr;
+    spgemm_status_t s = to_csc_operand(ctx, A, &P->Aconv, &pr.A);
+    if (s == SPGEMM_OK) s = to_csc_operand(ctx, B, &P->Bconv, &pr.B);
+    if (s == SPGEMM_OK) s = engine_setup(&P->E, ctx, sr, o, {pr}, o.use_predictor != 0);
     if (s != SPGEMM_OK) {
         spgemm_plan_destroy(P);
         return s;
@@ -417,61 +550,41 @@ spgemm_status_t spgemm_plan(spgemm_ctx_t ctx, spgemm_mat_t A, spgemm_mat_t B, sp
 
 spgemm_status_t spgemm_symbolic(spgemm_plan_t P, int64_t* nnz_C) {
     if (!P) return SPGEMM_ERR_INVALID_ARG;
-    if (!P->symbolic_done) {
-        run_symbolic_kernels(P);
-        SG_CUDA(P->ctx, cudaGetLastError());
-        SG_TRY(finish_colptr(P));
-        P->symbolic_done = true;
-    }
-    if (nnz_C) *nnz_C = P->nnzC;
+    SG_TRY(engine_symbolic(&P->E));
+    if (nnz_C) *nnz_C = P->E.nnz_total;
     return SPGEMM_OK;
 }
 
 spgemm_status_t spgemm_numeric(spgemm_plan_t P, spgemm_mat_t* C) {
     if (!P || !C) return SPGEMM_ERR_INVALID_ARG;
     spgemm_ctx* ctx = P->ctx;
-    if (!P->symbolic_done) SG_TRY(spgemm_symbolic(P, nullptr));
-    const size_t w = sr_size(P->sr);
-    auto rbuf = ctx_buf(ctx, 4 * (size_t)std::max<int64_t>(P->nnzC, 1));
-    auto vbuf = ctx_buf(ctx, w * (size_t)std::max<int64_t>(P->nnzC, 1));
-    if (!rbuf || !vbuf) return set_err(ctx, SPGEMM_ERR_OOM, "C arrays for nnz %lld", (long long)P->nnzC);
-    switch (P->sr) {
-    case SPGEMM_PLUS_TIMES_F64: dispatch_numeric<PT64>(P, (int32_t*)rbuf->p, vbuf->p); break;
-    case SPGEMM_MIN_PLUS_F32: dispatch_numeric<MP32>(P, (int32_t*)rbuf->p, vbuf->p); break;
-    case SPGEMM_OR_AND_BOOL: dispatch_numeric<BOOL8>(P, (int32_t*)rbuf->p, vbuf->p); break;
-    case SPGEMM_PLUS_TIMES_I64: dispatch_numeric<PTI64>(P, (int32_t*)rbuf->p, vbuf->p); break;
-    }
-    SG_CUDA(ctx, cudaGetLastError());
-    auto* M = new spgemm_mat();
-    M->ctx = ctx;
-    M->fmt = SPGEMM_FMT_CSC;
-    M->sr = P->sr;
-    M->m = P->m;
-    M->n = P->n;
-    M->nzc = P->n;
-    M->nnz = P->nnzC;
-    M->cp = P->Ccp;
-    M->ir = (const int32_t*)rbuf->p;
-    M->num = vbuf->p;
-    M->owned = {P->Ccp_buf, rbuf, vbuf};
-    *C = M;
+    Engine* E = &P->E;
+    SG_TRY(engine_symbolic(E));
+    std::shared_ptr<DevBuf> rbuf, vbuf, cpbuf;
+    SG_TRY(engine_alloc_out(E, &rbuf, &vbuf));
+    SG_TRY(engine_numeric(E, (int32_t*)rbuf->p, vbuf->p));
+    const int64_t* cp = nullptr;
+    SG_TRY(product_colptr(E, &cpbuf, &cp));
+    *C = new_owned_csc(ctx, P->sr, P->m, P->n, E->nnz_total, {cpbuf, rbuf, vbuf}, cp, (const int32_t*)rbuf->p,
+                       vbuf->p);
     return SPGEMM_OK;
 }
 
 spgemm_status_t spgemm_plan_stats(spgemm_plan_t P, int64_t* flops, int64_t* nnz_C, int64_t* tiers4,
                                   int64_t* overflow) {
     if (!P) return SPGEMM_ERR_INVALID_ARG;
-    if (flops) *flops = P->flops_total;
-    if (nnz_C) *nnz_C = P->nnzC;
+    const Engine& E = P->E;
+    if (flops) *flops = E.flops_total;
+    if (nnz_C) *nnz_C = E.nnz_total;
     if (tiers4) {
-        tiers4[0] = P->bin_cnt[0];
+        tiers4[0] = E.bin_cnt[0];
         tiers4[1] = 0;
         tiers4[2] = 0;
-        for (int b = 1; b <= NWARP; ++b) tiers4[1] += P->bin_cnt[b];
-        for (int b = NWARP + 1; b <= NWARP + NBLK; ++b) tiers4[2] += P->bin_cnt[b];
-        tiers4[3] = P->bin_cnt[BIN_DENSE];
+        for (int b = 1; b <= NWARP; ++b) tiers4[1] += E.bin_cnt[b];
+        for (int b = NWARP + 1; b <= NWARP + NBLK; ++b) tiers4[2] += E.bin_cnt[b];
+        tiers4[3] = E.bin_cnt[BIN_DENSE];
     }
-    if (overflow) *overflow = P->overflow_cols;
+    if (overflow) *overflow = E.overflow_items;
     return SPGEMM_OK;
 }
 
@@ -482,7 +595,7 @@ spgemm_status_t spgemm_plan_tier_stats(spgemm_plan_t P, int64_t* cols4, int64_t*
     auto buf = ctx_buf(ctx, 16 * 8);
     if (!buf) return set_err(ctx, SPGEMM_ERR_OOM, "tier stats");
     SG_CUDA(ctx, cudaMemsetAsync(buf->p, 0, 128, ctx->stream));
-    launch_tier_stats(ctx->stream, P->bin, P->flops, P->nnz_col, P->B.jc, P->B.cp, P->B.nzc,
+    launch_tier_stats(ctx->stream, P->E.it, P->E.bin, P->E.item_prod, P->E.flops, P->E.nnz_item,
                       (unsigned long long*)buf->p);
     unsigned long long h[16];
     SG_CUDA(ctx, cudaMemcpyAsync(h, buf->p, 128, cudaMemcpyDeviceToHost, ctx->stream));
@@ -490,7 +603,7 @@ spgemm_status_t spgemm_plan_tier_stats(spgemm_plan_t P, int64_t* cols4, int64_t*
     for (int t = 0; t < 4; ++t) {
         if (cols4) cols4[t] = (int64_t)h[t];
         if (flops4) flops4[t] = (int64_t)h[4 + t];
-        if (nnz4) nnz4[t] = P->symbolic_done ? (int64_t)h[8 + t] : -1;
+        if (nnz4) nnz4[t] = P->E.symbolic_done ? (int64_t)h[8 + t] : -1;
         if (bnnz4) bnnz4[t] = (int64_t)h[12 + t];
     }
     return SPGEMM_OK;

@@ -82,6 +82,19 @@ struct DMat {
     const void* num = nullptr;  // nullptr: pattern only (values = semiring one)
 };
 
+// One product of a batch.  Its items are the stored columns p of B; item p has
+// the global index item_base + p.  Output rows are written shifted by row_base.
+struct Prod {
+    DMat A, B;
+    int64_t item_base = 0;   // first global item of this product
+    int64_t bnz_base = 0;    // sum of nnz(B) over earlier products (cursor addressing)
+    int32_t row_base = 0;    // added to every output row id
+    int32_t G = 0;           // row slabs a long column needs at least: ceil(A.m / RB)
+    int64_t col_base = 0;    // global column of B's column 0 (2D blocks)
+    int32_t tag = 0;         // caller's label (SUMMA: the stage)
+    int32_t pad = 0;
+};
+
 template <class SR>
 __device__ __forceinline__ typename SR::T load_val(const DMat& M, int64_t idx) {
     if (M.num == nullptr) return (typename SR::T)SR::one();

@@ -170,6 +170,34 @@ __global__ void k_validate(const int64_t* __restrict__ cp, const int32_t* __rest
 
 }  // namespace
 
+// Stable sort of (key, payload) pairs by the low `bits` bits of key, LSD with
+// 8-bit digits.  Buffers (k0, v0) hold the input; the result ends in (k0, v0)
+// or (k1, v1): *in_second tells which.  tmp needs radix_tmp_bytes(n).
+size_t radix_tmp_bytes(int64_t n) {
+    const int64_t ntiles = std::max<int64_t>(1, ceil_div64(n, RS_TILE));
+    return 8 * (256 * ntiles + 1) * 2 + scan_tmp_bytes(256 * ntiles) + 256;
+}
+
+void radix_sort_pairs(cudaStream_t st, uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, int64_t n, int bits,
+                      void* tmp, bool* in_second) {
+    *in_second = false;
+    if (n <= 0 || bits <= 0) return;
+    const int64_t ntiles = std::max<int64_t>(1, ceil_div64(n, RS_TILE));
+    int64_t* hist = (int64_t*)tmp;
+    int64_t* off = hist + (256 * ntiles + 1);
+    void* stmp = off + (256 * ntiles + 1);
+    for (int shift = 0; shift < bits; shift += 8) {
+        k_rs_hist<<<(int)ntiles, RS_BLOCK, 0, st>>>(k0, n, shift, ntiles, hist);
+        note_launch();
+        launch_exclusive_scan(st, hist, 256 * ntiles, off, stmp);
+        k_rs_scatter<<<(int)ntiles, RS_BLOCK, 0, st>>>(k0, v0, n, shift, ntiles, off, k1, v1);
+        note_launch();
+        std::swap(k0, k1);
+        std::swap(v0, v1);
+        *in_second = !*in_second;
+    }
+}
+
 // CSC (m x n) -> CSC of the transpose (n x m), rows sorted.  `out` is filled in place.
 spgemm_status_t transpose_csc(spgemm_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const int64_t* cp,
                               const int32_t* ir, const void* num, size_t w, spgemm_mat_t out) {

@@ -59,39 +59,48 @@ struct spgemm_mat {
     std::vector<std::shared_ptr<DevBuf>> owned;
 };
 
+// One batched execution of products C_i = A_i * B_i over the item space
+// (see kernels.cuh): analyze -> bin -> symbolic -> scan -> numeric.
+struct Engine {
+    spgemm_ctx* ctx = nullptr;
+    spgemm_semiring_t sr = SPGEMM_PLUS_TIMES_F64;
+    spgemm_opts_t opts;
+    sg::TierCfg cfg;
+    std::vector<sg::Prod> hprods;
+    std::vector<int64_t> hitem_base;
+    sg::Items it;
+    std::vector<std::shared_ptr<DevBuf>> bufs;
+    int64_t* flops = nullptr;
+    uint8_t* bin = nullptr;
+    int32_t* item_prod = nullptr;
+    unsigned long long* ctr = nullptr;   // bin_count[NBIN], bin_cursor[NBIN], flops_total, slabs, ranges, err
+    int64_t* bin_off_dev = nullptr;
+    int2* list = nullptr;
+    int2* ditems = nullptr;
+    int8_t* nparts = nullptr;
+    int32_t* cursors = nullptr;
+    int32_t* part_count = nullptr;
+    sg::DenseWork dw;                    // range-tier state
+    int64_t* nnz_item = nullptr;
+    void* scan_tmp = nullptr;
+    float* feat = nullptr;               // predictor inputs (items x 8) when requested
+    std::shared_ptr<DevBuf> Coff_buf;    // item offsets (nitems + 1)
+    int64_t* Coff = nullptr;
+    int64_t bin_cnt[sg::NBIN] = {0};
+    int64_t bin_off[sg::NBIN] = {0};
+    int64_t flops_total = 0;
+    int64_t nnz_total = -1;
+    bool symbolic_done = false;
+    int64_t overflow_items = 0;
+};
+
 struct spgemm_plan {
     spgemm_ctx* ctx = nullptr;
     spgemm_semiring_t sr;
     spgemm_opts_t opts;
-    sg::DMat A, B;
+    Engine E;
     spgemm_mat_t Aconv = nullptr, Bconv = nullptr;   // owned conversions (CSR inputs)
-    sg::TierCfg cfg;
     int64_t m = 0, n = 0;          // output dimensions
-    int64_t G = 0;                 // dense chunks per column
-    std::vector<std::shared_ptr<DevBuf>> bufs;
-    int64_t* flops = nullptr;
-    uint8_t* bin = nullptr;
-    unsigned long long* ctr = nullptr;   // bin_count[NBIN], bin_cursor[NBIN], flops_total, nitems
-    int64_t* bin_off_dev = nullptr;
-    int32_t* list = nullptr;
-    int2* items = nullptr;
-    int8_t* nparts = nullptr;
-    int32_t* cursors = nullptr;
-    int32_t* part_count = nullptr;
-    int64_t* nnz_col = nullptr;
-    void* scan_tmp = nullptr;
-    float* feat = nullptr;
-    std::shared_ptr<DevBuf> Ccp_buf;
-    int64_t* Ccp = nullptr;
-    int64_t bin_cnt[sg::NBIN] = {0};
-    int64_t bin_off[sg::NBIN] = {0};
-    int64_t flops_total = 0;
-    int64_t nitems = 0;
-    int64_t nnzC = -1;
-    bool symbolic_done = false;
-    int64_t overflow_cols = 0;
-    // predictor path state
-    bool predicted = false;
 };
 
 spgemm_status_t set_err(spgemm_ctx* ctx, spgemm_status_t s, const char* fmt, ...);
@@ -128,10 +137,22 @@ spgemm_status_t sync_ctx(spgemm_ctx* ctx);
 spgemm_status_t transpose_csc(spgemm_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const int64_t* cp,
                               const int32_t* ir, const void* num, size_t w, spgemm_mat_t out_handle);
 spgemm_status_t make_dcsc(spgemm_ctx* ctx, const spgemm_mat* csc, bool aux, spgemm_mat* out);
+size_t radix_tmp_bytes(int64_t n);
+void radix_sort_pairs(cudaStream_t st, uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, int64_t n, int bits,
+                      void* tmp, bool* in_second);
 
-// flat product pieces used by summa/batch
-spgemm_status_t plan_build(spgemm_ctx* ctx, const sg::DMat& A, const sg::DMat& B, spgemm_semiring_t sr,
-                           const spgemm_opts_t& opts, struct spgemm_plan* P);
+// engine (api.cu)
+spgemm_status_t engine_setup(Engine* E, spgemm_ctx* ctx, spgemm_semiring_t sr, const spgemm_opts_t& opts,
+                             std::vector<sg::Prod> prods, bool want_features);
+spgemm_status_t engine_symbolic(Engine* E);
+spgemm_status_t engine_numeric(Engine* E, int32_t* Cir, void* Cv);
+// output arrays sized by the engine's nnz_total, values of the semiring width
+spgemm_status_t engine_alloc_out(Engine* E, std::shared_ptr<DevBuf>* rbuf, std::shared_ptr<DevBuf>* vbuf);
+sg::DMat csc_view(int64_t m, int64_t n, int64_t nnz, const int64_t* cp, const int32_t* ir, const void* num);
+spgemm_mat_t new_owned_csc(spgemm_ctx* ctx, spgemm_semiring_t sr, int64_t m, int64_t n, int64_t nnz,
+                           std::vector<std::shared_ptr<DevBuf>> owned, const int64_t* cp, const int32_t* ir,
+                           const void* num);
+spgemm_status_t to_csc_operand(spgemm_ctx* ctx, spgemm_mat_t M, spgemm_mat_t* conv, sg::DMat* d);
 
 #define SG_CUDA(ctx, call)                                                  \
     do {                                                                    \

@@ -1,17 +1,17 @@
-// Flat column-wise SpGEMM kernels (Gustavson's column-by-column formulation,
-// Section 2.1; accumulation in the spirit of the sparse accumulator of
-// Section 3.3), organised in three accumulator tiers chosen per output column
-// from cap_j = min(flops_j, m):
+// Batched column-wise SpGEMM kernels (Gustavson's column-by-column
+// formulation, Section 2.1; accumulation in the spirit of the sparse
+// accumulator of Section 3.3), organised in three accumulator tiers chosen per
+// output column from cap = min(flops, m):
 //   * warp-wide shared-memory hash tables (short columns),
 //   * CTA-wide shared-memory hash tables (medium columns),
 //   * a row-chunked dense accumulator (long columns): R rows of values plus an
 //     R-bit occupancy map per chunk, walked chunk by chunk with per-(column,k)
 //     cursors into A(:,k); rows come out sorted, so no sort is needed.
-// The symbolic pass counts nnz(C(:,j)); the numeric pass fills rows and values.
+// The symbolic pass counts nnz per output column; the numeric pass fills rows
+// and values.  Every kernel works on items (product, stored column of B).
 #include <algorithm>
-#include <climits>
-
 #include <atomic>
+#include <climits>
 
 #include "kernels.cuh"
 
@@ -22,7 +22,6 @@ void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 int64_t launches() { return g_launches.load(std::memory_order_relaxed); }
 
 constexpr int WARP_BLOCK = 256;   // 8 warp groups per CTA
-constexpr int DENSE_BLOCK = 512;
 
 __host__ __device__ __forceinline__ int bin_of(int64_t cap, int warp_max, int block_max) {
     if (cap <= 0) return 0;
@@ -50,33 +49,52 @@ int dense_rows_for(int semiring, int requested) {
     }
 }
 
+__device__ __forceinline__ int find_prod(const int64_t* __restrict__ base, int64_t nprod, int64_t u) {
+    // last product i with base[i] <= u
+    int64_t lo = 0, hi = nprod - 1;
+    while (lo < hi) {
+        int64_t mid = (lo + hi + 1) >> 1;
+        if (__ldg(base + mid) <= u) lo = mid;
+        else hi = mid - 1;
+    }
+    return (int)lo;
+}
+
+__device__ __forceinline__ int64_t out_col(const DMat& B, int64_t p) { return B.jc ? __ldg(B.jc + p) : p; }
+
 // ------------------------------------------------------------------ analysis
-// Groups of 8 lanes per stored column of B: flops_j = sum_k nnz(A(:,k))
-// (Section 1), the tier bin, and optionally the predictor inputs.
-__global__ void __launch_bounds__(256) k_analyze(DMat A, DMat B, TierCfg cfg, int64_t* __restrict__ flops,
-                                                 uint8_t* __restrict__ bin, unsigned long long* bin_count,
-                                                 unsigned long long* flops_total, const uint64_t* __restrict__ sketch,
-                                                 float* __restrict__ feat) {
+// Groups of 8 lanes per item: flops = sum_k nnz(A(:,k)) (Section 1's flops),
+// the tier bin, the product id, and optionally the predictor inputs.
+__global__ void __launch_bounds__(256) k_analyze(Items it, TierCfg cfg, int64_t* __restrict__ flops,
+                                                 uint8_t* __restrict__ bin, int32_t* __restrict__ item_prod,
+                                                 unsigned long long* bin_count, unsigned long long* flops_total,
+                                                 const uint64_t* __restrict__ sketch,
+                                                 const int64_t* __restrict__ sketch_base, float* __restrict__ feat) {
     __shared__ unsigned long long s_cnt[NBIN];
     __shared__ unsigned long long s_fl;
     if (threadIdx.x < NBIN) s_cnt[threadIdx.x] = 0;
     if (threadIdx.x == 0) s_fl = 0;
     __syncthreads();
     const int sub = threadIdx.x & 7;
-    const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
-    long long f = 0;
-    long long mx = 0;
+    const int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+    long long f = 0, mx = 0;
     unsigned long long sk = 0;
-    int64_t bs = 0, be = 0;
-    if (p < B.nzc) {
-        bs = __ldg(B.cp + p);
-        be = __ldg(B.cp + p + 1);
+    int64_t bs = 0, be = 0, am = 0;
+    int prod = 0;
+    if (u < it.nitems) {
+        prod = it.nprod == 1 ? 0 : find_prod(it.item_base, it.nprod, u);
+        const Prod* pr = it.prods + prod;
+        const int64_t p = u - __ldg(it.item_base + prod);
+        bs = __ldg(pr->B.cp + p);
+        be = __ldg(pr->B.cp + p + 1);
+        am = pr->A.m;
+        const uint64_t* skp = sketch ? sketch + sketch_base[prod] : nullptr;
         for (int64_t t = bs + sub; t < be; t += 8) {
-            int32_t k = __ldg(B.ir + t);
-            long long len = col_len(A, k);
+            int32_t k = __ldg(pr->B.ir + t);
+            long long len = col_len(pr->A, k);
             f += len;
             mx = len > mx ? len : mx;
-            if (sketch) sk |= __ldg(sketch + k);
+            if (skp && k >= 0 && k < pr->A.n) sk |= __ldg(skp + k);
         }
     }
 #pragma unroll
@@ -86,24 +104,25 @@ __global__ void __launch_bounds__(256) k_analyze(DMat A, DMat B, TierCfg cfg, in
         mx = om > mx ? om : mx;
         sk |= __shfl_xor_sync(0xffffffffu, sk, o, 8);
     }
-    if (p < B.nzc && sub == 0) {
-        flops[p] = f;
-        int64_t cap = f < A.m ? f : A.m;
+    if (u < it.nitems && sub == 0) {
+        flops[u] = f;
+        item_prod[u] = prod;
+        int64_t cap = f < am ? f : am;
         int b = bin_of(cap, cfg.warp_max, cfg.block_max);
-        bin[p] = (uint8_t)b;
+        bin[u] = (uint8_t)b;
         atomicAdd(&s_cnt[b], 1ull);
         atomicAdd(&s_fl, (unsigned long long)f);
         if (feat) {
-            // predictor inputs (see predictor.cu for the definition)
+            // predictor inputs (definitions in predictor.cu)
             float d = (float)(be - bs);
             int pc = __popcll(sk);
             float pcf = fminf((float)pc, 63.5f);
             float lc = 64.0f * logf(64.0f / (64.0f - pcf));
-            float* x = feat + p * 8;
+            float* x = feat + u * 8;
             x[0] = log1pf(d);
             x[1] = log1pf((float)f);
             x[2] = log1pf((float)mx);
-            x[3] = log1pf((float)A.m);
+            x[3] = log1pf((float)am);
             x[4] = log1pf(lc);
             x[5] = log1pf((float)cap);
             x[6] = log1pf((float)(f - mx));
@@ -115,13 +134,13 @@ __global__ void __launch_bounds__(256) k_analyze(DMat A, DMat B, TierCfg cfg, in
     if (threadIdx.x == 0 && flops_total) atomicAdd(flops_total, s_fl);
 }
 
-void launch_analyze(cudaStream_t st, const DMat& A, const DMat& B, TierCfg cfg, int64_t* flops, uint8_t* bin,
-                    unsigned long long* bin_count, unsigned long long* flops_total, const uint64_t* sketch_A,
-                    float* feat) {
-    if (B.nzc == 0) return;
-    int64_t threads = B.nzc * 8;
-    int grid = (int)ceil_div64(threads, 256);
-    k_analyze<<<grid, 256, 0, st>>>(A, B, cfg, flops, bin, bin_count, flops_total, sketch_A, feat);
+void launch_analyze(cudaStream_t st, const Items& it, TierCfg cfg, int64_t* flops, uint8_t* bin, int32_t* item_prod,
+                    unsigned long long* bin_count, unsigned long long* flops_total, const uint64_t* sketch,
+                    const int64_t* sketch_base, float* feat) {
+    if (it.nitems == 0) return;
+    int grid = (int)ceil_div64(it.nitems * 8, 256);
+    k_analyze<<<grid, 256, 0, st>>>(it, cfg, flops, bin, item_prod, bin_count, flops_total, sketch, sketch_base,
+                                    feat);
     note_launch();
 }
 
@@ -143,17 +162,17 @@ __global__ void k_row_sketch(DMat A, uint64_t* __restrict__ sk) {
 }
 
 void launch_row_sketch(cudaStream_t st, const DMat& A, uint64_t* sketch) {
-    if (A.jc) cudaMemsetAsync(sketch, 0, sizeof(uint64_t) * A.n, st);
+    if (A.jc) cudaMemsetAsync(sketch, 0, sizeof(uint64_t) * std::max<int64_t>(A.n, 1), st);
     if (A.nzc == 0) return;
     k_row_sketch<<<(int)ceil_div64(A.nzc * 8, 256), 256, 0, st>>>(A, sketch);
     note_launch();
 }
 
-// Stable-enough scatter of column ids into per-bin lists (warp-aggregated atomics).
-__global__ void k_bin_scatter(int64_t n, const uint8_t* __restrict__ bin, const int64_t* __restrict__ bin_off,
-                              unsigned long long* cursor, int32_t* __restrict__ list) {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int b = p < n ? bin[p] : -1;
+// Scatter of items into per-bin lists (warp-aggregated atomics).
+__global__ void k_bin_scatter(Items it, const uint8_t* __restrict__ bin, const int32_t* __restrict__ item_prod,
+                              const int64_t* __restrict__ bin_off, unsigned long long* cursor, int2* __restrict__ list) {
+    int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int b = u < it.nitems ? bin[u] : -1;
     unsigned mask = __match_any_sync(0xffffffffu, b);
     int lane = threadIdx.x & 31;
     int leader = __ffs(mask) - 1;
@@ -162,35 +181,16 @@ __global__ void k_bin_scatter(int64_t n, const uint8_t* __restrict__ bin, const 
     base = __shfl_sync(0xffffffffu, base, leader);
     if (b > 0) {
         int rank = __popc(mask & ((1u << lane) - 1));
-        list[bin_off[b] + base + rank] = (int32_t)p;
+        int prod = item_prod[u];
+        int p = (int)(u - __ldg(it.item_base + prod));
+        list[bin_off[b] + base + rank] = make_int2(prod, p);
     }
 }
 
-void launch_bin_scatter(cudaStream_t st, int64_t n, const uint8_t* bin, const int64_t* bin_off,
-                        unsigned long long* bin_cursor, int32_t* list) {
-    if (n == 0) return;
-    k_bin_scatter<<<(int)ceil_div64(n, 256), 256, 0, st>>>(n, bin, bin_off, bin_cursor, list);
-    note_launch();
-}
-
-__global__ void k_dense_items(const int32_t* __restrict__ dlist, int64_t nd, const int64_t* __restrict__ flops,
-                              int G, int part_flops, int2* items, unsigned long long* nitems, int8_t* nparts) {
-    int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (d >= nd) return;
-    int32_t p = dlist[d];
-    int64_t f = flops[p];
-    int maxp = G < MAX_PARTS ? G : MAX_PARTS;
-    int P = (int)std::min<int64_t>(std::max<int64_t>(ceil_div64(f, part_flops), 1), maxp);
-    nparts[d] = (int8_t)P;
-    unsigned long long base = atomicAdd(nitems, (unsigned long long)P);
-    for (int q = 0; q < P; ++q) items[base + q] = make_int2((int)d, q);
-}
-
-void launch_dense_items(cudaStream_t st, const int32_t* dense_list, int64_t ndense, const int64_t* flops, int G,
-                        int part_flops, int2* items, unsigned long long* nitems, int8_t* nparts) {
-    if (ndense == 0) return;
-    k_dense_items<<<(int)ceil_div64(ndense, 256), 256, 0, st>>>(dense_list, ndense, flops, G, part_flops, items,
-                                                               nitems, nparts);
+void launch_bin_scatter(cudaStream_t st, const Items& it, const uint8_t* bin, const int32_t* item_prod,
+                        const int64_t* bin_off, unsigned long long* bin_cursor, int2* list) {
+    if (it.nitems == 0) return;
+    k_bin_scatter<<<(int)ceil_div64(it.nitems, 256), 256, 0, st>>>(it, bin, item_prod, bin_off, bin_cursor, list);
     note_launch();
 }
 
@@ -233,8 +233,8 @@ __device__ __forceinline__ void bitonic_sort(int32_t* keys, Acc* vals, int P) {
 }
 
 template <class SR, int GS, int TBL, bool NUM, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_hash(DMat A, DMat B, const int32_t* __restrict__ list, int64_t count,
-                                                int64_t* __restrict__ nnz_col, const int64_t* __restrict__ Ccp,
+__global__ void __launch_bounds__(BLOCK) k_hash(Items it, const int2* __restrict__ list, int64_t count,
+                                                int64_t* __restrict__ nnz_item, const int64_t* __restrict__ Coff,
                                                 int32_t* __restrict__ Cir, typename SR::T* __restrict__ Cv) {
     using T = typename SR::T;
     using Acc = typename SR::Acc;
@@ -255,10 +255,11 @@ __global__ void __launch_bounds__(BLOCK) k_hash(DMat A, DMat B, const int32_t* _
     int* s_cnt = s_scan + 33;
     volatile int32_t* vkeys = keys;
 
-    for (int64_t it = (int64_t)blockIdx.x * NG + g; it < count; it += (int64_t)gridDim.x * NG) {
-        const int32_t p = __ldg(list + it);
-        const int64_t jout = B.jc ? __ldg(B.jc + p) : p;
-        const int64_t bs = __ldg(B.cp + p), be = __ldg(B.cp + p + 1);
+    for (int64_t w = (int64_t)blockIdx.x * NG + g; w < count; w += (int64_t)gridDim.x * NG) {
+        const int2 e = __ldg(list + w);
+        const Prod* pr = it.prods + e.x;
+        const int64_t u = __ldg(it.item_base + e.x) + e.y;
+        const int64_t bs = __ldg(pr->B.cp + e.y), be = __ldg(pr->B.cp + e.y + 1);
         for (int s = lane; s < TBL; s += GS) {
             keys[s] = -1;
             if constexpr (NUM) vals[s] = SR::zero();
@@ -272,12 +273,12 @@ __global__ void __launch_bounds__(BLOCK) k_hash(DMat A, DMat B, const int32_t* _
             int64_t a0 = 0;
             T bv = T(0);
             if (t < be) {
-                int32_t k = __ldg(B.ir + t);
-                int64_t s, e;
-                col_range(A, k, s, e);
+                int32_t k = __ldg(pr->B.ir + t);
+                int64_t s, en;
+                col_range(pr->A, k, s, en);
                 a0 = s;
-                len = (int)(e - s);
-                if constexpr (NUM) bv = load_val<SR>(B, t);
+                len = (int)(en - s);
+                if constexpr (NUM) bv = load_val<SR>(pr->B, t);
             }
             int total;
             int incl = group_incl_scan<GS>(len, s_scan, total);
@@ -285,15 +286,16 @@ __global__ void __launch_bounds__(BLOCK) k_hash(DMat A, DMat B, const int32_t* _
             s_a0[lane] = a0;
             if constexpr (NUM) s_bv[lane] = bv;
             G::sync();
-            for (int e = lane; e < total; e += GS) {
+            const int32_t* __restrict__ air = pr->A.ir;
+            for (int q = lane; q < total; q += GS) {
                 int lo = 0, hi = GS - 1;
                 while (lo < hi) {
                     int mid = (lo + hi) >> 1;
-                    if (s_incl[mid] > e) hi = mid;
+                    if (s_incl[mid] > q) hi = mid;
                     else lo = mid + 1;
                 }
-                const int64_t idx = s_a0[lo] + (e - (lo ? s_incl[lo - 1] : 0));
-                const int32_t row = __ldg(A.ir + idx);
+                const int64_t idx = s_a0[lo] + (q - (lo ? s_incl[lo - 1] : 0));
+                const int32_t row = __ldg(air + idx);
                 uint32_t h = hash_row(row) >> (32 - LOG2);
                 while (true) {
                     int32_t cur = vkeys[h];
@@ -305,23 +307,24 @@ __global__ void __launch_bounds__(BLOCK) k_hash(DMat A, DMat B, const int32_t* _
                     }
                     h = (h + 1) & (TBL - 1);
                 }
-                if constexpr (NUM) SR::atomic_add(&vals[h], SR::mul(load_val<SR>(A, idx), s_bv[lo]));
+                if constexpr (NUM) SR::atomic_add(&vals[h], SR::mul(load_val<SR>(pr->A, idx), s_bv[lo]));
             }
             G::sync();
         }
         if constexpr (!NUM) {
             int c = warp_sum(mycnt);
             if constexpr (GS == 32) {
-                if (lane == 0) nnz_col[jout] = c;
+                if (lane == 0) nnz_item[u] = c;
             } else {
                 if ((threadIdx.x & 31) == 0) atomicAdd(s_cnt, c);
                 __syncthreads();
-                if (lane == 0) nnz_col[jout] = *s_cnt;
+                if (lane == 0) nnz_item[u] = *s_cnt;
             }
             G::sync();
         } else {
-            const int64_t out0 = __ldg(Ccp + jout);
-            const int nnz = (int)(__ldg(Ccp + jout + 1) - out0);
+            const int64_t out0 = __ldg(Coff + u);
+            const int nnz = (int)(__ldg(Coff + u + 1) - out0);
+            const int32_t rb = pr->row_base;
             // in-place compaction toward the front: the i-th occupied slot moves to i <= its slot
             int pos = 0;
             for (int r0 = 0; r0 < TBL; r0 += GS) {
@@ -345,7 +348,7 @@ __global__ void __launch_bounds__(BLOCK) k_hash(DMat A, DMat B, const int32_t* _
             G::sync();
             bitonic_sort<GS>(keys, vals, P);
             for (int s = lane; s < nnz; s += GS) {
-                Cir[out0 + s] = keys[s];
+                Cir[out0 + s] = keys[s] + rb;
                 Cv[out0 + s] = SR::out(vals[s]);
             }
             G::sync();
@@ -354,8 +357,8 @@ __global__ void __launch_bounds__(BLOCK) k_hash(DMat A, DMat B, const int32_t* _
 }
 
 template <class SR, int GS, int TBL, bool NUM, int BLOCK>
-static void run_hash(cudaStream_t st, const DMat& A, const DMat& B, const int32_t* list, int64_t count,
-                     int64_t* nnz_col, const int64_t* Ccp, int32_t* Cir, typename SR::T* Cv) {
+static void run_hash(cudaStream_t st, const Items& it, const int2* list, int64_t count, int64_t* nnz_item,
+                     const int64_t* Coff, int32_t* Cir, typename SR::T* Cv) {
     if (count <= 0) return;
     using L = HashLayout<SR, GS, TBL, NUM>;
     constexpr int NG = BLOCK / GS;
@@ -366,28 +369,39 @@ static void run_hash(cudaStream_t st, const DMat& A, const DMat& B, const int32_
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr_done = true;
     }
-    int64_t groups = count;
-    int64_t want = ceil_div64(groups, NG);
+    int64_t want = ceil_div64(count, NG);
     int grid = (int)std::min<int64_t>(want, 152 * 32);
-    kern<<<grid, BLOCK, smem, st>>>(A, B, list, count, nnz_col, Ccp, Cir, Cv);
+    kern<<<grid, BLOCK, smem, st>>>(it, list, count, nnz_item, Coff, Cir, Cv);
     note_launch();
 }
 
 template <class SR, bool NUM>
-static void run_hash_bins(cudaStream_t st, const DMat& A, const DMat& B, const int32_t* list, const int64_t* off,
-                          const int64_t* cnt, int64_t* nnz_col, const int64_t* Ccp, int32_t* Cir,
-                          typename SR::T* Cv) {
-    run_hash<SR, 32, 64, NUM, WARP_BLOCK>(st, A, B, list + off[1], cnt[1], nnz_col, Ccp, Cir, Cv);
-    run_hash<SR, 32, 128, NUM, WARP_BLOCK>(st, A, B, list + off[2], cnt[2], nnz_col, Ccp, Cir, Cv);
-    run_hash<SR, 32, 256, NUM, WARP_BLOCK>(st, A, B, list + off[3], cnt[3], nnz_col, Ccp, Cir, Cv);
-    run_hash<SR, 32, 512, NUM, WARP_BLOCK>(st, A, B, list + off[4], cnt[4], nnz_col, Ccp, Cir, Cv);
-    run_hash<SR, 32, 1024, NUM, 128>(st, A, B, list + off[5], cnt[5], nnz_col, Ccp, Cir, Cv);
-    run_hash<SR, 256, 2048, NUM, 256>(st, A, B, list + off[6], cnt[6], nnz_col, Ccp, Cir, Cv);
-    run_hash<SR, 512, 4096, NUM, 512>(st, A, B, list + off[7], cnt[7], nnz_col, Ccp, Cir, Cv);
-    run_hash<SR, 512, 8192, NUM, 512>(st, A, B, list + off[8], cnt[8], nnz_col, Ccp, Cir, Cv);
+static void run_hash_bins(cudaStream_t st, const Items& it, const int2* list, const int64_t* off, const int64_t* cnt,
+                          int64_t* nnz_item, const int64_t* Coff, int32_t* Cir, typename SR::T* Cv) {
+    run_hash<SR, 32, 64, NUM, WARP_BLOCK>(st, it, list + off[1], cnt[1], nnz_item, Coff, Cir, Cv);
+    run_hash<SR, 32, 128, NUM, WARP_BLOCK>(st, it, list + off[2], cnt[2], nnz_item, Coff, Cir, Cv);
+    run_hash<SR, 32, 256, NUM, WARP_BLOCK>(st, it, list + off[3], cnt[3], nnz_item, Coff, Cir, Cv);
+    run_hash<SR, 32, 512, NUM, WARP_BLOCK>(st, it, list + off[4], cnt[4], nnz_item, Coff, Cir, Cv);
+    run_hash<SR, 32, 1024, NUM, 128>(st, it, list + off[5], cnt[5], nnz_item, Coff, Cir, Cv);
+    run_hash<SR, 256, 2048, NUM, 256>(st, it, list + off[6], cnt[6], nnz_item, Coff, Cir, Cv);
+    run_hash<SR, 512, 4096, NUM, 512>(st, it, list + off[7], cnt[7], nnz_item, Coff, Cir, Cv);
+    run_hash<SR, 512, 8192, NUM, 512>(st, it, list + off[8], cnt[8], nnz_item, Coff, Cir, Cv);
 }
 
-// ------------------------------------------------------------------ dense tier
+// ------------------------------------------------------------------ range tier (long columns)
+// A long output column is first split into at most MAX_PARTS row slabs of
+// at most RB rows ("symbolic items", balanced by flops).  The symbolic kernel
+// marks the rows of its slab in a shared-memory bitmap with a balanced,
+// flattened walk over the products, counts them, and cuts the slab into
+// "ranges" of at most H entries and W rows.  The numeric kernel walks the
+// ranges of a slab in row order with one cursor per k: a galloping search
+// finds where A(:,k) leaves the range, the products of the range are
+// accumulated in a shared-memory hash table (values) plus a bitmap of the
+// range's rows (order), and the bitmap is read back in row order, so each
+// range is written already sorted.
+constexpr int RT_BLOCK = 512;
+constexpr int RT_MAXB = 1024;
+
 __device__ __forceinline__ int32_t lower_bound_rows(const int32_t* __restrict__ r, int64_t len, int64_t v) {
     int64_t lo = 0, hi = len;
     while (lo < hi) {
@@ -398,177 +412,433 @@ __device__ __forceinline__ int32_t lower_bound_rows(const int32_t* __restrict__ 
     return (int32_t)lo;
 }
 
-template <class SR, bool NUM>
-__global__ void __launch_bounds__(DENSE_BLOCK) k_dense(DMat A, DMat B, const int32_t* __restrict__ dlist,
-                                                       int64_t ndense, const int2* __restrict__ items,
-                                                       const unsigned long long* __restrict__ nitems_dev, int R, int G,
-                                                       const int8_t* __restrict__ nparts, int32_t* __restrict__ cursors,
-                                                       int64_t nnzB, int32_t* __restrict__ part_count,
-                                                       const int64_t* __restrict__ Ccp, int32_t* __restrict__ Cir,
-                                                       typename SR::T* __restrict__ Cv) {
-    using Acc = typename SR::Acc;
+// rows [R0, R1) of symbolic item q of P over m rows (32-aligned cuts)
+__device__ __forceinline__ void slab_rows(int64_t m, int q, int P, int64_t& R0, int64_t& R1) {
+    R0 = ((int64_t)q * m / P) & ~int64_t(31);
+    R1 = q == P - 1 ? m : (((int64_t)(q + 1) * m / P) & ~int64_t(31));
+}
+
+// number of positions in [pos, en) whose row is < lim (rows ascending)
+__device__ __forceinline__ int64_t gallop_count(const int32_t* __restrict__ r, int64_t pos, int64_t en, int64_t lim) {
+    if (pos >= en || (int64_t)__ldg(r + pos) >= lim) return 0;
+    int64_t lo = pos, step = 1;   // r[lo] < lim
+    while (lo + step < en && (int64_t)__ldg(r + lo + step) < lim) {
+        lo += step;
+        step <<= 1;
+    }
+    int64_t hi = lo + step < en ? lo + step : en;   // r[hi] >= lim or hi == en
+    ++lo;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if ((int64_t)__ldg(r + mid) < lim) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo - pos;
+}
+
+struct RangeSmem {   // flattened-expansion scratch of one CTA
+    int incl[RT_BLOCK];
+    int64_t start[RT_BLOCK];
+    int64_t bv[RT_BLOCK];   // B value bits (read back as SR::T)
+    int scan[34];
+};
+
+__global__ void k_dense_items(Items it, const int2* __restrict__ dlist, int64_t nd, const int64_t* __restrict__ flops,
+                              int part_flops, int RB, int2* items, unsigned long long* nitems, int8_t* nparts) {
+    int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= nd) return;
+    const int2 e = dlist[d];
+    const Prod* pr = it.prods + e.x;
+    const int64_t f = flops[__ldg(it.item_base + e.x) + e.y];
+    const int64_t m = pr->A.m;
+    // slab rows stay <= RB: one slab when m fits, else cuts of at most RB - 32 rows plus alignment
+    int64_t pmin = m <= RB ? 1 : ceil_div64(m, (int64_t)RB - 32);
+    int64_t P = ceil_div64(f, part_flops);
+    P = P < pmin ? pmin : P;
+    P = P > MAX_PARTS ? MAX_PARTS : P;
+    P = P < 1 ? 1 : P;
+    nparts[d] = (int8_t)P;
+    unsigned long long base = atomicAdd(nitems, (unsigned long long)P);
+    for (int q = 0; q < P; ++q) items[base + q] = make_int2((int)d, q);
+}
+
+void launch_dense_items(cudaStream_t st, const Items& it, const int2* dense_list, int64_t ndense, const int64_t* flops,
+                        int part_flops, int RB, int2* items, unsigned long long* nitems, int8_t* nparts) {
+    if (ndense == 0) return;
+    k_dense_items<<<(int)ceil_div64(ndense, 256), 256, 0, st>>>(it, dense_list, ndense, flops, part_flops, RB, items,
+                                                               nitems, nparts);
+    note_launch();
+}
+
+// Symbolic range kernel: slab bitmap, count, cut into ranges.
+__global__ void __launch_bounds__(RT_BLOCK) k_range_sym(Items it, DenseWork dw) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int nw_max = R / 32;
-    uint32_t* bitmap = reinterpret_cast<uint32_t*>(smem);
-    Acc* vals = reinterpret_cast<Acc*>(smem + (size_t)nw_max * 4);
-    int* s_scan = reinterpret_cast<int*>(smem + (size_t)nw_max * 4 + (NUM ? (size_t)R * sizeof(Acc) : 0));
+    RangeSmem* sc = reinterpret_cast<RangeSmem*>(smem);
+    int* s_bw = reinterpret_cast<int*>(smem + sizeof(RangeSmem));          // boundary words
+    int* s_bp = s_bw + RT_MAXB + 1;                                           // set bits before them
+    int* s_misc = s_bp + RT_MAXB + 1;                                         // [0] boundary count, [1] base
+    uint32_t* bitmap = reinterpret_cast<uint32_t*>(s_misc + 4);
     const int tid = threadIdx.x;
-    const int64_t nitems = (int64_t)*nitems_dev;
-    if constexpr (NUM) {
-        for (int i = tid; i < R; i += DENSE_BLOCK) vals[i] = SR::zero();
+    const int64_t nsym = (int64_t)*dw.nitems;
+    for (int64_t w = blockIdx.x; w < nsym; w += gridDim.x) {
+        const int2 itm = dw.items[w];
+        const int d = itm.x, q = itm.y;
+        const int2 e = __ldg(dw.dlist + d);
+        const Prod* pr = it.prods + e.x;
+        const int P = dw.nparts[d];
+        const int64_t m = pr->A.m;
+        int64_t R0, R1;
+        slab_rows(m, q, P, R0, R1);
+        const int nw = (int)((R1 - R0 + 31) >> 5);
+        const int64_t bs = __ldg(pr->B.cp + e.y), be = __ldg(pr->B.cp + e.y + 1);
+        const int32_t* __restrict__ air = pr->A.ir;
+        for (int x = tid; x < nw; x += RT_BLOCK) bitmap[x] = 0u;
+        __syncthreads();
+        for (int64_t b0 = bs; b0 < be; b0 += RT_BLOCK) {
+            const int64_t t = b0 + tid;
+            int len = 0;
+            int64_t a = 0;
+            if (t < be) {
+                const int32_t k = __ldg(pr->B.ir + t);
+                int64_t s, en;
+                col_range(pr->A, k, s, en);
+                a = R0 == 0 ? s : s + lower_bound_rows(air + s, en - s, R0);
+                const int64_t b = R1 == m ? en : s + lower_bound_rows(air + s, en - s, R1);
+                len = (int)(b - a);
+            }
+            int total;
+            const int incl = group_incl_scan<RT_BLOCK>(len, sc->scan, total);
+            sc->incl[tid] = incl;
+            sc->start[tid] = a;
+            __syncthreads();
+            for (int x = tid; x < total; x += RT_BLOCK) {
+                int lo = 0, hi = RT_BLOCK - 1;
+                while (lo < hi) {
+                    int mid = (lo + hi) >> 1;
+                    if (sc->incl[mid] > x) hi = mid;
+                    else lo = mid + 1;
+                }
+                const int64_t idx = sc->start[lo] + (x - (lo ? sc->incl[lo - 1] : 0));
+                const int lr = (int)(__ldg(air + idx) - R0);
+                if ((unsigned)lr < (unsigned)(R1 - R0)) atomicOr(&bitmap[lr >> 5], 1u << (lr & 31));
+            }
+            __syncthreads();
+        }
+        // count per thread over a contiguous word range, then cut into ranges
+        const int wpt = (nw + RT_BLOCK - 1) / RT_BLOCK;
+        const int w0 = min(tid * wpt, nw), w1 = min(w0 + wpt, nw);
+        int cnt = 0;
+        for (int x = w0; x < w1; ++x) cnt += __popc(bitmap[x]);
+        int total;
+        const int excl = group_incl_scan<RT_BLOCK>(cnt, sc->scan, total) - cnt;
+        int nb = 0;
+        {
+            int bp = excl;
+            for (int x = w0; x < w1; ++x) {
+                const int prev = x > 0 ? bp - __popc(bitmap[x - 1]) : 0;
+                if (x == 0 || x % dw.WW == 0 || bp / dw.H > prev / dw.H) ++nb;
+                bp += __popc(bitmap[x]);
+            }
+        }
+        int nbt;
+        const int bexcl = group_incl_scan<RT_BLOCK>(nb, sc->scan, nbt) - nb;
+        {
+            int bp = excl, o = bexcl;
+            for (int x = w0; x < w1; ++x) {
+                const int prev = x > 0 ? bp - __popc(bitmap[x - 1]) : 0;
+                if (x == 0 || x % dw.WW == 0 || bp / dw.H > prev / dw.H) {
+                    if (o < RT_MAXB) {
+                        s_bw[o] = x;
+                        s_bp[o] = bp;
+                    }
+                    ++o;
+                }
+                bp += __popc(bitmap[x]);
+            }
+        }
+        if (tid == 0) {
+            const int nbc = nbt < RT_MAXB ? nbt : RT_MAXB;
+            s_bw[nbc] = nw;
+            s_bp[nbc] = total;
+            if (nbt > RT_MAXB) atomicExch(dw.err, 1);
+        }
+        __syncthreads();
+        const int nbc = nbt < RT_MAXB ? nbt : RT_MAXB;
+        // nonempty ranges in row order: thread tid owns ranges [i0, i1)
+        const int ipt = (nbc + RT_BLOCK - 1) / RT_BLOCK;
+        const int i0 = min(tid * ipt, nbc), i1 = min(i0 + ipt, nbc);
+        int ne = 0;
+        for (int i = i0; i < i1; ++i) ne += s_bp[i + 1] > s_bp[i];
+        int net;
+        const int neexcl = group_incl_scan<RT_BLOCK>(ne, sc->scan, net) - ne;
+        if (tid == 0) {
+            unsigned long long base = net ? atomicAdd(dw.parts_ctr, (unsigned long long)net) : 0ull;
+            const bool over = base + (unsigned long long)net > (unsigned long long)dw.parts_cap;
+            if (over) atomicExch(dw.err, 2);
+            s_misc[0] = over ? 1 : 0;
+            dw.pbase[w] = over ? 0 : (int64_t)base;
+            dw.pcnt[w] = over ? 0 : net;
+            dw.part_count[(int64_t)q * dw.ndense + d] = total;
+        }
+        __syncthreads();
+        if (!s_misc[0]) {
+            const int64_t base = dw.pbase[w];
+            int o = neexcl;
+            for (int i = i0; i < i1; ++i) {
+                if (s_bp[i + 1] > s_bp[i]) {
+                    RangePart rp;
+                    rp.d = d;
+                    rp.q = q;
+                    rp.r0 = (int32_t)(R0 + (int64_t)s_bw[i] * 32);
+                    rp.r1 = (int32_t)(R0 + (int64_t)s_bw[i + 1] * 32 < R1 ? R0 + (int64_t)s_bw[i + 1] * 32 : R1);
+                    rp.off = s_bp[i];
+                    rp.nnz = s_bp[i + 1] - s_bp[i];
+                    dw.parts[base + o] = rp;
+                    ++o;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Numeric range kernel: walk the ranges of a slab with per-k cursors.
+template <class SR, int TBL>
+__global__ void __launch_bounds__(RT_BLOCK) k_range_num(Items it, DenseWork dw, const int64_t* __restrict__ Coff,
+                                                        int32_t* __restrict__ Cir, typename SR::T* __restrict__ Cv) {
+    using Acc = typename SR::Acc;
+    using T = typename SR::T;
+    constexpr int LOG2 = __builtin_ctz(TBL);
+    extern __shared__ __align__(16) unsigned char smem[];
+    RangeSmem* sc = reinterpret_cast<RangeSmem*>(smem);
+    int32_t* keys = reinterpret_cast<int32_t*>(smem + sizeof(RangeSmem));
+    Acc* vals = reinterpret_cast<Acc*>(smem + sizeof(RangeSmem) + (size_t)TBL * 4);
+    uint32_t* bitmap = reinterpret_cast<uint32_t*>(smem + sizeof(RangeSmem) + (size_t)TBL * (4 + sizeof(Acc)));
+    volatile int32_t* vkeys = keys;
+    const int tid = threadIdx.x;
+    const int64_t nsym = (int64_t)*dw.nitems;
+    for (int x = tid; x < TBL; x += RT_BLOCK) {
+        keys[x] = -1;
+        vals[x] = SR::zero();
     }
     __syncthreads();
-    for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
-        const int2 itm = items[it];
+    for (int64_t w = blockIdx.x; w < nsym; w += gridDim.x) {
+        const int2 itm = dw.items[w];
         const int d = itm.x, q = itm.y;
-        const int32_t p = __ldg(dlist + d);
-        const int P = nparts[d];
-        const int64_t jout = B.jc ? __ldg(B.jc + p) : p;
-        const int64_t bs = __ldg(B.cp + p), be = __ldg(B.cp + p + 1);
+        const int2 e = __ldg(dw.dlist + d);
+        const Prod* pr = it.prods + e.x;
+        const int P = dw.nparts[d];
+        const int64_t m = pr->A.m;
+        const int64_t u = __ldg(it.item_base + e.x) + e.y;
+        const int32_t rb = pr->row_base;
+        int64_t R0, R1;
+        slab_rows(m, q, P, R0, R1);
+        const int64_t bs = __ldg(pr->B.cp + e.y), be = __ldg(pr->B.cp + e.y + 1);
         const int64_t deg = be - bs;
-        const int c0 = (int)((int64_t)q * G / P), c1 = (int)((int64_t)(q + 1) * G / P);
-        int32_t* cur = cursors + (int64_t)q * nnzB + bs;
-        for (int64_t t = tid; t < deg; t += DENSE_BLOCK) {
-            int32_t k = __ldg(B.ir + bs + t);
-            int64_t s, e;
-            col_range(A, k, s, e);
-            cur[t] = c0 == 0 ? 0 : lower_bound_rows(A.ir + s, e - s, (int64_t)c0 * R);
+        const int32_t* __restrict__ air = pr->A.ir;
+        // cursor slots are indexed relative to the product's first B position (blocks share arrays)
+        int32_t* cur = dw.cursors + (int64_t)q * it.total_bnz + pr->bnz_base + (bs - __ldg(pr->B.cp));
+        for (int64_t t = tid; t < deg; t += RT_BLOCK) {
+            const int32_t k = __ldg(pr->B.ir + bs + t);
+            int64_t s, en;
+            col_range(pr->A, k, s, en);
+            cur[t] = R0 == 0 ? 0 : lower_bound_rows(air + s, en - s, R0);
         }
-        int64_t outpos = 0;
-        if constexpr (NUM) {
-            outpos = __ldg(Ccp + jout);
-            for (int qq = 0; qq < q; ++qq) outpos += part_count[(int64_t)qq * ndense + d];
-        }
-        int64_t part_total = 0;
+        int64_t outbase = __ldg(Coff + u);
+        for (int qq = 0; qq < q; ++qq) outbase += dw.part_count[(int64_t)qq * dw.ndense + d];
+        const int64_t pb = dw.pbase[w];
+        const int np = dw.pcnt[w];
         __syncthreads();
-        for (int c = c0; c < c1; ++c) {
-            const int64_t r0 = (int64_t)c * R;
-            const int64_t r1 = std::min<int64_t>(r0 + R, A.m);
-            const int nwords = (int)((r1 - r0 + 31) >> 5);
-            for (int w = tid; w < nwords; w += DENSE_BLOCK) bitmap[w] = 0u;
+        for (int ip = 0; ip < np; ++ip) {
+            const RangePart rp = dw.parts[pb + ip];
+            const int64_t r0 = rp.r0, r1 = rp.r1;
+            const int nw = (int)((r1 - r0 + 31) >> 5);
+            for (int x = tid; x < nw; x += RT_BLOCK) bitmap[x] = 0u;
             __syncthreads();
-            for (int64_t t = tid; t < deg; t += DENSE_BLOCK) {
-                const int32_t k = __ldg(B.ir + bs + t);
-                int64_t s, e;
-                col_range(A, k, s, e);
-                int64_t pos = s + cur[t];
-                typename SR::T bv = typename SR::T(0);
-                if constexpr (NUM) bv = load_val<SR>(B, bs + t);
-                while (pos < e) {
-                    const int32_t r = __ldg(A.ir + pos);
-                    if (r >= r1) break;
-                    if (r < r0) { ++pos; continue; }   // only on unsorted (malformed) columns
-                    const int lr = (int)(r - r0);
-                    atomicOr(&bitmap[lr >> 5], 1u << (lr & 31));
-                    if constexpr (NUM) SR::atomic_add(&vals[lr], SR::mul(load_val<SR>(A, pos), bv));
-                    ++pos;
+            for (int64_t b0 = 0; b0 < deg; b0 += RT_BLOCK) {
+                const int64_t t = b0 + tid;
+                int len = 0;
+                int64_t a = 0;
+                T bv = T(0);
+                if (t < deg) {
+                    const int32_t k = __ldg(pr->B.ir + bs + t);
+                    int64_t s, en;
+                    col_range(pr->A, k, s, en);
+                    a = s + cur[t];
+                    const int64_t c = gallop_count(air, a, en, r1);
+                    cur[t] += (int32_t)c;
+                    len = (int)c;
+                    bv = load_val<SR>(pr->B, bs + t);
                 }
-                cur[t] = (int32_t)(pos - s);
-            }
-            __syncthreads();
-            const int wpt = (nwords + DENSE_BLOCK - 1) / DENSE_BLOCK;
-            const int w0 = tid * wpt, w1 = std::min(w0 + wpt, nwords);
-            int cnt = 0;
-            for (int w = w0; w < w1; ++w) cnt += __popc(bitmap[w]);
-            int total;
-            int incl = group_incl_scan<DENSE_BLOCK>(cnt, s_scan, total);
-            if constexpr (NUM) {
-                int64_t o = outpos + incl - cnt;
-                for (int w = w0; w < w1; ++w) {
-                    uint32_t bits = bitmap[w];
-                    while (bits) {
-                        int b = __ffs(bits) - 1;
-                        bits &= bits - 1;
-                        int lr = w * 32 + b;
-                        Cir[o] = (int32_t)(r0 + lr);
-                        Cv[o] = SR::out(vals[lr]);
-                        vals[lr] = SR::zero();
-                        ++o;
+                int total;
+                const int incl = group_incl_scan<RT_BLOCK>(len, sc->scan, total);
+                sc->incl[tid] = incl;
+                sc->start[tid] = a;
+                reinterpret_cast<T*>(&sc->bv[tid])[0] = bv;
+                __syncthreads();
+                for (int x = tid; x < total; x += RT_BLOCK) {
+                    int lo = 0, hi = RT_BLOCK - 1;
+                    while (lo < hi) {
+                        int mid = (lo + hi) >> 1;
+                        if (sc->incl[mid] > x) hi = mid;
+                        else lo = mid + 1;
                     }
+                    const int64_t idx = sc->start[lo] + (x - (lo ? sc->incl[lo - 1] : 0));
+                    const int32_t row = __ldg(air + idx);
+                    const int lr = (int)(row - r0);
+                    if ((unsigned)lr >= (unsigned)(r1 - r0)) continue;   // only on malformed input
+                    atomicOr(&bitmap[lr >> 5], 1u << (lr & 31));
+                    uint32_t h = hash_row(row) >> (32 - LOG2);
+                    while (true) {
+                        int32_t cu = vkeys[h];
+                        if (cu == row) break;
+                        if (cu == -1) {
+                            int32_t prev = atomicCAS(&keys[h], -1, row);
+                            if (prev == -1 || prev == row) break;
+                        }
+                        h = (h + 1) & (TBL - 1);
+                    }
+                    SR::atomic_add(&vals[h], SR::mul(load_val<SR>(pr->A, idx),
+                                                     reinterpret_cast<const T*>(&sc->bv[lo])[0]));
+                }
+                __syncthreads();
+            }
+            // read back in row order through the bitmap
+            const int wpt = (nw + RT_BLOCK - 1) / RT_BLOCK;
+            const int w0 = min(tid * wpt, nw), w1 = min(w0 + wpt, nw);
+            int cnt = 0;
+            for (int x = w0; x < w1; ++x) cnt += __popc(bitmap[x]);
+            int total;
+            const int excl = group_incl_scan<RT_BLOCK>(cnt, sc->scan, total) - cnt;
+            int64_t o = outbase + rp.off + excl;
+            for (int x = w0; x < w1; ++x) {
+                uint32_t bits = bitmap[x];
+                while (bits) {
+                    const int b = __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    const int32_t row = (int32_t)(r0 + x * 32 + b);
+                    uint32_t h = hash_row(row) >> (32 - LOG2);
+                    while (vkeys[h] != row) h = (h + 1) & (TBL - 1);
+                    Cir[o] = row + rb;
+                    Cv[o] = SR::out(vals[h]);
+                    ++o;
+                    // every inserted row has its bit set, so this empties the table again;
+                    // lookups never stop at an empty slot, so clearing during reads is safe
+                    vals[h] = SR::zero();
+                    keys[h] = -1;
                 }
             }
-            outpos += total;
-            part_total += total;
             __syncthreads();
-        }
-        if constexpr (!NUM) {
-            if (tid == 0) part_count[(int64_t)q * ndense + d] = (int32_t)part_total;
         }
     }
 }
 
-template <class SR, bool NUM>
-static void run_dense(cudaStream_t st, const DMat& A, const DMat& B, int R, const int32_t* dlist, int64_t ndense,
-                      const int2* items, const unsigned long long* nitems, int64_t nitems_host, const int8_t* nparts,
-                      int32_t* cursors, int32_t* part_count, const int64_t* Ccp, int32_t* Cir,
-                      typename SR::T* Cv) {
-    if (ndense <= 0 || A.m == 0) return;
-    const int G = (int)ceil_div64(A.m, R);
-    size_t smem = (size_t)(R / 32) * 4 + (NUM ? (size_t)R * sizeof(typename SR::Acc) : 0) + 34 * 4;
-    auto kern = k_dense<SR, NUM>;
-    static size_t attr_done = 0;
-    if (attr_done < smem) {
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr_done = smem;
+template <class SR>
+static void run_range(cudaStream_t st, const Items& it, const DenseWork& dw, bool numeric, const int64_t* Coff,
+                      int32_t* Cir, typename SR::T* Cv) {
+    if (dw.ndense <= 0) return;
+    const int grid = (int)std::min<int64_t>(dw.ndense * MAX_PARTS, 152 * 8);
+    if (!numeric) {
+        const size_t smem = sizeof(RangeSmem) + 2 * (RT_MAXB + 1) * 4 + 16 + (size_t)(dw.RB / 32) * 4;
+        static size_t attr = 0;
+        if (attr < smem) {
+            cudaFuncSetAttribute(k_range_sym, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            attr = smem;
+        }
+        k_range_sym<<<grid, RT_BLOCK, smem, st>>>(it, dw);
+    } else {
+        constexpr int TBL = RANGE_TBL;
+        const size_t smem = sizeof(RangeSmem) + (size_t)TBL * (4 + sizeof(typename SR::Acc)) + (size_t)(dw.WW) * 4;
+        auto kern = k_range_num<SR, TBL>;
+        static size_t attr = 0;
+        if (attr < smem) {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            attr = smem;
+        }
+        kern<<<grid, RT_BLOCK, smem, st>>>(it, dw, Coff, Cir, Cv);
     }
-    int64_t want = nitems_host > 0 ? nitems_host : ndense * MAX_PARTS;
-    int grid = (int)std::min<int64_t>(want, 152 * 8);
-    kern<<<grid, DENSE_BLOCK, smem, st>>>(A, B, dlist, ndense, items, nitems, R, G, nparts, cursors, B.nnz,
-                                          part_count, Ccp, Cir, Cv);
     note_launch();
 }
 
 template <class SR>
-void launch_symbolic(cudaStream_t st, const DMat& A, const DMat& B, TierCfg cfg, const int32_t* list,
-                     const int64_t* bin_off, const int64_t* bin_cnt, const int2* dense_items,
-                     const unsigned long long* nitems, int64_t nitems_host, const int8_t* nparts, int32_t* cursors,
-                     int32_t* part_count, int64_t* nnz_col, int which) {
-    if (which & 1) run_hash_bins<SR, false>(st, A, B, list, bin_off, bin_cnt, nnz_col, nullptr, nullptr, nullptr);
-    if (which & 2) run_dense<SR, false>(st, A, B, cfg.dense_rows, list + bin_off[BIN_DENSE], bin_cnt[BIN_DENSE], dense_items, nitems,
-                         nitems_host, nparts, cursors, part_count, nullptr, nullptr, nullptr);
+void launch_symbolic(cudaStream_t st, const Items& it, TierCfg cfg, const int2* list, const int64_t* bin_off,
+                     const int64_t* bin_cnt, const DenseWork& dw, int64_t* nnz_item, int which) {
+    (void)cfg;
+    if (which & 1) run_hash_bins<SR, false>(st, it, list, bin_off, bin_cnt, nnz_item, nullptr, nullptr, nullptr);
+    if (which & 2) run_range<SR>(st, it, dw, false, nullptr, nullptr, nullptr);
 }
 
 template <class SR>
-void launch_numeric(cudaStream_t st, const DMat& A, const DMat& B, TierCfg cfg, const int32_t* list,
-                    const int64_t* bin_off, const int64_t* bin_cnt, const int2* dense_items,
-                    const unsigned long long* nitems, int64_t nitems_host, int32_t* cursors,
-                    const int32_t* part_count, const int8_t* nparts, const int64_t* Ccp, int32_t* Cir,
+void launch_numeric(cudaStream_t st, const Items& it, TierCfg cfg, const int2* list, const int64_t* bin_off,
+                    const int64_t* bin_cnt, const DenseWork& dw, const int64_t* Coff, int32_t* Cir,
                     typename SR::T* Cv, int which) {
-    if (which & 1) run_hash_bins<SR, true>(st, A, B, list, bin_off, bin_cnt, nullptr, Ccp, Cir, Cv);
-    if (which & 2) run_dense<SR, true>(st, A, B, cfg.dense_rows, list + bin_off[BIN_DENSE], bin_cnt[BIN_DENSE], dense_items, nitems,
-                        nitems_host, nparts, cursors, const_cast<int32_t*>(part_count), Ccp, Cir, Cv);
+    (void)cfg;
+    if (which & 1) run_hash_bins<SR, true>(st, it, list, bin_off, bin_cnt, nullptr, Coff, Cir, Cv);
+    if (which & 2) run_range<SR>(st, it, dw, true, Coff, Cir, Cv);
 }
 
 #define SG_INST(SR)                                                                                              \
-    template void launch_symbolic<SR>(cudaStream_t, const DMat&, const DMat&, TierCfg, const int32_t*,           \
-                                      const int64_t*, const int64_t*, const int2*, const unsigned long long*,    \
-                                      int64_t, const int8_t*, int32_t*, int32_t*, int64_t*, int);                                    \
-    template void launch_numeric<SR>(cudaStream_t, const DMat&, const DMat&, TierCfg, const int32_t*,            \
-                                     const int64_t*, const int64_t*, const int2*, const unsigned long long*,     \
-                                     int64_t, int32_t*, const int32_t*, const int8_t*, const int64_t*, int32_t*, \
-                                     typename SR::T*, int);
+    template void launch_symbolic<SR>(cudaStream_t, const Items&, TierCfg, const int2*, const int64_t*,          \
+                                      const int64_t*, const DenseWork&, int64_t*, int);                          \
+    template void launch_numeric<SR>(cudaStream_t, const Items&, TierCfg, const int2*, const int64_t*,           \
+                                     const int64_t*, const DenseWork&, const int64_t*, int32_t*, typename SR::T*, \
+                                     int);
 SG_INST(PT64)
 SG_INST(MP32)
 SG_INST(BOOL8)
 SG_INST(PTI64)
 #undef SG_INST
 
-// ------------------------------------------------------------------ part sums, fills, scan
-__global__ void k_sum_parts(const int32_t* __restrict__ dlist, int64_t nd, const int8_t* __restrict__ nparts,
-                            const int32_t* __restrict__ pc, int64_t* __restrict__ nnz_col, const int32_t* __restrict__ jc) {
+
+// ------------------------------------------------------------------ part sums, colptrs, stats
+__global__ void k_sum_parts(Items it, const int2* __restrict__ dlist, int64_t nd, const int8_t* __restrict__ nparts,
+                            const int32_t* __restrict__ pc, int64_t* __restrict__ nnz_item) {
     int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (d >= nd) return;
     int P = nparts[d];
     int64_t s = 0;
     for (int q = 0; q < P; ++q) s += pc[(int64_t)q * nd + d];
-    int32_t p = dlist[d];
-    nnz_col[jc ? jc[p] : p] = s;
+    int2 e = dlist[d];
+    nnz_item[__ldg(it.item_base + e.x) + e.y] = s;
 }
 
-void launch_sum_parts(cudaStream_t st, const int32_t* dense_list, int64_t ndense, const int8_t* nparts,
-                      const int32_t* part_count, int64_t* nnz_col, const int32_t* jc) {
+void launch_sum_parts(cudaStream_t st, const Items& it, const int2* dense_list, int64_t ndense, const int8_t* nparts,
+                      const int32_t* part_count, int64_t* nnz_item) {
     if (ndense == 0) return;
-    k_sum_parts<<<(int)ceil_div64(ndense, 256), 256, 0, st>>>(dense_list, ndense, nparts, part_count, nnz_col, jc);
+    k_sum_parts<<<(int)ceil_div64(ndense, 256), 256, 0, st>>>(it, dense_list, ndense, nparts, part_count, nnz_item);
+    note_launch();
+}
+
+// colptr_i[j] = offset of the first stored column of B_i with id >= j, relative to the product's start
+__global__ void k_colptrs(Items it, const int64_t* __restrict__ colbase, int64_t total, const int64_t* __restrict__ Coff,
+                          int64_t* __restrict__ out) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
+        int prod = it.nprod == 1 ? 0 : find_prod(colbase, it.nprod, x);
+        const Prod* pr = it.prods + prod;
+        const int64_t j = x - colbase[prod];
+        const int64_t ib = __ldg(it.item_base + prod);
+        const int64_t nzc = pr->B.nzc;
+        int64_t p;
+        if (pr->B.jc == nullptr) {
+            p = j;
+        } else {
+            int64_t lo = 0, hi = nzc;
+            while (lo < hi) {
+                int64_t mid = (lo + hi) >> 1;
+                if ((int64_t)__ldg(pr->B.jc + mid) < j) lo = mid + 1;
+                else hi = mid;
+            }
+            p = lo;
+        }
+        out[x] = Coff[ib + p] - Coff[ib];
+    }
+}
+
+void launch_colptrs(cudaStream_t st, const Items& it, const int64_t* colbase, int64_t total_cols, const int64_t* Coff,
+                    int64_t* out) {
+    if (total_cols <= 0) return;
+    int grid = (int)std::min<int64_t>(ceil_div64(total_cols, 256), 152 * 16);
+    k_colptrs<<<grid, 256, 0, st>>>(it, colbase, total_cols, Coff, out);
     note_launch();
 }
 
@@ -584,6 +854,37 @@ void launch_fill_i64(cudaStream_t st, int64_t* p, int64_t n, int64_t v) {
     note_launch();
 }
 
+__global__ void k_tier_stats(Items it, const uint8_t* __restrict__ bin, const int32_t* __restrict__ item_prod,
+                             const int64_t* __restrict__ flops, const int64_t* __restrict__ nnz_item,
+                             unsigned long long* out) {
+    __shared__ unsigned long long s[16];
+    if (threadIdx.x < 16) s[threadIdx.x] = 0;
+    __syncthreads();
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < it.nitems;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        int b = bin[u];
+        int t = b == 0 ? 0 : (b <= NWARP ? 1 : (b < BIN_DENSE ? 2 : 3));
+        int prod = item_prod[u];
+        const Prod* pr = it.prods + prod;
+        int64_t p = u - __ldg(it.item_base + prod);
+        atomicAdd(&s[t], 1ull);
+        atomicAdd(&s[4 + t], (unsigned long long)flops[u]);
+        atomicAdd(&s[8 + t], (unsigned long long)nnz_item[u]);
+        atomicAdd(&s[12 + t], (unsigned long long)(pr->B.cp[p + 1] - pr->B.cp[p]));
+    }
+    __syncthreads();
+    if (threadIdx.x < 16 && s[threadIdx.x]) atomicAdd(out + threadIdx.x, s[threadIdx.x]);
+}
+
+void launch_tier_stats(cudaStream_t st, const Items& it, const uint8_t* bin, const int32_t* item_prod,
+                       const int64_t* flops, const int64_t* nnz_item, unsigned long long* out) {
+    if (it.nitems <= 0) return;
+    int grid = (int)std::min<int64_t>(ceil_div64(it.nitems, 256), 152 * 4);
+    k_tier_stats<<<grid, 256, 0, st>>>(it, bin, item_prod, flops, nnz_item, out);
+    note_launch();
+}
+
+// ------------------------------------------------------------------ device-wide exclusive scan
 constexpr int SCAN_BLOCK = 1024;
 constexpr int SCAN_ITEMS = 4;
 constexpr int SCAN_TILE = SCAN_BLOCK * SCAN_ITEMS;
@@ -653,32 +954,6 @@ __global__ void __launch_bounds__(SCAN_BLOCK) k_scan_apply(const int64_t* __rest
     }
 }
 
-__global__ void k_tier_stats(const uint8_t* __restrict__ bin, const int64_t* __restrict__ flops,
-                             const int64_t* __restrict__ nnz_col, const int32_t* __restrict__ jc,
-                             const int64_t* __restrict__ bcp, int64_t nzc, unsigned long long* out) {
-    __shared__ unsigned long long s[16];
-    if (threadIdx.x < 16) s[threadIdx.x] = 0;
-    __syncthreads();
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nzc; p += (int64_t)gridDim.x * blockDim.x) {
-        int b = bin[p];
-        int t = b == 0 ? 0 : (b <= NWARP ? 1 : (b < BIN_DENSE ? 2 : 3));
-        atomicAdd(&s[t], 1ull);
-        atomicAdd(&s[4 + t], (unsigned long long)flops[p]);
-        atomicAdd(&s[8 + t], (unsigned long long)nnz_col[jc ? jc[p] : p]);
-        atomicAdd(&s[12 + t], (unsigned long long)(bcp[p + 1] - bcp[p]));
-    }
-    __syncthreads();
-    if (threadIdx.x < 16 && s[threadIdx.x]) atomicAdd(out + threadIdx.x, s[threadIdx.x]);
-}
-
-void launch_tier_stats(cudaStream_t st, const uint8_t* bin, const int64_t* flops, const int64_t* nnz_col,
-                       const int32_t* jc, const int64_t* bcp, int64_t nzc, unsigned long long* out) {
-    if (nzc <= 0) return;
-    int grid = (int)std::min<int64_t>(ceil_div64(nzc, 256), 152 * 4);
-    k_tier_stats<<<grid, 256, 0, st>>>(bin, flops, nnz_col, jc, bcp, nzc, out);
-    note_launch();
-}
-
 size_t scan_tmp_bytes(int64_t n) { return (size_t)(ceil_div64(std::max<int64_t>(n, 1), SCAN_TILE) + 1) * 8; }
 
 void launch_exclusive_scan(cudaStream_t st, const int64_t* in, int64_t n, int64_t* out, void* tmp) {
@@ -689,11 +964,9 @@ void launch_exclusive_scan(cudaStream_t st, const int64_t* in, int64_t n, int64_
     int64_t nb = ceil_div64(n, SCAN_TILE);
     long long* sums = reinterpret_cast<long long*>(tmp);
     k_scan_reduce<<<(int)nb, SCAN_BLOCK, 0, st>>>(in, n, sums);
-    note_launch();
     k_scan_sums<<<1, SCAN_BLOCK, 0, st>>>(sums, nb);
-    note_launch();
     k_scan_apply<<<(int)nb, SCAN_BLOCK, 0, st>>>(in, n, sums, out);
-    note_launch();
+    note_launch(3);
 }
 
 }  // namespace sg

@@ -1,4 +1,10 @@
-// Kernel launch interface of the flat SpGEMM path (host side of kernels.cu).
+// Kernel launch interface of the batched column-wise SpGEMM (host side of kernels.cu).
+//
+// Work is expressed in an "item space": a batch holds nprod products
+// C_i = A_i * B_i (descriptors in device memory); item u = item_base_i + p is the
+// p-th stored column of B_i and produces one output column (or one DCSC column).
+// The flat product is a batch of one; the SUMMA stage products, the stage merge
+// and spgemm_batch are larger batches.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -7,7 +13,7 @@
 
 namespace sg {
 
-// Column tiers.  A column's capacity bound is cap_j = min(flops_j, m) >= nnz(C(:,j)).
+// Column tiers.  An item's capacity bound is cap = min(flops, m) >= nnz of its output.
 //   bin 0                  : cap == 0 (empty output column)
 //   bins 1 .. NWARP        : warp-wide hash tables of 64 .. 1024 slots (>= 2 cap)
 //   bins NWARP+1 .. +NBLK  : CTA-wide hash tables of 2048 .. 8192 slots (>= 2 cap)
@@ -23,54 +29,91 @@ constexpr int MAX_PARTS = 16;
 struct TierCfg {
     int warp_max;     // cap <= warp_max -> warp tables (<= 512)
     int block_max;    // cap <= block_max -> CTA tables (<= 4096)
-    int dense_rows;   // R, rows per dense chunk
-    int part_flops;   // target flops per dense part
+    int dense_rows;   // RB, most rows of one symbolic slab (bitmap bits in shared memory)
+    int part_flops;   // target flops per symbolic slab of a long column
 };
 
-struct FeatOut {          // optional per-column predictor inputs
-    float* x = nullptr;   // n x 8, row-major
+// Range tier: hash-table slots per numeric range, so a range holds < RANGE_TBL / 2 entries.
+constexpr int RANGE_TBL = 8192;
+constexpr int RANGE_H = RANGE_TBL / 2 - 32;   // cut a range once it holds this many entries
+constexpr int RANGE_W = 32768;                // and at most this many rows
+
+struct RangePart {   // one numeric range of a slab
+    int32_t d, q;    // dense-list position, slab
+    int32_t r0, r1;  // rows [r0, r1)
+    int32_t off;     // entries of the slab before this range
+    int32_t nnz;
 };
 
-// which: 1 = hash-table tiers, 2 = dense tier, 3 = both
-// per stored column p of B: flops, tier bin; bin counts accumulated into bin_count[NBIN].
-void launch_analyze(cudaStream_t st, const DMat& A, const DMat& B, TierCfg cfg, int64_t* flops, uint8_t* bin,
-                    unsigned long long* bin_count, unsigned long long* flops_total, const uint64_t* sketch_A,
-                    float* feat);
-void launch_bin_scatter(cudaStream_t st, int64_t n, const uint8_t* bin, const int64_t* bin_off,
-                        unsigned long long* bin_cursor, int32_t* list);
-// dense items: (list position d, part q) for each dense column
-void launch_dense_items(cudaStream_t st, const int32_t* dense_list, int64_t ndense, const int64_t* flops,
-                        int G, int part_flops, int2* items, unsigned long long* nitems, int8_t* nparts);
+struct DenseWork {   // state of the range tier shared by its kernels
+    const int2* dlist = nullptr;          // dense items (product, stored column)
+    int64_t ndense = 0;
+    const int2* items = nullptr;          // slabs (d, q)
+    const unsigned long long* nitems = nullptr;   // device count of slabs
+    const int8_t* nparts = nullptr;       // slabs per dense item
+    int32_t* cursors = nullptr;           // per slab and k: position inside A(:,k)
+    int32_t* part_count = nullptr;        // [q][d] entries per slab
+    RangePart* parts = nullptr;
+    unsigned long long* parts_ctr = nullptr;
+    int64_t parts_cap = 0;
+    int64_t* pbase = nullptr;             // per slab: first range
+    int32_t* pcnt = nullptr;              // per slab: number of ranges
+    int* err = nullptr;                   // nonzero: a capacity was exceeded
+    int RB = 1 << 20;                     // most rows per slab
+    int H = RANGE_H;
+    int WW = RANGE_W / 32;                // words per range window
+};
+
+struct Items {
+    const Prod* prods = nullptr;        // device, nprod descriptors
+    const int64_t* item_base = nullptr; // device, nprod + 1 (prefix of stored columns of B_i)
+    int64_t nprod = 0;
+    int64_t nitems = 0;
+    int64_t total_bnz = 0;              // sum of nnz(B_i): cursor stride per dense part
+};
+
+// flops and bin per item, product id per item, bin counts and total flops.
+// With feat != nullptr also the 8 predictor inputs per item; `sketch` holds the
+// per-column row sketches of the A operands concatenated, product i's starting
+// at sketch_base[i].
+void launch_analyze(cudaStream_t st, const Items& it, TierCfg cfg, int64_t* flops, uint8_t* bin, int32_t* item_prod,
+                    unsigned long long* bin_count, unsigned long long* flops_total, const uint64_t* sketch,
+                    const int64_t* sketch_base, float* feat);
 void launch_row_sketch(cudaStream_t st, const DMat& A, uint64_t* sketch);
+void launch_bin_scatter(cudaStream_t st, const Items& it, const uint8_t* bin, const int32_t* item_prod,
+                        const int64_t* bin_off, unsigned long long* bin_cursor, int2* list);
+// range-tier slabs (position d in the dense list, slab q); P_d slabs of at most RB rows each
+void launch_dense_items(cudaStream_t st, const Items& it, const int2* dense_list, int64_t ndense,
+                        const int64_t* flops, int part_flops, int RB, int2* items, unsigned long long* nitems,
+                        int8_t* nparts);
 
+// which: 1 = hash-table tiers, 2 = range tier, 3 = both
 template <class SR>
-void launch_symbolic(cudaStream_t st, const DMat& A, const DMat& B, TierCfg cfg, const int32_t* list,
-                     const int64_t* bin_off, const int64_t* bin_cnt, const int2* dense_items,
-                     const unsigned long long* nitems, int64_t nitems_host, const int8_t* nparts, int32_t* cursors,
-                     int32_t* part_count, int64_t* nnz_col, int which = 3);
+void launch_symbolic(cudaStream_t st, const Items& it, TierCfg cfg, const int2* list, const int64_t* bin_off,
+                     const int64_t* bin_cnt, const DenseWork& dw, int64_t* nnz_item, int which = 3);
 template <class SR>
-void launch_numeric(cudaStream_t st, const DMat& A, const DMat& B, TierCfg cfg, const int32_t* list,
-                    const int64_t* bin_off, const int64_t* bin_cnt, const int2* dense_items,
-                    const unsigned long long* nitems, int64_t nitems_host, int32_t* cursors,
-                    const int32_t* part_count, const int8_t* nparts, const int64_t* Ccp, int32_t* Cir,
+void launch_numeric(cudaStream_t st, const Items& it, TierCfg cfg, const int2* list, const int64_t* bin_off,
+                    const int64_t* bin_cnt, const DenseWork& dw, const int64_t* Coff, int32_t* Cir,
                     typename SR::T* Cv, int which = 3);
 
-// nnz of dense columns = sum of their part counts
-void launch_sum_parts(cudaStream_t st, const int32_t* dense_list, int64_t ndense, const int8_t* nparts,
-                      const int32_t* part_count, int64_t* nnz_col, const int32_t* jc);
+// nnz of dense items = sum of their part counts
+void launch_sum_parts(cudaStream_t st, const Items& it, const int2* dense_list, int64_t ndense, const int8_t* nparts,
+                      const int32_t* part_count, int64_t* nnz_item);
+// per-product column pointers from item offsets: out[colbase_i + j] for j in [0, n_i]
+void launch_colptrs(cudaStream_t st, const Items& it, const int64_t* colbase, int64_t total_cols, const int64_t* Coff,
+                    int64_t* out);
 // out[0] = 0, out[i+1] = sum_{t <= i} in[t]; tmp needs scan_tmp_bytes(n)
 size_t scan_tmp_bytes(int64_t n);
 void launch_exclusive_scan(cudaStream_t st, const int64_t* in, int64_t n, int64_t* out, void* tmp);
 void launch_fill_i64(cudaStream_t st, int64_t* p, int64_t n, int64_t v);
+// per-tier totals {cols, flops, nnz(C), nnz(B)} x 4 tiers into out[16] (device, zeroed by caller)
+void launch_tier_stats(cudaStream_t st, const Items& it, const uint8_t* bin, const int32_t* item_prod,
+                       const int64_t* flops, const int64_t* nnz_item, unsigned long long* out);
 
 int dense_rows_for(int semiring, int requested);
 
 // process-wide count of kernel launches made by this library
 void note_launch(int n = 1);
 int64_t launches();
-
-// per-tier totals {cols, flops, nnz(C), nnz(B)} x 4 tiers into out[16] (device, zeroed by caller)
-void launch_tier_stats(cudaStream_t st, const uint8_t* bin, const int64_t* flops, const int64_t* nnz_col,
-                       const int32_t* jc, const int64_t* bcp, int64_t nzc, unsigned long long* out);
 
 }  // namespace sg

@@ -1,14 +1,481 @@
-// 2D Sparse SUMMA on a virtual g x g block grid (Sections 3.2, 3.5, 5.3).
+// 2D Sparse SUMMA on a virtual g x g block grid of one GPU (Sections 3.2 and
+// 3.5; the paper's own single-processor simulation of the grid is Section 5.3).
+//
+//   1. A and B are split into g x g blocks of ceil(dim/g) rows and columns
+//      (Section 3.5: SUMMA generalises to dimensions that the grid does not
+//      divide; the last block may be short or empty).  Every block is stored as
+//      DCSC with the AUX column index (Section 2.3), built on the device.
+//   2. Stage s multiplies A(I,s) * B(s,J) for every I, J: hypersparse block
+//      products that walk the nonzero columns of B(s,J) and find A(I,s)(:,l)
+//      through AUX.  All stages run as one batched execution of the column
+//      kernels (or `summa_merge_every` stages at a time).
+//   3. The stage partials are merged into C (Section 6.1 keeps the partial
+//      triples and merges them later; Section 4.2 prices the additions).  The
+//      merge is itself computed as a product: with P the matrix whose columns are
+//      the partial columns and S the selector with S(u, j) = 1 when partial
+//      column u belongs to output column j, C = P * S, where (x) by the
+//      semiring's one is exact and (+) does the merge.
+#include <algorithm>
+#include <cstring>
+
 #include "internal.cuh"
 
+using namespace sg;
+
+namespace {
+
+__global__ void k_block_keys(const int64_t* __restrict__ cp, const int32_t* __restrict__ ir, int64_t n, int64_t mb,
+                             int64_t nb, int g, uint32_t* __restrict__ keys, uint32_t* __restrict__ pay) {
+    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+    const int sub = threadIdx.x & 7;
+    if (j >= n) return;
+    const uint32_t J = (uint32_t)(j / nb);
+    for (int64_t t = cp[j] + sub; t < cp[j + 1]; t += 8) {
+        const uint32_t I = (uint32_t)(ir[t] / mb);
+        keys[t] = J * (uint32_t)g + I;   // block (I, J), column-block major
+        pay[t] = (uint32_t)t;
+    }
+}
+
+__global__ void k_block_colid(const int64_t* __restrict__ cp, int64_t n, int32_t* __restrict__ col) {
+    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+    const int sub = threadIdx.x & 7;
+    if (j >= n) return;
+    for (int64_t t = cp[j] + sub; t < cp[j + 1]; t += 8) col[t] = (int32_t)j;
+}
+
+// Gather into block order, local indices; DCSC column-start flags; per-block counts.
+template <int W>
+__global__ void k_block_gather(const uint32_t* __restrict__ skey, const uint32_t* __restrict__ perm, int64_t nnz,
+                               const int32_t* __restrict__ ir, const int32_t* __restrict__ colid,
+                               const void* __restrict__ num, int64_t mb, int64_t nb, int g, int32_t* __restrict__ lir,
+                               int32_t* __restrict__ lcol, void* __restrict__ lnum, int64_t* __restrict__ flag,
+                               unsigned long long* __restrict__ bnnz, unsigned long long* __restrict__ bnzc) {
+    using Wt = typename std::conditional<W == 1, uint8_t, typename std::conditional<W == 4, uint32_t, uint64_t>::type>::type;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nnz; t += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t key = skey[t];
+        const uint32_t src = perm[t];
+        const int64_t I = key % (uint32_t)g, J = key / (uint32_t)g;
+        const int32_t c = colid[src];
+        lir[t] = (int32_t)(ir[src] - I * mb);
+        const int32_t lc = (int32_t)(c - J * nb);
+        lcol[t] = lc;
+        if (num) reinterpret_cast<Wt*>(lnum)[t] = reinterpret_cast<const Wt*>(num)[src];
+        int f = t == 0 || skey[t - 1] != key || colid[perm[t - 1]] != c;
+        flag[t] = f;
+        atomicAdd(bnnz + key, 1ull);
+        if (f) atomicAdd(bnzc + key, 1ull);
+    }
+}
+
+__global__ void k_block_dcsc(const uint32_t* __restrict__ skey, const int32_t* __restrict__ lcol,
+                             const int64_t* __restrict__ flag, const int64_t* __restrict__ pos, int64_t nnz,
+                             int32_t* __restrict__ jc, int64_t* __restrict__ dcp) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nnz; t += (int64_t)gridDim.x * blockDim.x) {
+        if (flag[t]) {
+            const int64_t q = pos[t];
+            jc[q] = lcol[t];
+            dcp[q + skey[t]] = t;   // block b's CP array is shifted by b for its end slot
+        }
+    }
+}
+
+// One CTA per block: end slot of CP and the AUX index.
+__global__ void k_block_aux(int nblk, const int64_t* __restrict__ boff, const int64_t* __restrict__ jcbase,
+                            const int64_t* __restrict__ auxbase, const int64_t* __restrict__ chunk,
+                            const int64_t* __restrict__ naux, const int32_t* __restrict__ jc, int64_t* __restrict__ dcp,
+                            int32_t* __restrict__ aux) {
+    const int b = blockIdx.x;
+    if (b >= nblk) return;
+    const int64_t nzc = jcbase[b + 1] - jcbase[b];
+    if (threadIdx.x == 0) dcp[jcbase[b] + b + nzc] = boff[b + 1];
+    const int32_t* bj = jc + jcbase[b];
+    int32_t* ba = aux + auxbase[b];
+    const int64_t na = naux[b], ch = chunk[b];
+    for (int64_t t = threadIdx.x; t <= na; t += blockDim.x) {
+        if (t == na) {
+            ba[t] = (int32_t)nzc;
+            continue;
+        }
+        int64_t v = t * ch, lo = 0, hi = nzc;
+        while (lo < hi) {
+            int64_t mid = (lo + hi) >> 1;
+            if ((int64_t)bj[mid] < v) lo = mid + 1;
+            else hi = mid;
+        }
+        ba[t] = (int32_t)lo;
+    }
+}
+
+// Output column of every item: col_base + JC[p] of the product's B.
+__global__ void k_item_outcol(Items it, const int32_t* __restrict__ item_prod, uint32_t* __restrict__ oc,
+                              uint32_t* __restrict__ pay, int64_t ofs) {
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < it.nitems; u += (int64_t)gridDim.x * blockDim.x) {
+        const int prod = item_prod[u];
+        const Prod* pr = it.prods + prod;
+        const int64_t p = u - it.item_base[prod];
+        const int64_t j = pr->B.jc ? pr->B.jc[p] : p;
+        oc[ofs + u] = (uint32_t)(pr->col_base + j);
+        pay[ofs + u] = (uint32_t)(ofs + u);
+    }
+}
+
+__global__ void k_iota_cols(uint32_t* oc, uint32_t* pay, int64_t n) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        oc[j] = (uint32_t)j;
+        pay[j] = (uint32_t)j;
+    }
+}
+
+__global__ void k_hist_u32(const uint32_t* __restrict__ k, int64_t n, int64_t* __restrict__ cnt) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(reinterpret_cast<unsigned long long*>(cnt + k[i]), 1ull);
+}
+
+__global__ void k_u32_to_i32(const uint32_t* __restrict__ in, int64_t n, int32_t* __restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (int32_t)in[i];
+}
+
+__global__ void k_add_offset(const int64_t* __restrict__ in, int64_t n, int64_t add, int64_t* __restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = in[i] + add;
+}
+
+__global__ void k_prod_flops(Items it, const int32_t* __restrict__ item_prod, const int64_t* __restrict__ flops,
+                             unsigned long long* __restrict__ pf) {
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < it.nitems; u += (int64_t)gridDim.x * blockDim.x)
+        if (flops[u]) atomicAdd(pf + item_prod[u], (unsigned long long)flops[u]);
+}
+
+int gridn(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div64(n, 256), 152 * 32)); }
+
+// A matrix split into g x g DCSC+AUX blocks (all blocks share the arrays).
+struct Blocked {
+    int g = 0;
+    int64_t m = 0, n = 0, mb = 0, nb = 0;
+    std::vector<DMat> blk;   // blk[J * g + I]
+    std::vector<std::shared_ptr<DevBuf>> bufs;
+    const DMat& at(int I, int J) const { return blk[(size_t)J * g + I]; }
+};
+
+spgemm_status_t partition(spgemm_ctx* ctx, const DMat& M, size_t w, int g, Blocked* out) {
+    cudaStream_t st = ctx->stream;
+    const int64_t m = M.m, n = M.n, nnz = M.nnz;
+    const int64_t mb = std::max<int64_t>(1, ceil_div64(m, g)), nb = std::max<int64_t>(1, ceil_div64(n, g));
+    const int nblk = g * g;
+    out->g = g;
+    out->m = m;
+    out->n = n;
+    out->mb = mb;
+    out->nb = nb;
+    if (nnz > (int64_t)UINT32_MAX) return set_err(ctx, SPGEMM_ERR_INDEX_OVERFLOW, "partition: nnz beyond 2^32");
+    const int64_t nz1 = std::max<int64_t>(nnz, 1);
+    // owned arrays of the blocks
+    auto irb = ctx_buf(ctx, 4 * nz1);
+    auto vb = ctx_buf(ctx, w * nz1);
+    auto jcb = ctx_buf(ctx, 4 * nz1);
+    auto cpb = ctx_buf(ctx, 8 * (nz1 + nblk + 1));
+    if (!irb || !vb || !jcb || !cpb) return set_err(ctx, SPGEMM_ERR_OOM, "partition arrays");
+    // temporaries
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += (bytes + 255) / 256 * 256;
+        return o;
+    };
+    size_t o_k0 = take(4 * nz1), o_v0 = take(4 * nz1), o_k1 = take(4 * nz1), o_v1 = take(4 * nz1);
+    size_t o_col = take(4 * nz1), o_lcol = take(4 * nz1), o_flag = take(8 * nz1), o_pos = take(8 * (nz1 + 1));
+    size_t o_cnt = take(8 * 2 * nblk), o_boff = take(8 * (nblk + 1)), o_jcb = take(8 * (nblk + 1));
+    size_t o_rs = take(radix_tmp_bytes(nz1)), o_sc = take(scan_tmp_bytes(std::max<int64_t>(nz1, nblk)));
+    auto tmp = ctx_buf(ctx, off);
+    if (!tmp) return set_err(ctx, SPGEMM_ERR_OOM, "partition temporaries");
+    char* t = (char*)tmp->p;
+    uint32_t *k0 = (uint32_t*)(t + o_k0), *v0 = (uint32_t*)(t + o_v0), *k1 = (uint32_t*)(t + o_k1),
+             *v1 = (uint32_t*)(t + o_v1);
+    int32_t* colid = (int32_t*)(t + o_col);
+    int32_t* lcol = (int32_t*)(t + o_lcol);
+    int64_t* flag = (int64_t*)(t + o_flag);
+    int64_t* pos = (int64_t*)(t + o_pos);
+    unsigned long long* bcnt = (unsigned long long*)(t + o_cnt);   // bnnz[nblk], bnzc[nblk]
+    int64_t* boff = (int64_t*)(t + o_boff);
+    int64_t* jcbase = (int64_t*)(t + o_jcb);
+    SG_CUDA(ctx, cudaMemsetAsync(bcnt, 0, 16 * nblk, st));
+    std::vector<int64_t> hnnz(nblk, 0), hnzc(nblk, 0);
+    if (nnz > 0) {
+        k_block_keys<<<(int)ceil_div64(n * 8, 256) + 1, 256, 0, st>>>(M.cp, M.ir, n, mb, nb, g, k0, v0);
+        k_block_colid<<<(int)ceil_div64(n * 8, 256) + 1, 256, 0, st>>>(M.cp, n, colid);
+        note_launch(2);
+        int bits = 0;
+        while (bits < 32 && (int64_t(1) << bits) < nblk) ++bits;
+        bool second = false;
+        radix_sort_pairs(st, k0, v0, k1, v1, nnz, bits, t + o_rs, &second);
+        uint32_t* sk = second ? k1 : k0;
+        uint32_t* sp = second ? v1 : v0;
+        switch (w) {
+        case 1: k_block_gather<1><<<gridn(nnz), 256, 0, st>>>(sk, sp, nnz, M.ir, colid, M.num, mb, nb, g, (int32_t*)irb->p, lcol, vb->p, flag, bcnt, bcnt + nblk); break;
+        case 4: k_block_gather<4><<<gridn(nnz), 256, 0, st>>>(sk, sp, nnz, M.ir, colid, M.num, mb, nb, g, (int32_t*)irb->p, lcol, vb->p, flag, bcnt, bcnt + nblk); break;
+        default: k_block_gather<8><<<gridn(nnz), 256, 0, st>>>(sk, sp, nnz, M.ir, colid, M.num, mb, nb, g, (int32_t*)irb->p, lcol, vb->p, flag, bcnt, bcnt + nblk); break;
+        }
+        note_launch();
+        launch_exclusive_scan(st, flag, nnz, pos, t + o_sc);
+        k_block_dcsc<<<gridn(nnz), 256, 0, st>>>(sk, lcol, flag, pos, nnz, (int32_t*)jcb->p, (int64_t*)cpb->p);
+        note_launch();
+        std::vector<unsigned long long> hc(2 * nblk);
+        SG_CUDA(ctx, cudaMemcpyAsync(hc.data(), bcnt, 16 * nblk, cudaMemcpyDeviceToHost, st));
+        SG_TRY(sync_ctx(ctx));
+        for (int b = 0; b < nblk; ++b) {
+            hnnz[b] = (int64_t)hc[b];
+            hnzc[b] = (int64_t)hc[nblk + b];
+        }
+    }
+    // per-block layout on the host
+    std::vector<int64_t> hboff(nblk + 1, 0), hjcb(nblk + 1, 0), hauxb(nblk + 1, 0), hchunk(nblk, 1), hnaux(nblk, 0);
+    for (int b = 0; b < nblk; ++b) {
+        const int I = b % g, J = b / g;
+        (void)I;
+        const int64_t ncols = std::max<int64_t>(0, std::min<int64_t>(nb, n - (int64_t)J * nb));
+        hboff[b + 1] = hboff[b] + hnnz[b];
+        hjcb[b + 1] = hjcb[b] + hnzc[b];
+        hchunk[b] = hnzc[b] > 0 ? ceil_div64(ncols, hnzc[b]) : std::max<int64_t>(ncols, 1);
+        hnaux[b] = ncols > 0 ? ceil_div64(ncols, hchunk[b]) : 0;
+        hauxb[b + 1] = hauxb[b] + hnaux[b] + 1;
+    }
+    auto auxb = ctx_buf(ctx, 4 * std::max<int64_t>(hauxb[nblk], 1));
+    auto meta = ctx_buf(ctx, 8 * (4 * (nblk + 1) + nblk));
+    if (!auxb || !meta) return set_err(ctx, SPGEMM_ERR_OOM, "aux arrays");
+    int64_t* dm = (int64_t*)meta->p;
+    std::vector<int64_t> hm;
+    hm.insert(hm.end(), hboff.begin(), hboff.end());
+    hm.insert(hm.end(), hjcb.begin(), hjcb.end());
+    hm.insert(hm.end(), hauxb.begin(), hauxb.end());
+    hm.insert(hm.end(), hchunk.begin(), hchunk.end());
+    hm.insert(hm.end(), hnaux.begin(), hnaux.end());
+    hm.push_back(0);
+    SG_CUDA(ctx, cudaMemcpyAsync(dm, hm.data(), 8 * hm.size(), cudaMemcpyHostToDevice, st));
+    k_block_aux<<<nblk, 128, 0, st>>>(nblk, dm, dm + (nblk + 1), dm + 2 * (nblk + 1), dm + 3 * (nblk + 1),
+                                      dm + 3 * (nblk + 1) + nblk, (const int32_t*)jcb->p, (int64_t*)cpb->p,
+                                      (int32_t*)auxb->p);
+    note_launch();
+    SG_TRY(sync_ctx(ctx));   // host vectors above are copied before they go out of scope
+    out->blk.assign(nblk, DMat());
+    for (int b = 0; b < nblk; ++b) {
+        const int I = b % g, J = b / g;
+        DMat d;
+        d.m = std::max<int64_t>(0, std::min<int64_t>(mb, m - (int64_t)I * mb));
+        d.n = std::max<int64_t>(0, std::min<int64_t>(nb, n - (int64_t)J * nb));
+        d.nzc = hnzc[b];
+        d.nnz = hnnz[b];
+        d.cp = (const int64_t*)cpb->p + hjcb[b] + b;
+        d.jc = (const int32_t*)jcb->p + hjcb[b];
+        d.aux = (const int32_t*)auxb->p + hauxb[b];
+        d.chunk = hchunk[b];
+        d.naux = hnaux[b];
+        d.ir = (const int32_t*)irb->p;
+        d.num = M.num ? vb->p : nullptr;
+        out->blk[b] = d;
+    }
+    out->bufs = {irb, vb, jcb, cpb, auxb};
+    return SPGEMM_OK;
+}
+
+// C (m x n) = merge of `ncols` sorted partial columns: column u of P (rows
+// global, colptr Pcp) is added into output column oc[u].
+spgemm_status_t merge_columns(spgemm_ctx* ctx, spgemm_semiring_t sr, const spgemm_opts_t& opts, int64_t m, int64_t n,
+                              int64_t ncols, const int64_t* Pcp, const int32_t* Pir, const void* Pv, int64_t pnnz,
+                              uint32_t* oc, uint32_t* pay, spgemm_mat_t* C) {
+    cudaStream_t st = ctx->stream;
+    PhaseTimer tm(ctx, SPGEMM_PHASE_MERGE, sr);
+    const int64_t nc1 = std::max<int64_t>(ncols, 1);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += (bytes + 255) / 256 * 256;
+        return o;
+    };
+    size_t o_k1 = take(4 * nc1), o_v1 = take(4 * nc1), o_cnt = take(8 * (n + 1)), o_rs = take(radix_tmp_bytes(nc1)),
+           o_sc = take(scan_tmp_bytes(std::max<int64_t>(n, 1)));
+    auto tmp = ctx_buf(ctx, off);
+    auto scp = ctx_buf(ctx, 8 * (n + 1));
+    auto sir = ctx_buf(ctx, 4 * nc1);
+    if (!tmp || !scp || !sir) return set_err(ctx, SPGEMM_ERR_OOM, "merge selector");
+    char* t = (char*)tmp->p;
+    int bits = 0;
+    while (bits < 32 && (int64_t(1) << bits) < std::max<int64_t>(n, 1)) ++bits;
+    bool second = false;
+    radix_sort_pairs(st, oc, pay, (uint32_t*)(t + o_k1), (uint32_t*)(t + o_v1), ncols, bits, t + o_rs, &second);
+    const uint32_t* sk = second ? (uint32_t*)(t + o_k1) : oc;
+    const uint32_t* sv = second ? (uint32_t*)(t + o_v1) : pay;
+    int64_t* cnt = (int64_t*)(t + o_cnt);
+    SG_CUDA(ctx, cudaMemsetAsync(cnt, 0, 8 * (n + 1), st));
+    if (ncols > 0) {
+        k_hist_u32<<<gridn(ncols), 256, 0, st>>>(sk, ncols, cnt);
+        k_u32_to_i32<<<gridn(ncols), 256, 0, st>>>(sv, ncols, (int32_t*)sir->p);
+        note_launch(2);
+    }
+    launch_exclusive_scan(st, cnt, n, (int64_t*)scp->p, t + o_sc);
+    // C = P * S
+    Prod pr;
+    pr.A = csc_view(m, ncols, pnnz, Pcp, Pir, Pv);
+    pr.B = csc_view(ncols, n, ncols, (const int64_t*)scp->p, (const int32_t*)sir->p, nullptr);
+    Engine E;
+    SG_TRY(engine_setup(&E, ctx, sr, opts, {pr}, false));
+    SG_TRY(engine_symbolic(&E));
+    std::shared_ptr<DevBuf> rbuf, vbuf;
+    SG_TRY(engine_alloc_out(&E, &rbuf, &vbuf));
+    SG_TRY(engine_numeric(&E, (int32_t*)rbuf->p, vbuf->p));
+    *C = new_owned_csc(ctx, sr, m, n, E.nnz_total, {E.Coff_buf, rbuf, vbuf}, E.Coff, (const int32_t*)rbuf->p,
+                       vbuf->p);
+    return SPGEMM_OK;
+}
+
+}  // namespace
+
 extern "C" {
-spgemm_status_t spgemm_summa_blocked(spgemm_ctx_t ctx, spgemm_mat_t A, spgemm_mat_t B, int g,
-                                     spgemm_semiring_t sr, const spgemm_opts_t* opts, spgemm_mat_t* C) {
-    (void)A; (void)B; (void)g; (void)sr; (void)opts; (void)C;
-    return set_err(ctx, SPGEMM_ERR_UNSUPPORTED, "summa not built yet");
+
+spgemm_status_t spgemm_summa_blocked(spgemm_ctx_t ctx, spgemm_mat_t A, spgemm_mat_t B, int g, spgemm_semiring_t sr,
+                                     const spgemm_opts_t* opts, spgemm_mat_t* C) {
+    if (!ctx || !A || !B || !C) return SPGEMM_ERR_INVALID_ARG;
+    if (g < 1 || g > 1024) return set_err(ctx, SPGEMM_ERR_INVALID_ARG, "grid size g = %d outside [1, 1024]", g);
+    if ((int)sr < 0 || (int)sr > 3) return set_err(ctx, SPGEMM_ERR_INVALID_ARG, "bad semiring");
+    if (A->sr != sr || B->sr != sr) return set_err(ctx, SPGEMM_ERR_INVALID_ARG, "operand semiring differs");
+    if (A->n != B->m) return set_err(ctx, SPGEMM_ERR_DIM_MISMATCH, "inner dimensions differ");
+    if (A->fmt == SPGEMM_FMT_DCSC || B->fmt == SPGEMM_FMT_DCSC)
+        return set_err(ctx, SPGEMM_ERR_UNSUPPORTED, "summa takes CSC or CSR operands");
+    spgemm_opts_t o;
+    spgemm_opts_default(&o);
+    if (opts) o = *opts;
+    spgemm_mat_t Ac = nullptr, Bc = nullptr;
+    DMat dA, dB;
+    SG_TRY(to_csc_operand(ctx, A, &Ac, &dA));
+    spgemm_status_t s = to_csc_operand(ctx, B, &Bc, &dB);
+    std::unique_ptr<spgemm_mat> holdA(Ac), holdB(Bc);
+    if (s != SPGEMM_OK) return s;
+    const size_t w = sr_size(sr);
+    const int64_t m = dA.m, n = dB.n;
+    Blocked bA, bB;
+    {
+        PhaseTimer tp(ctx, SPGEMM_PHASE_ANALYZE, sr);
+        SG_TRY(partition(ctx, dA, w, g, &bA));
+        SG_TRY(partition(ctx, dB, w, g, &bB));
+    }
+    // stage products A(I,s) * B(s,J), stage-major
+    std::vector<Prod> all;
+    for (int st = 0; st < g; ++st)
+        for (int J = 0; J < g; ++J)
+            for (int I = 0; I < g; ++I) {
+                const DMat& a = bA.at(I, st);
+                const DMat& b = bB.at(st, J);
+                if (a.nnz == 0 || b.nnz == 0 || a.m == 0 || b.n == 0) continue;
+                Prod pr;
+                pr.A = a;
+                pr.B = b;
+                pr.row_base = (int32_t)(I * bA.mb);
+                pr.col_base = (int64_t)J * bB.nb;
+                pr.tag = st;
+                all.push_back(pr);
+            }
+    ctx->summa_stage_flops.assign(g, 0);
+    ctx->summa_nonempty = (int64_t)all.size();
+    const int every = o.summa_merge_every > 0 ? std::min(o.summa_merge_every, g) : g;
+    spgemm_mat_t acc = nullptr;   // C merged so far
+    std::unique_ptr<spgemm_mat> hold_acc;
+    for (int s0 = 0; s0 < g; s0 += every) {
+        std::vector<Prod> grp;
+        for (auto& pr : all)
+            if (pr.tag >= s0 && pr.tag < s0 + every) grp.push_back(pr);
+        Engine E;
+        std::shared_ptr<DevBuf> rbuf, vbuf;
+        int64_t U = 0, pn = 0;
+        if (!grp.empty()) {
+            SG_TRY(engine_setup(&E, ctx, sr, o, grp, false));
+            SG_TRY(engine_symbolic(&E));
+            SG_TRY(engine_alloc_out(&E, &rbuf, &vbuf));
+            SG_TRY(engine_numeric(&E, (int32_t*)rbuf->p, vbuf->p));
+            U = E.it.nitems;
+            pn = E.nnz_total;
+            // stage flops for the statistics
+            auto pf = ctx_buf(ctx, 8 * grp.size());
+            if (!pf) return set_err(ctx, SPGEMM_ERR_OOM, "stage flops");
+            SG_CUDA(ctx, cudaMemsetAsync(pf->p, 0, 8 * grp.size(), ctx->stream));
+            k_prod_flops<<<gridn(U), 256, 0, ctx->stream>>>(E.it, E.item_prod, E.flops, (unsigned long long*)pf->p);
+            note_launch();
+            std::vector<unsigned long long> hpf(grp.size());
+            SG_CUDA(ctx, cudaMemcpyAsync(hpf.data(), pf->p, 8 * grp.size(), cudaMemcpyDeviceToHost, ctx->stream));
+            SG_TRY(sync_ctx(ctx));
+            for (size_t i = 0; i < grp.size(); ++i) ctx->summa_stage_flops[grp[i].tag] += (int64_t)hpf[i];
+        }
+        // columns to merge: the accumulated C (if any) followed by this group's partial columns
+        const int64_t nacc = acc ? n : 0;
+        const int64_t accnz = acc ? acc->nnz : 0;
+        const int64_t ncols = nacc + U;
+        const int64_t pnz = accnz + pn;
+        cudaStream_t stq = ctx->stream;
+        auto ocb = ctx_buf(ctx, 8 * std::max<int64_t>(ncols, 1));
+        if (!ocb) return set_err(ctx, SPGEMM_ERR_OOM, "merge keys");
+        uint32_t* oc = (uint32_t*)ocb->p;
+        uint32_t* pay = oc + std::max<int64_t>(ncols, 1);
+        std::shared_ptr<DevBuf> pcp, pir, pv;
+        const int64_t* Pcp;
+        const int32_t* Pir;
+        const void* Pv;
+        if (!acc && U > 0) {
+            // the partials alone: merge them in place
+            Pcp = E.Coff;
+            Pir = (const int32_t*)rbuf->p;
+            Pv = vbuf->p;
+        } else {
+            pcp = ctx_buf(ctx, 8 * (ncols + 1));
+            pir = ctx_buf(ctx, 4 * std::max<int64_t>(pnz, 1));
+            pv = ctx_buf(ctx, w * std::max<int64_t>(pnz, 1));
+            if (!pcp || !pir || !pv) return set_err(ctx, SPGEMM_ERR_OOM, "merge inputs");
+            if (acc) {
+                SG_CUDA(ctx, cudaMemcpyAsync(pcp->p, acc->cp, 8 * n, cudaMemcpyDeviceToDevice, stq));
+                if (accnz) {
+                    SG_CUDA(ctx, cudaMemcpyAsync(pir->p, acc->ir, 4 * accnz, cudaMemcpyDeviceToDevice, stq));
+                    SG_CUDA(ctx, cudaMemcpyAsync(pv->p, acc->num, w * accnz, cudaMemcpyDeviceToDevice, stq));
+                }
+            }
+            if (U > 0) {
+                k_add_offset<<<gridn(U + 1), 256, 0, stq>>>(E.Coff, U + 1, accnz, (int64_t*)pcp->p + nacc);
+                note_launch();
+                if (pn) {
+                    SG_CUDA(ctx, cudaMemcpyAsync((int32_t*)pir->p + accnz, rbuf->p, 4 * pn, cudaMemcpyDeviceToDevice, stq));
+                    SG_CUDA(ctx, cudaMemcpyAsync((char*)pv->p + w * accnz, vbuf->p, w * pn, cudaMemcpyDeviceToDevice, stq));
+                }
+            } else if (acc) {
+                SG_CUDA(ctx, cudaMemcpyAsync((int64_t*)pcp->p + n, acc->cp + n, 8, cudaMemcpyDeviceToDevice, stq));
+            } else {
+                SG_CUDA(ctx, cudaMemsetAsync(pcp->p, 0, 8, stq));
+            }
+            Pcp = (const int64_t*)pcp->p;
+            Pir = (const int32_t*)pir->p;
+            Pv = pv->p;
+        }
+        if (acc) {
+            k_iota_cols<<<gridn(n), 256, 0, stq>>>(oc, pay, n);
+            note_launch();
+        }
+        if (U > 0) {
+            k_item_outcol<<<gridn(U), 256, 0, stq>>>(E.it, E.item_prod, oc, pay, nacc);
+            note_launch();
+        }
+        spgemm_mat_t Cn = nullptr;
+        SG_TRY(merge_columns(ctx, sr, o, m, n, ncols, Pcp, Pir, Pv, pnz, oc, pay, &Cn));
+        hold_acc.reset(Cn);
+        acc = Cn;
+    }
+    *C = hold_acc.release();
+    return SPGEMM_OK;
 }
+
 spgemm_status_t spgemm_summa_stats(spgemm_ctx_t ctx, int64_t* stage_flops, int g, int64_t* nonempty) {
-    (void)stage_flops; (void)g; (void)nonempty;
-    return set_err(ctx, SPGEMM_ERR_UNSUPPORTED, "summa not built yet");
+    if (!ctx) return SPGEMM_ERR_INVALID_ARG;
+    if (stage_flops)
+        for (int s = 0; s < g; ++s)
+            stage_flops[s] = s < (int)ctx->summa_stage_flops.size() ? ctx->summa_stage_flops[s] : 0;
+    if (nonempty) *nonempty = ctx->summa_nonempty;
+    return SPGEMM_OK;
 }
-}
+
+}  // extern "C"
