@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--products", default="flat,summa",
                     help="comma list of product kinds in a step: flat, summa")
+    ap.add_argument("--opt", action="append", default=[],
+                    help="library option for every product, e.g. --opt range_table_slots=4096")
     return ap.parse_args()
 
 
@@ -195,12 +197,15 @@ def main():
         for sr in (sp.PLUS_TIMES_F64, sp.MIN_PLUS_F32):
             products.append((k, sr))
 
+    lib_opts = sp.default_opts(**{k: float(v) if k == "predictor_margin" else int(v)
+                                  for k, v in (o.split("=", 1) for o in args.opt)})
+
     def run_product(kind, sr, M):
         if kind == "flat":
-            plan = sp.spgemm_plan(ctx, M, M, sr)
+            plan = sp.spgemm_plan(ctx, M, M, sr, lib_opts)
             C = sp.spgemm_numeric(plan)
             return C, plan
-        C = sp.spgemm_summa_blocked(ctx, M, M, GRID, sr)
+        C = sp.spgemm_summa_blocked(ctx, M, M, GRID, sr, lib_opts)
         return C, None
 
     # probe which product kinds the library supports (summa may be absent in a build)
@@ -267,7 +272,7 @@ def main():
     hbm, peak_kind = peaks()
     roof = None
     if ("flat", sp.PLUS_TIMES_F64) in products:
-        plan = sp.spgemm_plan(ctx, mats[sp.PLUS_TIMES_F64], mats[sp.PLUS_TIMES_F64], sp.PLUS_TIMES_F64)
+        plan = sp.spgemm_plan(ctx, mats[sp.PLUS_TIMES_F64], mats[sp.PLUS_TIMES_F64], sp.PLUS_TIMES_F64, lib_opts)
         sp.spgemm_symbolic(plan)
         ts = plan.tier_stats()
         ms, cnt = phases[(sp.PLUS_TIMES_F64, "numeric_dense")]
@@ -352,7 +357,8 @@ def main():
                            "abcd": [0.57, 0.19, 0.19, 0.05], "seed": SEED, "grid": GRID,
                            "products": [f"{k}_{'pt64' if s == 0 else 'mp32'}" for k, s in products],
                            "flops_per_product": flops1, "nnz_A": A64.nnz, "l2": "flushed between steps (512 MiB write)",
-                           "pipeline_hbm_frac": pipeline_frac, "pipeline": pipe, "phase_ms_per_step": phase_tab},
+                           "pipeline_hbm_frac": pipeline_frac, "pipeline": pipe, "phase_ms_per_step": phase_tab,
+                           "lib_opts": {k: v for k, v in (o.split("=", 1) for o in args.opt)}},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -96,7 +96,9 @@ typedef struct {
                                  larger columns use row-chunked dense accumulators     */
     int dense_part_flops;     /* target flops per CTA when a dense column is split     */
     float predictor_margin;   /* capacity = (1 + margin) * prediction (+ slack)        */
-    int reserved[8];
+    int range_table_slots;    /* long columns: hash slots per row range, 4096 or 8192
+                                 (0 = default 8192); a range holds < slots/2 entries    */
+    int reserved[7];
 } spgemm_opts_t;
 
 void spgemm_opts_default(spgemm_opts_t* opts);
@@ -222,6 +224,24 @@ spgemm_status_t spgemm_summa_stats(spgemm_ctx_t ctx, int64_t* stage_flops, int g
  * handles (they share one allocation, freed with the last of them). */
 spgemm_status_t spgemm_batch(spgemm_ctx_t ctx, int count, const spgemm_mat_t* A, const spgemm_mat_t* B,
                              spgemm_semiring_t semiring, const spgemm_opts_t* opts, spgemm_mat_t* C);
+
+/* Reusable batch: analysis, symbolic pass and output allocation once; then
+ * spgemm_batch_execute recomputes every C[i]'s values from the current values
+ * of the A[i], B[i] arrays (same structure, same device pointers).  The numeric
+ * launches are captured into a CUDA graph on the first execute and replayed
+ * after that (on the legacy default stream, which cannot be captured, they are
+ * launched directly every time).  spgemm_batch_outputs returns handles that borrow the plan's
+ * arrays (valid until spgemm_plan_destroy). */
+spgemm_status_t spgemm_batch_plan(spgemm_ctx_t ctx, int count, const spgemm_mat_t* A, const spgemm_mat_t* B,
+                                  spgemm_semiring_t semiring, const spgemm_opts_t* opts, spgemm_plan_t* plan);
+spgemm_status_t spgemm_batch_execute(spgemm_plan_t plan);
+spgemm_status_t spgemm_batch_outputs(spgemm_plan_t plan, spgemm_mat_t* C);
+/* Autotuner: times the numeric phase of the batch for a small set of tier
+ * thresholds (warp_max_flops, block_max_flops, dense_part_flops) and writes the
+ * fastest into *opts (other fields kept).  Results are cached in the context
+ * per (semiring, number of products, total flops rounded to a power of two). */
+spgemm_status_t spgemm_autotune(spgemm_ctx_t ctx, int count, const spgemm_mat_t* A, const spgemm_mat_t* B,
+                                spgemm_semiring_t semiring, spgemm_opts_t* opts);
 
 /* ---------------------------------------------------------------- learned predictor */
 /* The nnz predictor is a small MLP (8 -> 32 -> 32 -> 1, ReLU, fp32) over per-column

@@ -229,6 +229,14 @@ spgemm_status_t spgemm_mat_destroy(spgemm_mat_t M) {
 
 }  // extern "C"
 
+spgemm_plan::~spgemm_plan() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+    if (Aconv) delete Aconv;
+    if (Bconv) delete Bconv;
+    for (auto* c : convs) delete c;
+}
+
 // ------------------------------------------------------------------ engine
 DMat csc_view(int64_t m, int64_t n, int64_t nnz, const int64_t* cp, const int32_t* ir, const void* num) {
     DMat d;
@@ -323,6 +331,7 @@ spgemm_status_t engine_setup(Engine* E, spgemm_ctx* ctx, spgemm_semiring_t sr, c
     size_t o_feat = want_features ? take(32 * U1) : 0;
     size_t o_sk = want_features ? take(8 * std::max<int64_t>(amax_n, 1)) : 0;
     size_t o_skb = want_features ? take(8 * (np + 1)) : 0;
+    size_t o_mx = want_features ? take(8 * U1) : 0;
     auto arena = ctx_buf(ctx, off);
     if (!arena) return set_err(ctx, SPGEMM_ERR_OOM, "engine arena of %zu bytes", off);
     E->bufs.push_back(arena);
@@ -349,6 +358,7 @@ spgemm_status_t engine_setup(Engine* E, spgemm_ctx* ctx, spgemm_semiring_t sr, c
     PhaseTimer t_an(ctx, SPGEMM_PHASE_ANALYZE, sr);
     if (want_features) {
         E->feat = (float*)(base + o_feat);
+        E->maxlen = (int64_t*)(base + o_mx);
         sketch = (uint64_t*)(base + o_sk);
         skbase = (int64_t*)(base + o_skb);
         std::vector<int64_t> hb(np + 1, 0);
@@ -360,7 +370,7 @@ spgemm_status_t engine_setup(Engine* E, spgemm_ctx* ctx, spgemm_semiring_t sr, c
     }
     SG_CUDA(ctx, cudaMemsetAsync(E->ctr, 0, 8 * (2 * NBIN + 4), st));
     launch_analyze(st, E->it, E->cfg, E->flops, E->bin, E->item_prod, E->ctr, E->ctr + 2 * NBIN, sketch, skbase,
-                   E->feat);
+                   E->feat, E->maxlen);
     unsigned long long hc[NBIN + 1];
     SG_CUDA(ctx, cudaMemcpyAsync(hc, E->ctr, sizeof(unsigned long long) * NBIN, cudaMemcpyDeviceToHost, st));
     SG_CUDA(ctx, cudaMemcpyAsync(hc + NBIN, E->ctr + 2 * NBIN, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
@@ -406,6 +416,8 @@ spgemm_status_t engine_setup(Engine* E, spgemm_ctx* ctx, spgemm_semiring_t sr, c
         dw.pbase = (int64_t*)(db + o_pb);
         dw.pcnt = (int32_t*)(db + o_pn);
         dw.RB = E->cfg.dense_rows;
+        dw.tbl = opts.range_table_slots > 0 && opts.range_table_slots <= 4096 ? 4096 : 8192;
+        dw.H = dw.tbl / 2 - 32;
         launch_dense_items(st, E->it, dw.dlist, nd, E->flops, E->cfg.part_flops, dw.RB, E->ditems,
                            E->ctr + 2 * NBIN + 1, E->nparts);
         unsigned long long nslabs = 0;
@@ -559,10 +571,15 @@ spgemm_status_t spgemm_numeric(spgemm_plan_t P, spgemm_mat_t* C) {
     if (!P || !C) return SPGEMM_ERR_INVALID_ARG;
     spgemm_ctx* ctx = P->ctx;
     Engine* E = &P->E;
-    SG_TRY(engine_symbolic(E));
     std::shared_ptr<DevBuf> rbuf, vbuf, cpbuf;
-    SG_TRY(engine_alloc_out(E, &rbuf, &vbuf));
-    SG_TRY(engine_numeric(E, (int32_t*)rbuf->p, vbuf->p));
+    if (P->opts.use_predictor && !E->symbolic_done) {
+        // learned path: no symbolic pass for the hash tiers (predictor.cu)
+        SG_TRY(engine_numeric_predicted(E, &rbuf, &vbuf));
+    } else {
+        SG_TRY(engine_symbolic(E));
+        SG_TRY(engine_alloc_out(E, &rbuf, &vbuf));
+        SG_TRY(engine_numeric(E, (int32_t*)rbuf->p, vbuf->p));
+    }
     const int64_t* cp = nullptr;
     SG_TRY(product_colptr(E, &cpbuf, &cp));
     *C = new_owned_csc(ctx, P->sr, P->m, P->n, E->nnz_total, {cpbuf, rbuf, vbuf}, cp, (const int32_t*)rbuf->p,
@@ -648,8 +665,6 @@ int64_t spgemm_launch_count(void) { return launches(); }
 
 spgemm_status_t spgemm_plan_destroy(spgemm_plan_t P) {
     if (!P) return SPGEMM_ERR_INVALID_ARG;
-    if (P->Aconv) spgemm_mat_destroy(P->Aconv);
-    if (P->Bconv) spgemm_mat_destroy(P->Bconv);
     delete P;
     return SPGEMM_OK;
 }

@@ -84,6 +84,7 @@ struct Engine {
     int64_t* nnz_item = nullptr;
     void* scan_tmp = nullptr;
     float* feat = nullptr;               // predictor inputs (items x 8) when requested
+    int64_t* maxlen = nullptr;           // max_k nnz(A(:,k)) per item when requested
     std::shared_ptr<DevBuf> Coff_buf;    // item offsets (nitems + 1)
     int64_t* Coff = nullptr;
     int64_t bin_cnt[sg::NBIN] = {0};
@@ -101,6 +102,14 @@ struct spgemm_plan {
     Engine E;
     spgemm_mat_t Aconv = nullptr, Bconv = nullptr;   // owned conversions (CSR inputs)
     int64_t m = 0, n = 0;          // output dimensions
+    // batch plans
+    bool is_batch = false;
+    std::vector<spgemm_mat_t> convs;                 // owned conversions of batch operands
+    std::vector<int64_t> pm, pn, colbase, outoff;    // per product: dims, colptr base, first entry
+    std::shared_ptr<DevBuf> out_cp, out_r, out_v;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    ~spgemm_plan();
 };
 
 spgemm_status_t set_err(spgemm_ctx* ctx, spgemm_status_t s, const char* fmt, ...);
@@ -146,6 +155,8 @@ spgemm_status_t engine_setup(Engine* E, spgemm_ctx* ctx, spgemm_semiring_t sr, c
                              std::vector<sg::Prod> prods, bool want_features);
 spgemm_status_t engine_symbolic(Engine* E);
 spgemm_status_t engine_numeric(Engine* E, int32_t* Cir, void* Cv);
+// predictor.cu: numeric pass without the symbolic pass of the hash tiers; returns C's arrays
+spgemm_status_t engine_numeric_predicted(Engine* E, std::shared_ptr<DevBuf>* rbuf, std::shared_ptr<DevBuf>* vbuf);
 // output arrays sized by the engine's nnz_total, values of the semiring width
 spgemm_status_t engine_alloc_out(Engine* E, std::shared_ptr<DevBuf>* rbuf, std::shared_ptr<DevBuf>* vbuf);
 sg::DMat csc_view(int64_t m, int64_t n, int64_t nnz, const int64_t* cp, const int32_t* ir, const void* num);

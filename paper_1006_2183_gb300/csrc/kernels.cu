@@ -69,7 +69,8 @@ __global__ void __launch_bounds__(256) k_analyze(Items it, TierCfg cfg, int64_t*
                                                  uint8_t* __restrict__ bin, int32_t* __restrict__ item_prod,
                                                  unsigned long long* bin_count, unsigned long long* flops_total,
                                                  const uint64_t* __restrict__ sketch,
-                                                 const int64_t* __restrict__ sketch_base, float* __restrict__ feat) {
+                                                 const int64_t* __restrict__ sketch_base, float* __restrict__ feat,
+                                                 int64_t* __restrict__ maxlen) {
     __shared__ unsigned long long s_cnt[NBIN];
     __shared__ unsigned long long s_fl;
     if (threadIdx.x < NBIN) s_cnt[threadIdx.x] = 0;
@@ -112,6 +113,7 @@ __global__ void __launch_bounds__(256) k_analyze(Items it, TierCfg cfg, int64_t*
         bin[u] = (uint8_t)b;
         atomicAdd(&s_cnt[b], 1ull);
         atomicAdd(&s_fl, (unsigned long long)f);
+        if (maxlen) maxlen[u] = mx;
         if (feat) {
             // predictor inputs (definitions in predictor.cu)
             float d = (float)(be - bs);
@@ -136,11 +138,11 @@ __global__ void __launch_bounds__(256) k_analyze(Items it, TierCfg cfg, int64_t*
 
 void launch_analyze(cudaStream_t st, const Items& it, TierCfg cfg, int64_t* flops, uint8_t* bin, int32_t* item_prod,
                     unsigned long long* bin_count, unsigned long long* flops_total, const uint64_t* sketch,
-                    const int64_t* sketch_base, float* feat) {
+                    const int64_t* sketch_base, float* feat, int64_t* maxlen) {
     if (it.nitems == 0) return;
     int grid = (int)ceil_div64(it.nitems * 8, 256);
     k_analyze<<<grid, 256, 0, st>>>(it, cfg, flops, bin, item_prod, bin_count, flops_total, sketch, sketch_base,
-                                    feat);
+                                    feat, maxlen);
     note_launch();
 }
 
@@ -322,25 +324,51 @@ __global__ void __launch_bounds__(BLOCK) k_hash(Items it, const int2* __restrict
             }
             G::sync();
         } else {
+            // exact mode: Coff holds exact offsets.  Predicted mode (nnz_item != nullptr): Coff holds
+            // capacity offsets; the exact count is recorded and the column is written only if it fits.
             const int64_t out0 = __ldg(Coff + u);
-            const int nnz = (int)(__ldg(Coff + u + 1) - out0);
+            const int64_t capn = __ldg(Coff + u + 1) - out0;
             const int32_t rb = pr->row_base;
-            // in-place compaction toward the front: the i-th occupied slot moves to i <= its slot
+            // in-place compaction toward the front: the i-th occupied slot moves to i <= its slot.
+            // Each lane holds a contiguous run of S slots in registers; rounds go up the table, and
+            // every destination lies below the slots of later rounds, so nothing unread is overwritten.
+            constexpr int S = (TBL / GS) < 8 ? (TBL / GS) : 8;
             int pos = 0;
-            for (int r0 = 0; r0 < TBL; r0 += GS) {
-                int s = r0 + lane;
-                int32_t k = keys[s];
-                Acc v = vals[s];
-                int occ = k != -1;
+            for (int r0 = 0; r0 < TBL; r0 += GS * S) {
+                const int base_s = r0 + lane * S;
+                int32_t kk[S];
+                Acc vv[S];
+                int occ = 0;
+#pragma unroll
+                for (int i = 0; i < S; ++i) {
+                    kk[i] = keys[base_s + i];
+                    vv[i] = vals[base_s + i];
+                    occ += kk[i] != -1;
+                }
                 int total;
-                int incl = group_incl_scan<GS>(occ, s_scan, total);
+                int o = pos + group_incl_scan<GS>(occ, s_scan, total) - occ;
                 G::sync();
-                if (occ) {
-                    keys[pos + incl - 1] = k;
-                    vals[pos + incl - 1] = v;
+#pragma unroll
+                for (int i = 0; i < S; ++i) {
+                    if (kk[i] != -1) {
+                        keys[o] = kk[i];
+                        vals[o] = vv[i];
+                        ++o;
+                    }
                 }
                 pos += total;
                 G::sync();
+            }
+            const int nnz = nnz_item ? pos : (int)capn;
+            if (nnz_item) {
+                if (lane == 0) nnz_item[u] = pos;
+                if (pos > capn) {   // overflow: recomputed into its exact place afterwards
+                    for (int s = lane; s < TBL; s += GS) {
+                        keys[s] = -1;
+                    }
+                    G::sync();
+                    continue;
+                }
             }
             int P = 1;
             while (P < nnz) P <<= 1;
@@ -401,6 +429,7 @@ static void run_hash_bins(cudaStream_t st, const Items& it, const int2* list, co
 // range is written already sorted.
 constexpr int RT_BLOCK = 512;
 constexpr int RT_MAXB = 1024;
+constexpr int RT_NEXT = 2048;
 
 __device__ __forceinline__ int32_t lower_bound_rows(const int32_t* __restrict__ r, int64_t len, int64_t v) {
     int64_t lo = 0, hi = len;
@@ -434,6 +463,25 @@ __device__ __forceinline__ int64_t gallop_count(const int32_t* __restrict__ r, i
         else hi = mid;
     }
     return lo - pos;
+}
+
+// bitmap[wd] |= bit for every lane with wd >= 0; lanes that hit the same word
+// combine their bits first, so each word takes one shared atomic per warp.
+// Called by all 32 lanes of the warp.
+__device__ __forceinline__ void or_bits_warp(uint32_t* bitmap, int wd, uint32_t bit) {
+    // lanes usually walk one segment in row order, so neighbours often share a word:
+    // fold runs of equal words with a shuffle before the shared atomic
+    const int lane = threadIdx.x & 31;
+    const int wprev = __shfl_up_sync(0xffffffffu, wd, 1);
+    const bool head = lane == 0 || wprev != wd;
+    uint32_t acc = bit;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t b2 = __shfl_down_sync(0xffffffffu, acc, o);
+        const int w2 = __shfl_down_sync(0xffffffffu, wd, o);
+        if (lane + o < 32 && w2 == wd) acc |= b2;
+    }
+    if (wd >= 0 && head) atomicOr(&bitmap[wd], acc);
 }
 
 struct RangeSmem {   // flattened-expansion scratch of one CTA
@@ -511,16 +559,26 @@ __global__ void __launch_bounds__(RT_BLOCK) k_range_sym(Items it, DenseWork dw) 
             sc->incl[tid] = incl;
             sc->start[tid] = a;
             __syncthreads();
-            for (int x = tid; x < total; x += RT_BLOCK) {
-                int lo = 0, hi = RT_BLOCK - 1;
-                while (lo < hi) {
-                    int mid = (lo + hi) >> 1;
-                    if (sc->incl[mid] > x) hi = mid;
-                    else lo = mid + 1;
+            // warp-uniform trip count so the whole warp can combine its bitmap updates
+            for (int x0 = tid & ~31; x0 < total; x0 += RT_BLOCK) {
+                const int x = x0 + (tid & 31);
+                int wd = -1;
+                uint32_t bit = 0;
+                if (x < total) {
+                    int lo = 0, hi = RT_BLOCK - 1;
+                    while (lo < hi) {
+                        int mid = (lo + hi) >> 1;
+                        if (sc->incl[mid] > x) hi = mid;
+                        else lo = mid + 1;
+                    }
+                    const int64_t idx = sc->start[lo] + (x - (lo ? sc->incl[lo - 1] : 0));
+                    const int lr = (int)(__ldg(air + idx) - R0);
+                    if ((unsigned)lr < (unsigned)(R1 - R0)) {
+                        wd = lr >> 5;
+                        bit = 1u << (lr & 31);
+                    }
                 }
-                const int64_t idx = sc->start[lo] + (x - (lo ? sc->incl[lo - 1] : 0));
-                const int lr = (int)(__ldg(air + idx) - R0);
-                if ((unsigned)lr < (unsigned)(R1 - R0)) atomicOr(&bitmap[lr >> 5], 1u << (lr & 31));
+                or_bits_warp(bitmap, wd, bit);
             }
             __syncthreads();
         }
@@ -614,6 +672,9 @@ __global__ void __launch_bounds__(RT_BLOCK) k_range_num(Items it, DenseWork dw, 
     int32_t* keys = reinterpret_cast<int32_t*>(smem + sizeof(RangeSmem));
     Acc* vals = reinterpret_cast<Acc*>(smem + sizeof(RangeSmem) + (size_t)TBL * 4);
     uint32_t* bitmap = reinterpret_cast<uint32_t*>(smem + sizeof(RangeSmem) + (size_t)TBL * (4 + sizeof(Acc)));
+    // next row of A(:,k) at the cursor, for the first RT_NEXT k's: a range that ends at or
+    // before it gets nothing from that k, which is then skipped without touching memory
+    int32_t* s_next = reinterpret_cast<int32_t*>(bitmap + dw.WW);
     volatile int32_t* vkeys = keys;
     const int tid = threadIdx.x;
     const int64_t nsym = (int64_t)*dw.nitems;
@@ -642,7 +703,9 @@ __global__ void __launch_bounds__(RT_BLOCK) k_range_num(Items it, DenseWork dw, 
             const int32_t k = __ldg(pr->B.ir + bs + t);
             int64_t s, en;
             col_range(pr->A, k, s, en);
-            cur[t] = R0 == 0 ? 0 : lower_bound_rows(air + s, en - s, R0);
+            const int32_t c0 = R0 == 0 ? 0 : lower_bound_rows(air + s, en - s, R0);
+            cur[t] = c0;
+            if (t < RT_NEXT) s_next[t] = s + c0 < en ? __ldg(air + s + c0) : INT_MAX;
         }
         int64_t outbase = __ldg(Coff + u);
         for (int qq = 0; qq < q; ++qq) outbase += dw.part_count[(int64_t)qq * dw.ndense + d];
@@ -653,6 +716,7 @@ __global__ void __launch_bounds__(RT_BLOCK) k_range_num(Items it, DenseWork dw, 
             const RangePart rp = dw.parts[pb + ip];
             const int64_t r0 = rp.r0, r1 = rp.r1;
             const int nw = (int)((r1 - r0 + 31) >> 5);
+            const bool direct = r1 - r0 <= TBL;
             for (int x = tid; x < nw; x += RT_BLOCK) bitmap[x] = 0u;
             __syncthreads();
             for (int64_t b0 = 0; b0 < deg; b0 += RT_BLOCK) {
@@ -660,7 +724,7 @@ __global__ void __launch_bounds__(RT_BLOCK) k_range_num(Items it, DenseWork dw, 
                 int len = 0;
                 int64_t a = 0;
                 T bv = T(0);
-                if (t < deg) {
+                if (t < deg && (t >= RT_NEXT || s_next[t] < r1)) {
                     const int32_t k = __ldg(pr->B.ir + bs + t);
                     int64_t s, en;
                     col_range(pr->A, k, s, en);
@@ -668,6 +732,7 @@ __global__ void __launch_bounds__(RT_BLOCK) k_range_num(Items it, DenseWork dw, 
                     const int64_t c = gallop_count(air, a, en, r1);
                     cur[t] += (int32_t)c;
                     len = (int)c;
+                    if (t < RT_NEXT) s_next[t] = a + c < en ? __ldg(air + a + c) : INT_MAX;
                     bv = load_val<SR>(pr->B, bs + t);
                 }
                 int total;
@@ -676,27 +741,44 @@ __global__ void __launch_bounds__(RT_BLOCK) k_range_num(Items it, DenseWork dw, 
                 sc->start[tid] = a;
                 reinterpret_cast<T*>(&sc->bv[tid])[0] = bv;
                 __syncthreads();
-                for (int x = tid; x < total; x += RT_BLOCK) {
-                    int lo = 0, hi = RT_BLOCK - 1;
-                    while (lo < hi) {
-                        int mid = (lo + hi) >> 1;
-                        if (sc->incl[mid] > x) hi = mid;
-                        else lo = mid + 1;
-                    }
-                    const int64_t idx = sc->start[lo] + (x - (lo ? sc->incl[lo - 1] : 0));
-                    const int32_t row = __ldg(air + idx);
-                    const int lr = (int)(row - r0);
-                    if ((unsigned)lr >= (unsigned)(r1 - r0)) continue;   // only on malformed input
-                    atomicOr(&bitmap[lr >> 5], 1u << (lr & 31));
-                    uint32_t h = hash_row(row) >> (32 - LOG2);
-                    while (true) {
-                        int32_t cu = vkeys[h];
-                        if (cu == row) break;
-                        if (cu == -1) {
-                            int32_t prev = atomicCAS(&keys[h], -1, row);
-                            if (prev == -1 || prev == row) break;
+                for (int x0 = tid & ~31; x0 < total; x0 += RT_BLOCK) {
+                    const int x = x0 + (tid & 31);
+                    int wd = -1;
+                    uint32_t bit = 0;
+                    int lo = 0;
+                    int64_t idx = 0;
+                    int32_t row = 0;
+                    if (x < total) {
+                        int hi = RT_BLOCK - 1;
+                        while (lo < hi) {
+                            int mid = (lo + hi) >> 1;
+                            if (sc->incl[mid] > x) hi = mid;
+                            else lo = mid + 1;
                         }
-                        h = (h + 1) & (TBL - 1);
+                        idx = sc->start[lo] + (x - (lo ? sc->incl[lo - 1] : 0));
+                        row = __ldg(air + idx);
+                        const int lr = (int)(row - r0);
+                        if ((unsigned)lr < (unsigned)(r1 - r0)) {   // fails only on malformed input
+                            wd = lr >> 5;
+                            bit = 1u << (lr & 31);
+                        }
+                    }
+                    or_bits_warp(bitmap, wd, bit);
+                    if (wd < 0) continue;
+                    uint32_t h;
+                    if (direct) {
+                        h = (uint32_t)(row - r0);   // narrow range: the table is a dense row array
+                    } else {
+                        h = hash_row(row) >> (32 - LOG2);
+                        while (true) {
+                            int32_t cu = vkeys[h];
+                            if (cu == row) break;
+                            if (cu == -1) {
+                                int32_t prev = atomicCAS(&keys[h], -1, row);
+                                if (prev == -1 || prev == row) break;
+                            }
+                            h = (h + 1) & (TBL - 1);
+                        }
                     }
                     SR::atomic_add(&vals[h], SR::mul(load_val<SR>(pr->A, idx),
                                                      reinterpret_cast<const T*>(&sc->bv[lo])[0]));
@@ -717,15 +799,20 @@ __global__ void __launch_bounds__(RT_BLOCK) k_range_num(Items it, DenseWork dw, 
                     const int b = __ffs(bits) - 1;
                     bits &= bits - 1;
                     const int32_t row = (int32_t)(r0 + x * 32 + b);
-                    uint32_t h = hash_row(row) >> (32 - LOG2);
-                    while (vkeys[h] != row) h = (h + 1) & (TBL - 1);
+                    uint32_t h;
+                    if (direct) {
+                        h = (uint32_t)(x * 32 + b);
+                    } else {
+                        h = hash_row(row) >> (32 - LOG2);
+                        while (vkeys[h] != row) h = (h + 1) & (TBL - 1);
+                    }
                     Cir[o] = row + rb;
                     Cv[o] = SR::out(vals[h]);
                     ++o;
                     // every inserted row has its bit set, so this empties the table again;
                     // lookups never stop at an empty slot, so clearing during reads is safe
                     vals[h] = SR::zero();
-                    keys[h] = -1;
+                    if (!direct) keys[h] = -1;
                 }
             }
             __syncthreads();
@@ -747,17 +834,27 @@ static void run_range(cudaStream_t st, const Items& it, const DenseWork& dw, boo
         }
         k_range_sym<<<grid, RT_BLOCK, smem, st>>>(it, dw);
     } else {
-        constexpr int TBL = RANGE_TBL;
-        const size_t smem = sizeof(RangeSmem) + (size_t)TBL * (4 + sizeof(typename SR::Acc)) + (size_t)(dw.WW) * 4;
-        auto kern = k_range_num<SR, TBL>;
-        static size_t attr = 0;
-        if (attr < smem) {
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            attr = smem;
-        }
-        kern<<<grid, RT_BLOCK, smem, st>>>(it, dw, Coff, Cir, Cv);
+        auto go = [&](auto kern, int tbl, size_t& attr) {
+            const size_t smem = sizeof(RangeSmem) + (size_t)tbl * (4 + sizeof(typename SR::Acc)) + (size_t)(dw.WW) * 4 +
+                                (size_t)RT_NEXT * 4;
+            if (attr < smem) {
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                attr = smem;
+            }
+            kern<<<grid, RT_BLOCK, smem, st>>>(it, dw, Coff, Cir, Cv);
+        };
+        static size_t attr4 = 0, attr8 = 0;
+        if (dw.tbl <= 4096) go(k_range_num<SR, 4096>, 4096, attr4);
+        else go(k_range_num<SR, 8192>, 8192, attr8);
     }
     note_launch();
+}
+
+template <class SR>
+void launch_numeric_predicted(cudaStream_t st, const Items& it, const int2* list, const int64_t* bin_off,
+                              const int64_t* bin_cnt, const int64_t* cap_off, int64_t* nnz_item, int32_t* Cir,
+                              typename SR::T* Cv) {
+    run_hash_bins<SR, true>(st, it, list, bin_off, bin_cnt, nnz_item, cap_off, Cir, Cv);
 }
 
 template <class SR>
@@ -782,7 +879,9 @@ void launch_numeric(cudaStream_t st, const Items& it, TierCfg cfg, const int2* l
                                       const int64_t*, const DenseWork&, int64_t*, int);                          \
     template void launch_numeric<SR>(cudaStream_t, const Items&, TierCfg, const int2*, const int64_t*,           \
                                      const int64_t*, const DenseWork&, const int64_t*, int32_t*, typename SR::T*, \
-                                     int);
+                                     int);                                                                       \
+    template void launch_numeric_predicted<SR>(cudaStream_t, const Items&, const int2*, const int64_t*,          \
+                                               const int64_t*, const int64_t*, int64_t*, int32_t*, typename SR::T*);
 SG_INST(PT64)
 SG_INST(MP32)
 SG_INST(BOOL8)

@@ -33,7 +33,8 @@ struct TierCfg {
     int part_flops;   // target flops per symbolic slab of a long column
 };
 
-// Range tier: hash-table slots per numeric range, so a range holds < RANGE_TBL / 2 entries.
+// Range tier: hash-table slots per numeric range (default; 4096 also built), so a
+// range holds < RANGE_TBL / 2 entries.
 constexpr int RANGE_TBL = 8192;
 constexpr int RANGE_H = RANGE_TBL / 2 - 32;   // cut a range once it holds this many entries
 constexpr int RANGE_W = 32768;                // and at most this many rows
@@ -60,8 +61,9 @@ struct DenseWork {   // state of the range tier shared by its kernels
     int32_t* pcnt = nullptr;              // per slab: number of ranges
     int* err = nullptr;                   // nonzero: a capacity was exceeded
     int RB = 1 << 20;                     // most rows per slab
-    int H = RANGE_H;
+    int H = RANGE_H;                      // cut a range once it holds this many entries (< tbl / 2)
     int WW = RANGE_W / 32;                // words per range window
+    int tbl = RANGE_TBL;                  // hash slots per numeric range (4096 or 8192)
 };
 
 struct Items {
@@ -78,7 +80,7 @@ struct Items {
 // at sketch_base[i].
 void launch_analyze(cudaStream_t st, const Items& it, TierCfg cfg, int64_t* flops, uint8_t* bin, int32_t* item_prod,
                     unsigned long long* bin_count, unsigned long long* flops_total, const uint64_t* sketch,
-                    const int64_t* sketch_base, float* feat);
+                    const int64_t* sketch_base, float* feat, int64_t* maxlen = nullptr);
 void launch_row_sketch(cudaStream_t st, const DMat& A, uint64_t* sketch);
 void launch_bin_scatter(cudaStream_t st, const Items& it, const uint8_t* bin, const int32_t* item_prod,
                         const int64_t* bin_off, unsigned long long* bin_cursor, int2* list);
@@ -95,6 +97,13 @@ template <class SR>
 void launch_numeric(cudaStream_t st, const Items& it, TierCfg cfg, const int2* list, const int64_t* bin_off,
                     const int64_t* bin_cnt, const DenseWork& dw, const int64_t* Coff, int32_t* Cir,
                     typename SR::T* Cv, int which = 3);
+
+// numeric pass of the hash tiers into a predicted layout: cap_off are capacity offsets;
+// every item's exact count goes to nnz_item, items that do not fit are not written
+template <class SR>
+void launch_numeric_predicted(cudaStream_t st, const Items& it, const int2* list, const int64_t* bin_off,
+                              const int64_t* bin_cnt, const int64_t* cap_off, int64_t* nnz_item, int32_t* Cir,
+                              typename SR::T* Cv);
 
 // nnz of dense items = sum of their part counts
 void launch_sum_parts(cudaStream_t st, const Items& it, const int2* dense_list, int64_t ndense, const int8_t* nparts,

@@ -52,7 +52,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("use_predictor", ctypes.c_int), ("summa_fused", ctypes.c_int),
                 ("summa_merge_every", ctypes.c_int), ("warp_max_flops", ctypes.c_int),
                 ("block_max_flops", ctypes.c_int), ("dense_part_flops", ctypes.c_int),
-                ("predictor_margin", ctypes.c_float), ("reserved", ctypes.c_int * 8)]
+                ("predictor_margin", ctypes.c_float), ("range_table_slots", ctypes.c_int),
+                ("reserved", ctypes.c_int * 7)]
 
 
 def _sig(name, args, res=ctypes.c_int):
@@ -85,6 +86,10 @@ _sig("spgemm_multiply", [P, P, P, ctypes.c_int, ctypes.POINTER(Opts), PP])
 _sig("spgemm_summa_blocked", [P, P, P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Opts), PP])
 _sig("spgemm_summa_stats", [P, ctypes.POINTER(I64), ctypes.c_int, ctypes.POINTER(I64)])
 _sig("spgemm_batch", [P, ctypes.c_int, PP, PP, ctypes.c_int, ctypes.POINTER(Opts), PP])
+_sig("spgemm_batch_plan", [P, ctypes.c_int, PP, PP, ctypes.c_int, ctypes.POINTER(Opts), PP])
+_sig("spgemm_batch_execute", [P])
+_sig("spgemm_batch_outputs", [P, PP])
+_sig("spgemm_autotune", [P, ctypes.c_int, PP, PP, ctypes.c_int, ctypes.POINTER(Opts)])
 _sig("spgemm_ctx_timing", [P, ctypes.c_int])
 _sig("spgemm_ctx_phase_ms", [P, P, P])
 _sig("spgemm_launch_count", [], I64)
@@ -130,6 +135,13 @@ def _view(ptr: int | None, n: int, typestr: str, dtype: torch.dtype, device) -> 
     if n == 0 or not ptr:
         return torch.empty(0, dtype=dtype, device=device)
     return torch.as_tensor(_CAI(ptr, n, typestr), device=device)
+
+
+def _order_after_current(ctx):
+    """Work the caller queued on torch's current stream (e.g. uploads) precedes the library's."""
+    cur = torch.cuda.current_stream()
+    if cur.cuda_stream != ctx.stream.cuda_stream:
+        ctx.stream.wait_stream(cur)
 
 
 class Context:
@@ -205,6 +217,7 @@ class Matrix:
             vals: torch.Tensor | None, semiring: int) -> "Matrix":
         h = ctypes.c_void_p()
         nnz = int(rowidx.numel())
+        _order_after_current(ctx)
         ctx._check(_lib.spgemm_mat_csc(ctx.handle, ctypes.byref(h), m, n, nnz, _ptr(colptr), _ptr(rowidx),
                                        _ptr(vals), semiring))
         return cls(ctx, h, semiring, (colptr, rowidx, vals))
@@ -213,6 +226,7 @@ class Matrix:
     def csr(cls, ctx: Context, m: int, n: int, rowptr: torch.Tensor, colidx: torch.Tensor,
             vals: torch.Tensor | None, semiring: int) -> "Matrix":
         h = ctypes.c_void_p()
+        _order_after_current(ctx)
         ctx._check(_lib.spgemm_mat_csr(ctx.handle, ctypes.byref(h), m, n, int(colidx.numel()), _ptr(rowptr),
                                        _ptr(colidx), _ptr(vals), semiring))
         return cls(ctx, h, semiring, (rowptr, colidx, vals))
@@ -382,6 +396,42 @@ def spgemm_batch(ctx: Context, As: list[Matrix], Bs: list[Matrix], semiring: int
     ch = (ctypes.c_void_p * n)()
     ctx._check(_lib.spgemm_batch(ctx.handle, n, ah, bh, semiring, _opts(opts), ch))
     return [Matrix(ctx, ctypes.c_void_p(ch[i]), semiring) for i in range(n)]
+
+
+def _handles(ms):
+    return (ctypes.c_void_p * len(ms))(*[m.handle.value for m in ms])
+
+
+class BatchPlan(Plan):
+    """Batch plan: analysis and symbolic pass done once; execute() recomputes values (CUDA graph replay)."""
+
+    def __init__(self, ctx, handle, As, Bs, semiring):
+        super().__init__(ctx, handle, None, None, semiring)
+        self._keep = (list(As), list(Bs))
+        self.count = len(As)
+
+    def execute(self):
+        self.ctx._check(_lib.spgemm_batch_execute(self._h))
+
+    def outputs(self) -> list[Matrix]:
+        ch = (ctypes.c_void_p * self.count)()
+        self.ctx._check(_lib.spgemm_batch_outputs(self._h, ch))
+        return [Matrix(self.ctx, ctypes.c_void_p(ch[i]), self.semiring, (self,)) for i in range(self.count)]
+
+
+def spgemm_batch_plan(ctx: Context, As: list[Matrix], Bs: list[Matrix], semiring: int,
+                      opts: Opts | None = None) -> BatchPlan:
+    h = ctypes.c_void_p()
+    ctx._check(_lib.spgemm_batch_plan(ctx.handle, len(As), _handles(As), _handles(Bs), semiring, _opts(opts),
+                                      ctypes.byref(h)))
+    return BatchPlan(ctx, h, As, Bs, semiring)
+
+
+def spgemm_autotune(ctx: Context, As: list[Matrix], Bs: list[Matrix], semiring: int,
+                    opts: Opts | None = None) -> Opts:
+    o = opts if opts is not None else default_opts()
+    ctx._check(_lib.spgemm_autotune(ctx.handle, len(As), _handles(As), _handles(Bs), semiring, ctypes.byref(o)))
+    return o
 
 
 def spgemm_mat_to_dcsc(ctx: Context, A: Matrix, build_aux: bool = True) -> Matrix:
