@@ -243,6 +243,35 @@ spgemm_status_t spgemm_batch_outputs(spgemm_plan_t plan, spgemm_mat_t* C);
 spgemm_status_t spgemm_autotune(spgemm_ctx_t ctx, int count, const spgemm_mat_t* A, const spgemm_mat_t* B,
                                 spgemm_semiring_t semiring, spgemm_opts_t* opts);
 
+/* ---------------------------------------------------------------- no device allocation */
+/* Column pointers of C = A*B (C's structure: Ccolptr[0] = 0, Ccolptr[j+1] -
+ * Ccolptr[j] = nnz(C(:,j))) computed without allocating any device memory.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory where they need C's structure -- programs that
+ * give the library a fixed, pre-planned memory budget, latency-critical paths
+ * where an allocation call and the synchronisation it can cause are not
+ * allowed, or plugins inside a host program whose memory manager owns all
+ * device memory.  Everything it touches is either the caller's (A, B as device
+ * CSC arrays of an m x k and a k x n matrix; Ccolptr, n+1 int64 on the device,
+ * written) or one file-scope device array of SPGEMM_NOALLOC_MAX_TILES int64
+ * (32 KiB, resident on every GPU that loads the library until the process
+ * exits).  Limits: m <= SPGEMM_NOALLOC_MAX_ROWS (a bitmap of m bits lives in
+ * shared memory) and n <= SPGEMM_NOALLOC_MAX_TILES * 4096; larger inputs return
+ * SPGEMM_ERR_UNSUPPORTED without launching anything.  Work is enqueued on
+ * cuda_stream (a cudaStream_t; NULL = legacy default stream) and the call does
+ * not synchronise.  The first call on a device looks up the device address of
+ * the scratch array (cudaGetSymbolAddress), so make that first call before any
+ * stream capture.  All calls share the scratch array, which keeps the last
+ * call's contents (each call overwrites what it reads); calls that overlap on
+ * the GPU -- on different streams or from different threads -- race on it and
+ * must be ordered by the caller.  Returns SPGEMM_ERR_INVALID_ARG for null or
+ * negative arguments and SPGEMM_ERR_CUDA when a CUDA call fails. */
+#define SPGEMM_NOALLOC_MAX_TILES 4096
+#define SPGEMM_NOALLOC_MAX_ROWS 1048576
+spgemm_status_t spgemm_colptr_noalloc(void* cuda_stream, int64_t m, int64_t k, int64_t n, const int64_t* Acolptr,
+                                      const int32_t* Arowidx, const int64_t* Bcolptr, const int32_t* Browidx,
+                                      int64_t* Ccolptr);
+
 /* ---------------------------------------------------------------- learned predictor */
 /* The nnz predictor is a small MLP (8 -> 32 -> 32 -> 1, ReLU, fp32) over per-column
  * features; it has no counterpart in the paper (its Section 8 lists structure

@@ -90,6 +90,7 @@ _sig("spgemm_batch_plan", [P, ctypes.c_int, PP, PP, ctypes.c_int, ctypes.POINTER
 _sig("spgemm_batch_execute", [P])
 _sig("spgemm_batch_outputs", [P, PP])
 _sig("spgemm_autotune", [P, ctypes.c_int, PP, PP, ctypes.c_int, ctypes.POINTER(Opts)])
+_sig("spgemm_colptr_noalloc", [P, I64, I64, I64, P, P, P, P, P])
 _sig("spgemm_ctx_timing", [P, ctypes.c_int])
 _sig("spgemm_ctx_phase_ms", [P, P, P])
 _sig("spgemm_launch_count", [], I64)
@@ -432,6 +433,18 @@ def spgemm_autotune(ctx: Context, As: list[Matrix], Bs: list[Matrix], semiring: 
     o = opts if opts is not None else default_opts()
     ctx._check(_lib.spgemm_autotune(ctx.handle, len(As), _handles(As), _handles(Bs), semiring, ctypes.byref(o)))
     return o
+
+
+def spgemm_colptr_noalloc(stream: torch.cuda.Stream, m: int, k: int, n: int, Acolptr: torch.Tensor,
+                          Arowidx: torch.Tensor, Bcolptr: torch.Tensor, Browidx: torch.Tensor,
+                          Ccolptr: torch.Tensor) -> int:
+    """C's column pointers into Ccolptr (n+1 int64, device) without any device allocation.
+
+    Returns the library status (0 on success); nothing is allocated by the
+    library or by this wrapper.
+    """
+    return int(_lib.spgemm_colptr_noalloc(ctypes.c_void_p(stream.cuda_stream), m, k, n, _ptr(Acolptr),
+                                          _ptr(Arowidx), _ptr(Bcolptr), _ptr(Browidx), _ptr(Ccolptr)))
 
 
 def spgemm_mat_to_dcsc(ctx: Context, A: Matrix, build_aux: bool = True) -> Matrix:
