@@ -97,7 +97,7 @@ typedef struct {
     int dense_part_flops;     /* target flops per CTA when a dense column is split     */
     float predictor_margin;   /* capacity = (1 + margin) * prediction (+ slack)        */
     int range_table_slots;    /* long columns: hash slots per row range, 4096 or 8192
-                                 (0 = default 8192); a range holds < slots/2 entries    */
+                                 (0 = default 4096); a range holds < slots/2 entries    */
     int reserved[7];
 } spgemm_opts_t;
 

@@ -416,7 +416,7 @@ spgemm_status_t engine_setup(Engine* E, spgemm_ctx* ctx, spgemm_semiring_t sr, c
         dw.pbase = (int64_t*)(db + o_pb);
         dw.pcnt = (int32_t*)(db + o_pn);
         dw.RB = E->cfg.dense_rows;
-        dw.tbl = opts.range_table_slots > 0 && opts.range_table_slots <= 4096 ? 4096 : 8192;
+        dw.tbl = opts.range_table_slots > 4096 ? 8192 : 4096;
         dw.H = dw.tbl / 2 - 32;
         launch_dense_items(st, E->it, dw.dlist, nd, E->flops, E->cfg.part_flops, dw.RB, E->ditems,
                            E->ctr + 2 * NBIN + 1, E->nparts);

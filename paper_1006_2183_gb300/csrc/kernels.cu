@@ -429,7 +429,7 @@ static void run_hash_bins(cudaStream_t st, const Items& it, const int2* list, co
 // range is written already sorted.
 constexpr int RT_BLOCK = 512;
 constexpr int RT_MAXB = 1024;
-constexpr int RT_NEXT = 2048;
+constexpr int RT_NEXT = 1024;   // k's per column whose cursor state lives in shared memory
 
 __device__ __forceinline__ int32_t lower_bound_rows(const int32_t* __restrict__ r, int64_t len, int64_t v) {
     int64_t lo = 0, hi = len;
@@ -484,13 +484,6 @@ __device__ __forceinline__ void or_bits_warp(uint32_t* bitmap, int wd, uint32_t 
     if (wd >= 0 && head) atomicOr(&bitmap[wd], acc);
 }
 
-struct RangeSmem {   // flattened-expansion scratch of one CTA
-    int incl[RT_BLOCK];
-    int64_t start[RT_BLOCK];
-    int64_t bv[RT_BLOCK];   // B value bits (read back as SR::T)
-    int scan[34];
-};
-
 __global__ void k_dense_items(Items it, const int2* __restrict__ dlist, int64_t nd, const int64_t* __restrict__ flops,
                               int part_flops, int RB, int2* items, unsigned long long* nitems, int8_t* nparts) {
     int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -518,14 +511,102 @@ void launch_dense_items(cudaStream_t st, const Items& it, const int2* dense_list
     note_launch();
 }
 
+// Inclusive scan of a 64-bit value over the CTA (RT_BLOCK threads).
+__device__ __forceinline__ unsigned long long rt_block_incl_scan64(unsigned long long v, unsigned long long* ws,
+                                                                   unsigned long long& total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        unsigned long long s = lane < RT_BLOCK / 32 ? ws[lane] : 0ull;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned long long y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < RT_BLOCK / 32) ws[lane] = s;
+    }
+    __syncthreads();
+    const unsigned long long add = w > 0 ? ws[w - 1] : 0ull;
+    total = ws[RT_BLOCK / 32 - 1];
+    __syncthreads();
+    return x + add;
+}
+
+struct RangeSmem {   // per-batch segments of the flattened expansion (compacted: all nonempty)
+    int end[RT_BLOCK];        // inclusive prefix of segment lengths (exclusive end in flattened space)
+    int64_t start[RT_BLOCK];  // first position of the segment in A.ir
+    int64_t bv[RT_BLOCK];     // B value bits (read back as SR::T)
+    unsigned long long ws[32];
+    int wc[RT_BLOCK / 32 + 1];
+};
+
+// Compacts the active (k, segment) pairs of this batch into sc and returns
+// (number of segments, number of products).  Called by all threads.
+__device__ __forceinline__ void rt_compact(RangeSmem* sc, bool active, int len, int64_t a, int64_t bvbits, int& ns,
+                                           int& T) {
+    const unsigned long long packed = active && len > 0 ? ((1ull << 32) | (unsigned)len) : 0ull;
+    unsigned long long tot;
+    const unsigned long long inc = rt_block_incl_scan64(packed, sc->ws, tot);
+    if (packed) {
+        const int pos = (int)(inc >> 32) - 1;
+        sc->end[pos] = (int)(inc & 0xffffffffull);
+        sc->start[pos] = a;
+        sc->bv[pos] = bvbits;
+    }
+    ns = (int)(tot >> 32);
+    T = (int)(tot & 0xffffffffull);
+    __syncthreads();
+}
+
+// Walks products x in [0, T) of the compacted segments: each warp takes a
+// contiguous slice; a lane finds its segment from the boundary mask of its
+// 32-product window.  f(valid, segment, offset) is called by all 32 lanes.
+template <class F>
+__device__ __forceinline__ void rt_expand(const RangeSmem* sc, int ns, int T, F&& f) {
+    constexpr int NW = RT_BLOCK / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int C = (T + NW * 32 - 1) / (NW * 32) * 32;
+    const int xb = warp * C, xe = min(T, xb + C);
+    if (xb >= xe) return;
+    // o0 = number of segment ends <= xb
+    int lo = 0, hi = ns;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (sc->end[mid] <= xb) lo = mid + 1;
+        else hi = mid;
+    }
+    int o0 = lo;
+    for (int x0 = xb; x0 < xe; x0 += 32) {
+        const int ej = o0 + lane < ns ? sc->end[o0 + lane] : INT_MAX;
+        const unsigned bitv = (ej > x0 && ej <= x0 + 32) ? (1u << (ej - x0 - 1)) : 0u;
+        const unsigned mask = __reduce_or_sync(0xffffffffu, bitv);
+        const int oi = o0 + __popc(mask & ((1u << lane) - 1u));
+        const int pe0 = o0 > 0 ? sc->end[o0 - 1] : 0;
+        const int src = oi - 1 - o0;
+        const int pe = __shfl_sync(0xffffffffu, ej, src < 0 ? 0 : src);
+        const int prev_end = src < 0 ? pe0 : pe;
+        const int x = x0 + lane;
+        f(x < xe, oi, x - prev_end);
+        o0 += __popc(mask);
+    }
+}
+
 // Symbolic range kernel: slab bitmap, count, cut into ranges.
 __global__ void __launch_bounds__(RT_BLOCK) k_range_sym(Items it, DenseWork dw) {
     extern __shared__ __align__(16) unsigned char smem[];
     RangeSmem* sc = reinterpret_cast<RangeSmem*>(smem);
     int* s_bw = reinterpret_cast<int*>(smem + sizeof(RangeSmem));          // boundary words
     int* s_bp = s_bw + RT_MAXB + 1;                                           // set bits before them
-    int* s_misc = s_bp + RT_MAXB + 1;                                         // [0] boundary count, [1] base
+    int* s_misc = s_bp + RT_MAXB + 1;
     uint32_t* bitmap = reinterpret_cast<uint32_t*>(s_misc + 4);
+    int* s_scan = reinterpret_cast<int*>(sc->wc);
     const int tid = threadIdx.x;
     const int64_t nsym = (int64_t)*dw.nitems;
     for (int64_t w = blockIdx.x; w < nsym; w += gridDim.x) {
@@ -554,32 +635,13 @@ __global__ void __launch_bounds__(RT_BLOCK) k_range_sym(Items it, DenseWork dw) 
                 const int64_t b = R1 == m ? en : s + lower_bound_rows(air + s, en - s, R1);
                 len = (int)(b - a);
             }
-            int total;
-            const int incl = group_incl_scan<RT_BLOCK>(len, sc->scan, total);
-            sc->incl[tid] = incl;
-            sc->start[tid] = a;
-            __syncthreads();
-            // warp-uniform trip count so the whole warp can combine its bitmap updates
-            for (int x0 = tid & ~31; x0 < total; x0 += RT_BLOCK) {
-                const int x = x0 + (tid & 31);
-                int wd = -1;
-                uint32_t bit = 0;
-                if (x < total) {
-                    int lo = 0, hi = RT_BLOCK - 1;
-                    while (lo < hi) {
-                        int mid = (lo + hi) >> 1;
-                        if (sc->incl[mid] > x) hi = mid;
-                        else lo = mid + 1;
-                    }
-                    const int64_t idx = sc->start[lo] + (x - (lo ? sc->incl[lo - 1] : 0));
-                    const int lr = (int)(__ldg(air + idx) - R0);
-                    if ((unsigned)lr < (unsigned)(R1 - R0)) {
-                        wd = lr >> 5;
-                        bit = 1u << (lr & 31);
-                    }
-                }
-                or_bits_warp(bitmap, wd, bit);
-            }
+            int ns, T;
+            rt_compact(sc, t < be, len, a, 0, ns, T);
+            rt_expand(sc, ns, T, [&](bool valid, int o, int off) {
+                if (!valid) return;
+                const int lr = (int)(__ldg(air + sc->start[o] + off) - R0);
+                if ((unsigned)lr < (unsigned)(R1 - R0)) atomicOr(&bitmap[lr >> 5], 1u << (lr & 31));
+            });
             __syncthreads();
         }
         // count per thread over a contiguous word range, then cut into ranges
@@ -588,7 +650,7 @@ __global__ void __launch_bounds__(RT_BLOCK) k_range_sym(Items it, DenseWork dw) 
         int cnt = 0;
         for (int x = w0; x < w1; ++x) cnt += __popc(bitmap[x]);
         int total;
-        const int excl = group_incl_scan<RT_BLOCK>(cnt, sc->scan, total) - cnt;
+        const int excl = group_incl_scan<RT_BLOCK>(cnt, s_scan, total) - cnt;
         int nb = 0;
         {
             int bp = excl;
@@ -599,7 +661,7 @@ __global__ void __launch_bounds__(RT_BLOCK) k_range_sym(Items it, DenseWork dw) 
             }
         }
         int nbt;
-        const int bexcl = group_incl_scan<RT_BLOCK>(nb, sc->scan, nbt) - nb;
+        const int bexcl = group_incl_scan<RT_BLOCK>(nb, s_scan, nbt) - nb;
         {
             int bp = excl, o = bexcl;
             for (int x = w0; x < w1; ++x) {
@@ -628,7 +690,7 @@ __global__ void __launch_bounds__(RT_BLOCK) k_range_sym(Items it, DenseWork dw) 
         int ne = 0;
         for (int i = i0; i < i1; ++i) ne += s_bp[i + 1] > s_bp[i];
         int net;
-        const int neexcl = group_incl_scan<RT_BLOCK>(ne, sc->scan, net) - ne;
+        const int neexcl = group_incl_scan<RT_BLOCK>(ne, s_scan, net) - ne;
         if (tid == 0) {
             unsigned long long base = net ? atomicAdd(dw.parts_ctr, (unsigned long long)net) : 0ull;
             const bool over = base + (unsigned long long)net > (unsigned long long)dw.parts_cap;
@@ -648,7 +710,8 @@ __global__ void __launch_bounds__(RT_BLOCK) k_range_sym(Items it, DenseWork dw) 
                     rp.d = d;
                     rp.q = q;
                     rp.r0 = (int32_t)(R0 + (int64_t)s_bw[i] * 32);
-                    rp.r1 = (int32_t)(R0 + (int64_t)s_bw[i + 1] * 32 < R1 ? R0 + (int64_t)s_bw[i + 1] * 32 : R1);
+                    const int64_t r1 = R0 + (int64_t)s_bw[i + 1] * 32;
+                    rp.r1 = (int32_t)(r1 < R1 ? r1 : R1);
                     rp.off = s_bp[i];
                     rp.nnz = s_bp[i + 1] - s_bp[i];
                     dw.parts[base + o] = rp;
@@ -667,6 +730,7 @@ __global__ void __launch_bounds__(RT_BLOCK) k_range_num(Items it, DenseWork dw, 
     using Acc = typename SR::Acc;
     using T = typename SR::T;
     constexpr int LOG2 = __builtin_ctz(TBL);
+    constexpr int NWARP = RT_BLOCK / 32;
     extern __shared__ __align__(16) unsigned char smem[];
     RangeSmem* sc = reinterpret_cast<RangeSmem*>(smem);
     int32_t* keys = reinterpret_cast<int32_t*>(smem + sizeof(RangeSmem));
@@ -675,8 +739,11 @@ __global__ void __launch_bounds__(RT_BLOCK) k_range_num(Items it, DenseWork dw, 
     // next row of A(:,k) at the cursor, for the first RT_NEXT k's: a range that ends at or
     // before it gets nothing from that k, which is then skipped without touching memory
     int32_t* s_next = reinterpret_cast<int32_t*>(bitmap + dw.WW);
+    // cursor state of the first RT_NEXT k's: position in A.ir and end of A(:,k)
+    int64_t* s_pos = reinterpret_cast<int64_t*>(s_next + RT_NEXT);
+    int64_t* s_end = s_pos + RT_NEXT;
     volatile int32_t* vkeys = keys;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t nsym = (int64_t)*dw.nitems;
     for (int x = tid; x < TBL; x += RT_BLOCK) {
         keys[x] = -1;
@@ -704,8 +771,13 @@ __global__ void __launch_bounds__(RT_BLOCK) k_range_num(Items it, DenseWork dw, 
             int64_t s, en;
             col_range(pr->A, k, s, en);
             const int32_t c0 = R0 == 0 ? 0 : lower_bound_rows(air + s, en - s, R0);
-            cur[t] = c0;
-            if (t < RT_NEXT) s_next[t] = s + c0 < en ? __ldg(air + s + c0) : INT_MAX;
+            if (t < RT_NEXT) {
+                s_pos[t] = s + c0;
+                s_end[t] = en;
+                s_next[t] = s + c0 < en ? __ldg(air + s + c0) : INT_MAX;
+            } else {
+                cur[t] = c0;
+            }
         }
         int64_t outbase = __ldg(Coff + u);
         for (int qq = 0; qq < q; ++qq) outbase += dw.part_count[(int64_t)qq * dw.ndense + d];
@@ -724,96 +796,176 @@ __global__ void __launch_bounds__(RT_BLOCK) k_range_num(Items it, DenseWork dw, 
                 int len = 0;
                 int64_t a = 0;
                 T bv = T(0);
-                if (t < deg && (t >= RT_NEXT || s_next[t] < r1)) {
-                    const int32_t k = __ldg(pr->B.ir + bs + t);
-                    int64_t s, en;
-                    col_range(pr->A, k, s, en);
-                    a = s + cur[t];
-                    const int64_t c = gallop_count(air, a, en, r1);
-                    cur[t] += (int32_t)c;
-                    len = (int)c;
-                    if (t < RT_NEXT) s_next[t] = a + c < en ? __ldg(air + a + c) : INT_MAX;
+                const bool act = t < deg && (t >= RT_NEXT || s_next[t] < r1);
+                if (act) {
                     bv = load_val<SR>(pr->B, bs + t);
-                }
-                int total;
-                const int incl = group_incl_scan<RT_BLOCK>(len, sc->scan, total);
-                sc->incl[tid] = incl;
-                sc->start[tid] = a;
-                reinterpret_cast<T*>(&sc->bv[tid])[0] = bv;
-                __syncthreads();
-                for (int x0 = tid & ~31; x0 < total; x0 += RT_BLOCK) {
-                    const int x = x0 + (tid & 31);
-                    int wd = -1;
-                    uint32_t bit = 0;
-                    int lo = 0;
-                    int64_t idx = 0;
-                    int32_t row = 0;
-                    if (x < total) {
-                        int hi = RT_BLOCK - 1;
-                        while (lo < hi) {
-                            int mid = (lo + hi) >> 1;
-                            if (sc->incl[mid] > x) hi = mid;
-                            else lo = mid + 1;
-                        }
-                        idx = sc->start[lo] + (x - (lo ? sc->incl[lo - 1] : 0));
-                        row = __ldg(air + idx);
-                        const int lr = (int)(row - r0);
-                        if ((unsigned)lr < (unsigned)(r1 - r0)) {   // fails only on malformed input
-                            wd = lr >> 5;
-                            bit = 1u << (lr & 31);
-                        }
-                    }
-                    or_bits_warp(bitmap, wd, bit);
-                    if (wd < 0) continue;
-                    uint32_t h;
-                    if (direct) {
-                        h = (uint32_t)(row - r0);   // narrow range: the table is a dense row array
+                    if (t < RT_NEXT) {
+                        a = s_pos[t];
+                        const int64_t en = s_end[t];
+                        const int64_t c = gallop_count(air, a, en, r1);
+                        s_pos[t] = a + c;
+                        s_next[t] = a + c < en ? __ldg(air + a + c) : INT_MAX;
+                        len = (int)c;
                     } else {
-                        h = hash_row(row) >> (32 - LOG2);
-                        while (true) {
-                            int32_t cu = vkeys[h];
-                            if (cu == row) break;
-                            if (cu == -1) {
-                                int32_t prev = atomicCAS(&keys[h], -1, row);
-                                if (prev == -1 || prev == row) break;
+                        const int32_t k = __ldg(pr->B.ir + bs + t);
+                        int64_t s, en;
+                        col_range(pr->A, k, s, en);
+                        a = s + cur[t];
+                        const int64_t c = gallop_count(air, a, en, r1);
+                        cur[t] += (int32_t)c;
+                        len = (int)c;
+                    }
+                }
+                int64_t bvbits = 0;
+                *reinterpret_cast<T*>(&bvbits) = bv;
+                int ns, Tn;
+                rt_compact(sc, act, len, a, bvbits, ns, Tn);
+                // warp slices of the products, 4 windows of 32 per step: owners first, then all
+                // loads, then the accumulations, so each warp keeps several loads in flight
+                {
+                    constexpr int U = 4;
+                    const int C = (Tn + NWARP * 32 - 1) / (NWARP * 32) * 32;
+                    const int xb = warp * C, xe = min(Tn, xb + C);
+                    if (xb < xe) {
+                        int lo = 0, hi = ns;
+                        while (lo < hi) {
+                            const int mid = (lo + hi) >> 1;
+                            if (sc->end[mid] <= xb) lo = mid + 1;
+                            else hi = mid;
+                        }
+                        int o0 = lo;
+                        for (int x0 = xb; x0 < xe; x0 += 32 * U) {
+                            int64_t idx[U];
+                            bool ok[U];
+                            int ob[U];
+#pragma unroll
+                            for (int uu = 0; uu < U; ++uu) {
+                                const int xw = x0 + 32 * uu;
+                                const int ej = o0 + lane < ns ? sc->end[o0 + lane] : INT_MAX;
+                                const unsigned bitv = (ej > xw && ej <= xw + 32) ? (1u << (ej - xw - 1)) : 0u;
+                                const unsigned mask = __reduce_or_sync(0xffffffffu, bitv);
+                                const int oi = o0 + __popc(mask & ((1u << lane) - 1u));
+                                const int pe0 = o0 > 0 ? sc->end[o0 - 1] : 0;
+                                const int src = oi - 1 - o0;
+                                const int pe = __shfl_sync(0xffffffffu, ej, src < 0 ? 0 : src);
+                                ok[uu] = xw + lane < xe;
+                                ob[uu] = oi;
+                                idx[uu] = ok[uu] ? sc->start[oi] + (xw + lane - (src < 0 ? pe0 : pe)) : 0;
+                                o0 += __popc(mask);
                             }
-                            h = (h + 1) & (TBL - 1);
+                            int32_t row[U];
+                            T av[U];
+#pragma unroll
+                            for (int uu = 0; uu < U; ++uu) {
+                                row[uu] = ok[uu] ? __ldg(air + idx[uu]) : 0;
+                                av[uu] = ok[uu] ? load_val<SR>(pr->A, idx[uu]) : T(0);
+                            }
+#pragma unroll
+                            for (int uu = 0; uu < U; ++uu) {
+                                if (!ok[uu]) continue;
+                                const int lr = (int)(row[uu] - r0);
+                                if ((unsigned)lr >= (unsigned)(r1 - r0)) continue;   // only on malformed input
+                                uint32_t h;
+                                if (direct) {
+                                    h = (uint32_t)lr;      // narrow range: the table is a dense row array,
+                                    keys[h] = row[uu];     // keys[] only marks occupancy
+                                } else {
+                                    h = hash_row(row[uu]) >> (32 - LOG2);
+                                    while (true) {
+                                        int32_t cu = vkeys[h];
+                                        if (cu == row[uu]) break;
+                                        if (cu == -1) {
+                                            int32_t prev = atomicCAS(&keys[h], -1, row[uu]);
+                                            if (prev == -1 || prev == row[uu]) break;
+                                        }
+                                        h = (h + 1) & (TBL - 1);
+                                    }
+                                }
+                                SR::atomic_add(&vals[h], SR::mul(av[uu], *reinterpret_cast<const T*>(&sc->bv[ob[uu]])));
+                            }
                         }
                     }
-                    SR::atomic_add(&vals[h], SR::mul(load_val<SR>(pr->A, idx),
-                                                     reinterpret_cast<const T*>(&sc->bv[lo])[0]));
                 }
                 __syncthreads();
             }
-            // read back in row order through the bitmap
-            const int wpt = (nw + RT_BLOCK - 1) / RT_BLOCK;
-            const int w0 = min(tid * wpt, nw), w1 = min(w0 + wpt, nw);
-            int cnt = 0;
-            for (int x = w0; x < w1; ++x) cnt += __popc(bitmap[x]);
-            int total;
-            const int excl = group_incl_scan<RT_BLOCK>(cnt, sc->scan, total) - cnt;
-            int64_t o = outbase + rp.off + excl;
-            for (int x = w0; x < w1; ++x) {
-                uint32_t bits = bitmap[x];
-                while (bits) {
-                    const int b = __ffs(bits) - 1;
-                    bits &= bits - 1;
-                    const int32_t row = (int32_t)(r0 + x * 32 + b);
-                    uint32_t h;
-                    if (direct) {
-                        h = (uint32_t)(x * 32 + b);
-                    } else {
-                        h = hash_row(row) >> (32 - LOG2);
-                        while (vkeys[h] != row) h = (h + 1) & (TBL - 1);
-                    }
-                    Cir[o] = row + rb;
-                    Cv[o] = SR::out(vals[h]);
-                    ++o;
-                    // every inserted row has its bit set, so this empties the table again;
-                    // lookups never stop at an empty slot, so clearing during reads is safe
-                    vals[h] = SR::zero();
-                    if (!direct) keys[h] = -1;
+            // the range's row bitmap, built once from the occupied table slots
+            if (direct) {
+                for (int wd = warp; wd < nw; wd += NWARP) {
+                    const unsigned occ = __ballot_sync(0xffffffffu, keys[wd * 32 + lane] != -1);
+                    if (lane == 0) bitmap[wd] = occ;
                 }
+            } else {
+                for (int x = tid; x < TBL; x += RT_BLOCK) {
+                    const int32_t kr = keys[x];
+                    if (kr != -1) {
+                        const int lr = (int)(kr - r0);
+                        atomicOr(&bitmap[lr >> 5], 1u << (lr & 31));
+                    }
+                }
+            }
+            __syncthreads();
+            // read back in row order: warp slices of the bitmap, coalesced stores
+            const int cw = (nw + NWARP * 32 - 1) / (NWARP * 32) * 32;
+            const int wb = min(warp * cw, nw), we = min(wb + cw, nw);
+            int cnt = 0;
+            for (int x = wb + lane; x < we; x += 32) cnt += __popc(bitmap[x]);
+            cnt = warp_sum(cnt);
+            if (lane == 0) sc->wc[warp] = cnt;
+            __syncthreads();
+            if (warp == 0) {
+                int v = lane < NWARP ? sc->wc[lane] : 0;
+                const int incl = warp_incl_scan(v);
+                if (lane < NWARP) sc->wc[lane] = incl - v;
+            }
+            __syncthreads();
+            int64_t o = outbase + rp.off + sc->wc[warp];
+            for (int x0 = wb; x0 < we; x0 += 32) {
+                const int x = x0 + lane;
+                const uint32_t word = x < we ? bitmap[x] : 0u;
+                const int pc = __popc(word);
+                const int incl = warp_incl_scan(pc);
+                const int tot = __shfl_sync(0xffffffffu, incl, 31);
+                for (int e0 = 0; e0 < tot; e0 += 32) {
+                    const int ee = e0 + lane;
+                    // lane j holding entry ee: smallest j with incl_j > ee
+                    int j = 0;
+#pragma unroll
+                    for (int s = 16; s >= 1; s >>= 1) {
+                        const int v = __shfl_sync(0xffffffffu, incl, j + s - 1);
+                        if (v <= ee) j += s;
+                    }
+                    j = j > 31 ? 31 : j;
+                    uint32_t wj = __shfl_sync(0xffffffffu, word, j);
+                    int rr = ee - (__shfl_sync(0xffffffffu, incl, j) - __popc(wj));
+                    if (ee < tot) {
+                        int pos = 0;
+#pragma unroll
+                        for (int s = 16; s >= 1; s >>= 1) {
+                            const int c = __popc(wj & ((1u << s) - 1u));
+                            if (rr >= c) {
+                                rr -= c;
+                                wj >>= s;
+                                pos += s;
+                            }
+                        }
+                        const int lr = (x0 + j) * 32 + pos;
+                        const int32_t row = (int32_t)(r0 + lr);
+                        uint32_t h;
+                        if (direct) {
+                            h = (uint32_t)lr;
+                        } else {
+                            h = hash_row(row) >> (32 - LOG2);
+                            while (vkeys[h] != row) h = (h + 1) & (TBL - 1);
+                        }
+                        Cir[o + ee] = row + rb;
+                        Cv[o + ee] = SR::out(vals[h]);
+                        // every inserted row has its bit set, so this empties the table again;
+                        // lookups never stop at an empty slot, so clearing during reads is safe
+                        vals[h] = SR::zero();
+                        keys[h] = -1;
+                    }
+                }
+                o += tot;
             }
             __syncthreads();
         }
@@ -827,6 +979,7 @@ static void run_range(cudaStream_t st, const Items& it, const DenseWork& dw, boo
     const int grid = (int)std::min<int64_t>(dw.ndense * MAX_PARTS, 152 * 8);
     if (!numeric) {
         const size_t smem = sizeof(RangeSmem) + 2 * (RT_MAXB + 1) * 4 + 16 + (size_t)(dw.RB / 32) * 4;
+        (void)0;
         static size_t attr = 0;
         if (attr < smem) {
             cudaFuncSetAttribute(k_range_sym, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -836,7 +989,7 @@ static void run_range(cudaStream_t st, const Items& it, const DenseWork& dw, boo
     } else {
         auto go = [&](auto kern, int tbl, size_t& attr) {
             const size_t smem = sizeof(RangeSmem) + (size_t)tbl * (4 + sizeof(typename SR::Acc)) + (size_t)(dw.WW) * 4 +
-                                (size_t)RT_NEXT * 4;
+                                (size_t)RT_NEXT * 20;
             if (attr < smem) {
                 cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
                 attr = smem;

@@ -37,7 +37,7 @@ struct TierCfg {
 // range holds < RANGE_TBL / 2 entries.
 constexpr int RANGE_TBL = 8192;
 constexpr int RANGE_H = RANGE_TBL / 2 - 32;   // cut a range once it holds this many entries
-constexpr int RANGE_W = 32768;                // and at most this many rows
+constexpr int RANGE_W = 65536;                // and at most this many rows
 
 struct RangePart {   // one numeric range of a slab
     int32_t d, q;    // dense-list position, slab
