@@ -39,6 +39,7 @@ UNIT = "GFLOPS"
 SCALE, EF, SEED = 18, 8, 0x1802
 GRID = 16
 L2_FLUSH_BYTES = 512 << 20
+CPU_STRIDE = 4   # oracle sample: every 4th output column (~25 core-seconds on the flat scale-18 product)
 
 
 def parse():
@@ -60,6 +61,34 @@ def parse():
 def flops_of(A) -> int:
     lens = np.diff(A.colptr)
     return int(lens[A.rowidx].sum())
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "kernels.cuh", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_1006_2183_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(scale: int):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary,
+    or None when the kernels changed since it was captured (or no capture exists)."""
+    path = os.path.join(ROOT, "profiles", f"k_range_num_pt64_rmat{scale}.md")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    for ln in open(path):
+        if ":" in ln and ln.startswith("- "):
+            k, v = ln[2:].split(":", 1)
+            kv[k.strip()] = v.strip().strip("`")
+    if kv.get("kernel source sha256/16") != kernel_source_hash():
+        return None
+    try:
+        return float(kv["dram bytes per launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 def peaks():
@@ -137,8 +166,8 @@ def run_reference(args, rank, world):
     import oracle
     A = gen.rmat(args.scale, EF, SEED, gen.PLUS_TIMES_F64)
     n = A.n
-    # bounded sample: every 16th output column of the flat plus-times FP64 product
-    cols = np.arange(0, n, 16)
+    # bounded sample: every 4th output column of the flat plus-times FP64 product
+    cols = np.arange(0, n, CPU_STRIDE)
     lens = np.diff(A.colptr)
     fl_cols = np.array([lens[A.rowidx[A.colptr[j]:A.colptr[j + 1]]].sum() for j in cols], np.int64)
     flops = int(fl_cols.sum())
@@ -152,7 +181,8 @@ def run_reference(args, rank, world):
             times.append(dt)
     tot = sum(times)
     value = 2.0 * flops * len(times) / tot / 1e9
-    sample = f"every 16th output column ({len(cols)} columns, {flops} flops) of the flat plus-times FP64 product"
+    sample = (f"every {CPU_STRIDE}th output column ({len(cols)} columns, {flops} flops) of the flat plus-times "
+              f"FP64 product")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -202,9 +232,11 @@ def main():
 
     def run_product(kind, sr, M):
         if kind == "flat":
+            ctx.timing_group(0)
             plan = sp.spgemm_plan(ctx, M, M, sr, lib_opts)
             C = sp.spgemm_numeric(plan)
             return C, plan
+        ctx.timing_group(1)
         C = sp.spgemm_summa_blocked(ctx, M, M, GRID, sr, lib_opts)
         return C, None
 
@@ -275,15 +307,16 @@ def main():
         plan = sp.spgemm_plan(ctx, mats[sp.PLUS_TIMES_F64], mats[sp.PLUS_TIMES_F64], sp.PLUS_TIMES_F64, lib_opts)
         sp.spgemm_symbolic(plan)
         ts = plan.tier_stats()
-        ms, cnt = phases[(sp.PLUS_TIMES_F64, "numeric_dense")]
+        ms, cnt = phases[(0, sp.PLUS_TIMES_F64, "numeric_dense")]
         if cnt:
             nnz_d, bnnz_d, cols_d = ts["nnz"][3], ts["bnnz"][3], ts["cols"][3]
             alg = nnz_d * 12 + bnnz_d * 12 + cols_d * 16 + A64.nnz * 12 + 8 * (A64.n + 1)
             per_launch_ms = ms / cnt
             ach = alg / (per_launch_ms / 1e3) / 1e9
             roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                    "traffic": None, "kernel": "k_dense<PT64,numeric>", "peak_kind": peak_kind,
-                    "alg_bytes_per_launch": alg, "ms_per_launch": per_launch_ms}
+                    "traffic": profiled_traffic(args.scale), "kernel": "k_range_num<PT64,4096>",
+                    "peak_kind": peak_kind, "alg_bytes_per_launch": alg, "ms_per_launch": per_launch_ms,
+                    "launches_timed": cnt}
         del plan
     # whole-product roofline on compulsory bytes (A read once, C written once)
     pipe = {}
@@ -291,8 +324,8 @@ def main():
         w = 8 if sr == sp.PLUS_TIMES_F64 else 4
         byt = (A64.n + 1) * 8 + A64.nnz * (4 + w) + (A64.n + 1) * 8 + nnz_seen[(kind, sr)] * (4 + w)
         pipe[f"{kind}_{'pt64' if w == 8 else 'mp32'}"] = {"compulsory_bytes": byt, "nnz_C": nnz_seen[(kind, sr)]}
-    phase_tab = {f"{'pt64' if s == 0 else 'mp32'}:{p}": round(v[0] / max(1, args.steps), 4)
-                 for (s, p), v in phases.items() if v[1]}
+    phase_tab = {f"{['flat', 'summa', 'g2', 'g3'][g]}:{'pt64' if s == 0 else 'mp32'}:{p}":
+                 round(v[0] / max(1, args.steps), 4) for (g, s, p), v in phases.items() if v[1]}
     byt_step = sum(v["compulsory_bytes"] for v in pipe.values())
     pipeline_frac = byt_step / (tot_ms / args.steps / 1e3) / 1e9 / hbm
 
@@ -339,15 +372,15 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
-        cols = np.arange(0, A64.n, 16)
+        cols = np.arange(0, A64.n, CPU_STRIDE)
         lens = np.diff(A64.colptr)
         fl = int(sum(lens[A64.rowidx[A64.colptr[j]:A64.colptr[j + 1]]].sum() for j in cols))
         t0 = time.perf_counter()
         oracle.spgemm_columns(A64, A64, oracle.PT_F64, cols)
         dt = time.perf_counter() - t0
         cpu = {"value": 2.0 * fl / dt / 1e9, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
-               "sample": f"every 16th output column ({len(cols)} columns, {fl} flops) of the flat "
-                         f"plus-times FP64 product, {dt:.2f} s"}
+               "sample": f"every {CPU_STRIDE}th output column ({len(cols)} columns, {fl} flops) of the flat "
+                         f"plus-times FP64 product, {dt:.2f} s wall on {oracle.max_threads()} threads"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

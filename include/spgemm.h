@@ -161,11 +161,16 @@ typedef enum {
     SPGEMM_PHASE_PREDICT = 6,        /* predictor inference + overflow repair           */
     SPGEMM_PHASE_MERGE = 7           /* SUMMA stage merge                               */
 } spgemm_phase_t;
+#define SPGEMM_NGROUP 4
 /* Enable (1) / disable (0) phase timing; enabling resets the accumulators. */
 spgemm_status_t spgemm_ctx_timing(spgemm_ctx_t ctx, int enable);
-/* Accumulated milliseconds and counts per (semiring, phase) since timing was
- * enabled (synchronises the stream).  ms and count each hold 4 * SPGEMM_NPHASE
- * entries, indexed [semiring * SPGEMM_NPHASE + phase]. */
+/* Label the phases timed from now on with a caller-chosen group in
+ * [0, SPGEMM_NGROUP) (e.g. one group per kind of product); default 0. */
+spgemm_status_t spgemm_ctx_timing_group(spgemm_ctx_t ctx, int group);
+/* Accumulated milliseconds and counts per (group, semiring, phase) since timing
+ * was enabled (synchronises the stream).  ms and count each hold
+ * SPGEMM_NGROUP * 4 * SPGEMM_NPHASE entries, indexed
+ * [(group * 4 + semiring) * SPGEMM_NPHASE + phase]. */
 spgemm_status_t spgemm_ctx_phase_ms(spgemm_ctx_t ctx, double* ms, int64_t* count);
 /* Number of kernels this library has launched in the process so far. */
 int64_t spgemm_launch_count(void);

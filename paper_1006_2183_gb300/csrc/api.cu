@@ -597,8 +597,8 @@ spgemm_status_t spgemm_plan_stats(spgemm_plan_t P, int64_t* flops, int64_t* nnz_
         tiers4[0] = E.bin_cnt[0];
         tiers4[1] = 0;
         tiers4[2] = 0;
-        for (int b = 1; b <= NWARP; ++b) tiers4[1] += E.bin_cnt[b];
-        for (int b = NWARP + 1; b <= NWARP + NBLK; ++b) tiers4[2] += E.bin_cnt[b];
+        for (int b = BIN_TINY; b < BIN_BLK0; ++b) tiers4[1] += E.bin_cnt[b];
+        for (int b = BIN_BLK0; b < BIN_DENSE; ++b) tiers4[2] += E.bin_cnt[b];
         tiers4[3] = E.bin_cnt[BIN_DENSE];
     }
     if (overflow) *overflow = E.overflow_items;
@@ -634,7 +634,7 @@ spgemm_status_t spgemm_ctx_timing(spgemm_ctx_t ctx, int enable) {
         cudaEventDestroy(pe.b);
     }
     ctx->pending.clear();
-    for (int i = 0; i < 4 * SPGEMM_NPHASE; ++i) {
+    for (int i = 0; i < SPGEMM_NGROUP * 4 * SPGEMM_NPHASE; ++i) {
         ctx->phase_ms[i] = 0;
         ctx->phase_cnt[i] = 0;
     }
@@ -654,7 +654,7 @@ spgemm_status_t spgemm_ctx_phase_ms(spgemm_ctx_t ctx, double* ms, int64_t* count
         cudaEventDestroy(pe.b);
     }
     ctx->pending.clear();
-    for (int i = 0; i < 4 * SPGEMM_NPHASE; ++i) {
+    for (int i = 0; i < SPGEMM_NGROUP * 4 * SPGEMM_NPHASE; ++i) {
         if (ms) ms[i] = ctx->phase_ms[i];
         if (count) count[i] = ctx->phase_cnt[i];
     }
@@ -662,6 +662,12 @@ spgemm_status_t spgemm_ctx_phase_ms(spgemm_ctx_t ctx, double* ms, int64_t* count
 }
 
 int64_t spgemm_launch_count(void) { return launches(); }
+
+spgemm_status_t spgemm_ctx_timing_group(spgemm_ctx_t ctx, int group) {
+    if (!ctx || group < 0 || group >= SPGEMM_NGROUP) return SPGEMM_ERR_INVALID_ARG;
+    ctx->group = group;
+    return SPGEMM_OK;
+}
 
 spgemm_status_t spgemm_plan_destroy(spgemm_plan_t P) {
     if (!P) return SPGEMM_ERR_INVALID_ARG;

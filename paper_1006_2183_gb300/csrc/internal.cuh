@@ -27,8 +27,9 @@ struct spgemm_ctx {
     bool timing = false;
     struct Pending { int slot; cudaEvent_t a, b; };
     std::vector<Pending> pending;
-    double phase_ms[4 * SPGEMM_NPHASE] = {0};
-    int64_t phase_cnt[4 * SPGEMM_NPHASE] = {0};
+    int group = 0;
+    double phase_ms[SPGEMM_NGROUP * 4 * SPGEMM_NPHASE] = {0};
+    int64_t phase_cnt[SPGEMM_NGROUP * 4 * SPGEMM_NPHASE] = {0};
     // statistics of the last SUMMA call
     std::vector<int64_t> summa_stage_flops;
     int64_t summa_nonempty = 0;
@@ -119,7 +120,7 @@ struct PhaseTimer {
     spgemm_ctx* ctx;
     int phase;
     cudaEvent_t a = nullptr;
-    PhaseTimer(spgemm_ctx* c, int ph, int sr) : ctx(c), phase(sr * SPGEMM_NPHASE + ph) {
+    PhaseTimer(spgemm_ctx* c, int ph, int sr) : ctx(c), phase((c->group * 4 + sr) * SPGEMM_NPHASE + ph) {
         if (ctx->timing) {
             cudaEventCreate(&a);
             cudaEventRecord(a, ctx->stream);

@@ -23,17 +23,18 @@ int64_t launches() { return g_launches.load(std::memory_order_relaxed); }
 
 constexpr int WARP_BLOCK = 256;   // 8 warp groups per CTA
 
-__host__ __device__ __forceinline__ int bin_of(int64_t cap, int warp_max, int block_max) {
+__host__ __device__ __forceinline__ int bin_of(int64_t flops, int64_t cap, int warp_max, int block_max) {
     if (cap <= 0) return 0;
+    if (flops <= TINY_MAX) return BIN_TINY;
     if (cap <= warp_max) {
         int64_t t = WARP_TBL0;
-        int b = 1;
+        int b = BIN_WARP0;
         while (t < 2 * cap) { t <<= 1; ++b; }
         return b;
     }
     if (cap <= block_max) {
         int64_t t = BLK_TBL0;
-        int b = 1 + NWARP;
+        int b = BIN_BLK0;
         while (t < 2 * cap) { t <<= 1; ++b; }
         return b;
     }
@@ -109,7 +110,7 @@ __global__ void __launch_bounds__(256) k_analyze(Items it, TierCfg cfg, int64_t*
         flops[u] = f;
         item_prod[u] = prod;
         int64_t cap = f < am ? f : am;
-        int b = bin_of(cap, cfg.warp_max, cfg.block_max);
+        int b = bin_of(f, cap, cfg.warp_max, cfg.block_max);
         bin[u] = (uint8_t)b;
         atomicAdd(&s_cnt[b], 1ull);
         atomicAdd(&s_fl, (unsigned long long)f);
@@ -403,17 +404,96 @@ static void run_hash(cudaStream_t st, const Items& it, const int2* list, int64_t
     note_launch();
 }
 
+// Tiny columns (flops <= TINY_MAX): one thread gathers the products in
+// registers, insertion-sorts them by row (stable, so equal rows keep ascending
+// k order), sums duplicates and writes the column.  No table, no barrier.
+template <class SR, bool NUM>
+__global__ void __launch_bounds__(256) k_tiny(Items it, const int2* __restrict__ list, int64_t count,
+                                              int64_t* __restrict__ nnz_item, const int64_t* __restrict__ Coff,
+                                              int32_t* __restrict__ Cir, typename SR::T* __restrict__ Cv) {
+    using Acc = typename SR::Acc;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < count; w += (int64_t)gridDim.x * blockDim.x) {
+        const int2 e = __ldg(list + w);
+        const Prod* pr = it.prods + e.x;
+        const int64_t u = __ldg(it.item_base + e.x) + e.y;
+        const int64_t bs = __ldg(pr->B.cp + e.y), be = __ldg(pr->B.cp + e.y + 1);
+        int32_t r[TINY_MAX];
+        Acc v[TINY_MAX];
+        int n = 0;
+        for (int64_t t = bs; t < be; ++t) {
+            const int32_t k = __ldg(pr->B.ir + t);
+            int64_t s0, en;
+            col_range(pr->A, k, s0, en);
+            typename SR::T bv = typename SR::T(0);
+            if constexpr (NUM) bv = load_val<SR>(pr->B, t);
+            for (int64_t q = s0; q < en && n < TINY_MAX; ++q) {
+                r[n] = __ldg(pr->A.ir + q);
+                if constexpr (NUM) v[n] = SR::mul(load_val<SR>(pr->A, q), bv);
+                ++n;
+            }
+        }
+        for (int i = 1; i < n; ++i) {
+            const int32_t key = r[i];
+            Acc val = NUM ? v[i] : Acc(0);
+            int j = i - 1;
+            while (j >= 0 && r[j] > key) {
+                r[j + 1] = r[j];
+                if constexpr (NUM) v[j + 1] = v[j];
+                --j;
+            }
+            r[j + 1] = key;
+            if constexpr (NUM) v[j + 1] = val;
+        }
+        int m = 0;
+        for (int i = 0; i < n; ++i) {
+            if (m > 0 && r[m - 1] == r[i]) {
+                if constexpr (NUM) v[m - 1] = SR::add(v[m - 1], v[i]);
+            } else {
+                r[m] = r[i];
+                if constexpr (NUM) v[m] = v[i];
+                ++m;
+            }
+        }
+        if constexpr (!NUM) {
+            nnz_item[u] = m;
+        } else {
+            // exact mode: Coff are exact offsets; predicted mode (nnz_item set): capacity offsets
+            const int64_t out0 = __ldg(Coff + u);
+            if (nnz_item) {
+                nnz_item[u] = m;
+                if (m > __ldg(Coff + u + 1) - out0) continue;   // overflow: redone in its exact place
+            }
+            const int32_t rb = pr->row_base;
+            for (int i = 0; i < m; ++i) {
+                Cir[out0 + i] = r[i] + rb;
+                Cv[out0 + i] = SR::out(v[i]);
+            }
+        }
+    }
+}
+
+template <class SR, bool NUM>
+static void run_tiny(cudaStream_t st, const Items& it, const int2* list, int64_t count, int64_t* nnz_item,
+                     const int64_t* Coff, int32_t* Cir, typename SR::T* Cv) {
+    if (count <= 0) return;
+    const int grid = (int)std::min<int64_t>(ceil_div64(count, 256), 152 * 16);
+    k_tiny<SR, NUM><<<grid, 256, 0, st>>>(it, list, count, nnz_item, Coff, Cir, Cv);
+    note_launch();
+}
+
 template <class SR, bool NUM>
 static void run_hash_bins(cudaStream_t st, const Items& it, const int2* list, const int64_t* off, const int64_t* cnt,
                           int64_t* nnz_item, const int64_t* Coff, int32_t* Cir, typename SR::T* Cv) {
-    run_hash<SR, 32, 64, NUM, WARP_BLOCK>(st, it, list + off[1], cnt[1], nnz_item, Coff, Cir, Cv);
-    run_hash<SR, 32, 128, NUM, WARP_BLOCK>(st, it, list + off[2], cnt[2], nnz_item, Coff, Cir, Cv);
-    run_hash<SR, 32, 256, NUM, WARP_BLOCK>(st, it, list + off[3], cnt[3], nnz_item, Coff, Cir, Cv);
-    run_hash<SR, 32, 512, NUM, WARP_BLOCK>(st, it, list + off[4], cnt[4], nnz_item, Coff, Cir, Cv);
-    run_hash<SR, 32, 1024, NUM, 128>(st, it, list + off[5], cnt[5], nnz_item, Coff, Cir, Cv);
-    run_hash<SR, 256, 2048, NUM, 256>(st, it, list + off[6], cnt[6], nnz_item, Coff, Cir, Cv);
-    run_hash<SR, 512, 4096, NUM, 512>(st, it, list + off[7], cnt[7], nnz_item, Coff, Cir, Cv);
-    run_hash<SR, 512, 8192, NUM, 512>(st, it, list + off[8], cnt[8], nnz_item, Coff, Cir, Cv);
+    constexpr int W0 = BIN_WARP0, B0 = BIN_BLK0;
+    run_tiny<SR, NUM>(st, it, list + off[BIN_TINY], cnt[BIN_TINY], nnz_item, Coff, Cir, Cv);
+    run_hash<SR, 32, 64, NUM, WARP_BLOCK>(st, it, list + off[W0], cnt[W0], nnz_item, Coff, Cir, Cv);
+    run_hash<SR, 32, 128, NUM, WARP_BLOCK>(st, it, list + off[W0 + 1], cnt[W0 + 1], nnz_item, Coff, Cir, Cv);
+    run_hash<SR, 32, 256, NUM, WARP_BLOCK>(st, it, list + off[W0 + 2], cnt[W0 + 2], nnz_item, Coff, Cir, Cv);
+    run_hash<SR, 32, 512, NUM, WARP_BLOCK>(st, it, list + off[W0 + 3], cnt[W0 + 3], nnz_item, Coff, Cir, Cv);
+    run_hash<SR, 32, 1024, NUM, 128>(st, it, list + off[W0 + 4], cnt[W0 + 4], nnz_item, Coff, Cir, Cv);
+    run_hash<SR, 256, 2048, NUM, 256>(st, it, list + off[B0], cnt[B0], nnz_item, Coff, Cir, Cv);
+    run_hash<SR, 512, 4096, NUM, 512>(st, it, list + off[B0 + 1], cnt[B0 + 1], nnz_item, Coff, Cir, Cv);
+    run_hash<SR, 512, 8192, NUM, 512>(st, it, list + off[B0 + 2], cnt[B0 + 2], nnz_item, Coff, Cir, Cv);
 }
 
 // ------------------------------------------------------------------ range tier (long columns)
@@ -1115,7 +1195,7 @@ __global__ void k_tier_stats(Items it, const uint8_t* __restrict__ bin, const in
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < it.nitems;
          u += (int64_t)gridDim.x * blockDim.x) {
         int b = bin[u];
-        int t = b == 0 ? 0 : (b <= NWARP ? 1 : (b < BIN_DENSE ? 2 : 3));
+        int t = b == 0 ? 0 : (b < BIN_BLK0 ? 1 : (b < BIN_DENSE ? 2 : 3));
         int prod = item_prod[u];
         const Prod* pr = it.prods + prod;
         int64_t p = u - __ldg(it.item_base + prod);

@@ -15,13 +15,18 @@ namespace sg {
 
 // Column tiers.  An item's capacity bound is cap = min(flops, m) >= nnz of its output.
 //   bin 0                  : cap == 0 (empty output column)
-//   bins 1 .. NWARP        : warp-wide hash tables of 64 .. 1024 slots (>= 2 cap)
-//   bins NWARP+1 .. +NBLK  : CTA-wide hash tables of 2048 .. 8192 slots (>= 2 cap)
-//   bin NBIN-1             : row-chunked dense accumulator, column split into parts
+//   bin 1                  : flops <= TINY_MAX: one thread, products sorted in registers
+//   bins 2 .. NWARP+1      : warp-wide hash tables of 64 .. 1024 slots (>= 2 cap)
+//   bins NWARP+2 .. +NBLK  : CTA-wide hash tables of 2048 .. 8192 slots (>= 2 cap)
+//   bin NBIN-1             : range tier (row slabs cut into ranges)
 constexpr int NWARP = 5;
 constexpr int NBLK = 3;
-constexpr int NBIN = 1 + NWARP + NBLK + 1;
+constexpr int NBIN = 2 + NWARP + NBLK + 1;
+constexpr int BIN_TINY = 1;
+constexpr int BIN_WARP0 = 2;
+constexpr int BIN_BLK0 = BIN_WARP0 + NWARP;
 constexpr int BIN_DENSE = NBIN - 1;
+constexpr int TINY_MAX = 16;
 constexpr int WARP_TBL0 = 64;
 constexpr int BLK_TBL0 = 2048;
 constexpr int MAX_PARTS = 16;

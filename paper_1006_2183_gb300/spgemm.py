@@ -26,6 +26,7 @@ NP_DTYPE = {PLUS_TIMES_F64: np.float64, MIN_PLUS_F32: np.float32, OR_AND_BOOL: n
 TYPESTR = {PLUS_TIMES_F64: "<f8", MIN_PLUS_F32: "<f4", OR_AND_BOOL: "|u1", PLUS_TIMES_I64: "<i8"}
 NPARAM = 1377
 NPHASE = 8
+NGROUP = 4
 PHASES = ["analyze", "symbolic_hash", "symbolic_dense", "scan", "numeric_hash", "numeric_dense", "predict", "merge"]
 STATUS = ["ok", "invalid argument", "dimension mismatch", "bad format", "out of memory", "index overflow",
           "timeout", "cuda error", "unsupported", "bad call order"]
@@ -93,6 +94,7 @@ _sig("spgemm_autotune", [P, ctypes.c_int, PP, PP, ctypes.c_int, ctypes.POINTER(O
 _sig("spgemm_colptr_noalloc", [P, I64, I64, I64, P, P, P, P, P])
 _sig("spgemm_ctx_timing", [P, ctypes.c_int])
 _sig("spgemm_ctx_phase_ms", [P, P, P])
+_sig("spgemm_ctx_timing_group", [P, ctypes.c_int])
 _sig("spgemm_launch_count", [], I64)
 _sig("spgemm_plan_tier_stats", [P, P, P, P, P])
 _sig("spgemm_predictor_set", [P, P])
@@ -185,12 +187,17 @@ class Context:
     def timing(self, enable: bool):
         self._check(_lib.spgemm_ctx_timing(self._h, int(enable)))
 
+    def timing_group(self, group: int):
+        self._check(_lib.spgemm_ctx_timing_group(self._h, group))
+
     def phase_ms(self) -> dict:
-        """{(semiring, phase name): (total ms, count)} since timing was enabled."""
-        ms = (ctypes.c_double * (4 * NPHASE))()
-        cnt = (I64 * (4 * NPHASE))()
+        """{(group, semiring, phase name): (total ms, count)} since timing was enabled."""
+        n = NGROUP * 4 * NPHASE
+        ms = (ctypes.c_double * n)()
+        cnt = (I64 * n)()
         self._check(_lib.spgemm_ctx_phase_ms(self._h, ms, cnt))
-        return {(sr, PHASES[i]): (ms[sr * NPHASE + i], cnt[sr * NPHASE + i]) for sr in range(4) for i in range(NPHASE)}
+        return {(g, sr, PHASES[i]): (ms[(g * 4 + sr) * NPHASE + i], cnt[(g * 4 + sr) * NPHASE + i])
+                for g in range(NGROUP) for sr in range(4) for i in range(NPHASE)}
 
     def close(self):
         if self._h:
