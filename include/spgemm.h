@@ -96,8 +96,8 @@ typedef struct {
                                  larger columns use row-chunked dense accumulators     */
     int dense_part_flops;     /* target flops per CTA when a dense column is split     */
     float predictor_margin;   /* capacity = (1 + margin) * prediction (+ slack)        */
-    int range_table_slots;    /* long columns: hash slots per row range, 4096 or 8192
-                                 (0 = default 4096); a range holds < slots/2 entries    */
+    int range_table_slots;    /* long columns: hash slots per row range, 2048, 4096 or
+                                 8192 (0 = default 4096); a range holds < slots/2 entries */
     int reserved[7];
 } spgemm_opts_t;
 

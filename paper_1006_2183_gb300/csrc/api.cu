@@ -353,6 +353,8 @@ spgemm_status_t engine_setup(Engine* E, spgemm_ctx* ctx, spgemm_semiring_t sr, c
     E->it.nprod = np;
     E->it.nitems = U;
     E->it.total_bnz = bnz;
+    E->it.max_m = 0;
+    for (auto& pr : E->hprods) E->it.max_m = std::max<int64_t>(E->it.max_m, pr.A.m);
     uint64_t* sketch = nullptr;
     int64_t* skbase = nullptr;
     PhaseTimer t_an(ctx, SPGEMM_PHASE_ANALYZE, sr);
@@ -416,7 +418,7 @@ spgemm_status_t engine_setup(Engine* E, spgemm_ctx* ctx, spgemm_semiring_t sr, c
         dw.pbase = (int64_t*)(db + o_pb);
         dw.pcnt = (int32_t*)(db + o_pn);
         dw.RB = E->cfg.dense_rows;
-        dw.tbl = opts.range_table_slots > 4096 ? 8192 : 4096;
+        dw.tbl = opts.range_table_slots > 4096 ? 8192 : (opts.range_table_slots > 0 && opts.range_table_slots <= 2048 ? 2048 : 4096);
         dw.H = dw.tbl / 2 - 32;
         launch_dense_items(st, E->it, dw.dlist, nd, E->flops, E->cfg.part_flops, dw.RB, E->ditems,
                            E->ctr + 2 * NBIN + 1, E->nparts);

@@ -25,6 +25,7 @@ struct spgemm_ctx {
     bool pred_ready = false;
     // phase timing (CUDA events on the context stream)
     bool timing = false;
+    int timing_quiet = 0;                // > 0: nested phases are not recorded (their parent is)
     struct Pending { int slot; cudaEvent_t a, b; };
     std::vector<Pending> pending;
     int group = 0;
@@ -121,7 +122,7 @@ struct PhaseTimer {
     int phase;
     cudaEvent_t a = nullptr;
     PhaseTimer(spgemm_ctx* c, int ph, int sr) : ctx(c), phase((c->group * 4 + sr) * SPGEMM_NPHASE + ph) {
-        if (ctx->timing) {
+        if (ctx->timing && ctx->timing_quiet == 0) {
             cudaEventCreate(&a);
             cudaEventRecord(a, ctx->stream);
         }

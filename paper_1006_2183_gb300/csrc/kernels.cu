@@ -235,10 +235,95 @@ __device__ __forceinline__ void bitonic_sort(int32_t* keys, Acc* vals, int P) {
     }
 }
 
+// Writes the rows marked in `bitmap` (nw words, bit b of word x = row row0 + 32x + b)
+// in ascending order with their values from the table, warp slices of the bitmap
+// per warp and coalesced stores, and empties the table and the bitmap behind it.
+// Called by all NW*32 threads of a CTA; returns the number of rows.  With
+// `pred`, nothing is written when the count exceeds capn.
+template <class SR, int TBL, int NW>
+__device__ __forceinline__ int bitmap_emit(uint32_t* bitmap, int nw, int64_t row0, int32_t* keys,
+                                           typename SR::Acc* vals, bool direct, bool pred, int64_t capn, int* wc,
+                                           int64_t outbase, int32_t rb, int32_t* __restrict__ Cir,
+                                           typename SR::T* __restrict__ Cv) {
+    constexpr int LOG2 = __builtin_ctz(TBL);
+    volatile int32_t* vkeys = keys;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int cw = (nw + NW * 32 - 1) / (NW * 32) * 32;
+    const int wb = min(warp * cw, nw), we = min(wb + cw, nw);
+    int cnt = 0;
+    for (int x = wb + lane; x < we; x += 32) cnt += __popc(bitmap[x]);
+    cnt = warp_sum(cnt);
+    if (lane == 0) wc[warp] = cnt;
+    __syncthreads();
+    if (warp == 0) {
+        int v = lane < NW ? wc[lane] : 0;
+        const int incl = warp_incl_scan(v);
+        if (lane < NW) wc[lane] = incl - v;
+        if (lane == NW - 1) wc[NW] = incl;
+    }
+    __syncthreads();
+    const int total = wc[NW];
+    const bool write = !pred || total <= capn;
+    int64_t o = outbase + wc[warp];
+    for (int x0 = wb; x0 < we; x0 += 32) {
+        const int x = x0 + lane;
+        const uint32_t word = x < we ? bitmap[x] : 0u;
+        const int pc = __popc(word);
+        const int incl = warp_incl_scan(pc);
+        const int tot = __shfl_sync(0xffffffffu, incl, 31);
+        for (int e0 = 0; e0 < tot; e0 += 32) {
+            const int ee = e0 + lane;
+            int j = 0;
+#pragma unroll
+            for (int s = 16; s >= 1; s >>= 1) {
+                const int v = __shfl_sync(0xffffffffu, incl, j + s - 1);
+                if (v <= ee) j += s;
+            }
+            j = j > 31 ? 31 : j;
+            uint32_t wj = __shfl_sync(0xffffffffu, word, j);
+            int rr = ee - (__shfl_sync(0xffffffffu, incl, j) - __popc(wj));
+            if (ee < tot) {
+                int pos = 0;
+#pragma unroll
+                for (int s = 16; s >= 1; s >>= 1) {
+                    const int c = __popc(wj & ((1u << s) - 1u));
+                    if (rr >= c) {
+                        rr -= c;
+                        wj >>= s;
+                        pos += s;
+                    }
+                }
+                const int lr = (x0 + j) * 32 + pos;
+                const int32_t row = (int32_t)(row0 + lr);
+                uint32_t h;
+                if (direct) {
+                    h = (uint32_t)lr;
+                } else {
+                    h = hash_row(row) >> (32 - LOG2);
+                    while (vkeys[h] != row) h = (h + 1) & (TBL - 1);
+                }
+                if (write) {
+                    Cir[o + ee] = row + rb;
+                    Cv[o + ee] = SR::out(vals[h]);
+                }
+                // every marked row is in the table; lookups never stop at an empty slot,
+                // so emptying slots while others still read is safe
+                vals[h] = SR::zero();
+                keys[h] = -1;
+            }
+        }
+        if (x < we) bitmap[x] = 0u;
+        o += tot;
+    }
+    __syncthreads();
+    return total;
+}
+
 template <class SR, int GS, int TBL, bool NUM, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_hash(Items it, const int2* __restrict__ list, int64_t count,
                                                 int64_t* __restrict__ nnz_item, const int64_t* __restrict__ Coff,
-                                                int32_t* __restrict__ Cir, typename SR::T* __restrict__ Cv) {
+                                                int32_t* __restrict__ Cir, typename SR::T* __restrict__ Cv,
+                                                int bm_words) {
     using T = typename SR::T;
     using Acc = typename SR::Acc;
     using L = HashLayout<SR, GS, TBL, NUM>;
@@ -257,6 +342,13 @@ __global__ void __launch_bounds__(BLOCK) k_hash(Items it, const int2* __restrict
     int* s_scan = reinterpret_cast<int*>(base + L::keys + L::vals + L::incl + L::a0 + L::bv);
     int* s_cnt = s_scan + 33;
     volatile int32_t* vkeys = keys;
+    // CTA-wide numeric tables order their output through a row bitmap when the rows fit
+    uint32_t* bitmap = reinterpret_cast<uint32_t*>(smem + (size_t)NG * L::group);
+    constexpr bool CAN_BM = NUM && GS == BLOCK && GS > 32;
+    if constexpr (CAN_BM) {
+        for (int x = threadIdx.x; x < bm_words; x += BLOCK) bitmap[x] = 0u;
+        __syncthreads();
+    }
 
     for (int64_t w = (int64_t)blockIdx.x * NG + g; w < count; w += (int64_t)gridDim.x * NG) {
         const int2 e = __ldg(list + w);
@@ -330,6 +422,21 @@ __global__ void __launch_bounds__(BLOCK) k_hash(Items it, const int2* __restrict
             const int64_t out0 = __ldg(Coff + u);
             const int64_t capn = __ldg(Coff + u + 1) - out0;
             const int32_t rb = pr->row_base;
+            if constexpr (CAN_BM) {
+                if (bm_words > 0) {
+                    const int nwc = (int)((pr->A.m + 31) >> 5);
+                    for (int s = threadIdx.x; s < TBL; s += BLOCK) {
+                        const int32_t kr = keys[s];
+                        if (kr >= 0 && (kr >> 5) < nwc) atomicOr(&bitmap[kr >> 5], 1u << (kr & 31));
+                    }
+                    __syncthreads();
+                    const int total = bitmap_emit<SR, TBL, BLOCK / 32>(bitmap, nwc, 0, keys, vals, false,
+                                                                        nnz_item != nullptr, capn, s_scan, out0, rb,
+                                                                        Cir, Cv);
+                    if (nnz_item && threadIdx.x == 0) nnz_item[u] = total;
+                    continue;
+                }
+            }
             // in-place compaction toward the front: the i-th occupied slot moves to i <= its slot.
             // Each lane holds a contiguous run of S slots in registers; rounds go up the table, and
             // every destination lies below the slots of later rounds, so nothing unread is overwritten.
@@ -391,16 +498,18 @@ static void run_hash(cudaStream_t st, const Items& it, const int2* list, int64_t
     if (count <= 0) return;
     using L = HashLayout<SR, GS, TBL, NUM>;
     constexpr int NG = BLOCK / GS;
-    size_t smem = L::group * NG;
+    constexpr bool CAN_BM = NUM && GS == BLOCK && GS > 32;
+    const int bm_words = CAN_BM && it.max_m > 0 && it.max_m <= BM_MAX_ROWS ? (int)((it.max_m + 31) / 32) : 0;
+    size_t smem = L::group * NG + (size_t)bm_words * 4;
     auto kern = k_hash<SR, GS, TBL, NUM, BLOCK>;
-    static bool attr_done = false;   // one attribute call per instantiation
-    if (!attr_done) {
+    static size_t attr_done = 0;
+    if (attr_done < smem) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr_done = true;
+        attr_done = smem;
     }
     int64_t want = ceil_div64(count, NG);
     int grid = (int)std::min<int64_t>(want, 152 * 32);
-    kern<<<grid, BLOCK, smem, st>>>(it, list, count, nnz_item, Coff, Cir, Cv);
+    kern<<<grid, BLOCK, smem, st>>>(it, list, count, nnz_item, Coff, Cir, Cv, bm_words);
     note_launch();
 }
 
@@ -509,7 +618,7 @@ static void run_hash_bins(cudaStream_t st, const Items& it, const int2* list, co
 // range is written already sorted.
 constexpr int RT_BLOCK = 512;
 constexpr int RT_MAXB = 1024;
-constexpr int RT_NEXT = 1024;   // k's per column whose cursor state lives in shared memory
+constexpr int RT_NEXT = 512;    // k's per column whose cursor state lives in shared memory
 
 __device__ __forceinline__ int32_t lower_bound_rows(const int32_t* __restrict__ r, int64_t len, int64_t v) {
     int64_t lo = 0, hi = len;
@@ -819,9 +928,9 @@ __global__ void __launch_bounds__(RT_BLOCK) k_range_num(Items it, DenseWork dw, 
     // next row of A(:,k) at the cursor, for the first RT_NEXT k's: a range that ends at or
     // before it gets nothing from that k, which is then skipped without touching memory
     int32_t* s_next = reinterpret_cast<int32_t*>(bitmap + dw.WW);
-    // cursor state of the first RT_NEXT k's: position in A.ir and end of A(:,k)
-    int64_t* s_pos = reinterpret_cast<int64_t*>(s_next + RT_NEXT);
-    int64_t* s_end = s_pos + RT_NEXT;
+    // cursor state of the first RT_NEXT k's: position in A.ir and entries left in A(:,k)
+    int32_t* s_rem = s_next + RT_NEXT;
+    int64_t* s_pos = reinterpret_cast<int64_t*>(s_rem + RT_NEXT);
     volatile int32_t* vkeys = keys;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t nsym = (int64_t)*dw.nitems;
@@ -853,7 +962,7 @@ __global__ void __launch_bounds__(RT_BLOCK) k_range_num(Items it, DenseWork dw, 
             const int32_t c0 = R0 == 0 ? 0 : lower_bound_rows(air + s, en - s, R0);
             if (t < RT_NEXT) {
                 s_pos[t] = s + c0;
-                s_end[t] = en;
+                s_rem[t] = (int32_t)(en - s - c0);
                 s_next[t] = s + c0 < en ? __ldg(air + s + c0) : INT_MAX;
             } else {
                 cur[t] = c0;
@@ -881,9 +990,10 @@ __global__ void __launch_bounds__(RT_BLOCK) k_range_num(Items it, DenseWork dw, 
                     bv = load_val<SR>(pr->B, bs + t);
                     if (t < RT_NEXT) {
                         a = s_pos[t];
-                        const int64_t en = s_end[t];
+                        const int64_t en = a + s_rem[t];
                         const int64_t c = gallop_count(air, a, en, r1);
                         s_pos[t] = a + c;
+                        s_rem[t] -= (int32_t)c;
                         s_next[t] = a + c < en ? __ldg(air + a + c) : INT_MAX;
                         len = (int)c;
                     } else {
@@ -1069,15 +1179,16 @@ static void run_range(cudaStream_t st, const Items& it, const DenseWork& dw, boo
     } else {
         auto go = [&](auto kern, int tbl, size_t& attr) {
             const size_t smem = sizeof(RangeSmem) + (size_t)tbl * (4 + sizeof(typename SR::Acc)) + (size_t)(dw.WW) * 4 +
-                                (size_t)RT_NEXT * 20;
+                                (size_t)RT_NEXT * 16;
             if (attr < smem) {
                 cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
                 attr = smem;
             }
             kern<<<grid, RT_BLOCK, smem, st>>>(it, dw, Coff, Cir, Cv);
         };
-        static size_t attr4 = 0, attr8 = 0;
-        if (dw.tbl <= 4096) go(k_range_num<SR, 4096>, 4096, attr4);
+        static size_t attr2 = 0, attr4 = 0, attr8 = 0;
+        if (dw.tbl <= 2048) go(k_range_num<SR, 2048>, 2048, attr2);
+        else if (dw.tbl <= 4096) go(k_range_num<SR, 4096>, 4096, attr4);
         else go(k_range_num<SR, 8192>, 8192, attr8);
     }
     note_launch();

@@ -77,7 +77,12 @@ struct Items {
     int64_t nprod = 0;
     int64_t nitems = 0;
     int64_t total_bnz = 0;              // sum of nnz(B_i): cursor stride per dense part
+    int64_t max_m = 0;                  // most rows of any A_i
 };
+
+// CTA-wide hash tables order their numeric output through a shared-memory row
+// bitmap (instead of sorting) when every A_i has at most this many rows.
+constexpr int64_t BM_MAX_ROWS = 262144;
 
 // flops and bin per item, product id per item, bin counts and total flops.
 // With feat != nullptr also the 8 predictor inputs per item; `sketch` holds the
