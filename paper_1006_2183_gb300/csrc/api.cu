@@ -328,6 +328,10 @@ spgemm_status_t engine_setup(Engine* E, spgemm_ctx* ctx, spgemm_semiring_t sr, c
     size_t o_list = take(sizeof(int2) * U1);
     size_t o_nnz = take(8 * U1);
     size_t o_scan = take(scan_tmp_bytes(U1));
+    size_t o_nbin = take(U1);
+    size_t o_nlist = take(sizeof(int2) * U1);
+    size_t o_nctr = take(8 * 2 * NBIN);
+    size_t o_nbinoff = take(8 * NBIN);
     size_t o_feat = want_features ? take(32 * U1) : 0;
     size_t o_sk = want_features ? take(8 * std::max<int64_t>(amax_n, 1)) : 0;
     size_t o_skb = want_features ? take(8 * (np + 1)) : 0;
@@ -346,6 +350,11 @@ spgemm_status_t engine_setup(Engine* E, spgemm_ctx* ctx, spgemm_semiring_t sr, c
     E->list = (int2*)(base + o_list);
     E->nnz_item = (int64_t*)(base + o_nnz);
     E->scan_tmp = base + o_scan;
+    E->nbin = (uint8_t*)(base + o_nbin);
+    E->nlist = (int2*)(base + o_nlist);
+    E->nctr = (unsigned long long*)(base + o_nctr);
+    E->nbin_off_dev = (int64_t*)(base + o_nbinoff);
+    E->numeric_bins = false;
     SG_CUDA(ctx, cudaMemcpyAsync(dprods, E->hprods.data(), sizeof(Prod) * np, cudaMemcpyHostToDevice, st));
     SG_CUDA(ctx, cudaMemcpyAsync(dbase, E->hitem_base.data(), 8 * (np + 1), cudaMemcpyHostToDevice, st));
     E->it.prods = dprods;
@@ -448,8 +457,9 @@ template <class SR>
 static void dispatch_numeric(Engine* E, int32_t* Cir, void* Cv) {
     for (int which = 1; which <= 2; ++which) {
         PhaseTimer t(E->ctx, which == 1 ? SPGEMM_PHASE_NUMERIC_HASH : SPGEMM_PHASE_NUMERIC_DENSE, E->sr);
-        launch_numeric<SR>(E->ctx->stream, E->it, E->cfg, E->list, E->bin_off, E->bin_cnt, E->dw, E->Coff, Cir,
-                           (typename SR::T*)Cv, which);
+        const bool nb = which == 1 && E->numeric_bins;
+        launch_numeric<SR>(E->ctx->stream, E->it, E->cfg, nb ? E->nlist : E->list, nb ? E->nbin_off : E->bin_off,
+                           nb ? E->nbin_cnt : E->bin_cnt, E->dw, E->Coff, Cir, (typename SR::T*)Cv, which);
     }
 }
 
@@ -476,11 +486,30 @@ spgemm_status_t engine_symbolic(Engine* E) {
     }
     int64_t nnz = 0;
     int err = 0;
+    unsigned long long nc[NBIN];
+    {
+        PhaseTimer t(ctx, SPGEMM_PHASE_SCAN, E->sr);
+        SG_CUDA(ctx, cudaMemsetAsync(E->nctr, 0, 8 * 2 * NBIN, st));
+        launch_numeric_bins(st, E->it, E->cfg, E->bin, E->flops, E->nnz_item, E->nbin, E->nctr);
+    }
+    SG_CUDA(ctx, cudaMemcpyAsync(nc, E->nctr, sizeof(nc), cudaMemcpyDeviceToHost, st));
     SG_CUDA(ctx, cudaMemcpyAsync(&nnz, E->Coff + U, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     SG_CUDA(ctx, cudaMemcpyAsync(&err, E->ctr + 2 * NBIN + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
     SG_TRY(sync_ctx(ctx));
     if (err) return set_err(ctx, SPGEMM_ERR_INDEX_OVERFLOW, "range tier capacity exceeded (code %d)", err);
     E->nnz_total = nnz;
+    int64_t acc = 0;
+    for (int b = 0; b < NBIN; ++b) {
+        E->nbin_cnt[b] = (int64_t)nc[b];
+        E->nbin_off[b] = acc;
+        acc += E->nbin_cnt[b];
+    }
+    {
+        PhaseTimer t(ctx, SPGEMM_PHASE_SCAN, E->sr);
+        SG_CUDA(ctx, cudaMemcpyAsync(E->nbin_off_dev, E->nbin_off, sizeof(int64_t) * NBIN, cudaMemcpyHostToDevice, st));
+        launch_bin_scatter(st, E->it, E->nbin, E->item_prod, E->nbin_off_dev, E->nctr + NBIN, E->nlist);
+    }
+    E->numeric_bins = true;
     E->symbolic_done = true;
     return SPGEMM_OK;
 }

@@ -102,8 +102,12 @@ spgemm_status_t batch_plan_build(spgemm_ctx* ctx, int count, const spgemm_mat_t*
 template <class SR>
 void numeric_launches(struct spgemm_plan* P) {
     Engine& E = P->E;
+    const bool nb = E.numeric_bins;   // hash tiers binned by exact counts
+    launch_numeric<SR>(P->ctx->stream, E.it, E.cfg, nb ? E.nlist : E.list, nb ? E.nbin_off : E.bin_off,
+                       nb ? E.nbin_cnt : E.bin_cnt, E.dw, E.Coff, (int32_t*)P->out_r->p,
+                       (typename SR::T*)P->out_v->p, 1);
     launch_numeric<SR>(P->ctx->stream, E.it, E.cfg, E.list, E.bin_off, E.bin_cnt, E.dw, E.Coff,
-                       (int32_t*)P->out_r->p, (typename SR::T*)P->out_v->p, 3);
+                       (int32_t*)P->out_r->p, (typename SR::T*)P->out_v->p, 2);
 }
 
 void all_numeric_launches(struct spgemm_plan* P) {

@@ -92,8 +92,18 @@ struct Prod {
     int32_t G = 0;           // row slabs a long column needs at least: ceil(A.m / RB)
     int64_t col_base = 0;    // global column of B's column 0 (2D blocks)
     int32_t tag = 0;         // caller's label (SUMMA: the stage)
-    int32_t pad = 0;
+    int32_t blk = 0;         // caller's second label (SUMMA: the block row)
+    int32_t rb_cycle = 0;    // > 0: item p's rows also get (p mod rb_cycle) * rb_step
+    int32_t rb_step = 0;
 };
+
+// Offset added to the output rows of column p of a product: row_base, plus
+// (p mod rb_cycle) * rb_step when B's columns interleave row blocks (the SUMMA
+// merge numbers its output columns j * g + I for row block I).
+__device__ __forceinline__ int32_t out_row_base(const Prod* pr, int64_t p) {
+    const int32_t c = pr->rb_cycle;
+    return pr->row_base + (c > 0 ? (int32_t)(p % c) * pr->rb_step : 0);
+}
 
 template <class SR>
 __device__ __forceinline__ typename SR::T load_val(const DMat& M, int64_t idx) {

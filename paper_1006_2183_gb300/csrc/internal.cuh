@@ -91,6 +91,14 @@ struct Engine {
     int64_t* Coff = nullptr;
     int64_t bin_cnt[sg::NBIN] = {0};
     int64_t bin_off[sg::NBIN] = {0};
+    // numeric lists of the hash tiers, binned by exact counts (set by the symbolic pass)
+    uint8_t* nbin = nullptr;
+    int2* nlist = nullptr;
+    unsigned long long* nctr = nullptr;   // count[NBIN], cursor[NBIN]
+    int64_t* nbin_off_dev = nullptr;
+    int64_t nbin_cnt[sg::NBIN] = {0};
+    int64_t nbin_off[sg::NBIN] = {0};
+    bool numeric_bins = false;
     int64_t flops_total = 0;
     int64_t nnz_total = -1;
     bool symbolic_done = false;

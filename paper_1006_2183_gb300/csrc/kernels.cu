@@ -171,6 +171,35 @@ void launch_row_sketch(cudaStream_t st, const DMat& A, uint64_t* sketch) {
     note_launch();
 }
 
+// Numeric bins of the hash-tier items from their exact counts: the table needs
+// only 2 nnz slots, not 2 min(flops, m).  Range-tier and empty items get bin 0
+// (not listed).
+__global__ void k_numeric_bins(Items it, TierCfg cfg, const uint8_t* __restrict__ bin,
+                               const int64_t* __restrict__ flops, const int64_t* __restrict__ nnz_item,
+                               uint8_t* __restrict__ nbin, unsigned long long* __restrict__ cnt) {
+    __shared__ unsigned long long s_cnt[NBIN];
+    for (int b = threadIdx.x; b < NBIN; b += blockDim.x) s_cnt[b] = 0;
+    __syncthreads();
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < it.nitems; u += (int64_t)gridDim.x * blockDim.x) {
+        const int b = bin[u];
+        int nb = 0;
+        if (b >= BIN_TINY && b < BIN_DENSE) nb = bin_of(flops[u], nnz_item[u], cfg.warp_max, cfg.block_max);
+        nbin[u] = (uint8_t)nb;
+        if (nb) atomicAdd(&s_cnt[nb], 1ull);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < NBIN; b += blockDim.x)
+        if (s_cnt[b]) atomicAdd(cnt + b, s_cnt[b]);
+}
+
+void launch_numeric_bins(cudaStream_t st, const Items& it, TierCfg cfg, const uint8_t* bin, const int64_t* flops,
+                         const int64_t* nnz_item, uint8_t* nbin, unsigned long long* cnt) {
+    if (it.nitems == 0) return;
+    const int grid = (int)std::min<int64_t>(ceil_div64(it.nitems, 256), 152 * 8);
+    k_numeric_bins<<<grid, 256, 0, st>>>(it, cfg, bin, flops, nnz_item, nbin, cnt);
+    note_launch();
+}
+
 // Scatter of items into per-bin lists (warp-aggregated atomics).
 __global__ void k_bin_scatter(Items it, const uint8_t* __restrict__ bin, const int32_t* __restrict__ item_prod,
                               const int64_t* __restrict__ bin_off, unsigned long long* cursor, int2* __restrict__ list) {
@@ -238,8 +267,9 @@ __device__ __forceinline__ void bitonic_sort(int32_t* keys, Acc* vals, int P) {
 // Writes the rows marked in `bitmap` (nw words, bit b of word x = row row0 + 32x + b)
 // in ascending order with their values from the table, warp slices of the bitmap
 // per warp and coalesced stores, and empties the table and the bitmap behind it.
-// Called by all NW*32 threads of a CTA; returns the number of rows.  With
-// `pred`, nothing is written when the count exceeds capn.
+// Called by all NW*32 threads of a CTA (NW > 1) or by one warp (NW == 1);
+// returns the number of rows.  With `pred`, nothing is written when the count
+// exceeds capn.
 template <class SR, int TBL, int NW>
 __device__ __forceinline__ int bitmap_emit(uint32_t* bitmap, int nw, int64_t row0, int32_t* keys,
                                            typename SR::Acc* vals, bool direct, bool pred, int64_t capn, int* wc,
@@ -247,24 +277,31 @@ __device__ __forceinline__ int bitmap_emit(uint32_t* bitmap, int nw, int64_t row
                                            typename SR::T* __restrict__ Cv) {
     constexpr int LOG2 = __builtin_ctz(TBL);
     volatile int32_t* vkeys = keys;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = NW == 1 ? 0 : threadIdx.x >> 5;
     const int cw = (nw + NW * 32 - 1) / (NW * 32) * 32;
     const int wb = min(warp * cw, nw), we = min(wb + cw, nw);
     int cnt = 0;
     for (int x = wb + lane; x < we; x += 32) cnt += __popc(bitmap[x]);
     cnt = warp_sum(cnt);
-    if (lane == 0) wc[warp] = cnt;
-    __syncthreads();
-    if (warp == 0) {
-        int v = lane < NW ? wc[lane] : 0;
-        const int incl = warp_incl_scan(v);
-        if (lane < NW) wc[lane] = incl - v;
-        if (lane == NW - 1) wc[NW] = incl;
+    int total, first;
+    if constexpr (NW == 1) {
+        total = cnt;
+        first = 0;
+    } else {
+        if (lane == 0) wc[warp] = cnt;
+        __syncthreads();
+        if (warp == 0) {
+            int v = lane < NW ? wc[lane] : 0;
+            const int incl = warp_incl_scan(v);
+            if (lane < NW) wc[lane] = incl - v;
+            if (lane == NW - 1) wc[NW] = incl;
+        }
+        __syncthreads();
+        total = wc[NW];
+        first = wc[warp];
     }
-    __syncthreads();
-    const int total = wc[NW];
     const bool write = !pred || total <= capn;
-    int64_t o = outbase + wc[warp];
+    int64_t o = outbase + first;
     for (int x0 = wb; x0 < we; x0 += 32) {
         const int x = x0 + lane;
         const uint32_t word = x < we ? bitmap[x] : 0u;
@@ -315,7 +352,8 @@ __device__ __forceinline__ int bitmap_emit(uint32_t* bitmap, int nw, int64_t row
         if (x < we) bitmap[x] = 0u;
         o += tot;
     }
-    __syncthreads();
+    if constexpr (NW == 1) __syncwarp();
+    else __syncthreads();
     return total;
 }
 
@@ -342,12 +380,13 @@ __global__ void __launch_bounds__(BLOCK) k_hash(Items it, const int2* __restrict
     int* s_scan = reinterpret_cast<int*>(base + L::keys + L::vals + L::incl + L::a0 + L::bv);
     int* s_cnt = s_scan + 33;
     volatile int32_t* vkeys = keys;
-    // CTA-wide numeric tables order their output through a row bitmap when the rows fit
-    uint32_t* bitmap = reinterpret_cast<uint32_t*>(smem + (size_t)NG * L::group);
-    constexpr bool CAN_BM = NUM && GS == BLOCK && GS > 32;
+    // Numeric tables order their output through a row bitmap (one per group) when
+    // the rows fit; otherwise they compact and sort.
+    uint32_t* bitmap = reinterpret_cast<uint32_t*>(smem + (size_t)NG * L::group) + (size_t)g * bm_words;
+    constexpr bool CAN_BM = NUM && (GS == BLOCK || GS == 32);
     if constexpr (CAN_BM) {
-        for (int x = threadIdx.x; x < bm_words; x += BLOCK) bitmap[x] = 0u;
-        __syncthreads();
+        for (int x = lane; x < bm_words; x += GS) bitmap[x] = 0u;
+        G::sync();
     }
 
     for (int64_t w = (int64_t)blockIdx.x * NG + g; w < count; w += (int64_t)gridDim.x * NG) {
@@ -382,27 +421,46 @@ __global__ void __launch_bounds__(BLOCK) k_hash(Items it, const int2* __restrict
             if constexpr (NUM) s_bv[lane] = bv;
             G::sync();
             const int32_t* __restrict__ air = pr->A.ir;
-            for (int q = lane; q < total; q += GS) {
-                int lo = 0, hi = GS - 1;
-                while (lo < hi) {
-                    int mid = (lo + hi) >> 1;
-                    if (s_incl[mid] > q) hi = mid;
-                    else lo = mid + 1;
-                }
-                const int64_t idx = s_a0[lo] + (q - (lo ? s_incl[lo - 1] : 0));
-                const int32_t row = __ldg(air + idx);
-                uint32_t h = hash_row(row) >> (32 - LOG2);
-                while (true) {
-                    int32_t cur = vkeys[h];
-                    if (cur == row) break;
-                    if (cur == -1) {
-                        int32_t prev = atomicCAS(&keys[h], -1, row);
-                        if (prev == -1) { ++mycnt; break; }
-                        if (prev == row) break;
+            // U products per lane per round: their loads are all issued before the first insert
+            constexpr int U = 4;
+            for (int q0 = 0; q0 < total; q0 += GS * U) {
+                int32_t row[U];
+                T av[U];
+                int seg[U];
+#pragma unroll
+                for (int i = 0; i < U; ++i) {
+                    const int q = q0 + i * GS + lane;
+                    row[i] = -1;
+                    if (q < total) {
+                        int lo = 0, hi = GS - 1;
+                        while (lo < hi) {
+                            int mid = (lo + hi) >> 1;
+                            if (s_incl[mid] > q) hi = mid;
+                            else lo = mid + 1;
+                        }
+                        const int64_t idx = s_a0[lo] + (q - (lo ? s_incl[lo - 1] : 0));
+                        row[i] = __ldg(air + idx);
+                        if constexpr (NUM) av[i] = load_val<SR>(pr->A, idx);
+                        seg[i] = lo;
                     }
-                    h = (h + 1) & (TBL - 1);
                 }
-                if constexpr (NUM) SR::atomic_add(&vals[h], SR::mul(load_val<SR>(pr->A, idx), s_bv[lo]));
+#pragma unroll
+                for (int i = 0; i < U; ++i) {
+                    if (row[i] < 0) continue;
+                    const int32_t r = row[i];
+                    uint32_t h = hash_row(r) >> (32 - LOG2);
+                    while (true) {
+                        int32_t cur = vkeys[h];
+                        if (cur == r) break;
+                        if (cur == -1) {
+                            int32_t prev = atomicCAS(&keys[h], -1, r);
+                            if (prev == -1) { ++mycnt; break; }
+                            if (prev == r) break;
+                        }
+                        h = (h + 1) & (TBL - 1);
+                    }
+                    if constexpr (NUM) SR::atomic_add(&vals[h], SR::mul(av[i], s_bv[seg[i]]));
+                }
             }
             G::sync();
         }
@@ -421,19 +479,22 @@ __global__ void __launch_bounds__(BLOCK) k_hash(Items it, const int2* __restrict
             // capacity offsets; the exact count is recorded and the column is written only if it fits.
             const int64_t out0 = __ldg(Coff + u);
             const int64_t capn = __ldg(Coff + u + 1) - out0;
-            const int32_t rb = pr->row_base;
+            const int32_t rb = out_row_base(pr, e.y);
             if constexpr (CAN_BM) {
-                if (bm_words > 0) {
-                    const int nwc = (int)((pr->A.m + 31) >> 5);
-                    for (int s = threadIdx.x; s < TBL; s += BLOCK) {
+                const int nwc = (int)((pr->A.m + 31) >> 5);
+                // a warp prefers the bitmap once sorting the entries would cost more than scanning it
+                bool use_bm = bm_words > 0;
+                if constexpr (GS == 32) use_bm = use_bm && nwc <= 8 * warp_sum(mycnt);
+                if (use_bm) {
+                    for (int s = lane; s < TBL; s += GS) {
                         const int32_t kr = keys[s];
                         if (kr >= 0 && (kr >> 5) < nwc) atomicOr(&bitmap[kr >> 5], 1u << (kr & 31));
                     }
-                    __syncthreads();
-                    const int total = bitmap_emit<SR, TBL, BLOCK / 32>(bitmap, nwc, 0, keys, vals, false,
-                                                                        nnz_item != nullptr, capn, s_scan, out0, rb,
-                                                                        Cir, Cv);
-                    if (nnz_item && threadIdx.x == 0) nnz_item[u] = total;
+                    G::sync();
+                    const int total = bitmap_emit<SR, TBL, GS / 32>(bitmap, nwc, 0, keys, vals, false,
+                                                                     nnz_item != nullptr, capn, s_scan, out0, rb,
+                                                                     Cir, Cv);
+                    if (nnz_item && lane == 0) nnz_item[u] = total;
                     continue;
                 }
             }
@@ -498,9 +559,10 @@ static void run_hash(cudaStream_t st, const Items& it, const int2* list, int64_t
     if (count <= 0) return;
     using L = HashLayout<SR, GS, TBL, NUM>;
     constexpr int NG = BLOCK / GS;
-    constexpr bool CAN_BM = NUM && GS == BLOCK && GS > 32;
-    const int bm_words = CAN_BM && it.max_m > 0 && it.max_m <= BM_MAX_ROWS ? (int)((it.max_m + 31) / 32) : 0;
-    size_t smem = L::group * NG + (size_t)bm_words * 4;
+    constexpr bool CAN_BM = NUM && (GS == BLOCK || GS == 32);
+    constexpr int64_t bm_rows = GS == 32 ? BM_WARP_MAX_ROWS : BM_MAX_ROWS;
+    const int bm_words = CAN_BM && it.max_m > 0 && it.max_m <= bm_rows ? (int)((it.max_m + 31) / 32) : 0;
+    size_t smem = L::group * NG + (size_t)bm_words * 4 * NG;
     auto kern = k_hash<SR, GS, TBL, NUM, BLOCK>;
     static size_t attr_done = 0;
     if (attr_done < smem) {
@@ -572,7 +634,7 @@ __global__ void __launch_bounds__(256) k_tiny(Items it, const int2* __restrict__
                 nnz_item[u] = m;
                 if (m > __ldg(Coff + u + 1) - out0) continue;   // overflow: redone in its exact place
             }
-            const int32_t rb = pr->row_base;
+            const int32_t rb = out_row_base(pr, e.y);
             for (int i = 0; i < m; ++i) {
                 Cir[out0 + i] = r[i] + rb;
                 Cv[out0 + i] = SR::out(v[i]);
@@ -947,7 +1009,7 @@ __global__ void __launch_bounds__(RT_BLOCK) k_range_num(Items it, DenseWork dw, 
         const int P = dw.nparts[d];
         const int64_t m = pr->A.m;
         const int64_t u = __ldg(it.item_base + e.x) + e.y;
-        const int32_t rb = pr->row_base;
+        const int32_t rb = out_row_base(pr, e.y);
         int64_t R0, R1;
         slab_rows(m, q, P, R0, R1);
         const int64_t bs = __ldg(pr->B.cp + e.y), be = __ldg(pr->B.cp + e.y + 1);

@@ -83,6 +83,8 @@ struct Items {
 // CTA-wide hash tables order their numeric output through a shared-memory row
 // bitmap (instead of sorting) when every A_i has at most this many rows.
 constexpr int64_t BM_MAX_ROWS = 262144;
+// The same for warp tables (one bitmap per warp), and only where sorting costs more.
+constexpr int64_t BM_WARP_MAX_ROWS = 16384;
 
 // flops and bin per item, product id per item, bin counts and total flops.
 // With feat != nullptr also the 8 predictor inputs per item; `sketch` holds the
@@ -94,6 +96,9 @@ void launch_analyze(cudaStream_t st, const Items& it, TierCfg cfg, int64_t* flop
 void launch_row_sketch(cudaStream_t st, const DMat& A, uint64_t* sketch);
 void launch_bin_scatter(cudaStream_t st, const Items& it, const uint8_t* bin, const int32_t* item_prod,
                         const int64_t* bin_off, unsigned long long* bin_cursor, int2* list);
+// hash-tier bins from exact counts (after the symbolic pass); cnt[NBIN] accumulates
+void launch_numeric_bins(cudaStream_t st, const Items& it, TierCfg cfg, const uint8_t* bin, const int64_t* flops,
+                         const int64_t* nnz_item, uint8_t* nbin, unsigned long long* cnt);
 // range-tier slabs (position d in the dense list, slab q); P_d slabs of at most RB rows each
 void launch_dense_items(cudaStream_t st, const Items& it, const int2* dense_list, int64_t ndense,
                         const int64_t* flops, int part_flops, int RB, int2* items, unsigned long long* nitems,

@@ -12,9 +12,13 @@
 //   3. The stage partials are merged into C (Section 6.1 keeps the partial
 //      triples and merges them later; Section 4.2 prices the additions).  The
 //      merge is itself computed as a product: with P the matrix whose columns are
-//      the partial columns and S the selector with S(u, j) = 1 when partial
-//      column u belongs to output column j, C = P * S, where (x) by the
-//      semiring's one is exact and (+) does the merge.
+//      the partial columns and S the selector with S(u, t) = 1 when partial
+//      column u belongs to output column t, C = P * S, where (x) by the
+//      semiring's one is exact and (+) does the merge.  Partials keep the local
+//      rows of their block row I, and the merge's output columns are
+//      t = j * g + I: each merge column covers one block of mb rows, and the g
+//      blocks of C(:, j) are adjacent, so C's column pointers are every g-th
+//      entry of the merge's.
 #include <algorithm>
 #include <cstring>
 
@@ -108,14 +112,14 @@ __global__ void k_block_aux(int nblk, const int64_t* __restrict__ boff, const in
 }
 
 // Output column of every item: col_base + JC[p] of the product's B.
-__global__ void k_item_outcol(Items it, const int32_t* __restrict__ item_prod, uint32_t* __restrict__ oc,
+__global__ void k_item_outcol(Items it, const int32_t* __restrict__ item_prod, int g, uint32_t* __restrict__ oc,
                               uint32_t* __restrict__ pay, int64_t ofs) {
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < it.nitems; u += (int64_t)gridDim.x * blockDim.x) {
         const int prod = item_prod[u];
         const Prod* pr = it.prods + prod;
         const int64_t p = u - it.item_base[prod];
         const int64_t j = pr->B.jc ? pr->B.jc[p] : p;
-        oc[ofs + u] = (uint32_t)(pr->col_base + j);
+        oc[ofs + u] = (uint32_t)((pr->col_base + j) * g + pr->blk);
         pay[ofs + u] = (uint32_t)(ofs + u);
     }
 }
@@ -125,6 +129,12 @@ __global__ void k_iota_cols(uint32_t* oc, uint32_t* pay, int64_t n) {
         oc[j] = (uint32_t)j;
         pay[j] = (uint32_t)j;
     }
+}
+
+// C's column pointers from the merge's: cp[j] = Coff[j * g], j = 0..n.
+__global__ void k_every_gth(const int64_t* __restrict__ Coff, int64_t n, int g, int64_t* __restrict__ cp) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j <= n; j += (int64_t)gridDim.x * blockDim.x)
+        cp[j] = Coff[j * g];
 }
 
 __global__ void k_hist_u32(const uint32_t* __restrict__ k, int64_t n, int64_t* __restrict__ cnt) {
@@ -281,11 +291,16 @@ spgemm_status_t partition(spgemm_ctx* ctx, const DMat& M, size_t w, int g, Block
 
 // C (m x n) = merge of `ncols` sorted partial columns: column u of P (rows
 // global, colptr Pcp) is added into output column oc[u].
-spgemm_status_t merge_columns(spgemm_ctx* ctx, spgemm_semiring_t sr, const spgemm_opts_t& opts, int64_t m, int64_t n,
-                              int64_t ncols, const int64_t* Pcp, const int32_t* Pir, const void* Pv, int64_t pnnz,
-                              uint32_t* oc, uint32_t* pay, spgemm_mat_t* C) {
+// Merges the partial columns P (local rows < mb; column u goes to merge column
+// oc[u] = j * g + I) into the mb x (n g) matrix of merge columns, or, when
+// `final`, into C (m x n, global rows I * mb + local row).
+spgemm_status_t merge_columns(spgemm_ctx* ctx, spgemm_semiring_t sr, const spgemm_opts_t& opts, int64_t m,
+                              int64_t mb, int64_t n0, int g, bool final, int64_t ncols, const int64_t* Pcp,
+                              const int32_t* Pir, const void* Pv, int64_t pnnz, uint32_t* oc, uint32_t* pay,
+                              spgemm_mat_t* C) {
     cudaStream_t st = ctx->stream;
     PhaseTimer tm(ctx, SPGEMM_PHASE_MERGE, sr);
+    const int64_t n = n0 * g;   // merge columns
     const int64_t nc1 = std::max<int64_t>(ncols, 1);
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -316,8 +331,12 @@ spgemm_status_t merge_columns(spgemm_ctx* ctx, spgemm_semiring_t sr, const spgem
     launch_exclusive_scan(st, cnt, n, (int64_t*)scp->p, t + o_sc);
     // C = P * S
     Prod pr;
-    pr.A = csc_view(m, ncols, pnnz, Pcp, Pir, Pv);
+    pr.A = csc_view(mb, ncols, pnnz, Pcp, Pir, Pv);
     pr.B = csc_view(ncols, n, ncols, (const int64_t*)scp->p, (const int32_t*)sir->p, nullptr);
+    if (final) {
+        pr.rb_cycle = g;
+        pr.rb_step = (int32_t)mb;
+    }
     Engine E;
     struct Quiet {   // the merge's own phases are reported as one MERGE phase
         spgemm_ctx* c;
@@ -329,7 +348,16 @@ spgemm_status_t merge_columns(spgemm_ctx* ctx, spgemm_semiring_t sr, const spgem
     std::shared_ptr<DevBuf> rbuf, vbuf;
     SG_TRY(engine_alloc_out(&E, &rbuf, &vbuf));
     SG_TRY(engine_numeric(&E, (int32_t*)rbuf->p, vbuf->p));
-    *C = new_owned_csc(ctx, sr, m, n, E.nnz_total, {E.Coff_buf, rbuf, vbuf}, E.Coff, (const int32_t*)rbuf->p,
+    if (!final) {
+        *C = new_owned_csc(ctx, sr, mb, n, E.nnz_total, {E.Coff_buf, rbuf, vbuf}, E.Coff, (const int32_t*)rbuf->p,
+                           vbuf->p);
+        return SPGEMM_OK;
+    }
+    auto cp = ctx_buf(ctx, 8 * (n0 + 1));
+    if (!cp) return set_err(ctx, SPGEMM_ERR_OOM, "merge column pointers");
+    k_every_gth<<<gridn(n0 + 1), 256, 0, st>>>(E.Coff, n0, g, (int64_t*)cp->p);
+    note_launch();
+    *C = new_owned_csc(ctx, sr, m, n0, E.nnz_total, {cp, rbuf, vbuf}, (const int64_t*)cp->p, (const int32_t*)rbuf->p,
                        vbuf->p);
     return SPGEMM_OK;
 }
@@ -358,6 +386,8 @@ spgemm_status_t spgemm_summa_blocked(spgemm_ctx_t ctx, spgemm_mat_t A, spgemm_ma
     if (s != SPGEMM_OK) return s;
     const size_t w = sr_size(sr);
     const int64_t m = dA.m, n = dB.n;
+    if (n * g >= (int64_t(1) << 32))
+        return set_err(ctx, SPGEMM_ERR_UNSUPPORTED, "n * g = %lld merge columns exceed 2^32", (long long)(n * g));
     Blocked bA, bB;
     {
         PhaseTimer tp(ctx, SPGEMM_PHASE_ANALYZE, sr);
@@ -375,9 +405,10 @@ spgemm_status_t spgemm_summa_blocked(spgemm_ctx_t ctx, spgemm_mat_t A, spgemm_ma
                 Prod pr;
                 pr.A = a;
                 pr.B = b;
-                pr.row_base = (int32_t)(I * bA.mb);
+                pr.row_base = 0;   // local rows; the merge adds I * mb
                 pr.col_base = (int64_t)J * bB.nb;
                 pr.tag = st;
+                pr.blk = I;
                 all.push_back(pr);
             }
     ctx->summa_stage_flops.assign(g, 0);
@@ -411,7 +442,7 @@ spgemm_status_t spgemm_summa_blocked(spgemm_ctx_t ctx, spgemm_mat_t A, spgemm_ma
             for (size_t i = 0; i < grp.size(); ++i) ctx->summa_stage_flops[grp[i].tag] += (int64_t)hpf[i];
         }
         // columns to merge: the accumulated C (if any) followed by this group's partial columns
-        const int64_t nacc = acc ? n : 0;
+        const int64_t nacc = acc ? n * g : 0;   // merge columns so far
         const int64_t accnz = acc ? acc->nnz : 0;
         const int64_t ncols = nacc + U;
         const int64_t pnz = accnz + pn;
@@ -435,7 +466,7 @@ spgemm_status_t spgemm_summa_blocked(spgemm_ctx_t ctx, spgemm_mat_t A, spgemm_ma
             pv = ctx_buf(ctx, w * std::max<int64_t>(pnz, 1));
             if (!pcp || !pir || !pv) return set_err(ctx, SPGEMM_ERR_OOM, "merge inputs");
             if (acc) {
-                SG_CUDA(ctx, cudaMemcpyAsync(pcp->p, acc->cp, 8 * n, cudaMemcpyDeviceToDevice, stq));
+                SG_CUDA(ctx, cudaMemcpyAsync(pcp->p, acc->cp, 8 * nacc, cudaMemcpyDeviceToDevice, stq));
                 if (accnz) {
                     SG_CUDA(ctx, cudaMemcpyAsync(pir->p, acc->ir, 4 * accnz, cudaMemcpyDeviceToDevice, stq));
                     SG_CUDA(ctx, cudaMemcpyAsync(pv->p, acc->num, w * accnz, cudaMemcpyDeviceToDevice, stq));
@@ -449,7 +480,7 @@ spgemm_status_t spgemm_summa_blocked(spgemm_ctx_t ctx, spgemm_mat_t A, spgemm_ma
                     SG_CUDA(ctx, cudaMemcpyAsync((char*)pv->p + w * accnz, vbuf->p, w * pn, cudaMemcpyDeviceToDevice, stq));
                 }
             } else if (acc) {
-                SG_CUDA(ctx, cudaMemcpyAsync((int64_t*)pcp->p + n, acc->cp + n, 8, cudaMemcpyDeviceToDevice, stq));
+                SG_CUDA(ctx, cudaMemcpyAsync((int64_t*)pcp->p + nacc, acc->cp + nacc, 8, cudaMemcpyDeviceToDevice, stq));
             } else {
                 SG_CUDA(ctx, cudaMemsetAsync(pcp->p, 0, 8, stq));
             }
@@ -458,15 +489,16 @@ spgemm_status_t spgemm_summa_blocked(spgemm_ctx_t ctx, spgemm_mat_t A, spgemm_ma
             Pv = pv->p;
         }
         if (acc) {
-            k_iota_cols<<<gridn(n), 256, 0, stq>>>(oc, pay, n);
+            k_iota_cols<<<gridn(nacc), 256, 0, stq>>>(oc, pay, nacc);
             note_launch();
         }
         if (U > 0) {
-            k_item_outcol<<<gridn(U), 256, 0, stq>>>(E.it, E.item_prod, oc, pay, nacc);
+            k_item_outcol<<<gridn(U), 256, 0, stq>>>(E.it, E.item_prod, g, oc, pay, nacc);
             note_launch();
         }
         spgemm_mat_t Cn = nullptr;
-        SG_TRY(merge_columns(ctx, sr, o, m, n, ncols, Pcp, Pir, Pv, pnz, oc, pay, &Cn));
+        const bool final = s0 + every >= g;
+        SG_TRY(merge_columns(ctx, sr, o, m, bA.mb, n, g, final, ncols, Pcp, Pir, Pv, pnz, oc, pay, &Cn));
         hold_acc.reset(Cn);
         acc = Cn;
     }
