@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--scale", type=int, default=SCALE)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--semirings", default="pt64,mp32",
+                    help="comma list of pt64 (plus-times FP64) and mp32 (min-plus FP32)")
     ap.add_argument("--products", default="flat,summa",
                     help="comma list of product kinds in a step: flat, summa")
     ap.add_argument("--opt", action="append", default=[],
@@ -223,9 +225,10 @@ def main():
     mats = {sp.PLUS_TIMES_F64: sp.Matrix.from_host(ctx, A64, sp.PLUS_TIMES_F64),
             sp.MIN_PLUS_F32: sp.Matrix.from_host(ctx, A32, sp.MIN_PLUS_F32)}
     products = []
+    srs = {"pt64": sp.PLUS_TIMES_F64, "mp32": sp.MIN_PLUS_F32}
     for k in kinds:
-        for sr in (sp.PLUS_TIMES_F64, sp.MIN_PLUS_F32):
-            products.append((k, sr))
+        for name in [x for x in args.semirings.split(",") if x]:
+            products.append((k, srs[name]))
 
     lib_opts = sp.default_opts(**{k: float(v) if k == "predictor_margin" else int(v)
                                   for k, v in (o.split("=", 1) for o in args.opt)})

@@ -206,6 +206,31 @@ __device__ __forceinline__ int group_incl_scan(int v, int* scratch, int& total) 
     }
 }
 
+// group_incl_scan without its closing barrier: the caller must reach another
+// barrier of the group (or, for a warp, a full-warp shuffle) before the next call
+// writes `scratch` again.
+template <int GS>
+__device__ __forceinline__ int group_incl_scan_open(int v, int* scratch, int& total) {
+    int x = warp_incl_scan(v);
+    if constexpr (GS == 32) {
+        total = __shfl_sync(0xffffffffu, x, 31);
+        return x;
+    } else {
+        constexpr int NW = GS / 32;
+        int lane = threadIdx.x & 31, w = (threadIdx.x % GS) >> 5;
+        if (lane == 31) scratch[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            int s = lane < NW ? scratch[lane] : 0;
+            s = warp_incl_scan(s);
+            if (lane < NW) scratch[lane] = s;
+        }
+        __syncthreads();
+        total = scratch[NW - 1];
+        return x + (w > 0 ? scratch[w - 1] : 0);
+    }
+}
+
 __host__ __device__ __forceinline__ int64_t ceil_div64(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 __device__ __forceinline__ uint32_t hash_row(int32_t r) { return (uint32_t)r * 0x9E3779B1u; }

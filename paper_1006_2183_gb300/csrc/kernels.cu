@@ -383,23 +383,30 @@ __global__ void __launch_bounds__(BLOCK) k_hash(Items it, const int2* __restrict
     // Numeric tables order their output through a row bitmap (one per group) when
     // the rows fit; otherwise they compact and sort.
     uint32_t* bitmap = reinterpret_cast<uint32_t*>(smem + (size_t)NG * L::group) + (size_t)g * bm_words;
-    constexpr bool CAN_BM = NUM && (GS == BLOCK || GS == 32);
+    constexpr bool CAN_BM = NUM && (GS == BLOCK || (GS == 32 && TBL >= BM_WARP_MIN_TBL));
     if constexpr (CAN_BM) {
         for (int x = lane; x < bm_words; x += GS) bitmap[x] = 0u;
-        G::sync();
     }
+    // Numeric tables start empty and every column leaves its table empty again (the
+    // bitmap emit resets the slots it reads; the sorting path clears the table).
+    if constexpr (NUM) {
+        for (int s = lane; s < TBL; s += GS) {
+            keys[s] = -1;
+            vals[s] = SR::zero();
+        }
+    }
+    G::sync();
 
     for (int64_t w = (int64_t)blockIdx.x * NG + g; w < count; w += (int64_t)gridDim.x * NG) {
         const int2 e = __ldg(list + w);
         const Prod* pr = it.prods + e.x;
         const int64_t u = __ldg(it.item_base + e.x) + e.y;
         const int64_t bs = __ldg(pr->B.cp + e.y), be = __ldg(pr->B.cp + e.y + 1);
-        for (int s = lane; s < TBL; s += GS) {
-            keys[s] = -1;
-            if constexpr (NUM) vals[s] = SR::zero();
+        if constexpr (!NUM) {
+            for (int s = lane; s < TBL; s += GS) keys[s] = -1;
+            if (lane == 0) *s_cnt = 0;
+            G::sync();
         }
-        if (lane == 0) *s_cnt = 0;
-        G::sync();
         int mycnt = 0;
         for (int64_t b0 = bs; b0 < be; b0 += GS) {
             const int64_t t = b0 + lane;
@@ -414,8 +421,11 @@ __global__ void __launch_bounds__(BLOCK) k_hash(Items it, const int2* __restrict
                 len = (int)(en - s);
                 if constexpr (NUM) bv = load_val<SR>(pr->B, t);
             }
+            // Every member finished the previous chunk's expansion before the scan's
+            // barrier (or the warp's shuffles), so the chunk arrays can be rewritten
+            // after it without a closing barrier.
             int total;
-            int incl = group_incl_scan<GS>(len, s_scan, total);
+            int incl = group_incl_scan_open<GS>(len, s_scan, total);
             s_incl[lane] = incl;
             s_a0[lane] = a0;
             if constexpr (NUM) s_bv[lane] = bv;
@@ -462,8 +472,9 @@ __global__ void __launch_bounds__(BLOCK) k_hash(Items it, const int2* __restrict
                     if constexpr (NUM) SR::atomic_add(&vals[h], SR::mul(av[i], s_bv[seg[i]]));
                 }
             }
-            G::sync();
+            if constexpr (GS == 32) __syncwarp();
         }
+        G::sync();
         if constexpr (!NUM) {
             int c = warp_sum(mycnt);
             if constexpr (GS == 32) {
@@ -534,6 +545,7 @@ __global__ void __launch_bounds__(BLOCK) k_hash(Items it, const int2* __restrict
                 if (pos > capn) {   // overflow: recomputed into its exact place afterwards
                     for (int s = lane; s < TBL; s += GS) {
                         keys[s] = -1;
+                        vals[s] = SR::zero();
                     }
                     G::sync();
                     continue;
@@ -549,6 +561,11 @@ __global__ void __launch_bounds__(BLOCK) k_hash(Items it, const int2* __restrict
                 Cv[out0 + s] = SR::out(vals[s]);
             }
             G::sync();
+            for (int s = lane; s < TBL; s += GS) {
+                keys[s] = -1;
+                vals[s] = SR::zero();
+            }
+            G::sync();
         }
     }
 }
@@ -559,7 +576,7 @@ static void run_hash(cudaStream_t st, const Items& it, const int2* list, int64_t
     if (count <= 0) return;
     using L = HashLayout<SR, GS, TBL, NUM>;
     constexpr int NG = BLOCK / GS;
-    constexpr bool CAN_BM = NUM && (GS == BLOCK || GS == 32);
+    constexpr bool CAN_BM = NUM && (GS == BLOCK || (GS == 32 && TBL >= BM_WARP_MIN_TBL));
     constexpr int64_t bm_rows = GS == 32 ? BM_WARP_MAX_ROWS : BM_MAX_ROWS;
     const int bm_words = CAN_BM && it.max_m > 0 && it.max_m <= bm_rows ? (int)((it.max_m + 31) / 32) : 0;
     size_t smem = L::group * NG + (size_t)bm_words * 4 * NG;

@@ -85,6 +85,7 @@ struct Items {
 constexpr int64_t BM_MAX_ROWS = 262144;
 // The same for warp tables (one bitmap per warp), and only where sorting costs more.
 constexpr int64_t BM_WARP_MAX_ROWS = 16384;
+constexpr int BM_WARP_MIN_TBL = 256;   // smaller tables hold too few rows to prefer the bitmap
 
 // flops and bin per item, product id per item, bin counts and total flops.
 // With feat != nullptr also the 8 predictor inputs per item; `sketch` holds the

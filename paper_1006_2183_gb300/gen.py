@@ -18,6 +18,9 @@ restriction and the triple product).
 """
 from __future__ import annotations
 
+import os
+import threading
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass
 
 import numpy as np
@@ -94,7 +97,9 @@ class CSC:
 def csc_from_coo(m: int, n: int, rows: np.ndarray, cols: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
     """Pattern of the COO list with duplicates merged, in CSC order."""
     key = cols.astype(np.int64) * np.int64(max(m, 1)) + rows.astype(np.int64)
-    key = np.unique(key)
+    key = np.sort(key)   # sorted distinct keys (a plain sort is much faster than np.unique here)
+    if len(key) > 1:
+        key = key[np.concatenate(([True], key[1:] != key[:-1]))]
     c = key // max(m, 1)
     r = (key - c * max(m, 1)).astype(np.int32)
     colptr = np.zeros(n + 1, dtype=np.int64)
@@ -120,6 +125,24 @@ def values_for(semiring: int, seed: int, nnz: int) -> np.ndarray:
     return _values(kind, seed, nnz)
 
 
+# Large draws are split into chunks of counters that threads fill independently
+# (numpy releases the GIL in its array loops).  Every value depends only on its
+# counter, so the result does not depend on the chunking or the thread count.
+_EDGE_CHUNK = 1 << 20
+_pools: dict[str, ThreadPoolExecutor] = {}
+_pools_lock = threading.Lock()
+_tls = threading.local()
+
+
+def _pool(name: str) -> ThreadPoolExecutor:
+    with _pools_lock:
+        p = _pools.get(name)
+        if p is None:
+            p = ThreadPoolExecutor(max_workers=max(1, min(16, os.cpu_count() or 1)))
+            _pools[name] = p
+        return p
+
+
 def rmat_edges(scale: int, nedges: int, a: float, b: float, c: float, seed: int,
                first_edge: int = 0) -> tuple[np.ndarray, np.ndarray]:
     """R-MAT edge list: per edge and per level pick a quadrant with probs (a, b, c, d).
@@ -127,16 +150,30 @@ def rmat_edges(scale: int, nedges: int, a: float, b: float, c: float, seed: int,
     Quadrant a = (row bit 0, col bit 0), b = (0, 1), c = (1, 0), d = (1, 1); bits
     are placed from the most significant end.  No noise, no relabelling.
     """
-    e = np.arange(first_edge, first_edge + nedges, dtype=np.uint64)
-    rows = np.zeros(nedges, dtype=np.int64)
-    cols = np.zeros(nedges, dtype=np.int64)
+    rows = np.empty(nedges, dtype=np.int64)
+    cols = np.empty(nedges, dtype=np.int64)
     ab, abc = a + b, a + b + c
-    for lvl in range(scale):
-        u = uniform01(seed, 1 + lvl, e)
-        rbit = u >= ab
-        cbit = ((u >= a) & (u < ab)) | (u >= abc)
-        rows = (rows << 1) | rbit
-        cols = (cols << 1) | cbit
+
+    def fill(lo: int) -> None:
+        hi = min(lo + _EDGE_CHUNK, nedges)
+        e = np.arange(first_edge + lo, first_edge + hi, dtype=np.uint64)
+        r = np.zeros(hi - lo, dtype=np.int64)
+        q = np.zeros(hi - lo, dtype=np.int64)
+        for lvl in range(scale):
+            u = uniform01(seed, 1 + lvl, e)
+            rbit = u >= ab
+            cbit = ((u >= a) & (u < ab)) | (u >= abc)
+            r = (r << 1) | rbit
+            q = (q << 1) | cbit
+        rows[lo:hi] = r
+        cols[lo:hi] = q
+
+    starts = range(0, nedges, _EDGE_CHUNK)
+    if nedges > _EDGE_CHUNK and not getattr(_tls, "serial", False):
+        list(_pool("edges").map(fill, starts))
+    else:
+        for lo in starts:
+            fill(lo)
     return rows, cols
 
 
@@ -154,8 +191,10 @@ def rmat(scale: int, edge_factor: int, seed: int, semiring: int = PLUS_TIMES_F64
     want = edge_factor * n
     rows_l, cols_l = [], []
     got, first = 0, 0
+    pow2 = n == 1 << scale
     while got < want:
-        batch = max(want - got, 1024) + (want - got) // 2
+        # the kept edges are the first `want` in counter order, whatever the batch sizes
+        batch = want - got if pow2 else max(want - got, 1024) + (want - got) // 2
         r, c = rmat_edges(scale, batch, abc[0], abc[1], abc[2], seed, first)
         first += batch
         keep = (r < n) & (c < n)
@@ -278,8 +317,8 @@ def batch_pairs(count: int, seed: int, lo_log2: float = 10.0, hi_log2: float = 1
     Each matrix is Erdos-Renyi or R-MAT(0.57, 0.19, 0.19) by coin flip with edge
     factor uniform in {4, 8, 16, 32}; pair i uses seed + i.
     """
-    out = []
-    for i in range(count):
+    def pair(i: int) -> tuple[CSC, CSC]:
+        _tls.serial = True   # pairs are the unit of parallelism here
         s = seed + i
         u = uniform01(s, 60, np.arange(8, dtype=np.uint64))
         n = int(np.floor(2.0 ** (lo_log2 + u[0] * (hi_log2 - lo_log2))))
@@ -292,8 +331,9 @@ def batch_pairs(count: int, seed: int, lo_log2: float = 10.0, hi_log2: float = 1
             else:
                 scale = max(1, int(np.ceil(np.log2(n))))
                 mats.append(rmat(scale, ef, ms, semiring, n=n))
-        out.append((mats[0], mats[1]))
-    return out
+        return mats[0], mats[1]
+
+    return list(_pool("pairs").map(pair, range(count)))
 
 
 def random_csc(m: int, n: int, density: float, seed: int, semiring: int = PLUS_TIMES_F64) -> CSC:
