@@ -42,6 +42,102 @@ L2_FLUSH_BYTES = 512 << 20
 CPU_STRIDE = 4   # oracle sample: every 4th output column (~25 core-seconds on the flat scale-18 product)
 
 
+def _train_predictor(sp, ctx):
+    """Predictor trained on exact symbolic counts of R-MAT and ER squares (scales 14-16)
+    drawn from seeds disjoint from the measured workloads."""
+    import torch
+    Xs, ys = [], []
+    for M in (gen.rmat(14, 8, 0x7000), gen.erdos_renyi(16384, 16384, 8, 0x7100), gen.rmat(16, 4, 0x7200),
+              gen.rmat(15, 16, 0x7300)):
+        d = sp.Matrix.from_host(ctx, M, sp.PLUS_TIMES_F64)
+        X, y = sp.spgemm_predictor_features(ctx, d, d)
+        keep = y > 0
+        Xs.append(X[keep])
+        ys.append(torch.log1p(y[keep].double()).float())
+    X, y = torch.cat(Xs), torch.cat(ys)
+    sp.spgemm_predictor_set(ctx, np.random.default_rng(11).normal(0, 0.2, sp.NPARAM).astype(np.float32))
+    for _ in range(400):
+        loss, _ = sp.spgemm_predictor_train_step(ctx, X, y, 3e-3)
+    return loss
+
+
+def learned_vs_plain(sp, ctx, steps: int, warmup: int) -> dict:
+    """The batched workloads, plain (one plan -> symbolic -> numeric per product, in
+    sequence) against learned+batched (all products of the workload in one batched
+    execution, the predictor sizing the output instead of the symbolic pass, bins from
+    the autotuner).  Wall time on the device, synchronised on both sides; outputs
+    compared by nnz."""
+    import torch
+    import oracle
+    loss = _train_predictor(sp, ctx)
+    work = {}
+    pairs = gen.batch_pairs(512, 0x4004)
+    As = [sp.Matrix.from_host(ctx, a, sp.PLUS_TIMES_I64) for a, _ in pairs]
+    Bs = [sp.Matrix.from_host(ctx, b, sp.PLUS_TIMES_I64) for _, b in pairs]
+    fl = sum(int(oracle.flops_per_col(a, b).sum()) for a, b in pairs)
+    work["batch512_int64"] = (As, Bs, sp.PLUS_TIMES_I64, fl,
+                              "512 uneven int64 pairs, n_i = 2^U(10,16), ER or R-MAT, edge factor in {4,8,16,32}")
+    Ab = gen.rmat(20, 16, 0x4F00, gen.OR_AND_BOOL)
+    F = gen.frontier(Ab.m, 128, 0x4F01, 1, 1000)
+    work["bfs_step_bool"] = ([sp.Matrix.from_host(ctx, Ab, sp.OR_AND_BOOL)], [sp.Matrix.from_host(ctx, F, sp.OR_AND_BOOL)],
+                             sp.OR_AND_BOOL, int(oracle.flops_per_col(Ab, F).sum()),
+                             "boolean R-MAT scale 20 (edge factor 16) times a 2^20 x 128 frontier")
+    N = 128
+    A, P = gen.grid3d_laplacian(N), gen.aggregation_2x2x2(N)
+    R = gen.transpose_host(P)
+    dA, dP, dR = (sp.Matrix.from_host(ctx, M, sp.PLUS_TIMES_F64) for M in (A, P, R))
+    out = {"predictor_train_loss": loss}
+
+    def timed(fn):
+        for _ in range(max(1, warmup)):
+            fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            r = fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / steps * 1e3, r
+
+    def nnz_of(Cs):
+        return sum(C.shape()[2] for C in Cs)
+
+    for name, (As_, Bs_, sr, flops, desc) in work.items():
+        tuned = sp.spgemm_autotune(ctx, As_, Bs_, sr)
+        lo = sp.default_opts(use_predictor=1, warp_max_flops=tuned.warp_max_flops,
+                             block_max_flops=tuned.block_max_flops, dense_part_flops=tuned.dense_part_flops)
+        t_plain, Cp = timed(lambda: [sp.spgemm_multiply(ctx, a, b, sr) for a, b in zip(As_, Bs_)])
+        nz_plain = nnz_of(Cp)
+        del Cp
+        t_lb, Cl = timed(lambda: sp.spgemm_batch(ctx, As_, Bs_, sr, lo))
+        nz_lb = nnz_of(Cl)
+        del Cl
+        out[name] = {"workload": desc, "flops": flops, "plain_ms": t_plain, "learned_batched_ms": t_lb,
+                     "speedup": t_plain / t_lb, "plain_gflops": 2 * flops / t_plain / 1e6,
+                     "learned_batched_gflops": 2 * flops / t_lb / 1e6, "same_nnz": nz_plain == nz_lb,
+                     "tuned": [tuned.warp_max_flops, tuned.block_max_flops, tuned.dense_part_flops]}
+        torch.cuda.empty_cache()
+    # Galerkin triple product R*(A*P), FP64: plain products vs the learned+autotuned batch form
+    tuned = sp.spgemm_autotune(ctx, [dA], [dP], sp.PLUS_TIMES_F64)
+    lo = sp.default_opts(use_predictor=1, warp_max_flops=tuned.warp_max_flops,
+                         block_max_flops=tuned.block_max_flops, dense_part_flops=tuned.dense_part_flops)
+
+    def rap_plain():
+        AP = sp.spgemm_multiply(ctx, dA, dP, sp.PLUS_TIMES_F64)
+        return sp.spgemm_multiply(ctx, dR, AP, sp.PLUS_TIMES_F64)
+
+    def rap_learned():
+        AP = sp.spgemm_batch(ctx, [dA], [dP], sp.PLUS_TIMES_F64, lo)[0]
+        return sp.spgemm_batch(ctx, [dR], [AP], sp.PLUS_TIMES_F64, lo)[0]
+
+    fl = A.nnz + 32 * 64 ** 3 - 24 * 64 ** 2   # flops(A*P) = nnz(A), flops(R*(AP)) = nnz(AP)
+    t_plain, C1 = timed(rap_plain)
+    t_lb, C2 = timed(rap_learned)
+    out["galerkin128_fp64"] = {"workload": "R*(A*P), 7-point Laplacian on 128^3, 2x2x2 aggregation",
+                               "flops": fl, "plain_ms": t_plain, "learned_batched_ms": t_lb,
+                               "speedup": t_plain / t_lb, "same_nnz": C1.shape()[2] == C2.shape()[2]}
+    return out
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -51,6 +147,8 @@ def parse():
     ap.add_argument("--scale", type=int, default=SCALE)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned+batched vs plain comparison on the batched workloads")
     ap.add_argument("--semirings", default="pt64,mp32",
                     help="comma list of pt64 (plus-times FP64) and mp32 (min-plus FP32)")
     ap.add_argument("--products", default="flat,summa",
@@ -385,6 +483,10 @@ def main():
                "sample": f"every {CPU_STRIDE}th output column ({len(cols)} columns, {fl} flops) of the flat "
                          f"plus-times FP64 product, {dt:.2f} s wall on {oracle.max_threads()} threads"}
 
+    lvp = None
+    if rank == 0 and world == 1 and not args.no_learned:
+        lvp = learned_vs_plain(sp, ctx, steps=2, warmup=1)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
@@ -395,7 +497,8 @@ def main():
                            "flops_per_product": flops1, "nnz_A": A64.nnz, "l2": "flushed between steps (512 MiB write)",
                            "pipeline_hbm_frac": pipeline_frac, "pipeline": pipe, "phase_ms_per_step": phase_tab,
                            "lib_opts": {k: v for k, v in (o.split("=", 1) for o in args.opt)}},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches}
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
+                "learned_batched_vs_plain": lvp}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

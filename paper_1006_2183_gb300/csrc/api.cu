@@ -298,6 +298,11 @@ spgemm_status_t engine_setup(Engine* E, spgemm_ctx* ctx, spgemm_semiring_t sr, c
     E->cfg.dense_rows = (int)std::min<int64_t>((mmax + 31) / 32 * 32, 1 << 20);
     E->cfg.part_flops = std::max(1024, opts.dense_part_flops);
     cudaStream_t st = ctx->stream;
+    {
+        const cudaError_t pending = cudaGetLastError();
+        if (pending != cudaSuccess)
+            return set_err(ctx, SPGEMM_ERR_CUDA, "CUDA error pending before this call: %s", cudaGetErrorString(pending));
+    }
     const int64_t np = (int64_t)prods.size();
     E->hitem_base.assign(np + 1, 0);
     int64_t bnz = 0, amax_n = 0;
@@ -475,6 +480,7 @@ spgemm_status_t engine_symbolic(Engine* E) {
     case SPGEMM_OR_AND_BOOL: dispatch_symbolic<BOOL8>(E); break;
     case SPGEMM_PLUS_TIMES_I64: dispatch_symbolic<PTI64>(E); break;
     }
+    SG_CUDA(ctx, cudaGetLastError());   // launch errors of the symbolic kernels
     launch_sum_parts(st, E->it, E->list + E->bin_off[BIN_DENSE], E->bin_cnt[BIN_DENSE], E->nparts, E->part_count,
                      E->nnz_item);
     E->Coff_buf = ctx_buf(ctx, 8 * (U + 1));

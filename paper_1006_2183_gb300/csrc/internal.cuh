@@ -175,10 +175,13 @@ spgemm_mat_t new_owned_csc(spgemm_ctx* ctx, spgemm_semiring_t sr, int64_t m, int
                            const void* num);
 spgemm_status_t to_csc_operand(spgemm_ctx* ctx, spgemm_mat_t M, spgemm_mat_t* conv, sg::DMat* d);
 
+#define SG_STR2(x) #x
+#define SG_STR(x) SG_STR2(x)
+#define SG_WHERE __FILE_NAME__ ":" SG_STR(__LINE__)
 #define SG_CUDA(ctx, call)                                                  \
     do {                                                                    \
         cudaError_t e__ = (call);                                           \
-        if (e__ != cudaSuccess) return check_cuda((ctx), e__, #call);       \
+        if (e__ != cudaSuccess) return check_cuda((ctx), e__, #call " at " SG_WHERE); \
     } while (0)
 
 #define SG_TRY(call)                               \

@@ -12,6 +12,9 @@
 #include <algorithm>
 #include <atomic>
 #include <climits>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "kernels.cuh"
 
@@ -20,6 +23,20 @@ namespace sg {
 static std::atomic<int64_t> g_launches{0};
 void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 int64_t launches() { return g_launches.load(std::memory_order_relaxed); }
+
+// Raises a kernel's dynamic shared-memory limit on the current device to at least
+// `bytes`; never lowers it (the limit belongs to the kernel, whichever launcher
+// asks).  A refused request is not remembered, so the launch reports the error.
+static void smem_at_least(const void* fn, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> limit;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    size_t& cur = limit[{dev, fn}];
+    if (cur < bytes && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess)
+        cur = bytes;
+}
 
 constexpr int WARP_BLOCK = 256;   // 8 warp groups per CTA
 
@@ -581,11 +598,7 @@ static void run_hash(cudaStream_t st, const Items& it, const int2* list, int64_t
     const int bm_words = CAN_BM && it.max_m > 0 && it.max_m <= bm_rows ? (int)((it.max_m + 31) / 32) : 0;
     size_t smem = L::group * NG + (size_t)bm_words * 4 * NG;
     auto kern = k_hash<SR, GS, TBL, NUM, BLOCK>;
-    static size_t attr_done = 0;
-    if (attr_done < smem) {
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr_done = smem;
-    }
+    smem_at_least((const void*)kern, smem);
     int64_t want = ceil_div64(count, NG);
     int grid = (int)std::min<int64_t>(want, 152 * 32);
     kern<<<grid, BLOCK, smem, st>>>(it, list, count, nnz_item, Coff, Cir, Cv, bm_words);
@@ -697,7 +710,8 @@ static void run_hash_bins(cudaStream_t st, const Items& it, const int2* list, co
 // range is written already sorted.
 constexpr int RT_BLOCK = 512;
 constexpr int RT_MAXB = 1024;
-constexpr int RT_NEXT = 512;    // k's per column whose cursor state lives in shared memory
+constexpr int RT_NEXT = 512;
+static_assert(RANGE_W / 32 <= 4 * RT_BLOCK, "range emit: one 4-word group of the row bitmap per thread");    // k's per column whose cursor state lives in shared memory
 
 __device__ __forceinline__ int32_t lower_bound_rows(const int32_t* __restrict__ r, int64_t len, int64_t v) {
     int64_t lo = 0, hi = len;
@@ -731,6 +745,31 @@ __device__ __forceinline__ int64_t gallop_count(const int32_t* __restrict__ r, i
         else hi = mid;
     }
     return lo - pos;
+}
+
+// gallop_count, plus the row at pos + count (INT_MAX past en).  The first 8
+// positions are read with independent loads, so the common short run costs one
+// memory round trip; longer runs continue with the gallop.
+__device__ __forceinline__ int64_t count_below(const int32_t* __restrict__ r, int64_t pos, int64_t en, int64_t lim,
+                                               int32_t& next) {
+    constexpr int F = 8;
+    int32_t v[F];
+#pragma unroll
+    for (int i = 0; i < F; ++i) v[i] = pos + i < en ? __ldg(r + pos + i) : INT_MAX;
+    int c = 0;
+#pragma unroll
+    for (int i = 0; i < F; ++i) c += (int64_t)v[i] < lim;   // a prefix, rows ascending
+    if (c < F) {
+        next = v[0];
+#pragma unroll
+        for (int i = 1; i < F; ++i)
+            if (i == c) next = v[i];
+        return c;
+    }
+    const int64_t p = pos + F - 1;   // r[p] < lim
+    const int64_t cnt = F - 1 + gallop_count(r, p, en, lim);
+    next = pos + cnt < en ? __ldg(r + pos + cnt) : INT_MAX;
+    return cnt;
 }
 
 // bitmap[wd] |= bit for every lane with wd >= 0; lanes that hit the same word
@@ -1070,17 +1109,19 @@ __global__ void __launch_bounds__(RT_BLOCK) k_range_num(Items it, DenseWork dw, 
                     if (t < RT_NEXT) {
                         a = s_pos[t];
                         const int64_t en = a + s_rem[t];
-                        const int64_t c = gallop_count(air, a, en, r1);
+                        int32_t nx;
+                        const int64_t c = count_below(air, a, en, r1, nx);
                         s_pos[t] = a + c;
                         s_rem[t] -= (int32_t)c;
-                        s_next[t] = a + c < en ? __ldg(air + a + c) : INT_MAX;
+                        s_next[t] = nx;
                         len = (int)c;
                     } else {
                         const int32_t k = __ldg(pr->B.ir + bs + t);
                         int64_t s, en;
                         col_range(pr->A, k, s, en);
                         a = s + cur[t];
-                        const int64_t c = gallop_count(air, a, en, r1);
+                        int32_t nx;
+                        const int64_t c = count_below(air, a, en, r1, nx);
                         cur[t] += (int32_t)c;
                         len = (int)c;
                     }
@@ -1173,68 +1214,34 @@ __global__ void __launch_bounds__(RT_BLOCK) k_range_num(Items it, DenseWork dw, 
                 }
             }
             __syncthreads();
-            // read back in row order: warp slices of the bitmap, coalesced stores
-            const int cw = (nw + NWARP * 32 - 1) / (NWARP * 32) * 32;
-            const int wb = min(warp * cw, nw), we = min(wb + cw, nw);
-            int cnt = 0;
-            for (int x = wb + lane; x < we; x += 32) cnt += __popc(bitmap[x]);
-            cnt = warp_sum(cnt);
-            if (lane == 0) sc->wc[warp] = cnt;
-            __syncthreads();
-            if (warp == 0) {
-                int v = lane < NWARP ? sc->wc[lane] : 0;
-                const int incl = warp_incl_scan(v);
-                if (lane < NWARP) sc->wc[lane] = incl - v;
+            // Output in row order without sorting: the rank of row lr in the range is the
+            // number of bitmap bits below it, from per-group prefixes (4 words = 128 rows
+            // per group, one group per thread) plus at most 4 words of popcounts.  Each
+            // occupied slot writes its entry at that rank and empties itself.
+            int* s_gp = sc->end;   // free once the range's products are accumulated
+            {
+                const int x0 = tid * 4;
+                int c = 0;
+                for (int x = x0; x < x0 + 4 && x < nw; ++x) c += __popc(bitmap[x]);
+                int total;
+                s_gp[tid] = group_incl_scan<RT_BLOCK>(c, sc->wc, total) - c;
             }
             __syncthreads();
-            int64_t o = outbase + rp.off + sc->wc[warp];
-            for (int x0 = wb; x0 < we; x0 += 32) {
-                const int x = x0 + lane;
-                const uint32_t word = x < we ? bitmap[x] : 0u;
-                const int pc = __popc(word);
-                const int incl = warp_incl_scan(pc);
-                const int tot = __shfl_sync(0xffffffffu, incl, 31);
-                for (int e0 = 0; e0 < tot; e0 += 32) {
-                    const int ee = e0 + lane;
-                    // lane j holding entry ee: smallest j with incl_j > ee
-                    int j = 0;
-#pragma unroll
-                    for (int s = 16; s >= 1; s >>= 1) {
-                        const int v = __shfl_sync(0xffffffffu, incl, j + s - 1);
-                        if (v <= ee) j += s;
-                    }
-                    j = j > 31 ? 31 : j;
-                    uint32_t wj = __shfl_sync(0xffffffffu, word, j);
-                    int rr = ee - (__shfl_sync(0xffffffffu, incl, j) - __popc(wj));
-                    if (ee < tot) {
-                        int pos = 0;
-#pragma unroll
-                        for (int s = 16; s >= 1; s >>= 1) {
-                            const int c = __popc(wj & ((1u << s) - 1u));
-                            if (rr >= c) {
-                                rr -= c;
-                                wj >>= s;
-                                pos += s;
-                            }
-                        }
-                        const int lr = (x0 + j) * 32 + pos;
-                        const int32_t row = (int32_t)(r0 + lr);
-                        uint32_t h;
-                        if (direct) {
-                            h = (uint32_t)lr;
-                        } else {
-                            h = hash_row(row) >> (32 - LOG2);
-                            while (vkeys[h] != row) h = (h + 1) & (TBL - 1);
-                        }
-                        Cir[o + ee] = row + rb;
-                        Cv[o + ee] = SR::out(vals[h]);
-                        // every inserted row has its bit set, so this empties the table again;
-                        // lookups never stop at an empty slot, so clearing during reads is safe
-                        vals[h] = SR::zero();
-                        keys[h] = -1;
-                    }
+            {
+                const int64_t ob = outbase + rp.off;
+                const int nslots = direct ? (int)(r1 - r0) : TBL;
+                for (int x = tid; x < nslots; x += RT_BLOCK) {
+                    const int32_t kr = keys[x];
+                    if (kr == -1) continue;
+                    const int lr = direct ? x : (int)(kr - r0);
+                    const int wd = lr >> 5;
+                    int rank = s_gp[wd >> 2] + __popc(bitmap[wd] & ((1u << (lr & 31)) - 1u));
+                    for (int y = wd & ~3; y < wd; ++y) rank += __popc(bitmap[y]);
+                    Cir[ob + rank] = kr + rb;
+                    Cv[ob + rank] = SR::out(vals[x]);
+                    keys[x] = -1;
+                    vals[x] = SR::zero();
                 }
-                o += tot;
             }
             __syncthreads();
         }
@@ -1248,27 +1255,18 @@ static void run_range(cudaStream_t st, const Items& it, const DenseWork& dw, boo
     const int grid = (int)std::min<int64_t>(dw.ndense * MAX_PARTS, 152 * 8);
     if (!numeric) {
         const size_t smem = sizeof(RangeSmem) + 2 * (RT_MAXB + 1) * 4 + 16 + (size_t)(dw.RB / 32) * 4;
-        (void)0;
-        static size_t attr = 0;
-        if (attr < smem) {
-            cudaFuncSetAttribute(k_range_sym, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            attr = smem;
-        }
+        smem_at_least((const void*)k_range_sym, smem);
         k_range_sym<<<grid, RT_BLOCK, smem, st>>>(it, dw);
     } else {
-        auto go = [&](auto kern, int tbl, size_t& attr) {
+        auto go = [&](auto kern, int tbl) {
             const size_t smem = sizeof(RangeSmem) + (size_t)tbl * (4 + sizeof(typename SR::Acc)) + (size_t)(dw.WW) * 4 +
                                 (size_t)RT_NEXT * 16;
-            if (attr < smem) {
-                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-                attr = smem;
-            }
+            smem_at_least((const void*)kern, smem);
             kern<<<grid, RT_BLOCK, smem, st>>>(it, dw, Coff, Cir, Cv);
         };
-        static size_t attr2 = 0, attr4 = 0, attr8 = 0;
-        if (dw.tbl <= 2048) go(k_range_num<SR, 2048>, 2048, attr2);
-        else if (dw.tbl <= 4096) go(k_range_num<SR, 4096>, 4096, attr4);
-        else go(k_range_num<SR, 8192>, 8192, attr8);
+        if (dw.tbl <= 2048) go(k_range_num<SR, 2048>, 2048);
+        else if (dw.tbl <= 4096) go(k_range_num<SR, 4096>, 4096);
+        else go(k_range_num<SR, 8192>, 8192);
     }
     note_launch();
 }
