@@ -287,7 +287,13 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"rmat{args.scale}_AxA", "scale": args.scale, "edge_factor": EF,
-                       "abcd": [0.57, 0.19, 0.19, 0.05], "seed": SEED},
+                       "abcd": [0.57, 0.19, 0.19, 0.05], "seed": SEED, "grid": GRID,
+                       "products": [f"{k}_{s}" for k in args.products.split(",") if k
+                                    for s in args.semirings.split(",") if s],
+                       "flops_per_product": flops_of(A), "nnz_A": A.nnz,
+                       "reference_sample": "the oracle computes the sampled columns of the flat plus-times FP64 "
+                                           "product; blocking and the semiring change only the order of the same "
+                                           "column work"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)

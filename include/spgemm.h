@@ -86,15 +86,16 @@ typedef struct {
     int use_predictor;        /* 1: size outputs from the learned nnz predictor and skip
                                  the exact symbolic pass; overflowed columns are redone
                                  exactly, so the result is unchanged.  Default 0.      */
-    int summa_fused;          /* spgemm_summa_blocked: 1 = accumulate all stages of a
-                                 block column in one accumulator, 0 = materialise each
-                                 stage's partial products and merge them.  Default 0.  */
+    int summa_fused;          /* reserved, must be 0: spgemm_summa_blocked always
+                                 materialises each stage's partial products and merges
+                                 them (SPGEMM_ERR_UNSUPPORTED otherwise).              */
     int summa_merge_every;    /* staged mode: merge after this many stages (0 = after
                                  the last stage, the paper's buffered triples).        */
     int warp_max_flops;       /* columns with flops <= this use warp-wide hash tables  */
     int block_max_flops;      /* columns with flops <= this use CTA-wide hash tables;
-                                 larger columns use row-chunked dense accumulators     */
-    int dense_part_flops;     /* target flops per CTA when a dense column is split     */
+                                 longer columns (the range tier) are cut into row ranges
+                                 of bounded output, each accumulated by one CTA          */
+    int dense_part_flops;     /* range tier: target flops per row slab of a long column */
     float predictor_margin;   /* capacity = (1 + margin) * prediction (+ slack)        */
     int range_table_slots;    /* long columns: hash slots per row range, 2048, 4096 or
                                  8192 (0 = default 4096); a range holds < slots/2 entries */

@@ -1,14 +1,19 @@
 // Batched column-wise SpGEMM kernels (Gustavson's column-by-column
 // formulation, Section 2.1; accumulation in the spirit of the sparse
-// accumulator of Section 3.3), organised in three accumulator tiers chosen per
+// accumulator of Section 3.3), organised in accumulator tiers chosen per
 // output column from cap = min(flops, m):
+//   * one thread per column for flops <= 16 (insertion sort in registers),
 //   * warp-wide shared-memory hash tables (short columns),
 //   * CTA-wide shared-memory hash tables (medium columns),
-//   * a row-chunked dense accumulator (long columns): R rows of values plus an
-//     R-bit occupancy map per chunk, walked chunk by chunk with per-(column,k)
-//     cursors into A(:,k); rows come out sorted, so no sort is needed.
+//   * the range tier (long columns): the symbolic pass marks the column's rows
+//     in a shared-memory bitmap per row slab and cuts the slab into row ranges
+//     of bounded output; the numeric pass walks the ranges in row order with
+//     per-(column, k) cursors into A(:,k), accumulates each range in a hash
+//     table (or a dense row array when the range is narrow) and writes it out
+//     in row order through the range's bitmap.
 // The symbolic pass counts nnz per output column; the numeric pass fills rows
-// and values.  Every kernel works on items (product, stored column of B).
+// and values, in ascending row order without a sort wherever a row bitmap fits
+// in shared memory.  Every kernel works on items (product, stored column of B).
 #include <algorithm>
 #include <atomic>
 #include <climits>
@@ -56,15 +61,6 @@ __host__ __device__ __forceinline__ int bin_of(int64_t flops, int64_t cap, int w
         return b;
     }
     return BIN_DENSE;
-}
-
-int dense_rows_for(int semiring, int requested) {
-    if (requested > 0) return std::max(32, (requested / 32) * 32);
-    switch (semiring) {
-    case SPGEMM_PLUS_TIMES_F64:
-    case SPGEMM_PLUS_TIMES_I64: return 8192;
-    default: return 16384;
-    }
 }
 
 __device__ __forceinline__ int find_prod(const int64_t* __restrict__ base, int64_t nprod, int64_t u) {

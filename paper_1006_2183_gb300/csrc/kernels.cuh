@@ -135,7 +135,6 @@ void launch_fill_i64(cudaStream_t st, int64_t* p, int64_t n, int64_t v);
 void launch_tier_stats(cudaStream_t st, const Items& it, const uint8_t* bin, const int32_t* item_prod,
                        const int64_t* flops, const int64_t* nnz_item, unsigned long long* out);
 
-int dense_rows_for(int semiring, int requested);
 
 // process-wide count of kernel launches made by this library
 void note_launch(int n = 1);

@@ -378,6 +378,7 @@ spgemm_status_t spgemm_summa_blocked(spgemm_ctx_t ctx, spgemm_mat_t A, spgemm_ma
     spgemm_opts_t o;
     spgemm_opts_default(&o);
     if (opts) o = *opts;
+    if (o.summa_fused != 0) return set_err(ctx, SPGEMM_ERR_UNSUPPORTED, "summa_fused is reserved (must be 0)");
     spgemm_mat_t Ac = nullptr, Bc = nullptr;
     DMat dA, dB;
     SG_TRY(to_csc_operand(ctx, A, &Ac, &dA));

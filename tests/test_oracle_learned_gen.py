@@ -128,3 +128,24 @@ def test_batch_pairs_shapes():
     for A, B in pairs:
         assert A.n == B.m and 64 <= A.n < 512
         assert A.vals.dtype == np.int64 and A.vals.min() >= -8 and A.vals.max() <= 8
+
+
+def test_generators_do_not_depend_on_threads(monkeypatch):
+    """Threaded generation fills chunks of counters; the matrices must not depend on
+    the chunking or on whether threads are used."""
+    ref = gen.rmat(12, 8, 0x77)
+    refp = gen.batch_pairs(3, 0x99, 6, 9)
+    monkeypatch.setattr(gen, "_EDGE_CHUNK", 1000)
+    thr = gen.rmat(12, 8, 0x77)
+    gen._tls.serial = True
+    try:
+        ser = gen.rmat(12, 8, 0x77)
+    finally:
+        gen._tls.serial = False
+    for M in (thr, ser):
+        np.testing.assert_array_equal(M.colptr, ref.colptr)
+        np.testing.assert_array_equal(M.rowidx, ref.rowidx)
+        np.testing.assert_array_equal(M.vals, ref.vals)
+    for (a, b), (c, d) in zip(gen.batch_pairs(3, 0x99, 6, 9), refp):
+        np.testing.assert_array_equal(a.rowidx, c.rowidx)
+        np.testing.assert_array_equal(b.vals, d.vals)
