@@ -954,22 +954,49 @@ __global__ void __launch_bounds__(RT_BLOCK) k_range_sym(Items it, DenseWork dw) 
         for (int x = w0; x < w1; ++x) cnt += __popc(bitmap[x]);
         int total;
         const int excl = group_incl_scan<RT_BLOCK>(cnt, s_scan, total) - cnt;
-        int nb = 0;
+        // Entries before each window of WW words (the numeric bitmap's reach): every
+        // window is cut into the fewest ranges of < H entries, of equal size, so a
+        // window never leaves a small remainder range.
+        int* s_win = reinterpret_cast<int*>(sc->ws);   // <= 33 windows per slab (RB <= 2^20 rows)
         {
             int bp = excl;
             for (int x = w0; x < w1; ++x) {
-                const int prev = x > 0 ? bp - __popc(bitmap[x - 1]) : 0;
-                if (x == 0 || x % dw.WW == 0 || bp / dw.H > prev / dw.H) ++nb;
+                if (x % dw.WW == 0) s_win[x / dw.WW] = bp;
+                bp += __popc(bitmap[x]);
+            }
+            if (tid == 0) s_win[(nw + dw.WW - 1) / dw.WW] = total;
+        }
+        __syncthreads();
+        // cut words of this thread's word range, as a mask (wpt <= 64 words): a window
+        // start, or the first word at or past the window's next multiple of `size`
+        uint64_t cuts = 0;
+        {
+            int bp = excl, base = 0, size = 1, next = INT_MAX;
+            for (int x = w0; x < w1; ++x) {
+                const bool wstart = x % dw.WW == 0;
+                if (wstart || x == w0) {
+                    base = s_win[x / dw.WW];
+                    const int e = s_win[x / dw.WW + 1] - base;
+                    const int nr = (e + dw.H - 1) / dw.H;
+                    size = nr > 0 ? (e + nr - 1) / nr : 1;
+                    // the next multiple of size above the entries before word x - 1
+                    const int prev = wstart ? bp : bp - __popc(bitmap[x - 1]);
+                    next = base + ((prev - base) / size + 1) * size;
+                }
+                if (wstart || bp >= next) {
+                    cuts |= 1ull << (x - w0);
+                    if (!wstart) next = base + ((bp - base) / size + 1) * size;
+                }
                 bp += __popc(bitmap[x]);
             }
         }
+        const int nb = __popcll(cuts);
         int nbt;
         const int bexcl = group_incl_scan<RT_BLOCK>(nb, s_scan, nbt) - nb;
         {
             int bp = excl, o = bexcl;
             for (int x = w0; x < w1; ++x) {
-                const int prev = x > 0 ? bp - __popc(bitmap[x - 1]) : 0;
-                if (x == 0 || x % dw.WW == 0 || bp / dw.H > prev / dw.H) {
+                if ((cuts >> (x - w0)) & 1) {
                     if (o < RT_MAXB) {
                         s_bw[o] = x;
                         s_bp[o] = bp;
