@@ -138,6 +138,37 @@ def learned_vs_plain(sp, ctx, steps: int, warmup: int) -> dict:
     return out
 
 
+def imbalance(bf: np.ndarray) -> dict:
+    """Load imbalance of Section 7.1 (max flops of any processor / mean) from the
+    block-product flops bf[s, J, I] of a g x g grid: per stage with SUMMA's pairing
+    A(I,s)B(s,J) and with Sparse Cannon's A(I,k)B(k,J), k = (I+J+s) mod g (the
+    pairing of the paper's Fig. 25/26 simulation), and over all stages."""
+    g = bf.shape[0]
+    I, J = np.meshgrid(np.arange(g), np.arange(g), indexing="ij")
+
+    def ratio(x):
+        mu = x.mean()
+        return float(x.max() / mu) if mu > 0 else 1.0
+    summa = [ratio(bf[s]) for s in range(g)]
+    cannon = [ratio(bf[(I + J + s) % g, J, I]) for s in range(g)]
+    return {"overall": ratio(bf.sum(axis=0)), "per_stage_mean_summa": float(np.mean(summa)),
+            "per_stage_max_summa": float(np.max(summa)), "per_stage_mean_cannon": float(np.mean(cannon)),
+            "per_stage_max_cannon": float(np.max(cannon))}
+
+
+def summa_imbalance(sp, ctx, M, g: int, seed: int = 0x5EED) -> dict:
+    """Block-work imbalance of the virtual grid for A*A, as given and after a random
+    symmetric permutation A' = PAP^T (Section 5.3.3), both computed on the device."""
+    import torch
+    out = {"grid": g, "plain": imbalance(sp.spgemm_summa_block_flops(ctx, M, M, g))}
+    perm = torch.from_numpy(np.random.default_rng(seed).permutation(M.shape()[0]).astype(np.int32)).to(ctx.device)
+    Mp = sp.spgemm_mat_permute(ctx, M, perm, perm)
+    out["permuted"] = imbalance(sp.spgemm_summa_block_flops(ctx, Mp, Mp, g))
+    out["paper_context"] = ("Sparse Cannon on R-MAT scale 20 (a=0.6, b=c=d=0.13), 256 processors, permuted: "
+                            "per-stage mean 1.46, overall below 1.1 (Section 7.1, Figs. 25-26)")
+    return out
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -489,6 +520,7 @@ def main():
                "sample": f"every {CPU_STRIDE}th output column ({len(cols)} columns, {fl} flops) of the flat "
                          f"plus-times FP64 product, {dt:.2f} s wall on {oracle.max_threads()} threads"}
 
+    imb = summa_imbalance(sp, ctx, mats[sp.PLUS_TIMES_F64], GRID) if rank == 0 else None
     lvp = None
     if rank == 0 and world == 1 and not args.no_learned:
         lvp = learned_vs_plain(sp, ctx, steps=2, warmup=1)
@@ -504,7 +536,7 @@ def main():
                            "pipeline_hbm_frac": pipeline_frac, "pipeline": pipe, "phase_ms_per_step": phase_tab,
                            "lib_opts": {k: v for k, v in (o.split("=", 1) for o in args.opt)}},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
-                "learned_batched_vs_plain": lvp}
+                "learned_batched_vs_plain": lvp, "summa_imbalance": imb}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

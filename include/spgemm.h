@@ -139,6 +139,15 @@ spgemm_status_t spgemm_mat_validate(spgemm_mat_t mat);
 spgemm_status_t spgemm_mat_to_dcsc(spgemm_ctx_t ctx, spgemm_mat_t csc, int build_aux, spgemm_mat_t* out);
 /* Transpose (Section 2.4 transposes B once): CSC of A^T, rows sorted.  Owns its arrays. */
 spgemm_status_t spgemm_mat_transpose(spgemm_ctx_t ctx, spgemm_mat_t a, spgemm_mat_t* out);
+/* Permuted copy B = P A Q^T, B(row_perm[i], col_perm[j]) = A(i, j) (the random
+ * symmetric permutation of Section 5.3.3 relabels vertices so that
+ * C' = (PAP^T)(PBP^T) = PCP^T balances the 2D grid).  row_perm (m entries) and
+ * col_perm (n entries) are device int32 arrays, each a permutation; NULL means
+ * the identity.  A is CSC or CSR.  Result: CSC, rows sorted, owning its arrays.
+ * Errors: INVALID_ARG when an array is not a permutation (checked on the device;
+ * synchronises the stream), UNSUPPORTED for DCSC, INDEX_OVERFLOW for nnz >= 2^32. */
+spgemm_status_t spgemm_mat_permute(spgemm_ctx_t ctx, spgemm_mat_t a, const int32_t* row_perm,
+                                   const int32_t* col_perm, spgemm_mat_t* out);
 /* Read back a handle's shape and device arrays.  For DCSC, colptr is CP,
  * jc/aux/nzc/chunk describe the compressed column index (NULL outputs are
  * skipped).  Pointers stay owned by the handle. */
@@ -221,6 +230,12 @@ spgemm_status_t spgemm_summa_blocked(spgemm_ctx_t ctx, spgemm_mat_t A, spgemm_ma
 /* Block statistics of the last summa call on this context: per-stage flops
  * (g entries) and the number of nonempty block products.  Outputs may be NULL. */
 spgemm_status_t spgemm_summa_stats(spgemm_ctx_t ctx, int64_t* stage_flops, int g, int64_t* nonempty_products);
+/* Work of every block product of the virtual grid, without computing it:
+ * flops[(s*g + J)*g + I] = flops(A_{I,s} * B_{s,J}) (multiply count), for the
+ * load-imbalance measure of Section 7.1 (max over processors / mean, per stage
+ * and over all stages).  flops is a host array of g*g*g int64; A and B as for
+ * spgemm_summa_blocked (only the structure is used).  Synchronises the stream. */
+spgemm_status_t spgemm_summa_block_flops(spgemm_ctx_t ctx, spgemm_mat_t A, spgemm_mat_t B, int g, int64_t* flops);
 
 /* ---------------------------------------------------------------- batching */
 /* count independent products C[i] = A[i]*B[i] (all over one semiring) in one

@@ -96,3 +96,16 @@ def partition(m: int, n: int, colptr, rowidx, vals, g: int):
             cp, ir, nv = extract_block(m, n, colptr, rowidx, vals, r0, r1, c0, c1)
             out[(I, J)] = (r0, r1, c0, c1, cp, ir, nv)
     return out
+
+
+def permute(m: int, n: int, colptr, rowidx, vals, p, q):
+    """B = P A Q^T, i.e. B(p[i], q[j]) = A(i, j): the vertex relabelling of Section
+    5.3.3 (C' = (PAP^T)(PBP^T) = PCP^T).  By the definition: every entry moves to
+    (p[row], q[col]), then the entries are ordered by (column, row)."""
+    cols = np.repeat(np.arange(n, dtype=np.int64), np.diff(colptr))
+    r2 = np.asarray(p, dtype=np.int64)[np.asarray(rowidx, dtype=np.int64)]
+    c2 = np.asarray(q, dtype=np.int64)[cols]
+    order = np.lexsort((r2, c2))
+    cp = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(np.bincount(c2, minlength=n), out=cp[1:])
+    return cp, r2[order].astype(np.int32), np.asarray(vals)[order]

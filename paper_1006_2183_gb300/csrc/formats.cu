@@ -326,7 +326,172 @@ spgemm_status_t make_dcsc(spgemm_ctx* ctx, const spgemm_mat* M, bool with_aux, s
     return SPGEMM_OK;
 }
 
+// ------------------------------------------------------------------ permutation
+// B = P A Q^T, B(p[i], q[j]) = A(i, j): the relabelling behind the random symmetric
+// permutation of Section 5.3.3 (C' = (PAP^T)(PBP^T) = PCP^T) used to balance the 2D grid.
+
+// counts[v]++ for every permutation entry; entries outside [0, n) raise the flag
+__global__ void k_perm_count(const int32_t* __restrict__ perm, int64_t n, int32_t* __restrict__ cnt, int* bad) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = perm[i];
+        if (v < 0 || v >= n) atomicExch(bad, 1);
+        else atomicAdd(cnt + v, 1);
+    }
+}
+
+// a permutation hits every value exactly once
+__global__ void k_perm_check(const int32_t* __restrict__ cnt, int64_t n, int* bad) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (cnt[i] != 1) atomicExch(bad, 1);
+}
+
+// first sort key: the new row p[ir[t]] of every entry, and the entry index
+__global__ void k_perm_rows(const int32_t* __restrict__ ir, const int32_t* __restrict__ rowp, int64_t nnz,
+                            uint32_t* __restrict__ key, uint32_t* __restrict__ idx) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nnz; t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t r = ir[t];
+        key[t] = (uint32_t)(rowp ? rowp[r] : r);
+        idx[t] = (uint32_t)t;
+    }
+}
+
+// second sort key: the new column q[col(t)] of the entries in their row-sorted order
+__global__ void k_perm_cols(const uint32_t* __restrict__ idx, const int32_t* __restrict__ colid,
+                            const int32_t* __restrict__ colp, int64_t nnz, uint32_t* __restrict__ key,
+                            int64_t* __restrict__ colcnt) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = colid[idx[i]];
+        const uint32_t nc = (uint32_t)(colp ? colp[c] : c);
+        key[i] = nc;
+        atomicAdd(reinterpret_cast<unsigned long long*>(colcnt + nc), 1ull);
+    }
+}
+
+template <int W>
+__global__ void k_perm_gather(const uint32_t* __restrict__ idx, const int32_t* __restrict__ ir,
+                              const int32_t* __restrict__ rowp, const void* __restrict__ vin, int64_t nnz,
+                              int32_t* __restrict__ ir_out, void* __restrict__ vout) {
+    using T = typename Word<W>::T;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t t = idx[i];
+        const int32_t r = ir[t];
+        ir_out[i] = rowp ? rowp[r] : r;
+        if (vin) reinterpret_cast<T*>(vout)[i] = reinterpret_cast<const T*>(vin)[t];
+    }
+}
+
+static int bits_for(int64_t n) {
+    int b = 0;
+    while (b < 32 && (int64_t(1) << b) < n) ++b;
+    return b;
+}
+
+// Checks that perm (n entries) is a permutation of 0..n-1 (synchronises the stream).
+static spgemm_status_t check_perm(spgemm_ctx* ctx, const int32_t* perm, int64_t n, const char* what) {
+    if (!perm || n == 0) return SPGEMM_OK;
+    cudaStream_t st = ctx->stream;
+    auto b = ctx_buf(ctx, 4 * n + 16);
+    if (!b) return set_err(ctx, SPGEMM_ERR_OOM, "permutation check");
+    int32_t* cnt = (int32_t*)b->p;
+    int* bad = (int*)(cnt + n);
+    SG_CUDA(ctx, cudaMemsetAsync(b->p, 0, 4 * n + 16, st));
+    k_perm_count<<<grid_for(n), 256, 0, st>>>(perm, n, cnt, bad);
+    k_perm_check<<<grid_for(n), 256, 0, st>>>(cnt, n, bad);
+    note_launch(2);
+    int h = 0;
+    SG_CUDA(ctx, cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SG_TRY(sync_ctx(ctx));
+    if (h) return set_err(ctx, SPGEMM_ERR_INVALID_ARG, "%s is not a permutation of 0..%lld", what, (long long)(n - 1));
+    return SPGEMM_OK;
+}
+
+static spgemm_status_t permute_csc(spgemm_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const int64_t* cp,
+                                   const int32_t* ir, const void* num, size_t w, const int32_t* rowp,
+                                   const int32_t* colp, spgemm_mat* out) {
+    cudaStream_t st = ctx->stream;
+    if (nnz > (int64_t)UINT32_MAX) return set_err(ctx, SPGEMM_ERR_INDEX_OVERFLOW, "permute: nnz beyond 2^32");
+    const int64_t nz1 = std::max<int64_t>(nnz, 1);
+    auto cpb = ctx_buf(ctx, 8 * (n + 1));
+    auto irb = ctx_buf(ctx, 4 * nz1);
+    auto vb = ctx_buf(ctx, w * nz1);
+    const size_t rs = radix_tmp_bytes(nnz);
+    auto tmp = ctx_buf(ctx, 5 * 4 * nz1 + 8 * (n + 1) + rs + scan_tmp_bytes(std::max<int64_t>(n, 1)) + 1024);
+    if (!cpb || !irb || !vb || !tmp) return set_err(ctx, SPGEMM_ERR_OOM, "permute buffers");
+    char* t = (char*)tmp->p;
+    uint32_t* k0 = (uint32_t*)t; t += 4 * nz1;
+    uint32_t* k1 = (uint32_t*)t; t += 4 * nz1;
+    uint32_t* v0 = (uint32_t*)t; t += 4 * nz1;
+    uint32_t* v1 = (uint32_t*)t; t += 4 * nz1;
+    int32_t* colid = (int32_t*)t; t += 4 * nz1;
+    t = (char*)(((uintptr_t)t + 255) / 256 * 256);
+    int64_t* colcnt = (int64_t*)t; t += 8 * (n + 1);
+    t = (char*)(((uintptr_t)t + 255) / 256 * 256);
+    void* rtmp = t; t += rs;
+    t = (char*)(((uintptr_t)t + 255) / 256 * 256);
+    void* stmp = t;
+    int64_t* ocp = (int64_t*)cpb->p;
+    SG_CUDA(ctx, cudaMemsetAsync(colcnt, 0, 8 * (n + 1), st));
+    if (nnz > 0) {
+        // LSD order: by new row, then stably by new column
+        k_perm_rows<<<grid_for(nnz), 256, 0, st>>>(ir, rowp, nnz, k0, v0);
+        k_expand_cols<<<(int)ceil_div64(n * 8, 256) + 1, 256, 0, st>>>(cp, n, colid);
+        note_launch(2);
+        bool second = false;
+        radix_sort_pairs(st, k0, v0, k1, v1, nnz, bits_for(m), rtmp, &second);
+        uint32_t* vr = second ? v1 : v0;   // entry indices in new-row order
+        uint32_t* kA = second ? k0 : k1;   // free key buffer
+        uint32_t* kB = second ? k1 : k0;   // the row keys, no longer needed
+        uint32_t* vB = second ? v0 : v1;   // free value buffer
+        k_perm_cols<<<grid_for(nnz), 256, 0, st>>>(vr, colid, colp, nnz, kA, colcnt);
+        note_launch();
+        bool second2 = false;
+        radix_sort_pairs(st, kA, vr, kB, vB, nnz, bits_for(n), rtmp, &second2);
+        const uint32_t* fin = second2 ? vB : vr;
+        switch (w) {
+        case 1: k_perm_gather<1><<<grid_for(nnz), 256, 0, st>>>(fin, ir, rowp, num, nnz, (int32_t*)irb->p, vb->p); break;
+        case 4: k_perm_gather<4><<<grid_for(nnz), 256, 0, st>>>(fin, ir, rowp, num, nnz, (int32_t*)irb->p, vb->p); break;
+        default: k_perm_gather<8><<<grid_for(nnz), 256, 0, st>>>(fin, ir, rowp, num, nnz, (int32_t*)irb->p, vb->p); break;
+        }
+        note_launch();
+    }
+    launch_exclusive_scan(st, colcnt, n, ocp, stmp);
+    SG_CUDA(ctx, cudaGetLastError());
+    out->ctx = ctx;
+    out->fmt = SPGEMM_FMT_CSC;
+    out->m = m;
+    out->n = n;
+    out->nnz = nnz;
+    out->nzc = n;
+    out->cp = ocp;
+    out->ir = (const int32_t*)irb->p;
+    out->num = num ? vb->p : nullptr;
+    out->owned = {cpb, irb, vb};
+    SG_TRY(sync_ctx(ctx));   // the temporaries are released when this call returns
+    return SPGEMM_OK;
+}
+
 extern "C" {
+
+spgemm_status_t spgemm_mat_permute(spgemm_ctx_t ctx, spgemm_mat_t a, const int32_t* row_perm,
+                                   const int32_t* col_perm, spgemm_mat_t* out) {
+    if (!ctx || !a || !out) return SPGEMM_ERR_INVALID_ARG;
+    if (a->fmt == SPGEMM_FMT_DCSC) return set_err(ctx, SPGEMM_ERR_UNSUPPORTED, "permute of a DCSC handle");
+    SG_TRY(check_perm(ctx, row_perm, a->m, "row_perm"));
+    SG_TRY(check_perm(ctx, col_perm, a->n, "col_perm"));
+    spgemm_mat_t conv = nullptr;
+    DMat d;
+    SG_TRY(to_csc_operand(ctx, a, &conv, &d));
+    std::unique_ptr<spgemm_mat> hold(conv);
+    auto* P = new spgemm_mat();
+    spgemm_status_t s = permute_csc(ctx, d.m, d.n, d.nnz, d.cp, d.ir, d.num, sr_size(a->sr), row_perm, col_perm, P);
+    if (s != SPGEMM_OK) {
+        delete P;
+        return s;
+    }
+    P->sr = a->sr;
+    *out = P;
+    return SPGEMM_OK;
+}
 
 spgemm_status_t spgemm_mat_transpose(spgemm_ctx_t ctx, spgemm_mat_t a, spgemm_mat_t* out) {
     if (!ctx || !a || !out) return SPGEMM_ERR_INVALID_ARG;

@@ -507,6 +507,55 @@ spgemm_status_t spgemm_summa_blocked(spgemm_ctx_t ctx, spgemm_mat_t A, spgemm_ma
     return SPGEMM_OK;
 }
 
+spgemm_status_t spgemm_summa_block_flops(spgemm_ctx_t ctx, spgemm_mat_t A, spgemm_mat_t B, int g, int64_t* flops) {
+    if (!ctx || !A || !B || !flops) return SPGEMM_ERR_INVALID_ARG;
+    if (g < 1 || g > 1024) return set_err(ctx, SPGEMM_ERR_INVALID_ARG, "grid size g = %d outside [1, 1024]", g);
+    if (A->n != B->m) return set_err(ctx, SPGEMM_ERR_DIM_MISMATCH, "inner dimensions differ");
+    if (A->fmt == SPGEMM_FMT_DCSC || B->fmt == SPGEMM_FMT_DCSC)
+        return set_err(ctx, SPGEMM_ERR_UNSUPPORTED, "summa takes CSC or CSR operands");
+    spgemm_mat_t Ac = nullptr, Bc = nullptr;
+    DMat dA, dB;
+    SG_TRY(to_csc_operand(ctx, A, &Ac, &dA));
+    spgemm_status_t st0 = to_csc_operand(ctx, B, &Bc, &dB);
+    std::unique_ptr<spgemm_mat> holdA(Ac), holdB(Bc);
+    if (st0 != SPGEMM_OK) return st0;
+    const size_t w = sr_size(A->sr);
+    Blocked bA, bB;
+    SG_TRY(partition(ctx, dA, w, g, &bA));
+    SG_TRY(partition(ctx, dB, w, g, &bB));
+    const size_t g3 = (size_t)g * g * g;
+    std::fill(flops, flops + g3, int64_t(0));
+    std::vector<Prod> all;
+    std::vector<size_t> slot;
+    for (int st = 0; st < g; ++st)
+        for (int J = 0; J < g; ++J)
+            for (int I = 0; I < g; ++I) {
+                const DMat& a = bA.at(I, st);
+                const DMat& b = bB.at(st, J);
+                if (a.nnz == 0 || b.nnz == 0 || a.m == 0 || b.n == 0) continue;
+                Prod pr;
+                pr.A = a;
+                pr.B = b;
+                all.push_back(pr);
+                slot.push_back(((size_t)st * g + J) * g + I);
+            }
+    if (all.empty()) return SPGEMM_OK;
+    spgemm_opts_t o;
+    spgemm_opts_default(&o);
+    Engine E;
+    SG_TRY(engine_setup(&E, ctx, A->sr, o, all, false));
+    auto pf = ctx_buf(ctx, 8 * all.size());
+    if (!pf) return set_err(ctx, SPGEMM_ERR_OOM, "block flops");
+    SG_CUDA(ctx, cudaMemsetAsync(pf->p, 0, 8 * all.size(), ctx->stream));
+    k_prod_flops<<<gridn(E.it.nitems), 256, 0, ctx->stream>>>(E.it, E.item_prod, E.flops, (unsigned long long*)pf->p);
+    note_launch();
+    std::vector<unsigned long long> h(all.size());
+    SG_CUDA(ctx, cudaMemcpyAsync(h.data(), pf->p, 8 * all.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    SG_TRY(sync_ctx(ctx));
+    for (size_t i = 0; i < all.size(); ++i) flops[slot[i]] = (int64_t)h[i];
+    return SPGEMM_OK;
+}
+
 spgemm_status_t spgemm_summa_stats(spgemm_ctx_t ctx, int64_t* stage_flops, int g, int64_t* nonempty) {
     if (!ctx) return SPGEMM_ERR_INVALID_ARG;
     if (stage_flops)

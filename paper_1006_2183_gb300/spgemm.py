@@ -74,6 +74,8 @@ _sig("spgemm_mat_csr", [P, PP, I64, I64, I64, P, P, P, ctypes.c_int])
 _sig("spgemm_mat_validate", [P])
 _sig("spgemm_mat_to_dcsc", [P, P, ctypes.c_int, PP])
 _sig("spgemm_mat_transpose", [P, P, PP])
+_sig("spgemm_mat_permute", [P, P, P, P, PP])
+_sig("spgemm_summa_block_flops", [P, P, P, ctypes.c_int, ctypes.POINTER(I64)])
 _sig("spgemm_mat_export", [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64), PP, PP, PP])
 _sig("spgemm_mat_export_dcsc", [P, ctypes.POINTER(I64), PP, PP, ctypes.POINTER(I64), ctypes.POINTER(I64)])
 _sig("spgemm_mat_format", [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)])
@@ -458,6 +460,26 @@ def spgemm_mat_to_dcsc(ctx: Context, A: Matrix, build_aux: bool = True) -> Matri
     h = ctypes.c_void_p()
     ctx._check(_lib.spgemm_mat_to_dcsc(ctx.handle, A.handle, int(build_aux), ctypes.byref(h)))
     return Matrix(ctx, h, A.semiring, (A,))
+
+
+def spgemm_mat_permute(ctx: Context, A: Matrix, row_perm: torch.Tensor | None = None,
+                       col_perm: torch.Tensor | None = None) -> Matrix:
+    """B = P A Q^T with B(row_perm[i], col_perm[j]) = A(i, j); perms are device int32 tensors."""
+    for t in (row_perm, col_perm):
+        if t is not None:
+            assert t.dtype == torch.int32 and t.is_cuda and t.is_contiguous()
+    _order_after_current(ctx)
+    h = ctypes.c_void_p()
+    ctx._check(_lib.spgemm_mat_permute(ctx.handle, A.handle, _ptr(row_perm), _ptr(col_perm), ctypes.byref(h)))
+    return Matrix(ctx, h, A.semiring, (A,))
+
+
+def spgemm_summa_block_flops(ctx: Context, A: Matrix, B: Matrix, g: int) -> np.ndarray:
+    """flops of every block product of the g x g grid, as an array indexed [s, J, I]."""
+    out = (I64 * (g * g * g))()
+    _order_after_current(ctx)
+    ctx._check(_lib.spgemm_summa_block_flops(ctx.handle, A.handle, B.handle, g, out))
+    return np.frombuffer(out, dtype=np.int64).reshape(g, g, g).copy()
 
 
 def spgemm_mat_transpose(ctx: Context, A: Matrix) -> Matrix:

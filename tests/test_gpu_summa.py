@@ -122,3 +122,73 @@ def test_summa_scale18_sampled(ctx):
         got = C.vals[C.colptr[j]:C.colptr[j + 1]]
         ref = R.vals[R.colptr[t]:R.colptr[t + 1]]
         assert np.all(np.abs(got - ref) <= 1e-13 * np.abs(ref)), j
+
+
+@pytest.mark.parametrize("g", [4, 7, 16])
+def test_summa_block_flops_match_oracle(ctx, g):
+    """Per-block work flops(A(I,s) * B(s,J)) against the oracle's block split, and
+    their sum against the flat flops (Section 7.1's load-imbalance input)."""
+    s = sp()
+    A = gen.rmat(11, 8, 0x7101, PT_F64)
+    B = gen.erdos_renyi(A.n, 300, 5, 0x7102, PT_F64)
+    got = s.spgemm_summa_block_flops(ctx, s.Matrix.from_host(ctx, A, PT_F64), s.Matrix.from_host(ctx, B, PT_F64), g)
+    ba = of.partition(A.m, A.n, A.colptr, A.rowidx, A.vals, g)
+    bb = of.partition(B.m, B.n, B.colptr, B.rowidx, B.vals, g)
+    want = np.zeros((g, g, g), np.int64)
+    for st in range(g):
+        for J in range(g):
+            for I in range(g):
+                r0, r1, c0, c1, cpa, ira, va = ba[(I, st)]
+                s0, s1, d0, d1, cpb, irb, vb = bb[(st, J)]
+                Ab = CSC(r1 - r0, c1 - c0, cpa, ira, va)
+                Bb = CSC(s1 - s0, d1 - d0, cpb, irb, vb)
+                if Ab.n and Bb.n:
+                    want[st, J, I] = int(oracle.flops_per_col(Ab, Bb).sum())
+    np.testing.assert_array_equal(got, want)
+    assert got.sum() == int(oracle.flops_per_col(A, B).sum())
+
+
+@pytest.mark.parametrize("sr", [PT_I64, OR_BOOL])
+def test_random_symmetric_permutation(ctx, sr):
+    """A' = P A P^T on the device equals the oracle's permutation, and
+    A'A' = P (AA) P^T exactly, flat and on the grid (Section 5.3.3)."""
+    import torch
+    s = sp()
+    A = gen.rmat(13, 8, 0x7201, sr)
+    p = np.random.default_rng(0x7202).permutation(A.n).astype(np.int32)
+    pd = torch.from_numpy(p).to(ctx.device)
+    dA = s.Matrix.from_host(ctx, A, sr)
+    dAp = s.spgemm_mat_permute(ctx, dA, pd, pd)
+    ref = of.permute(A.m, A.n, A.colptr, A.rowidx, A.vals, p, p)
+    Ap = dAp.to_host()
+    np.testing.assert_array_equal(Ap.colptr, ref[0])
+    np.testing.assert_array_equal(Ap.rowidx, ref[1])
+    np.testing.assert_array_equal(Ap.vals, ref[2])
+    C = s.spgemm_multiply(ctx, dA, dA, sr)
+    Cperm = s.spgemm_mat_permute(ctx, C, pd, pd).to_host()
+    for Cp in (s.spgemm_multiply(ctx, dAp, dAp, sr).to_host(), s.spgemm_summa_blocked(ctx, dAp, dAp, 16, sr).to_host()):
+        assert_matches(Cp, Cperm, sr)
+    # a rectangular permutation with different row and column maps
+    B = gen.random_csc(300, 170, 0.05, 0x7203, sr)
+    pr = np.random.default_rng(1).permutation(300).astype(np.int32)
+    pc = np.random.default_rng(2).permutation(170).astype(np.int32)
+    got = s.spgemm_mat_permute(ctx, s.Matrix.from_host(ctx, B, sr), torch.from_numpy(pr).to(ctx.device),
+                               torch.from_numpy(pc).to(ctx.device)).to_host()
+    ref = of.permute(B.m, B.n, B.colptr, B.rowidx, B.vals, pr, pc)
+    np.testing.assert_array_equal(got.colptr, ref[0])
+    np.testing.assert_array_equal(got.rowidx, ref[1])
+    np.testing.assert_array_equal(got.vals, ref[2])
+
+
+def test_permute_rejects_non_permutations(ctx):
+    import torch
+    s = sp()
+    A = gen.random_csc(50, 50, 0.1, 0x7301, PT_I64)
+    dA = s.Matrix.from_host(ctx, A, PT_I64)
+    dup = torch.zeros(50, dtype=torch.int32, device=ctx.device)
+    out_of_range = torch.arange(50, dtype=torch.int32, device=ctx.device) + 1
+    for bad in (dup, out_of_range):
+        with pytest.raises(s.SpGEMMError):
+            s.spgemm_mat_permute(ctx, dA, bad, None)
+    ok = s.spgemm_mat_permute(ctx, dA, None, None).to_host()   # identity
+    np.testing.assert_array_equal(ok.rowidx, A.rowidx)

@@ -358,3 +358,30 @@ def test_threads_do_not_change_result():
     C4 = oracle.spgemm(A, A, PT_F64, nthreads=4)
     np.testing.assert_array_equal(C1.rowidx, C4.rowidx)
     np.testing.assert_array_equal(C1.vals, C4.vals)
+
+
+def test_permute_definition_and_pcpt_identity():
+    """permute moves A(i,j) to (p[i], q[j]) (checked on dense arrays), the inverse
+    permutation undoes it, and (PAP^T)(PAP^T) = P(AA)P^T exactly (Section 5.3.3)."""
+    A = gen.random_csc(40, 40, 0.12, 0x51, PT_I64)
+    p = np.random.default_rng(5).permutation(40)
+    q = np.random.default_rng(6).permutation(40)
+    cp, ir, v = of.permute(A.m, A.n, A.colptr, A.rowidx, A.vals, p, q)
+    dense_a = np.zeros((40, 40), np.int64)
+    for j in range(40):
+        dense_a[A.rowidx[A.colptr[j]:A.colptr[j + 1]], j] = A.vals[A.colptr[j]:A.colptr[j + 1]]
+    dense_b = np.zeros((40, 40), np.int64)
+    for j in range(40):
+        seg = slice(cp[j], cp[j + 1])
+        assert np.all(np.diff(ir[seg]) > 0)
+        dense_b[ir[seg], j] = v[seg]
+    assert np.array_equal(dense_b[np.ix_(p, q)], dense_a)
+    back = of.permute(40, 40, cp, ir, v, np.argsort(p), np.argsort(q))
+    assert np.array_equal(back[0], A.colptr) and np.array_equal(back[1], A.rowidx) and np.array_equal(back[2], A.vals)
+    B = gen.rmat(9, 8, 0x52, PT_I64)
+    p = np.random.default_rng(7).permutation(B.n)
+    Bp = CSC(B.m, B.n, *of.permute(B.m, B.n, B.colptr, B.rowidx, B.vals, p, p))
+    C = oracle.spgemm(B, B, PT_I64)
+    Cp = oracle.spgemm(Bp, Bp, PT_I64)
+    ref = of.permute(C.m, C.n, C.colptr, C.rowidx, C.vals, p, p)
+    assert np.array_equal(Cp.colptr, ref[0]) and np.array_equal(Cp.rowidx, ref[1]) and np.array_equal(Cp.vals, ref[2])
