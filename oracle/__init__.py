@@ -13,6 +13,8 @@ Contents
     definitions in numpy.
   * ``features.py`` / ``mlp.py``: the per-column predictor features and a
     float64 forward/backward of the nnz predictor network.
+  * ``hgemm.py``: a second, independent formulation of the product, the
+    hypersparse outer-product multiply of Section 2.4 (Isect, heap merge).
 
 Parity status of every function is listed in ``PARITY`` below; all are
 pinned by ``tests/test_oracle_*.py``.
@@ -44,6 +46,8 @@ PARITY = {
     "partition": "pinned: block reassembly equals the input; block products sum to the flat product",
     "features": "pinned: brute-force per-column sets on small inputs",
     "mlp": "pinned: central finite differences and a closed-form linear case",
+    "permute": "pinned: dense definition, inverse permutation, (PAP^T)(PAP^T) = P(AA)P^T",
+    "hgemm": "pinned: Fig. 8 Isect, flops identity (19) and pattern; equals the Gustavson oracle",
 }
 
 

@@ -385,3 +385,39 @@ def test_permute_definition_and_pcpt_identity():
     Cp = oracle.spgemm(Bp, Bp, PT_I64)
     ref = of.permute(C.m, C.n, C.colptr, C.rowidx, C.vals, p, p)
     assert np.array_equal(Cp.colptr, ref[0]) and np.array_equal(Cp.rowidx, ref[1]) and np.array_equal(Cp.vals, ref[2])
+
+
+# ---------------------------------------------------------------- second oracle: H_GEMM (Section 2.4)
+def test_hgemm_fig8_isect_flops_and_pattern():
+    """The heap-merged outer products on the Fig. 8 operands: the printed Isect,
+    the flops identity (19) and the pattern of C by column."""
+    from oracle import hgemm as oh
+    A_rows, B_rows, C_cols, kv = _fig8()
+    A = pattern_matrix(A_rows, 6, 6, by_row=True, sr=PT_I64)
+    B = pattern_matrix(B_rows, 6, 6, by_row=True, sr=PT_I64, seed=3)
+    tcp = of.transpose(B.m, B.n, B.colptr, B.rowidx, B.vals)[0]
+    assert [i + 1 for i in oh.isect(A.colptr, tcp)] == list(kv["Isect"])
+    assert oh.flops(A, B) == kv["flops"][0]
+    cp, ir, v = oh.hgemm(A, B, PT_I64)
+    for j in range(6):
+        assert list(ir[cp[j]:cp[j + 1]] + 1) == C_cols[j + 1]
+
+
+@pytest.mark.parametrize("sr", SEMIRINGS)
+def test_hgemm_equals_gustavson(sr):
+    """Two independent formulations of C = A*B (heap merge of outer products vs
+    column-wise SPA) agree: structure and exact semirings bit for bit, FP64 within
+    the tolerance."""
+    from oracle import hgemm as oh
+    cases = [(gen.random_csc(23, 17, 0.2, 0x61, sr), gen.random_csc(17, 29, 0.15, 0x62, sr)),
+             (gen.rmat(7, 6, 0x63, sr), gen.rmat(7, 6, 0x64, sr)),
+             (gen.random_csc(40, 60, 0.02, 0x65, sr), gen.random_csc(60, 30, 0.03, 0x66, sr))]   # hypersparse
+    for A, B in cases:
+        R = oracle.spgemm(A, B, sr)
+        cp, ir, v = oh.hgemm(A, B, sr)
+        np.testing.assert_array_equal(cp, R.colptr)
+        np.testing.assert_array_equal(ir, R.rowidx)
+        if sr == PT_F64:
+            assert np.all(np.abs(v - R.vals) <= FP64_RTOL * np.abs(R.vals))
+        else:
+            np.testing.assert_array_equal(v, R.vals)
