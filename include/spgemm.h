@@ -99,7 +99,11 @@ typedef struct {
     float predictor_margin;   /* capacity = (1 + margin) * prediction (+ slack)        */
     int range_table_slots;    /* long columns: hash slots per row range, 2048, 4096 or
                                  8192 (0 = default 4096); a range holds < slots/2 entries */
-    int reserved[7];
+    int block_kernel;         /* spgemm_summa_blocked stage products: 0 = the column
+                                 tiers (default), 1 = expand-sort-compress, the
+                                 data-parallel form of the outer-product multiply of
+                                 Section 2.4 (needs < 2^32 products per merge group) */
+    int reserved[6];
 } spgemm_opts_t;
 
 void spgemm_opts_default(spgemm_opts_t* opts);

@@ -167,6 +167,8 @@ spgemm_status_t engine_symbolic(Engine* E);
 spgemm_status_t engine_numeric(Engine* E, int32_t* Cir, void* Cv);
 // predictor.cu: numeric pass without the symbolic pass of the hash tiers; returns C's arrays
 spgemm_status_t engine_numeric_predicted(Engine* E, std::shared_ptr<DevBuf>* rbuf, std::shared_ptr<DevBuf>* vbuf);
+// esc.cu: all products of E by expand-sort-compress (local rows); sets Coff and nnz_total
+spgemm_status_t engine_esc(Engine* E, std::shared_ptr<DevBuf>* rbuf, std::shared_ptr<DevBuf>* vbuf);
 // output arrays sized by the engine's nnz_total, values of the semiring width
 spgemm_status_t engine_alloc_out(Engine* E, std::shared_ptr<DevBuf>* rbuf, std::shared_ptr<DevBuf>* vbuf);
 sg::DMat csc_view(int64_t m, int64_t n, int64_t nnz, const int64_t* cp, const int32_t* ir, const void* num);

@@ -379,6 +379,9 @@ spgemm_status_t spgemm_summa_blocked(spgemm_ctx_t ctx, spgemm_mat_t A, spgemm_ma
     spgemm_opts_default(&o);
     if (opts) o = *opts;
     if (o.summa_fused != 0) return set_err(ctx, SPGEMM_ERR_UNSUPPORTED, "summa_fused is reserved (must be 0)");
+    if (o.block_kernel != 0 && o.block_kernel != 1)
+        return set_err(ctx, SPGEMM_ERR_INVALID_ARG, "block_kernel %d: 0 (column tiers) or 1 (expand-sort-compress)",
+                       o.block_kernel);
     spgemm_mat_t Ac = nullptr, Bc = nullptr;
     DMat dA, dB;
     SG_TRY(to_csc_operand(ctx, A, &Ac, &dA));
@@ -426,9 +429,13 @@ spgemm_status_t spgemm_summa_blocked(spgemm_ctx_t ctx, spgemm_mat_t A, spgemm_ma
         int64_t U = 0, pn = 0;
         if (!grp.empty()) {
             SG_TRY(engine_setup(&E, ctx, sr, o, grp, false));
-            SG_TRY(engine_symbolic(&E));
-            SG_TRY(engine_alloc_out(&E, &rbuf, &vbuf));
-            SG_TRY(engine_numeric(&E, (int32_t*)rbuf->p, vbuf->p));
+            if (o.block_kernel == 1) {
+                SG_TRY(engine_esc(&E, &rbuf, &vbuf));   // outer-product order, Section 2.4
+            } else {
+                SG_TRY(engine_symbolic(&E));
+                SG_TRY(engine_alloc_out(&E, &rbuf, &vbuf));
+                SG_TRY(engine_numeric(&E, (int32_t*)rbuf->p, vbuf->p));
+            }
             U = E.it.nitems;
             pn = E.nnz_total;
             // stage flops for the statistics

@@ -192,3 +192,30 @@ def test_permute_rejects_non_permutations(ctx):
             s.spgemm_mat_permute(ctx, dA, bad, None)
     ok = s.spgemm_mat_permute(ctx, dA, None, None).to_host()   # identity
     np.testing.assert_array_equal(ok.rowidx, A.rowidx)
+
+
+@pytest.mark.parametrize("sr", SEMIRINGS)
+def test_summa_expand_sort_compress(ctx, sr):
+    """Stage products by expand-sort-compress (the data-parallel outer-product
+    multiply of Section 2.4) give the oracle's C, ragged grids and merge groups
+    included."""
+    for t, (m, k, n, d, g, every) in enumerate([(37, 29, 41, 0.1, 4, 0), (300, 200, 150, 0.03, 16, 0),
+                                                (100, 64, 90, 0.05, 7, 3)]):
+        A = gen.random_csc(m, k, d, 500 + t, sr)
+        B = gen.random_csc(k, n, d, 600 + t, sr)
+        C = blocked(ctx, A, B, sr, g, block_kernel=1, summa_merge_every=every)
+        assert_matches(C, oracle.spgemm(A, B, sr), sr, what=f"{(m, k, n, g, every)}")
+    A = gen.rmat(12, 8, 0x1216, sr)
+    assert_matches(blocked(ctx, A, A, sr, 16, block_kernel=1), oracle.spgemm(A, A, sr), sr)
+
+
+def test_summa_expand_sort_compress_matches_column_tiers_scale16(ctx):
+    """Both stage-product kernels give identical C on R-MAT scale 16 (exact semiring)."""
+    sr = PT_I64
+    A = gen.rmat(16, 8, 0x1616, sr)
+    C0 = blocked(ctx, A, A, sr, 16)
+    C1 = blocked(ctx, A, A, sr, 16, block_kernel=1)
+    np.testing.assert_array_equal(C0.colptr, C1.colptr)
+    np.testing.assert_array_equal(C0.rowidx, C1.rowidx)
+    np.testing.assert_array_equal(C0.vals, C1.vals)
+    np.testing.assert_array_equal(np.diff(C0.colptr), oracle.symbolic(A, A))
