@@ -177,6 +177,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--scale", type=int, default=SCALE)
     ap.add_argument("--grid", type=int, default=GRID, help="virtual SUMMA grid size g (g x g blocks)")
+    ap.add_argument("--workload", default="rmat_square", choices=["rmat_square", "restriction", "tallskinny"],
+                    help="rmat_square: the default A*A step; restriction: A S^T and S (A S^T) of orders 2, 4, 8 "
+                         "(Section 6.2.3); tallskinny: R-MAT times n x n/2^13 ER with c2 = 1 .. 10^5 per column "
+                         "(Section 6.2.2)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-learned", action="store_true",
@@ -331,6 +335,77 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_sweep(args) -> None:
+    """The second workloads of Section 6.2 on one GPU: every case timed on the device
+    (CUDA events on the context stream around the public product call, L2 flushed
+    before each run), one JSON line with the aggregate and the per-case numbers."""
+    import torch
+    from paper_1006_2183_gb300 import build as _build
+    _build.build()
+    from paper_1006_2183_gb300 import spgemm as sp
+    import oracle
+    ctx = sp.Context()
+    dev = ctx.device
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    sr = sp.PLUS_TIMES_F64
+    cases = []   # (name, callable returning the product, flops)
+    if args.workload == "restriction":
+        A = gen.rmat(args.scale, EF, SEED, gen.PLUS_TIMES_F64)
+        dA = sp.Matrix.from_host(ctx, A, sr)
+        for order in (2, 4, 8):
+            S = gen.restriction(A.n, order, 0x6202 + order)
+            St = gen.transpose_host(S)
+            dS, dSt = sp.Matrix.from_host(ctx, S, sr), sp.Matrix.from_host(ctx, St, sr)
+            fl_ast = A.nnz   # one S^T entry per row of S^T: flops(A S^T) = nnz(A)
+            cases.append((f"A*S^T order {order}", lambda dSt=dSt: sp.spgemm_multiply(ctx, dA, dSt, sr), fl_ast))
+            ASt = sp.spgemm_multiply(ctx, dA, dSt, sr)
+            fl_sast = ASt.shape()[2]   # flops(S (A S^T)) = nnz(A S^T): one S entry per column
+            cases.append((f"S*(A*S^T) order {order}",
+                          lambda dS=dS, ASt=ASt: sp.spgemm_multiply(ctx, dS, ASt, sr), fl_sast))
+        workload = {"workload": f"rmat{args.scale}_restriction", "scale": args.scale, "edge_factor": EF,
+                    "seed": SEED, "orders": [2, 4, 8]}
+    else:
+        n_scale = args.scale
+        A = gen.rmat(n_scale, EF, SEED, gen.PLUS_TIMES_F64)
+        dA = sp.Matrix.from_host(ctx, A, sr)
+        k = max(1, A.n >> 13)
+        for c2 in (1, 10, 100, 1000, 10000, 100000):
+            if c2 > A.n:
+                continue
+            F = gen.erdos_renyi(A.n, k, c2, 0x6302 + c2, gen.PLUS_TIMES_F64)
+            dF = sp.Matrix.from_host(ctx, F, sr)
+            fl = int(oracle.flops_per_col(A, F).sum())
+            cases.append((f"c2 = {c2}", lambda dF=dF: sp.spgemm_multiply(ctx, dA, dF, sr), fl))
+        workload = {"workload": f"rmat{args.scale}_times_tall_skinny_er", "scale": args.scale, "edge_factor": EF,
+                    "seed": SEED, "k": k, "c2": [1, 10, 100, 1000, 10000, 100000]}
+    st = ctx.stream
+    out = []
+    tot_ms = tot_fl = 0.0
+    for name, fn, fl in cases:
+        for _ in range(max(3, args.warmup)):
+            fn()
+        ts = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            C = fn()
+            e1.record(st)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+            del C
+        ms = statistics.median(ts)
+        out.append({"case": name, "flops": fl, "ms": ms, "gflops": 2 * fl / ms / 1e6})
+        tot_ms += ms
+        tot_fl += fl
+    line = {"metric": METRIC, "value": 2 * tot_fl / tot_ms / 1e6, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": tot_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(workload, l2="flushed before every timed run (512 MiB write)"), "cases": out}
+    print(json.dumps(line), flush=True)
+
+
 # ---------------------------------------------------------------- our arm
 def main():
     args = parse()
@@ -339,6 +414,10 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload != "rmat_square":
+        if rank == 0:
+            run_sweep(args)
         return
     import torch
     import torch.distributed as dist

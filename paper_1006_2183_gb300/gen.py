@@ -287,6 +287,22 @@ def aggregation_2x2x2(N: int) -> CSC:
     return CSC(n, M ** 3, colptr, idx[order].astype(np.int32), np.ones(n, dtype=np.float64))
 
 
+def restriction(n: int, order: int, seed: int, semiring: int = PLUS_TIMES_F64) -> CSC:
+    """Restriction operator S (ceil(n/order) x n, n nonzeros) of a graph contraction of
+    the given order (Section 6.2.3): vertex v joins aggregate perm[v] // order for a
+    seeded random permutation perm, so every aggregate but the last has `order`
+    vertices; S(perm[v] // order, v) = 1."""
+    keys = u64(seed, 90, np.arange(n, dtype=np.uint64))
+    perm = np.empty(n, dtype=np.int64)
+    perm[np.argsort(keys, kind="stable")] = np.arange(n, dtype=np.int64)
+    agg = perm // order
+    colptr = np.arange(n + 1, dtype=np.int64)   # one nonzero per column v
+    one = np.ones(n, dtype=SEMIRING_DTYPE[semiring])
+    if semiring == MIN_PLUS_F32:
+        one = np.zeros(n, dtype=np.float32)      # the min-plus "one" is 0
+    return CSC(-(-n // order), n, colptr, agg.astype(np.int32), one)
+
+
 def transpose_host(A: CSC) -> CSC:
     """Plain host transpose (used only to build R = P^T as an input)."""
     cols = np.repeat(np.arange(A.n, dtype=np.int64), np.diff(A.colptr))

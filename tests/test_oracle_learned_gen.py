@@ -149,3 +149,11 @@ def test_generators_do_not_depend_on_threads(monkeypatch):
     for (a, b), (c, d) in zip(gen.batch_pairs(3, 0x99, 6, 9), refp):
         np.testing.assert_array_equal(a.rowidx, c.rowidx)
         np.testing.assert_array_equal(b.vals, d.vals)
+
+
+def test_restriction_shape():
+    for n, order in ((1000, 2), (1000, 4), (1003, 8)):
+        S = gen.restriction(n, order, 0x88)
+        assert S.m == -(-n // order) and S.n == n and S.nnz == n
+        sizes = np.bincount(S.rowidx, minlength=S.m)
+        assert np.all(sizes[:-1] == order) and 1 <= sizes[-1] <= order
