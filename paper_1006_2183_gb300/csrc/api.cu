@@ -410,7 +410,7 @@ spgemm_status_t engine_setup(Engine* E, spgemm_ctx* ctx, spgemm_semiring_t sr, c
         size_t o_pc = take(4 * nd * MAX_PARTS);
         size_t o_pb = take(8 * nd * MAX_PARTS);
         size_t o_pn = take(4 * nd * MAX_PARTS);
-        size_t o_cur = take(4 * std::max<int64_t>(bnz, 1) * MAX_PARTS);
+        size_t o_cur = take(sizeof(int2) * std::max<int64_t>(bnz, 1) * MAX_PARTS);
         auto dbuf = ctx_buf(ctx, off);
         if (!dbuf) return set_err(ctx, SPGEMM_ERR_OOM, "range-tier arena of %zu bytes", off);
         E->bufs.push_back(dbuf);
@@ -418,7 +418,7 @@ spgemm_status_t engine_setup(Engine* E, spgemm_ctx* ctx, spgemm_semiring_t sr, c
         E->ditems = (int2*)(db + o_items);
         E->nparts = (int8_t*)(db + o_np);
         E->part_count = (int32_t*)(db + o_pc);
-        E->cursors = (int32_t*)(db + o_cur);
+        E->cursors = (int2*)(db + o_cur);
         DenseWork& dw = E->dw;
         dw.dlist = E->list + E->bin_off[BIN_DENSE];
         dw.ndense = nd;

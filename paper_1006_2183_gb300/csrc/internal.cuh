@@ -80,7 +80,7 @@ struct Engine {
     int2* list = nullptr;
     int2* ditems = nullptr;
     int8_t* nparts = nullptr;
-    int32_t* cursors = nullptr;
+    int2* cursors = nullptr;
     int32_t* part_count = nullptr;
     sg::DenseWork dw;                    // range-tier state
     int64_t* nnz_item = nullptr;

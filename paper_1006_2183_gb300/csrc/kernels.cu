@@ -1095,18 +1095,20 @@ __global__ void __launch_bounds__(RT_BLOCK) k_range_num(Items it, DenseWork dw, 
         const int64_t deg = be - bs;
         const int32_t* __restrict__ air = pr->A.ir;
         // cursor slots are indexed relative to the product's first B position (blocks share arrays)
-        int32_t* cur = dw.cursors + (int64_t)q * it.total_bnz + pr->bnz_base + (bs - __ldg(pr->B.cp));
+        // beyond the first RT_NEXT k's: (cursor offset in A(:,k), row at the cursor) in global memory
+        int2* cur = dw.cursors + (int64_t)q * it.total_bnz + pr->bnz_base + (bs - __ldg(pr->B.cp));
         for (int64_t t = tid; t < deg; t += RT_BLOCK) {
             const int32_t k = __ldg(pr->B.ir + bs + t);
             int64_t s, en;
             col_range(pr->A, k, s, en);
             const int32_t c0 = R0 == 0 ? 0 : lower_bound_rows(air + s, en - s, R0);
+            const int32_t nx = s + c0 < en ? __ldg(air + s + c0) : INT_MAX;
             if (t < RT_NEXT) {
                 s_pos[t] = s + c0;
                 s_rem[t] = (int32_t)(en - s - c0);
-                s_next[t] = s + c0 < en ? __ldg(air + s + c0) : INT_MAX;
+                s_next[t] = nx;
             } else {
-                cur[t] = c0;
+                cur[t] = make_int2(c0, nx);
             }
         }
         int64_t outbase = __ldg(Coff + u);
@@ -1126,7 +1128,11 @@ __global__ void __launch_bounds__(RT_BLOCK) k_range_num(Items it, DenseWork dw, 
                 int len = 0;
                 int64_t a = 0;
                 T bv = T(0);
-                const bool act = t < deg && (t >= RT_NEXT || s_next[t] < r1);
+                // a k whose next row lies at or past r1 gives nothing to this range
+                int2 cv = make_int2(0, INT_MAX);
+                if (t < deg && t >= RT_NEXT) cv = cur[t];
+                const bool act = t < deg && (t < RT_NEXT ? s_next[t] < r1 : cv.y < r1);
+                if (b0 >= RT_NEXT && !__syncthreads_or(act)) continue;   // a chunk with nothing for the range
                 if (act) {
                     bv = load_val<SR>(pr->B, bs + t);
                     if (t < RT_NEXT) {
@@ -1142,10 +1148,10 @@ __global__ void __launch_bounds__(RT_BLOCK) k_range_num(Items it, DenseWork dw, 
                         const int32_t k = __ldg(pr->B.ir + bs + t);
                         int64_t s, en;
                         col_range(pr->A, k, s, en);
-                        a = s + cur[t];
+                        a = s + cv.x;
                         int32_t nx;
                         const int64_t c = count_below(air, a, en, r1, nx);
-                        cur[t] += (int32_t)c;
+                        cur[t] = make_int2(cv.x + (int32_t)c, nx);
                         len = (int)c;
                     }
                 }

@@ -57,7 +57,7 @@ struct DenseWork {   // state of the range tier shared by its kernels
     const int2* items = nullptr;          // slabs (d, q)
     const unsigned long long* nitems = nullptr;   // device count of slabs
     const int8_t* nparts = nullptr;       // slabs per dense item
-    int32_t* cursors = nullptr;           // per slab and k: position inside A(:,k)
+    int2* cursors = nullptr;              // per slab and k: (position inside A(:,k), row there)
     int32_t* part_count = nullptr;        // [q][d] entries per slab
     RangePart* parts = nullptr;
     unsigned long long* parts_ctr = nullptr;
