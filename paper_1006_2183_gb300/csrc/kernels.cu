@@ -689,7 +689,12 @@ static void run_hash_bins(cudaStream_t st, const Items& it, const int2* list, co
     run_hash<SR, 32, 512, NUM, WARP_BLOCK>(st, it, list + off[W0 + 3], cnt[W0 + 3], nnz_item, Coff, Cir, Cv);
     run_hash<SR, 32, 1024, NUM, 128>(st, it, list + off[W0 + 4], cnt[W0 + 4], nnz_item, Coff, Cir, Cv);
     run_hash<SR, 256, 2048, NUM, 256>(st, it, list + off[B0], cnt[B0], nnz_item, Coff, Cir, Cv);
-    run_hash<SR, 512, 4096, NUM, 512>(st, it, list + off[B0 + 1], cnt[B0 + 1], nnz_item, Coff, Cir, Cv);
+    // 4096-slot tables: 256 threads per column when the row bitmap is small (more columns
+    // in flight per SM), 512 when a large bitmap already limits the CTAs per SM
+    if (it.max_m <= 65536)
+        run_hash<SR, 256, 4096, NUM, 256>(st, it, list + off[B0 + 1], cnt[B0 + 1], nnz_item, Coff, Cir, Cv);
+    else
+        run_hash<SR, 512, 4096, NUM, 512>(st, it, list + off[B0 + 1], cnt[B0 + 1], nnz_item, Coff, Cir, Cv);
     run_hash<SR, 512, 8192, NUM, 512>(st, it, list + off[B0 + 2], cnt[B0 + 2], nnz_item, Coff, Cir, Cv);
 }
 
