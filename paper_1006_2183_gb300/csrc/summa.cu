@@ -169,6 +169,12 @@ struct Blocked {
     const DMat& at(int I, int J) const { return blk[(size_t)J * g + I]; }
 };
 
+// Two operands that are the same stored matrix (same arrays and shape).
+bool same_arrays(const DMat& a, const DMat& b) {
+    return a.m == b.m && a.n == b.n && a.nnz == b.nnz && a.cp == b.cp && a.ir == b.ir && a.num == b.num &&
+           a.jc == b.jc;
+}
+
 spgemm_status_t partition(spgemm_ctx* ctx, const DMat& M, size_t w, int g, Blocked* out) {
     cudaStream_t st = ctx->stream;
     const int64_t m = M.m, n = M.n, nnz = M.nnz;
@@ -396,7 +402,9 @@ spgemm_status_t spgemm_summa_blocked(spgemm_ctx_t ctx, spgemm_mat_t A, spgemm_ma
     {
         PhaseTimer tp(ctx, SPGEMM_PHASE_ANALYZE, sr);
         SG_TRY(partition(ctx, dA, w, g, &bA));
-        SG_TRY(partition(ctx, dB, w, g, &bB));
+        // the same matrix on both sides (A*A): one split serves as A's and as B's blocks
+        if (same_arrays(dA, dB)) bB = bA;
+        else SG_TRY(partition(ctx, dB, w, g, &bB));
     }
     // stage products A(I,s) * B(s,J), stage-major
     std::vector<Prod> all;
@@ -529,7 +537,8 @@ spgemm_status_t spgemm_summa_block_flops(spgemm_ctx_t ctx, spgemm_mat_t A, spgem
     const size_t w = sr_size(A->sr);
     Blocked bA, bB;
     SG_TRY(partition(ctx, dA, w, g, &bA));
-    SG_TRY(partition(ctx, dB, w, g, &bB));
+    if (same_arrays(dA, dB)) bB = bA;
+    else SG_TRY(partition(ctx, dB, w, g, &bB));
     const size_t g3 = (size_t)g * g * g;
     std::fill(flops, flops + g3, int64_t(0));
     std::vector<Prod> all;
