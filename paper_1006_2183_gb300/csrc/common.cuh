@@ -80,6 +80,7 @@ struct DMat {
     int64_t chunk = 1, naux = 0;
     const int32_t* ir = nullptr;
     const void* num = nullptr;  // nullptr: pattern only (values = semiring one)
+    const int64_t* ce = nullptr;  // CSC with gaps: column k holds [cp[k], ce[k]) (else [cp[k], cp[k+1]))
 };
 
 // One product of a batch.  Its items are the stored columns p of B; item p has
@@ -120,7 +121,7 @@ __device__ __forceinline__ void col_range(const DMat& A, int32_t k, int64_t& s, 
     }
     if (A.jc == nullptr) {
         s = __ldg(A.cp + k);
-        e = __ldg(A.cp + k + 1);
+        e = A.ce ? __ldg(A.ce + k) : __ldg(A.cp + k + 1);
         return;
     }
     int64_t t = k / A.chunk;

@@ -167,6 +167,11 @@ spgemm_status_t engine_symbolic(Engine* E);
 spgemm_status_t engine_numeric(Engine* E, int32_t* Cir, void* Cv);
 // predictor.cu: numeric pass without the symbolic pass of the hash tiers; returns C's arrays
 spgemm_status_t engine_numeric_predicted(Engine* E, std::shared_ptr<DevBuf>* rbuf, std::shared_ptr<DevBuf>* vbuf);
+// bounded.cu: numeric pass into min(flops, m) slots per hash-tier column (no symbolic pass
+// for them); output is a CSC with gaps: column u in [col_start[u], col_end[u])
+spgemm_status_t engine_numeric_bounded(Engine* E, std::shared_ptr<DevBuf>* rbuf, std::shared_ptr<DevBuf>* vbuf,
+                                       std::shared_ptr<DevBuf>* colbuf, const int64_t** col_start,
+                                       const int64_t** col_end);
 // esc.cu: all products of E by expand-sort-compress (local rows); sets Coff and nnz_total
 spgemm_status_t engine_esc(Engine* E, std::shared_ptr<DevBuf>* rbuf, std::shared_ptr<DevBuf>* vbuf);
 // output arrays sized by the engine's nnz_total, values of the semiring width

@@ -166,7 +166,7 @@ __global__ void k_row_sketch(DMat A, uint64_t* __restrict__ sk) {
     int sub = threadIdx.x & 7;
     unsigned long long v = 0;
     if (p < A.nzc) {
-        int64_t s = __ldg(A.cp + p), e = __ldg(A.cp + p + 1);
+        int64_t s = __ldg(A.cp + p), e = A.ce ? __ldg(A.ce + p) : __ldg(A.cp + p + 1);
         for (int64_t t = s + sub; t < e; t += 8) {
             uint32_t h = (uint32_t)__ldg(A.ir + t) * 0x9E3779B1u;
             v |= 1ull << (h >> 26);

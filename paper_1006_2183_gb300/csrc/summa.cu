@@ -297,13 +297,16 @@ spgemm_status_t partition(spgemm_ctx* ctx, const DMat& M, size_t w, int g, Block
 
 // C (m x n) = merge of `ncols` sorted partial columns: column u of P (rows
 // global, colptr Pcp) is added into output column oc[u].
+// Stage partials go to upper-bound slots (no count pass) below this many slots.
+constexpr int64_t BOUNDED_MAX_SLOTS = int64_t(1) << 30;
+
 // Merges the partial columns P (local rows < mb; column u goes to merge column
 // oc[u] = j * g + I) into the mb x (n g) matrix of merge columns, or, when
 // `final`, into C (m x n, global rows I * mb + local row).
 spgemm_status_t merge_columns(spgemm_ctx* ctx, spgemm_semiring_t sr, const spgemm_opts_t& opts, int64_t m,
                               int64_t mb, int64_t n0, int g, bool final, int64_t ncols, const int64_t* Pcp,
-                              const int32_t* Pir, const void* Pv, int64_t pnnz, uint32_t* oc, uint32_t* pay,
-                              spgemm_mat_t* C) {
+                              const int64_t* Pce, const int32_t* Pir, const void* Pv, int64_t pnnz, uint32_t* oc,
+                              uint32_t* pay, spgemm_mat_t* C) {
     cudaStream_t st = ctx->stream;
     PhaseTimer tm(ctx, SPGEMM_PHASE_MERGE, sr);
     const int64_t n = n0 * g;   // merge columns
@@ -338,6 +341,7 @@ spgemm_status_t merge_columns(spgemm_ctx* ctx, spgemm_semiring_t sr, const spgem
     // C = P * S
     Prod pr;
     pr.A = csc_view(mb, ncols, pnnz, Pcp, Pir, Pv);
+    pr.A.ce = Pce;   // partials written into bounded slots: column u ends at Pce[u]
     pr.B = csc_view(ncols, n, ncols, (const int64_t*)scp->p, (const int32_t*)sir->p, nullptr);
     if (final) {
         pr.rb_cycle = g;
@@ -433,12 +437,17 @@ spgemm_status_t spgemm_summa_blocked(spgemm_ctx_t ctx, spgemm_mat_t A, spgemm_ma
         for (auto& pr : all)
             if (pr.tag >= s0 && pr.tag < s0 + every) grp.push_back(pr);
         Engine E;
-        std::shared_ptr<DevBuf> rbuf, vbuf;
+        std::shared_ptr<DevBuf> rbuf, vbuf, colbuf;
+        const int64_t* pstart = nullptr;   // partial columns with gaps (bounded slots), or null
+        const int64_t* pend = nullptr;
         int64_t U = 0, pn = 0;
         if (!grp.empty()) {
             SG_TRY(engine_setup(&E, ctx, sr, o, grp, false));
             if (o.block_kernel == 1) {
                 SG_TRY(engine_esc(&E, &rbuf, &vbuf));   // outer-product order, Section 2.4
+            } else if (!acc && s0 + every >= g && E.flops_total <= BOUNDED_MAX_SLOTS) {
+                // one merge reads the partials where they were written: no count pass for them
+                SG_TRY(engine_numeric_bounded(&E, &rbuf, &vbuf, &colbuf, &pstart, &pend));
             } else {
                 SG_TRY(engine_symbolic(&E));
                 SG_TRY(engine_alloc_out(&E, &rbuf, &vbuf));
@@ -471,9 +480,11 @@ spgemm_status_t spgemm_summa_blocked(spgemm_ctx_t ctx, spgemm_mat_t A, spgemm_ma
         const int64_t* Pcp;
         const int32_t* Pir;
         const void* Pv;
+        const int64_t* Pce = nullptr;
         if (!acc && U > 0) {
             // the partials alone: merge them in place
-            Pcp = E.Coff;
+            Pcp = pstart ? pstart : E.Coff;
+            Pce = pend;
             Pir = (const int32_t*)rbuf->p;
             Pv = vbuf->p;
         } else {
@@ -514,7 +525,7 @@ spgemm_status_t spgemm_summa_blocked(spgemm_ctx_t ctx, spgemm_mat_t A, spgemm_ma
         }
         spgemm_mat_t Cn = nullptr;
         const bool final = s0 + every >= g;
-        SG_TRY(merge_columns(ctx, sr, o, m, bA.mb, n, g, final, ncols, Pcp, Pir, Pv, pnz, oc, pay, &Cn));
+        SG_TRY(merge_columns(ctx, sr, o, m, bA.mb, n, g, final, ncols, Pcp, Pce, Pir, Pv, pnz, oc, pay, &Cn));
         hold_acc.reset(Cn);
         acc = Cn;
     }
