@@ -277,96 +277,45 @@ __device__ __forceinline__ void bitonic_sort(int32_t* keys, Acc* vals, int P) {
     }
 }
 
-// Writes the rows marked in `bitmap` (nw words, bit b of word x = row row0 + 32x + b)
-// in ascending order with their values from the table, warp slices of the bitmap
-// per warp and coalesced stores, and empties the table and the bitmap behind it.
-// Called by all NW*32 threads of a CTA (NW > 1) or by one warp (NW == 1);
-// returns the number of rows.  With `pred`, nothing is written when the count
-// exceeds capn.
-template <class SR, int TBL, int NW>
-__device__ __forceinline__ int bitmap_emit(uint32_t* bitmap, int nw, int64_t row0, int32_t* keys,
-                                           typename SR::Acc* vals, bool direct, bool pred, int64_t capn, int* wc,
-                                           int64_t outbase, int32_t rb, int32_t* __restrict__ Cir,
-                                           typename SR::T* __restrict__ Cv) {
-    constexpr int LOG2 = __builtin_ctz(TBL);
-    volatile int32_t* vkeys = keys;
-    const int lane = threadIdx.x & 31, warp = NW == 1 ? 0 : threadIdx.x >> 5;
-    const int cw = (nw + NW * 32 - 1) / (NW * 32) * 32;
-    const int wb = min(warp * cw, nw), we = min(wb + cw, nw);
-    int cnt = 0;
-    for (int x = wb + lane; x < we; x += 32) cnt += __popc(bitmap[x]);
-    cnt = warp_sum(cnt);
-    int total, first;
-    if constexpr (NW == 1) {
-        total = cnt;
-        first = 0;
-    } else {
-        if (lane == 0) wc[warp] = cnt;
-        __syncthreads();
-        if (warp == 0) {
-            int v = lane < NW ? wc[lane] : 0;
-            const int incl = warp_incl_scan(v);
-            if (lane < NW) wc[lane] = incl - v;
-            if (lane == NW - 1) wc[NW] = incl;
-        }
-        __syncthreads();
-        total = wc[NW];
-        first = wc[warp];
-    }
+// Writes a group's table in row order: the rank of row r among the marked rows of
+// `bitmap` (nw words) is the number of bits below it, from per-member prefix counts
+// of groups of gw words plus the popcounts inside r's group, so every occupied slot
+// writes its entry at its rank directly (no sort, no probing).  Empties the table
+// and the bitmap.  Called by all GS members; returns the number of entries.  With
+// `pred`, nothing is written when the count exceeds capn.
+template <class SR, int TBL, int GS>
+__device__ __forceinline__ int rank_emit(uint32_t* bitmap, int nw, int32_t* keys, typename SR::Acc* vals, int* gp,
+                                         int* scratch, bool pred, int64_t capn, int64_t out0, int32_t rb,
+                                         int32_t* __restrict__ Cir, typename SR::T* __restrict__ Cv) {
+    using G = Group<GS>;
+    const int lane = G::lane();
+    int lgw = 0;   // words per group: a power of two with GS groups covering nw words
+    while ((GS << lgw) < nw) ++lgw;
+    const int gw = 1 << lgw;
+    int c = 0;
+    for (int x = lane * gw; x < (lane + 1) * gw && x < nw; ++x) c += __popc(bitmap[x]);
+    int total;
+    const int incl = group_incl_scan<GS>(c, scratch, total);
+    gp[lane] = incl - c;
+    G::sync();
     const bool write = !pred || total <= capn;
-    int64_t o = outbase + first;
-    for (int x0 = wb; x0 < we; x0 += 32) {
-        const int x = x0 + lane;
-        const uint32_t word = x < we ? bitmap[x] : 0u;
-        const int pc = __popc(word);
-        const int incl = warp_incl_scan(pc);
-        const int tot = __shfl_sync(0xffffffffu, incl, 31);
-        for (int e0 = 0; e0 < tot; e0 += 32) {
-            const int ee = e0 + lane;
-            int j = 0;
-#pragma unroll
-            for (int s = 16; s >= 1; s >>= 1) {
-                const int v = __shfl_sync(0xffffffffu, incl, j + s - 1);
-                if (v <= ee) j += s;
-            }
-            j = j > 31 ? 31 : j;
-            uint32_t wj = __shfl_sync(0xffffffffu, word, j);
-            int rr = ee - (__shfl_sync(0xffffffffu, incl, j) - __popc(wj));
-            if (ee < tot) {
-                int pos = 0;
-#pragma unroll
-                for (int s = 16; s >= 1; s >>= 1) {
-                    const int c = __popc(wj & ((1u << s) - 1u));
-                    if (rr >= c) {
-                        rr -= c;
-                        wj >>= s;
-                        pos += s;
-                    }
-                }
-                const int lr = (x0 + j) * 32 + pos;
-                const int32_t row = (int32_t)(row0 + lr);
-                uint32_t h;
-                if (direct) {
-                    h = (uint32_t)lr;
-                } else {
-                    h = hash_row(row) >> (32 - LOG2);
-                    while (vkeys[h] != row) h = (h + 1) & (TBL - 1);
-                }
-                if (write) {
-                    Cir[o + ee] = row + rb;
-                    Cv[o + ee] = SR::out(vals[h]);
-                }
-                // every marked row is in the table; lookups never stop at an empty slot,
-                // so emptying slots while others still read is safe
-                vals[h] = SR::zero();
-                keys[h] = -1;
-            }
+    for (int s = lane; s < TBL; s += GS) {
+        const int32_t kr = keys[s];
+        if (kr < 0) continue;
+        const int wd = kr >> 5;
+        if (wd < nw && write) {   // rows past the bitmap occur only on malformed input
+            const int g = wd >> lgw;
+            int rank = gp[g] + __popc(bitmap[wd] & ((1u << (kr & 31)) - 1u));
+            for (int y = g << lgw; y < wd; ++y) rank += __popc(bitmap[y]);
+            Cir[out0 + rank] = kr + rb;
+            Cv[out0 + rank] = SR::out(vals[s]);
         }
-        if (x < we) bitmap[x] = 0u;
-        o += tot;
+        keys[s] = -1;
+        vals[s] = SR::zero();
     }
-    if constexpr (NW == 1) __syncwarp();
-    else __syncthreads();
+    G::sync();
+    for (int x = lane; x < nw; x += GS) bitmap[x] = 0u;
+    G::sync();
     return total;
 }
 
@@ -515,9 +464,8 @@ __global__ void __launch_bounds__(BLOCK) k_hash(Items it, const int2* __restrict
                         if (kr >= 0 && (kr >> 5) < nwc) atomicOr(&bitmap[kr >> 5], 1u << (kr & 31));
                     }
                     G::sync();
-                    const int total = bitmap_emit<SR, TBL, GS / 32>(bitmap, nwc, 0, keys, vals, false,
-                                                                     nnz_item != nullptr, capn, s_scan, out0, rb,
-                                                                     Cir, Cv);
+                    const int total = rank_emit<SR, TBL, GS>(bitmap, nwc, keys, vals, s_incl, s_scan,
+                                                             nnz_item != nullptr, capn, out0, rb, Cir, Cv);
                     if (nnz_item && lane == 0) nnz_item[u] = total;
                     continue;
                 }
