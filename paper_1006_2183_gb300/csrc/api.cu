@@ -341,6 +341,11 @@ spgemm_status_t engine_setup(Engine* E, spgemm_ctx* ctx, spgemm_semiring_t sr, c
     size_t o_sk = want_features ? take(8 * std::max<int64_t>(amax_n, 1)) : 0;
     size_t o_skb = want_features ? take(8 * (np + 1)) : 0;
     size_t o_mx = want_features ? take(8 * U1) : 0;
+    // A-column cache for DCSC operands (SUMMA blocks): 12 bytes per entry of the B_i
+    bool any_dcsc = false;
+    for (auto& pr : E->hprods) any_dcsc = any_dcsc || pr.A.jc != nullptr;
+    size_t o_acs = any_dcsc ? take(8 * std::max<int64_t>(bnz, 1)) : 0;
+    size_t o_acl = any_dcsc ? take(4 * std::max<int64_t>(bnz, 1)) : 0;
     auto arena = ctx_buf(ctx, off);
     if (!arena) return set_err(ctx, SPGEMM_ERR_OOM, "engine arena of %zu bytes", off);
     E->bufs.push_back(arena);
@@ -367,6 +372,8 @@ spgemm_status_t engine_setup(Engine* E, spgemm_ctx* ctx, spgemm_semiring_t sr, c
     E->it.nprod = np;
     E->it.nitems = U;
     E->it.total_bnz = bnz;
+    E->it.acs = any_dcsc ? (int64_t*)(base + o_acs) : nullptr;
+    E->it.acl = any_dcsc ? (int32_t*)(base + o_acl) : nullptr;
     E->it.max_m = 0;
     for (auto& pr : E->hprods) E->it.max_m = std::max<int64_t>(E->it.max_m, pr.A.m);
     uint64_t* sketch = nullptr;

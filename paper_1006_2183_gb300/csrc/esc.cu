@@ -51,7 +51,7 @@ __global__ void k_esc_expand(Items it, const int32_t* __restrict__ item_prod, co
             T bv = T(0);
             if (t < be) {
                 int64_t s, en;
-                col_range(pr->A, __ldg(pr->B.ir + t), s, en);
+                a_col(it, pr, t, __ldg(pr->B.ir + t), s, en);
                 a0 = s;
                 len = (int)(en - s);
                 bv = load_val<SR>(pr->B, t);

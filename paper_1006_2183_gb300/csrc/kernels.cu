@@ -104,9 +104,16 @@ __global__ void __launch_bounds__(256) k_analyze(Items it, TierCfg cfg, int64_t*
         be = __ldg(pr->B.cp + p + 1);
         am = pr->A.m;
         const uint64_t* skp = sketch ? sketch + sketch_base[prod] : nullptr;
+        const int64_t b0 = it.acs ? pr->bnz_base - __ldg(pr->B.cp) : 0;
         for (int64_t t = bs + sub; t < be; t += 8) {
             int32_t k = __ldg(pr->B.ir + t);
-            long long len = col_len(pr->A, k);
+            int64_t cs, ce;
+            col_range(pr->A, k, cs, ce);
+            long long len = ce - cs;
+            if (it.acs) {   // fill the A-column cache for the later passes
+                it.acs[b0 + t] = cs;
+                it.acl[b0 + t] = (int32_t)len;
+            }
             f += len;
             mx = len > mx ? len : mx;
             if (skp && k >= 0 && k < pr->A.n) sk |= __ldg(skp + k);
@@ -378,7 +385,7 @@ __global__ void __launch_bounds__(BLOCK) k_hash(Items it, const int2* __restrict
             if (t < be) {
                 int32_t k = __ldg(pr->B.ir + t);
                 int64_t s, en;
-                col_range(pr->A, k, s, en);
+                a_col(it, pr, t, k, s, en);
                 a0 = s;
                 len = (int)(en - s);
                 if constexpr (NUM) bv = load_val<SR>(pr->B, t);
@@ -568,7 +575,7 @@ __global__ void __launch_bounds__(256) k_tiny(Items it, const int2* __restrict__
         for (int64_t t = bs; t < be; ++t) {
             const int32_t k = __ldg(pr->B.ir + t);
             int64_t s0, en;
-            col_range(pr->A, k, s0, en);
+            a_col(it, pr, t, k, s0, en);
             typename SR::T bv = typename SR::T(0);
             if constexpr (NUM) bv = load_val<SR>(pr->B, t);
             for (int64_t q = s0; q < en && n < TINY_MAX; ++q) {
@@ -886,7 +893,7 @@ __global__ void __launch_bounds__(RT_BLOCK) k_range_sym(Items it, DenseWork dw) 
             if (t < be) {
                 const int32_t k = __ldg(pr->B.ir + t);
                 int64_t s, en;
-                col_range(pr->A, k, s, en);
+                a_col(it, pr, t, k, s, en);
                 a = R0 == 0 ? s : s + lower_bound_rows(air + s, en - s, R0);
                 const int64_t b = R1 == m ? en : s + lower_bound_rows(air + s, en - s, R1);
                 len = (int)(b - a);
@@ -1053,7 +1060,7 @@ __global__ void __launch_bounds__(RT_BLOCK) k_range_num(Items it, DenseWork dw, 
         for (int64_t t = tid; t < deg; t += RT_BLOCK) {
             const int32_t k = __ldg(pr->B.ir + bs + t);
             int64_t s, en;
-            col_range(pr->A, k, s, en);
+            a_col(it, pr, bs + t, k, s, en);
             const int32_t c0 = R0 == 0 ? 0 : lower_bound_rows(air + s, en - s, R0);
             const int32_t nx = s + c0 < en ? __ldg(air + s + c0) : INT_MAX;
             if (t < RT_NEXT) {
@@ -1100,7 +1107,7 @@ __global__ void __launch_bounds__(RT_BLOCK) k_range_num(Items it, DenseWork dw, 
                     } else {
                         const int32_t k = __ldg(pr->B.ir + bs + t);
                         int64_t s, en;
-                        col_range(pr->A, k, s, en);
+                        a_col(it, pr, bs + t, k, s, en);
                         a = s + cv.x;
                         int32_t nx;
                         const int64_t c = count_below(air, a, en, r1, nx);

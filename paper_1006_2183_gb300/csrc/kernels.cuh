@@ -78,7 +78,24 @@ struct Items {
     int64_t nitems = 0;
     int64_t total_bnz = 0;              // sum of nnz(B_i): cursor stride per dense part
     int64_t max_m = 0;                  // most rows of any A_i
+    // A-column cache (DCSC A only): for every stored entry B_i(k, j), where A_i(:,k)
+    // starts and how long it is, filled by the analysis pass so that later passes
+    // skip the DCSC lookup.  Indexed by bnz_base + position within B_i.
+    int64_t* acs = nullptr;
+    int32_t* acl = nullptr;
 };
+
+// A(:,k) for the B entry at position t of product pr (cached when the engine has
+// the A-column cache, else looked up).
+__device__ __forceinline__ void a_col(const Items& it, const Prod* pr, int64_t t, int32_t k, int64_t& s, int64_t& e) {
+    if (it.acs) {
+        const int64_t i = pr->bnz_base + (t - __ldg(pr->B.cp));
+        s = __ldg(it.acs + i);
+        e = s + __ldg(it.acl + i);
+    } else {
+        col_range(pr->A, k, s, e);
+    }
+}
 
 // CTA-wide hash tables order their numeric output through a shared-memory row
 // bitmap (instead of sorting) when every A_i has at most this many rows.
