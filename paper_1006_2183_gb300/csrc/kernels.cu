@@ -667,7 +667,9 @@ static void run_hash_bins(cudaStream_t st, const Items& it, const int2* list, co
 constexpr int RT_BLOCK = 512;
 constexpr int RT_MAXB = 1024;
 constexpr int RT_NEXT = 512;
-static_assert(RANGE_W / 32 <= 4 * RT_BLOCK, "range emit: one 4-word group of the row bitmap per thread");    // k's per column whose cursor state lives in shared memory
+static_assert(RANGE_W / 32 <= 4 * RT_BLOCK, "range emit: one 4-word group of the row bitmap per thread");
+// the rank order of a range (< TBL / 2 entries of 2 bytes) lives in RangeSmem.start and .bv
+static_assert(RANGE_TBL / 2 * 2 <= 2 * RT_BLOCK * 8, "range emit: the rank order of a range fits start + bv");    // k's per column whose cursor state lives in shared memory
 
 __device__ __forceinline__ int32_t lower_bound_rows(const int32_t* __restrict__ r, int64_t len, int64_t v) {
     int64_t lo = 0, hi = len;
@@ -1208,28 +1210,51 @@ __global__ void __launch_bounds__(RT_BLOCK) k_range_num(Items it, DenseWork dw, 
             // per group, one group per thread) plus at most 4 words of popcounts.  Each
             // occupied slot writes its entry at that rank and empties itself.
             int* s_gp = sc->end;   // free once the range's products are accumulated
+            int marked;            // rows in the range's bitmap
             {
                 const int x0 = tid * 4;
                 int c = 0;
                 for (int x = x0; x < x0 + 4 && x < nw; ++x) c += __popc(bitmap[x]);
-                int total;
-                s_gp[tid] = group_incl_scan<RT_BLOCK>(c, sc->wc, total) - c;
+                s_gp[tid] = group_incl_scan<RT_BLOCK>(c, sc->wc, marked) - c;
             }
             __syncthreads();
             {
                 const int64_t ob = outbase + rp.off;
-                const int nslots = direct ? (int)(r1 - r0) : TBL;
-                for (int x = tid; x < nslots; x += RT_BLOCK) {
-                    const int32_t kr = keys[x];
-                    if (kr == -1) continue;
-                    const int lr = direct ? x : (int)(kr - r0);
-                    const int wd = lr >> 5;
-                    int rank = s_gp[wd >> 2] + __popc(bitmap[wd] & ((1u << (lr & 31)) - 1u));
-                    for (int y = wd & ~3; y < wd; ++y) rank += __popc(bitmap[y]);
-                    Cir[ob + rank] = kr + rb;
-                    Cv[ob + rank] = SR::out(vals[x]);
-                    keys[x] = -1;
-                    vals[x] = SR::zero();
+                if (direct) {
+                    // slots are rows: ranks grow with the slot, so the stores are nearly coalesced
+                    const int nslots = (int)(r1 - r0);
+                    for (int x = tid; x < nslots; x += RT_BLOCK) {
+                        const int32_t kr = keys[x];
+                        if (kr == -1) continue;
+                        const int wd = x >> 5;
+                        int rank = s_gp[wd >> 2] + __popc(bitmap[wd] & ((1u << (x & 31)) - 1u));
+                        for (int y = wd & ~3; y < wd; ++y) rank += __popc(bitmap[y]);
+                        Cir[ob + rank] = kr + rb;
+                        Cv[ob + rank] = SR::out(vals[x]);
+                        keys[x] = -1;
+                        vals[x] = SR::zero();
+                    }
+                } else {
+                    // hashed slots: record the slot of every rank first, then store in rank
+                    // order, so consecutive threads write consecutive entries
+                    uint16_t* order = reinterpret_cast<uint16_t*>(sc->start);   // spans start and bv
+                    for (int x = tid; x < TBL; x += RT_BLOCK) {
+                        const int32_t kr = keys[x];
+                        if (kr == -1) continue;
+                        const int lr = (int)(kr - r0);
+                        const int wd = lr >> 5;
+                        int rank = s_gp[wd >> 2] + __popc(bitmap[wd] & ((1u << (lr & 31)) - 1u));
+                        for (int y = wd & ~3; y < wd; ++y) rank += __popc(bitmap[y]);
+                        order[rank] = (uint16_t)x;
+                    }
+                    __syncthreads();
+                    for (int i = tid; i < marked; i += RT_BLOCK) {
+                        const int x = order[i];
+                        Cir[ob + i] = keys[x] + rb;
+                        Cv[ob + i] = SR::out(vals[x]);
+                        keys[x] = -1;
+                        vals[x] = SR::zero();
+                    }
                 }
             }
             __syncthreads();
