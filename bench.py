@@ -138,6 +138,21 @@ def learned_vs_plain(sp, ctx, steps: int, warmup: int) -> dict:
     return out
 
 
+def aggregate_ranks(local_ms: float, flops_step: int, steps: int, world: int, device=None):
+    """Whole-job time and GFLOPS over `world` replicas: every rank ran `steps` steps of
+    `flops_step` flops; the job took as long as its slowest rank (max over ranks).
+    Returns (max time in ms, GFLOPS of all ranks' flops over that time)."""
+    tot_ms = float(local_ms)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([tot_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+        dist.barrier()
+    return tot_ms, 2.0 * flops_step * steps * world / (tot_ms / 1e3) / 1e9
+
+
 def imbalance(bf: np.ndarray) -> dict:
     """Load imbalance of Section 7.1 (max flops of any processor / mean) from the
     block-product flops bf[s, J, I] of a g x g grid: per stage with SUMMA's pairing
@@ -503,13 +518,7 @@ def main():
     phases = ctx.phase_ms()
     ctx.timing(False)
     clocks = clk.summary()
-    tot_ms = sum(times)
-    if world > 1:
-        t = torch.tensor([tot_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-        dist.barrier()
-    value = 2.0 * flops_step * args.steps * world / (tot_ms / 1e3) / 1e9
+    tot_ms, value = aggregate_ranks(sum(times), flops_step, args.steps, world, dev)
 
     # dominant kernel: numeric dense tier of the flat plus-times FP64 product
     hbm, peak_kind = peaks()
