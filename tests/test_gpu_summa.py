@@ -219,3 +219,31 @@ def test_summa_expand_sort_compress_matches_column_tiers_scale16(ctx):
     np.testing.assert_array_equal(C0.rowidx, C1.rowidx)
     np.testing.assert_array_equal(C0.vals, C1.vals)
     np.testing.assert_array_equal(np.diff(C0.colptr), oracle.symbolic(A, A))
+
+
+def test_degenerate_inputs_on_the_newer_paths(ctx):
+    """Empty operands, an empty grid row, 1 x 1 and g larger than the matrix, through
+    the expand-sort-compress stage kernel, the permutation and the block work."""
+    import torch
+    s = sp()
+    Z = CSC(9, 7, np.zeros(8, np.int64), np.zeros(0, np.int32), np.zeros(0))
+    Y = CSC(7, 5, np.zeros(6, np.int64), np.zeros(0, np.int32), np.zeros(0))
+    C = blocked(ctx, Z, Y, PT_F64, 4, block_kernel=1)
+    assert C.nnz == 0 and list(C.colptr) == [0] * 6
+    one = CSC(1, 1, np.array([0, 1]), np.array([0], np.int32), np.array([3.0]))
+    for kw in ({}, {"block_kernel": 1}):
+        C = blocked(ctx, one, one, PT_F64, 4, **kw)    # g > dimension: 15 of 16 blocks empty
+        assert C.nnz == 1 and C.vals[0] == 9.0
+    # rows only in the first quarter: three block rows of A are empty
+    A = gen.random_csc(40, 40, 0.1, 0x71, PT_I64)
+    keep = A.rowidx < 10
+    cp = np.concatenate([[0], np.cumsum([keep[A.colptr[j]:A.colptr[j + 1]].sum() for j in range(40)])])
+    A = CSC(40, 40, cp.astype(np.int64), A.rowidx[keep], A.vals[keep])
+    R = oracle.spgemm(A, A, PT_I64)
+    for kw in ({}, {"block_kernel": 1}):
+        assert_matches(blocked(ctx, A, A, PT_I64, 4, **kw), R, PT_I64, what=str(kw))
+    dZ = s.Matrix.from_host(ctx, Z, PT_F64)
+    assert s.spgemm_mat_permute(ctx, dZ, torch.arange(9, dtype=torch.int32, device=ctx.device).flip(0),
+                                None).to_host().nnz == 0
+    bf = s.spgemm_summa_block_flops(ctx, dZ, s.Matrix.from_host(ctx, Y, PT_F64), 3)
+    assert bf.shape == (3, 3, 3) and bf.sum() == 0
