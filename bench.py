@@ -192,10 +192,12 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--scale", type=int, default=SCALE)
     ap.add_argument("--grid", type=int, default=GRID, help="virtual SUMMA grid size g (g x g blocks)")
-    ap.add_argument("--workload", default="rmat_square", choices=["rmat_square", "restriction", "tallskinny"],
+    ap.add_argument("--workload", default="rmat_square",
+                    choices=["rmat_square", "restriction", "tallskinny", "summa_pipeline"],
                     help="rmat_square: the default A*A step; restriction: A S^T and S (A S^T) of orders 2, 4, 8 "
                          "(Section 6.2.3); tallskinny: R-MAT times n x n/2^13 ER with c2 = 1 .. 10^5 per column "
-                         "(Section 6.2.2)")
+                         "(Section 6.2.2); summa_pipeline: R-MAT A*A on the g x g grid with merges every "
+                         "1, 2, 4, 8 stages, one stream vs two streams (Sections 7.2-7.3)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-learned", action="store_true",
@@ -351,7 +353,8 @@ def run_reference(args, rank, world):
 
 
 def run_sweep(args) -> None:
-    """The second workloads of Section 6.2 on one GPU: every case timed on the device
+    """The second workloads of Section 6.2 and the stage pipeline of Sections 7.2-7.3 on one
+    GPU: every case timed on the device
     (CUDA events on the context stream around the public product call, L2 flushed
     before each run), one JSON line with the aggregate and the per-case numbers."""
     import torch
@@ -379,6 +382,24 @@ def run_sweep(args) -> None:
                           lambda dS=dS, ASt=ASt: sp.spgemm_multiply(ctx, dS, ASt, sr), fl_sast))
         workload = {"workload": f"rmat{args.scale}_restriction", "scale": args.scale, "edge_factor": EF,
                     "seed": SEED, "orders": [2, 4, 8]}
+    elif args.workload == "summa_pipeline":
+        A = gen.rmat(args.scale, EF, SEED, gen.PLUS_TIMES_F64)
+        dA = sp.Matrix.from_host(ctx, A, sr)
+        mctx = sp.Context(stream=torch.cuda.Stream())
+        g = args.grid
+        fl = flops_of(A)
+        for every in (1, 2, 4, 8):
+            if every >= g:
+                continue
+            o = sp.default_opts(summa_merge_every=every)
+            cases.append((f"one stream, merge every {every}",
+                          lambda o=o: sp.spgemm_summa_blocked(ctx, dA, dA, g, sr, o), fl))
+            cases.append((f"two streams, merge every {every}",
+                          lambda o=o: sp.spgemm_summa_pipelined(ctx, mctx, dA, dA, g, sr, o), fl))
+        cases.append((f"one stream, one merge after stage {g}",
+                      lambda: sp.spgemm_summa_blocked(ctx, dA, dA, g, sr), fl))
+        workload = {"workload": f"rmat{args.scale}_AxA_summa{g}_pipeline", "scale": args.scale, "edge_factor": EF,
+                    "seed": SEED, "grid": g}
     else:
         n_scale = args.scale
         A = gen.rmat(n_scale, EF, SEED, gen.PLUS_TIMES_F64)

@@ -231,6 +231,22 @@ spgemm_status_t spgemm_multiply(spgemm_ctx_t ctx, spgemm_mat_t A, spgemm_mat_t B
  * Errors as spgemm_plan; INVALID_ARG for g < 1. */
 spgemm_status_t spgemm_summa_blocked(spgemm_ctx_t ctx, spgemm_mat_t A, spgemm_mat_t B, int g,
                                      spgemm_semiring_t semiring, const spgemm_opts_t* opts, spgemm_mat_t* C);
+/* The same product with the stage merges on a second stream (Sections 7.2-7.3:
+ * overlap each stage's data movement with the local work; on one GPU the
+ * overlap is between the merge of one group of summa_merge_every stages and the
+ * stage products of the next group).  Stage products run on ctx's stream from
+ * the calling thread; merges run on merge_ctx's stream from a worker thread the
+ * library starts and joins within this call, so merge_ctx's allocator callbacks
+ * are called from that thread and must be thread-safe.  ctx's callbacks stay on
+ * the calling thread.  The result is identical to spgemm_summa_blocked with the
+ * same opts (for plus-times FP64 up to summation order) and is allocated
+ * through merge_ctx, which must outlive it.  Both contexts must be on the same
+ * device; the call returns after both streams have finished its work.
+ * INVALID_ARG if merge_ctx is NULL, equal to ctx or on another device; other
+ * errors as spgemm_summa_blocked (a merge error is reported on ctx). */
+spgemm_status_t spgemm_summa_pipelined(spgemm_ctx_t ctx, spgemm_ctx_t merge_ctx, spgemm_mat_t A, spgemm_mat_t B,
+                                       int g, spgemm_semiring_t semiring, const spgemm_opts_t* opts,
+                                       spgemm_mat_t* C);
 /* Block statistics of the last summa call on this context: per-stage flops
  * (g entries) and the number of nonempty block products.  Outputs may be NULL. */
 spgemm_status_t spgemm_summa_stats(spgemm_ctx_t ctx, int64_t* stage_flops, int g, int64_t* nonempty_products);

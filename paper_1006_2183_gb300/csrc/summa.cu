@@ -20,7 +20,11 @@
 //      blocks of C(:, j) are adjacent, so C's column pointers are every g-th
 //      entry of the merge's.
 #include <algorithm>
+#include <condition_variable>
 #include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
 
 #include "internal.cuh"
 
@@ -372,12 +376,173 @@ spgemm_status_t merge_columns(spgemm_ctx* ctx, spgemm_semiring_t sr, const spgem
     return SPGEMM_OK;
 }
 
-}  // namespace
+// One group of stages, multiplied and ready to merge.
+struct Group {
+    Engine E;
+    std::shared_ptr<DevBuf> rbuf, vbuf, colbuf;
+    const int64_t* pstart = nullptr;   // partial columns with gaps (bounded slots), or null
+    const int64_t* pend = nullptr;
+    int64_t U = 0, pn = 0;             // partial columns, partial entries
+    bool final = false;                // the last group: its merge writes C
+    cudaEvent_t ready = nullptr;       // recorded after the products (pipelined mode)
+};
 
-extern "C" {
+// Stage products A(I,s) * B(s,J) of one group, on ctx's stream (stage-major items).
+spgemm_status_t stage_products(spgemm_ctx* ctx, spgemm_semiring_t sr, const spgemm_opts_t& o,
+                               const std::vector<Prod>& grp, bool single_merge, Group* G) {
+    if (grp.empty()) return SPGEMM_OK;
+    Engine& E = G->E;
+    SG_TRY(engine_setup(&E, ctx, sr, o, grp, false));
+    if (o.block_kernel == 1) {
+        SG_TRY(engine_esc(&E, &G->rbuf, &G->vbuf));   // outer-product order, Section 2.4
+    } else if (single_merge && E.flops_total <= BOUNDED_MAX_SLOTS) {
+        // one merge reads the partials where they were written: no count pass for them
+        SG_TRY(engine_numeric_bounded(&E, &G->rbuf, &G->vbuf, &G->colbuf, &G->pstart, &G->pend));
+    } else {
+        SG_TRY(engine_symbolic(&E));
+        SG_TRY(engine_alloc_out(&E, &G->rbuf, &G->vbuf));
+        SG_TRY(engine_numeric(&E, (int32_t*)G->rbuf->p, G->vbuf->p));
+    }
+    G->U = E.it.nitems;
+    G->pn = E.nnz_total;
+    // stage flops for the statistics
+    auto pf = ctx_buf(ctx, 8 * grp.size());
+    if (!pf) return set_err(ctx, SPGEMM_ERR_OOM, "stage flops");
+    SG_CUDA(ctx, cudaMemsetAsync(pf->p, 0, 8 * grp.size(), ctx->stream));
+    k_prod_flops<<<gridn(G->U), 256, 0, ctx->stream>>>(E.it, E.item_prod, E.flops, (unsigned long long*)pf->p);
+    note_launch();
+    std::vector<unsigned long long> hpf(grp.size());
+    SG_CUDA(ctx, cudaMemcpyAsync(hpf.data(), pf->p, 8 * grp.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    SG_TRY(sync_ctx(ctx));
+    for (size_t i = 0; i < grp.size(); ++i) ctx->summa_stage_flops[grp[i].tag] += (int64_t)hpf[i];
+    return SPGEMM_OK;
+}
 
-spgemm_status_t spgemm_summa_blocked(spgemm_ctx_t ctx, spgemm_mat_t A, spgemm_mat_t B, int g, spgemm_semiring_t sr,
-                                     const spgemm_opts_t* opts, spgemm_mat_t* C) {
+// Merges the group's partials with the accumulated merge columns `acc` (null
+// before the first merge), on mctx's stream and through mctx's allocator.
+spgemm_status_t merge_group(spgemm_ctx* mctx, spgemm_semiring_t sr, const spgemm_opts_t& o, int64_t m, int64_t mb,
+                            int64_t n, int g, Group& G, spgemm_mat_t acc, spgemm_mat_t* Cn) {
+    const size_t w = sr_size(sr);
+    const int64_t U = G.U, pn = G.pn;
+    const Engine& E = G.E;
+    // columns to merge: the accumulated C (if any) followed by this group's partial columns
+    const int64_t nacc = acc ? n * g : 0;   // merge columns so far
+    const int64_t accnz = acc ? acc->nnz : 0;
+    const int64_t ncols = nacc + U;
+    const int64_t pnz = accnz + pn;
+    cudaStream_t stq = mctx->stream;
+    auto ocb = ctx_buf(mctx, 8 * std::max<int64_t>(ncols, 1));
+    if (!ocb) return set_err(mctx, SPGEMM_ERR_OOM, "merge keys");
+    uint32_t* oc = (uint32_t*)ocb->p;
+    uint32_t* pay = oc + std::max<int64_t>(ncols, 1);
+    std::shared_ptr<DevBuf> pcp, pir, pv;
+    const int64_t* Pcp;
+    const int32_t* Pir;
+    const void* Pv;
+    const int64_t* Pce = nullptr;
+    if (!acc && U > 0) {
+        // the partials alone: merge them in place
+        Pcp = G.pstart ? G.pstart : E.Coff;
+        Pce = G.pend;
+        Pir = (const int32_t*)G.rbuf->p;
+        Pv = G.vbuf->p;
+    } else {
+        pcp = ctx_buf(mctx, 8 * (ncols + 1));
+        pir = ctx_buf(mctx, 4 * std::max<int64_t>(pnz, 1));
+        pv = ctx_buf(mctx, w * std::max<int64_t>(pnz, 1));
+        if (!pcp || !pir || !pv) return set_err(mctx, SPGEMM_ERR_OOM, "merge inputs");
+        if (acc) {
+            SG_CUDA(mctx, cudaMemcpyAsync(pcp->p, acc->cp, 8 * nacc, cudaMemcpyDeviceToDevice, stq));
+            if (accnz) {
+                SG_CUDA(mctx, cudaMemcpyAsync(pir->p, acc->ir, 4 * accnz, cudaMemcpyDeviceToDevice, stq));
+                SG_CUDA(mctx, cudaMemcpyAsync(pv->p, acc->num, w * accnz, cudaMemcpyDeviceToDevice, stq));
+            }
+        }
+        if (U > 0) {
+            k_add_offset<<<gridn(U + 1), 256, 0, stq>>>(E.Coff, U + 1, accnz, (int64_t*)pcp->p + nacc);
+            note_launch();
+            if (pn) {
+                SG_CUDA(mctx, cudaMemcpyAsync((int32_t*)pir->p + accnz, G.rbuf->p, 4 * pn, cudaMemcpyDeviceToDevice, stq));
+                SG_CUDA(mctx, cudaMemcpyAsync((char*)pv->p + w * accnz, G.vbuf->p, w * pn, cudaMemcpyDeviceToDevice, stq));
+            }
+        } else if (acc) {
+            SG_CUDA(mctx, cudaMemcpyAsync((int64_t*)pcp->p + nacc, acc->cp + nacc, 8, cudaMemcpyDeviceToDevice, stq));
+        } else {
+            SG_CUDA(mctx, cudaMemsetAsync(pcp->p, 0, 8, stq));
+        }
+        Pcp = (const int64_t*)pcp->p;
+        Pir = (const int32_t*)pir->p;
+        Pv = pv->p;
+    }
+    if (acc) {
+        k_iota_cols<<<gridn(nacc), 256, 0, stq>>>(oc, pay, nacc);
+        note_launch();
+    }
+    if (U > 0) {
+        k_item_outcol<<<gridn(U), 256, 0, stq>>>(E.it, E.item_prod, g, oc, pay, nacc);
+        note_launch();
+    }
+    return merge_columns(mctx, sr, o, m, mb, n, g, G.final, ncols, Pcp, Pce, Pir, Pv, pnz, oc, pay, Cn);
+}
+
+// Hand-over between the products (calling thread, ctx's stream) and the merges
+// (worker thread, merge context's stream) of the two-stream pipeline.
+struct Pipe {
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<std::unique_ptr<Group>> todo;   // multiplied, not merged
+    std::deque<std::unique_ptr<Group>> done;   // merged: freed by the calling thread
+    bool closed = false;                       // no more groups will come
+    bool abort = false;                        // the products failed: merge nothing more
+    spgemm_status_t status = SPGEMM_OK;        // the worker's (read after join)
+    spgemm_mat_t result = nullptr;             // C, after the final group's merge
+};
+
+void merge_worker(Pipe* P, spgemm_ctx* mctx, spgemm_semiring_t sr, spgemm_opts_t o, int64_t m, int64_t mb,
+                  int64_t n, int g) {
+    cudaSetDevice(mctx->device);
+    spgemm_mat_t acc = nullptr;
+    std::unique_ptr<spgemm_mat> hold;
+    for (;;) {
+        std::unique_ptr<Group> G;
+        bool abort;
+        {
+            std::unique_lock<std::mutex> lk(P->mu);
+            P->cv.wait(lk, [&] { return !P->todo.empty() || P->closed; });
+            if (P->todo.empty()) break;   // closed and drained
+            G = std::move(P->todo.front());
+            P->todo.pop_front();
+            abort = P->abort;
+        }
+        if (P->status == SPGEMM_OK && !abort) {
+            spgemm_status_t s = SPGEMM_OK;
+            cudaError_t e = cudaStreamWaitEvent(mctx->stream, G->ready, 0);
+            if (e != cudaSuccess) s = check_cuda(mctx, e, "wait for the stage products at " SG_WHERE);
+            spgemm_mat_t Cn = nullptr;
+            if (s == SPGEMM_OK) s = merge_group(mctx, sr, o, m, mb, n, g, *G, acc, &Cn);
+            if (s == SPGEMM_OK) {
+                hold.reset(Cn);
+                acc = Cn;
+                if (G->final) P->result = hold.release();
+            }
+            P->status = s;
+        }
+        // the merge no longer reads the group's arrays once its stream is drained
+        cudaError_t e = cudaStreamSynchronize(mctx->stream);
+        if (e != cudaSuccess && P->status == SPGEMM_OK) P->status = check_cuda(mctx, e, "merge stream at " SG_WHERE);
+        cudaEventDestroy(G->ready);
+        G->ready = nullptr;
+        std::lock_guard<std::mutex> lk(P->mu);
+        P->done.push_back(std::move(G));
+    }
+}
+
+// Common driver of spgemm_summa_blocked (mctx null: one stream) and
+// spgemm_summa_pipelined (merges on mctx's stream, overlapping the next
+// group's stage products; Sections 7.2-7.3 overlap the stage broadcasts with
+// the local work, which on one GPU becomes this stage/merge overlap).
+spgemm_status_t summa_run(spgemm_ctx_t ctx, spgemm_ctx_t mctx, spgemm_mat_t A, spgemm_mat_t B, int g,
+                          spgemm_semiring_t sr, const spgemm_opts_t* opts, spgemm_mat_t* C) {
     if (!ctx || !A || !B || !C) return SPGEMM_ERR_INVALID_ARG;
     if (g < 1 || g > 1024) return set_err(ctx, SPGEMM_ERR_INVALID_ARG, "grid size g = %d outside [1, 1024]", g);
     if ((int)sr < 0 || (int)sr > 3) return set_err(ctx, SPGEMM_ERR_INVALID_ARG, "bad semiring");
@@ -430,107 +595,88 @@ spgemm_status_t spgemm_summa_blocked(spgemm_ctx_t ctx, spgemm_mat_t A, spgemm_ma
     ctx->summa_stage_flops.assign(g, 0);
     ctx->summa_nonempty = (int64_t)all.size();
     const int every = o.summa_merge_every > 0 ? std::min(o.summa_merge_every, g) : g;
-    spgemm_mat_t acc = nullptr;   // C merged so far
-    std::unique_ptr<spgemm_mat> hold_acc;
-    for (int s0 = 0; s0 < g; s0 += every) {
+    auto group_of = [&](int s0) {
         std::vector<Prod> grp;
         for (auto& pr : all)
             if (pr.tag >= s0 && pr.tag < s0 + every) grp.push_back(pr);
-        Engine E;
-        std::shared_ptr<DevBuf> rbuf, vbuf, colbuf;
-        const int64_t* pstart = nullptr;   // partial columns with gaps (bounded slots), or null
-        const int64_t* pend = nullptr;
-        int64_t U = 0, pn = 0;
-        if (!grp.empty()) {
-            SG_TRY(engine_setup(&E, ctx, sr, o, grp, false));
-            if (o.block_kernel == 1) {
-                SG_TRY(engine_esc(&E, &rbuf, &vbuf));   // outer-product order, Section 2.4
-            } else if (!acc && s0 + every >= g && E.flops_total <= BOUNDED_MAX_SLOTS) {
-                // one merge reads the partials where they were written: no count pass for them
-                SG_TRY(engine_numeric_bounded(&E, &rbuf, &vbuf, &colbuf, &pstart, &pend));
-            } else {
-                SG_TRY(engine_symbolic(&E));
-                SG_TRY(engine_alloc_out(&E, &rbuf, &vbuf));
-                SG_TRY(engine_numeric(&E, (int32_t*)rbuf->p, vbuf->p));
-            }
-            U = E.it.nitems;
-            pn = E.nnz_total;
-            // stage flops for the statistics
-            auto pf = ctx_buf(ctx, 8 * grp.size());
-            if (!pf) return set_err(ctx, SPGEMM_ERR_OOM, "stage flops");
-            SG_CUDA(ctx, cudaMemsetAsync(pf->p, 0, 8 * grp.size(), ctx->stream));
-            k_prod_flops<<<gridn(U), 256, 0, ctx->stream>>>(E.it, E.item_prod, E.flops, (unsigned long long*)pf->p);
-            note_launch();
-            std::vector<unsigned long long> hpf(grp.size());
-            SG_CUDA(ctx, cudaMemcpyAsync(hpf.data(), pf->p, 8 * grp.size(), cudaMemcpyDeviceToHost, ctx->stream));
-            SG_TRY(sync_ctx(ctx));
-            for (size_t i = 0; i < grp.size(); ++i) ctx->summa_stage_flops[grp[i].tag] += (int64_t)hpf[i];
+        return grp;
+    };
+    if (!mctx) {
+        spgemm_mat_t acc = nullptr;   // C merged so far
+        std::unique_ptr<spgemm_mat> hold_acc;
+        for (int s0 = 0; s0 < g; s0 += every) {
+            Group G;
+            G.final = s0 + every >= g;
+            SG_TRY(stage_products(ctx, sr, o, group_of(s0), !acc && G.final, &G));
+            spgemm_mat_t Cn = nullptr;
+            SG_TRY(merge_group(ctx, sr, o, m, bA.mb, n, g, G, acc, &Cn));
+            hold_acc.reset(Cn);
+            acc = Cn;
         }
-        // columns to merge: the accumulated C (if any) followed by this group's partial columns
-        const int64_t nacc = acc ? n * g : 0;   // merge columns so far
-        const int64_t accnz = acc ? acc->nnz : 0;
-        const int64_t ncols = nacc + U;
-        const int64_t pnz = accnz + pn;
-        cudaStream_t stq = ctx->stream;
-        auto ocb = ctx_buf(ctx, 8 * std::max<int64_t>(ncols, 1));
-        if (!ocb) return set_err(ctx, SPGEMM_ERR_OOM, "merge keys");
-        uint32_t* oc = (uint32_t*)ocb->p;
-        uint32_t* pay = oc + std::max<int64_t>(ncols, 1);
-        std::shared_ptr<DevBuf> pcp, pir, pv;
-        const int64_t* Pcp;
-        const int32_t* Pir;
-        const void* Pv;
-        const int64_t* Pce = nullptr;
-        if (!acc && U > 0) {
-            // the partials alone: merge them in place
-            Pcp = pstart ? pstart : E.Coff;
-            Pce = pend;
-            Pir = (const int32_t*)rbuf->p;
-            Pv = vbuf->p;
-        } else {
-            pcp = ctx_buf(ctx, 8 * (ncols + 1));
-            pir = ctx_buf(ctx, 4 * std::max<int64_t>(pnz, 1));
-            pv = ctx_buf(ctx, w * std::max<int64_t>(pnz, 1));
-            if (!pcp || !pir || !pv) return set_err(ctx, SPGEMM_ERR_OOM, "merge inputs");
-            if (acc) {
-                SG_CUDA(ctx, cudaMemcpyAsync(pcp->p, acc->cp, 8 * nacc, cudaMemcpyDeviceToDevice, stq));
-                if (accnz) {
-                    SG_CUDA(ctx, cudaMemcpyAsync(pir->p, acc->ir, 4 * accnz, cudaMemcpyDeviceToDevice, stq));
-                    SG_CUDA(ctx, cudaMemcpyAsync(pv->p, acc->num, w * accnz, cudaMemcpyDeviceToDevice, stq));
-                }
-            }
-            if (U > 0) {
-                k_add_offset<<<gridn(U + 1), 256, 0, stq>>>(E.Coff, U + 1, accnz, (int64_t*)pcp->p + nacc);
-                note_launch();
-                if (pn) {
-                    SG_CUDA(ctx, cudaMemcpyAsync((int32_t*)pir->p + accnz, rbuf->p, 4 * pn, cudaMemcpyDeviceToDevice, stq));
-                    SG_CUDA(ctx, cudaMemcpyAsync((char*)pv->p + w * accnz, vbuf->p, w * pn, cudaMemcpyDeviceToDevice, stq));
-                }
-            } else if (acc) {
-                SG_CUDA(ctx, cudaMemcpyAsync((int64_t*)pcp->p + nacc, acc->cp + nacc, 8, cudaMemcpyDeviceToDevice, stq));
-            } else {
-                SG_CUDA(ctx, cudaMemsetAsync(pcp->p, 0, 8, stq));
-            }
-            Pcp = (const int64_t*)pcp->p;
-            Pir = (const int32_t*)pir->p;
-            Pv = pv->p;
-        }
-        if (acc) {
-            k_iota_cols<<<gridn(nacc), 256, 0, stq>>>(oc, pay, nacc);
-            note_launch();
-        }
-        if (U > 0) {
-            k_item_outcol<<<gridn(U), 256, 0, stq>>>(E.it, E.item_prod, g, oc, pay, nacc);
-            note_launch();
-        }
-        spgemm_mat_t Cn = nullptr;
-        const bool final = s0 + every >= g;
-        SG_TRY(merge_columns(ctx, sr, o, m, bA.mb, n, g, final, ncols, Pcp, Pce, Pir, Pv, pnz, oc, pay, &Cn));
-        hold_acc.reset(Cn);
-        acc = Cn;
+        *C = hold_acc.release();
+        return SPGEMM_OK;
     }
-    *C = hold_acc.release();
+    // two streams: group k's merge (worker) overlaps group k+1's stage products (here)
+    Pipe P;
+    std::thread worker(merge_worker, &P, mctx, sr, o, m, bA.mb, n, g);
+    auto release_done = [&] {
+        std::deque<std::unique_ptr<Group>> d;
+        {
+            std::lock_guard<std::mutex> lk(P.mu);
+            d.swap(P.done);
+        }
+    };
+    for (int s0 = 0; s0 < g && s == SPGEMM_OK; s0 += every) {
+        auto G = std::make_unique<Group>();
+        G->final = s0 + every >= g;
+        s = stage_products(ctx, sr, o, group_of(s0), every >= g, G.get());
+        if (s != SPGEMM_OK) break;
+        cudaError_t e = cudaEventCreateWithFlags(&G->ready, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(G->ready, ctx->stream);
+        if (e != cudaSuccess) {
+            if (G->ready) cudaEventDestroy(G->ready);
+            s = check_cuda(ctx, e, "stage products event at " SG_WHERE);
+            break;
+        }
+        {
+            std::lock_guard<std::mutex> lk(P.mu);
+            P.todo.push_back(std::move(G));
+        }
+        P.cv.notify_one();
+        release_done();
+    }
+    {
+        std::lock_guard<std::mutex> lk(P.mu);
+        P.closed = true;
+        P.abort = s != SPGEMM_OK;
+    }
+    P.cv.notify_one();
+    worker.join();
+    release_done();
+    std::unique_ptr<spgemm_mat> result(P.result);
+    if (s != SPGEMM_OK) return s;
+    if (P.status != SPGEMM_OK) return set_err(ctx, P.status, "pipelined merge: %s", mctx->err.c_str());
+    if (!result) return set_err(ctx, SPGEMM_ERR_CUDA, "pipelined merge produced no result");
+    *C = result.release();
     return SPGEMM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+spgemm_status_t spgemm_summa_blocked(spgemm_ctx_t ctx, spgemm_mat_t A, spgemm_mat_t B, int g, spgemm_semiring_t sr,
+                                     const spgemm_opts_t* opts, spgemm_mat_t* C) {
+    return summa_run(ctx, nullptr, A, B, g, sr, opts, C);
+}
+
+spgemm_status_t spgemm_summa_pipelined(spgemm_ctx_t ctx, spgemm_ctx_t merge_ctx, spgemm_mat_t A, spgemm_mat_t B,
+                                       int g, spgemm_semiring_t sr, const spgemm_opts_t* opts, spgemm_mat_t* C) {
+    if (!ctx || !merge_ctx) return SPGEMM_ERR_INVALID_ARG;
+    if (merge_ctx == ctx) return set_err(ctx, SPGEMM_ERR_INVALID_ARG, "the merge context must be a second context");
+    if (merge_ctx->device != ctx->device)
+        return set_err(ctx, SPGEMM_ERR_INVALID_ARG, "contexts on devices %d and %d", ctx->device, merge_ctx->device);
+    return summa_run(ctx, merge_ctx, A, B, g, sr, opts, C);
 }
 
 spgemm_status_t spgemm_summa_block_flops(spgemm_ctx_t ctx, spgemm_mat_t A, spgemm_mat_t B, int g, int64_t* flops) {

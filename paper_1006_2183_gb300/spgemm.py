@@ -87,6 +87,7 @@ _sig("spgemm_plan_stats", [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.P
 _sig("spgemm_plan_destroy", [P])
 _sig("spgemm_multiply", [P, P, P, ctypes.c_int, ctypes.POINTER(Opts), PP])
 _sig("spgemm_summa_blocked", [P, P, P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Opts), PP])
+_sig("spgemm_summa_pipelined", [P, P, P, P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Opts), PP])
 _sig("spgemm_summa_stats", [P, ctypes.POINTER(I64), ctypes.c_int, ctypes.POINTER(I64)])
 _sig("spgemm_batch", [P, ctypes.c_int, PP, PP, ctypes.c_int, ctypes.POINTER(Opts), PP])
 _sig("spgemm_batch_plan", [P, ctypes.c_int, PP, PP, ctypes.c_int, ctypes.POINTER(Opts), PP])
@@ -389,6 +390,16 @@ def spgemm_summa_blocked(ctx: Context, A: Matrix, B: Matrix, g: int, semiring: i
     h = ctypes.c_void_p()
     ctx._check(_lib.spgemm_summa_blocked(ctx.handle, A.handle, B.handle, g, semiring, _opts(opts), ctypes.byref(h)))
     return Matrix(ctx, h, semiring)
+
+
+def spgemm_summa_pipelined(ctx: Context, merge_ctx: Context, A: Matrix, B: Matrix, g: int, semiring: int,
+                           opts: Opts | None = None) -> Matrix:
+    """spgemm_summa_blocked with the stage merges on merge_ctx's stream; C belongs to merge_ctx."""
+    h = ctypes.c_void_p()
+    _order_after_current(ctx)
+    ctx._check(_lib.spgemm_summa_pipelined(ctx.handle, merge_ctx.handle, A.handle, B.handle, g, semiring,
+                                           _opts(opts), ctypes.byref(h)))
+    return Matrix(merge_ctx, h, semiring)
 
 
 def spgemm_summa_stats(ctx: Context, g: int):
