@@ -38,6 +38,11 @@ METRIC = "SpGEMM GFLOPS (2*flops/s)"
 UNIT = "GFLOPS"
 SCALE, EF, SEED = 18, 8, 0x1802
 GRID = 16
+# R-MAT seeds of the A*A workloads by scale (scale 20 is the larger flat + 32 x 32 grid configuration)
+SEED_OF_SCALE = {18: 0x1802, 20: 0x2005}
+# semiring ids of the C ABI: name and value width in bytes
+SR_NAME = {0: "pt64", 1: "mp32", 2: "bool", 3: "pti64"}
+SR_WIDTH = {0: 8, 1: 4, 2: 1, 3: 8}
 L2_FLUSH_BYTES = 512 << 20
 CPU_STRIDE = 4   # oracle sample: every 4th output column (~25 core-seconds on the flat scale-18 product)
 
@@ -203,7 +208,7 @@ def parse():
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned+batched vs plain comparison on the batched workloads")
     ap.add_argument("--semirings", default="pt64,mp32",
-                    help="comma list of pt64 (plus-times FP64) and mp32 (min-plus FP32)")
+                    help="comma list of pt64 (plus-times FP64), mp32 (min-plus FP32), bool (or-and)")
     ap.add_argument("--products", default="flat,summa",
                     help="comma list of product kinds in a step: flat, summa")
     ap.add_argument("--opt", action="append", default=[],
@@ -317,7 +322,8 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     import oracle
-    A = gen.rmat(args.scale, EF, SEED, gen.PLUS_TIMES_F64)
+    seed = SEED_OF_SCALE.get(args.scale, SEED)
+    A = gen.rmat(args.scale, EF, seed, gen.PLUS_TIMES_F64)
     n = A.n
     # bounded sample: every 4th output column of the flat plus-times FP64 product
     cols = np.arange(0, n, CPU_STRIDE)
@@ -340,7 +346,7 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"rmat{args.scale}_AxA", "scale": args.scale, "edge_factor": EF,
-                       "abcd": [0.57, 0.19, 0.19, 0.05], "seed": SEED, "grid": args.grid,
+                       "abcd": [0.57, 0.19, 0.19, 0.05], "seed": seed, "grid": args.grid,
                        "products": [f"{k}_{s}" for k in args.products.split(",") if k
                                     for s in args.semirings.split(",") if s],
                        "flops_per_product": flops_of(A), "nnz_A": A.nnz,
@@ -468,17 +474,22 @@ def main():
     from paper_1006_2183_gb300 import spgemm as sp
 
     kinds = [k for k in args.products.split(",") if k]
-    A64 = gen.rmat(args.scale, EF, SEED, gen.PLUS_TIMES_F64)
-    A32 = A64.with_vals(A64.vals.astype(np.float32))
+    seed = SEED_OF_SCALE.get(args.scale, SEED)
+    A64 = gen.rmat(args.scale, EF, seed, gen.PLUS_TIMES_F64)
     flops1 = flops_of(A64)
     ctx = sp.Context()
     dev = ctx.device
-    mats = {sp.PLUS_TIMES_F64: sp.Matrix.from_host(ctx, A64, sp.PLUS_TIMES_F64),
-            sp.MIN_PLUS_F32: sp.Matrix.from_host(ctx, A32, sp.MIN_PLUS_F32)}
+    srs = {"pt64": sp.PLUS_TIMES_F64, "mp32": sp.MIN_PLUS_F32, "bool": sp.OR_AND_BOOL}
+    wanted = [x for x in args.semirings.split(",") if x]
+    # the same pattern in every semiring: FP64 values, their FP32 rounding, boolean ones
+    host = {sp.PLUS_TIMES_F64: A64, sp.MIN_PLUS_F32: A64.with_vals(A64.vals.astype(np.float32)),
+            sp.OR_AND_BOOL: A64.with_vals(np.ones(A64.nnz, dtype=np.uint8))}
+    mats = {srs[nm]: sp.Matrix.from_host(ctx, host[srs[nm]], srs[nm]) for nm in wanted}
+    if sp.PLUS_TIMES_F64 not in mats:
+        mats[sp.PLUS_TIMES_F64] = sp.Matrix.from_host(ctx, A64, sp.PLUS_TIMES_F64)   # imbalance report
     products = []
-    srs = {"pt64": sp.PLUS_TIMES_F64, "mp32": sp.MIN_PLUS_F32}
     for k in kinds:
-        for name in [x for x in args.semirings.split(",") if x]:
+        for name in wanted:
             products.append((k, srs[name]))
 
     lib_opts = sp.default_opts(**{k: float(v) if k == "predictor_margin" else int(v)
@@ -562,10 +573,10 @@ def main():
     # whole-product roofline on compulsory bytes (A read once, C written once)
     pipe = {}
     for (kind, sr) in products:
-        w = 8 if sr == sp.PLUS_TIMES_F64 else 4
+        w = SR_WIDTH[sr]
         byt = (A64.n + 1) * 8 + A64.nnz * (4 + w) + (A64.n + 1) * 8 + nnz_seen[(kind, sr)] * (4 + w)
-        pipe[f"{kind}_{'pt64' if w == 8 else 'mp32'}"] = {"compulsory_bytes": byt, "nnz_C": nnz_seen[(kind, sr)]}
-    phase_tab = {f"{['flat', 'summa', 'g2', 'g3'][g]}:{'pt64' if s == 0 else 'mp32'}:{p}":
+        pipe[f"{kind}_{SR_NAME[sr]}"] = {"compulsory_bytes": byt, "nnz_C": nnz_seen[(kind, sr)]}
+    phase_tab = {f"{['flat', 'summa', 'g2', 'g3'][g]}:{SR_NAME[s]}:{p}":
                  round(v[0] / max(1, args.steps), 4) for (g, s, p), v in phases.items() if v[1]}
     byt_step = sum(v["compulsory_bytes"] for v in pipe.values())
     pipeline_frac = byt_step / (tot_ms / args.steps / 1e3) / 1e9 / hbm
@@ -575,7 +586,8 @@ def main():
     if not args.no_e2e:
         import torch as _t
         pinned = {}
-        for sr, H in ((sp.PLUS_TIMES_F64, A64), (sp.MIN_PLUS_F32, A32)):
+        for sr in {sr for _, sr in products}:
+            H = host[sr]
             pinned[sr] = (_t.from_numpy(H.colptr).pin_memory(), _t.from_numpy(H.rowidx).pin_memory(),
                           _t.from_numpy(np.ascontiguousarray(H.vals)).pin_memory())
         h2d = sum(sum(t.numel() * t.element_size() for t in pinned[sr]) for _, sr in products)
@@ -583,7 +595,7 @@ def main():
         d2h = 0
         for (kind, sr) in products:
             nz = nnz_seen[(kind, sr)]
-            w = 8 if sr == sp.PLUS_TIMES_F64 else 4
+            w = SR_WIDTH[sr]
             outbuf[(kind, sr)] = (_t.empty(A64.n + 1, dtype=_t.int64).pin_memory(),
                                   _t.empty(nz, dtype=_t.int32).pin_memory(),
                                   _t.empty(nz, dtype=sp.TORCH_DTYPE[sr]).pin_memory())
@@ -633,8 +645,8 @@ def main():
                 "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": f"rmat{args.scale}_AxA", "scale": args.scale, "edge_factor": EF,
-                           "abcd": [0.57, 0.19, 0.19, 0.05], "seed": SEED, "grid": args.grid,
-                           "products": [f"{k}_{'pt64' if s == 0 else 'mp32'}" for k, s in products],
+                           "abcd": [0.57, 0.19, 0.19, 0.05], "seed": seed, "grid": args.grid,
+                           "products": [f"{k}_{SR_NAME[s]}" for k, s in products],
                            "flops_per_product": flops1, "nnz_A": A64.nnz, "l2": "flushed between steps (512 MiB write)",
                            "pipeline_hbm_frac": pipeline_frac, "pipeline": pipe, "phase_ms_per_step": phase_tab,
                            "lib_opts": {k: v for k, v in (o.split("=", 1) for o in args.opt)}},

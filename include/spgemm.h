@@ -103,7 +103,13 @@ typedef struct {
                                  tiers (default), 1 = expand-sort-compress, the
                                  data-parallel form of the outer-product multiply of
                                  Section 2.4 (needs < 2^32 products per merge group) */
-    int reserved[6];
+    int range_slab_rows;      /* long columns: most rows of one symbolic row slab (its
+                                 row bitmap lives in shared memory), rounded to a
+                                 multiple of 32 and clamped to [4096, 2^20]; raised
+                                 where a column would need more than 16 slabs.
+                                 0 = default (2^19).  A long column of more than
+                                 16 * (2^20 - 32) rows is SPGEMM_ERR_UNSUPPORTED.   */
+    int reserved[5];
 } spgemm_opts_t;
 
 void spgemm_opts_default(spgemm_opts_t* opts);

@@ -113,6 +113,7 @@ void spgemm_opts_default(spgemm_opts_t* o) {
     o->warp_max_flops = 512;
     o->block_max_flops = 4096;
     o->dense_part_flops = 65536;
+    o->range_slab_rows = 0;
     o->predictor_margin = 0.25f;
 }
 
@@ -295,7 +296,15 @@ spgemm_status_t engine_setup(Engine* E, spgemm_ctx* ctx, spgemm_semiring_t sr, c
     E->cfg.block_max = std::max(E->cfg.warp_max, std::min(opts.block_max_flops, 4096));
     int64_t mmax = 32;
     for (auto& pr : prods) mmax = std::max<int64_t>(mmax, pr.A.m);
-    E->cfg.dense_rows = (int)std::min<int64_t>((mmax + 31) / 32 * 32, 1 << 20);
+    {
+        // symbolic slabs: at most MAX_PARTS per column, each within the shared-memory bitmap
+        const int64_t cap = opts.range_slab_rows > 0
+                                ? std::min<int64_t>(std::max<int64_t>((opts.range_slab_rows + 31) / 32 * 32, 4096), 1 << 20)
+                                : DEFAULT_SLAB_ROWS;
+        const int64_t need = (ceil_div64(mmax, MAX_PARTS) + 32 + 31) / 32 * 32;
+        E->cfg.dense_rows = (int)std::min<int64_t>({(mmax + 31) / 32 * 32, std::max(cap, need), int64_t(1) << 20});
+        E->slab_rows_short = mmax > (int64_t)MAX_PARTS * (E->cfg.dense_rows - 32);
+    }
     E->cfg.part_flops = std::max(1024, opts.dense_part_flops);
     cudaStream_t st = ctx->stream;
     {
@@ -409,6 +418,10 @@ spgemm_status_t engine_setup(Engine* E, spgemm_ctx* ctx, spgemm_semiring_t sr, c
     launch_bin_scatter(st, E->it, E->bin, E->item_prod, E->bin_off_dev, E->ctr + NBIN, E->list);
     const int64_t nd = E->bin_cnt[BIN_DENSE];
     E->dw = DenseWork();
+    if (nd > 0 && E->slab_rows_short)
+        return set_err(ctx, SPGEMM_ERR_UNSUPPORTED,
+                       "long columns of more than %d * (2^20 - 32) rows need more than %d row slabs", MAX_PARTS,
+                       MAX_PARTS);
     if (nd > 0) {
         // slabs of the long columns, then the range buffers sized from their count
         off = 0;

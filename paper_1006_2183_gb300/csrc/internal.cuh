@@ -99,6 +99,7 @@ struct Engine {
     int64_t nbin_cnt[sg::NBIN] = {0};
     int64_t nbin_off[sg::NBIN] = {0};
     bool numeric_bins = false;
+    bool slab_rows_short = false;        // a column of the largest m would need > MAX_PARTS slabs
     int64_t flops_total = 0;
     int64_t nnz_total = -1;
     bool symbolic_done = false;

@@ -30,6 +30,9 @@ constexpr int TINY_MAX = 16;
 constexpr int WARP_TBL0 = 64;
 constexpr int BLK_TBL0 = 2048;
 constexpr int MAX_PARTS = 16;
+// default most rows of one symbolic slab: a 64 KB row bitmap keeps two symbolic CTAs
+// per SM (a 2^20-row slab holds one)
+constexpr int DEFAULT_SLAB_ROWS = 1 << 19;
 
 struct TierCfg {
     int warp_max;     // cap <= warp_max -> warp tables (<= 512)

@@ -54,7 +54,8 @@ class Opts(ctypes.Structure):
                 ("summa_merge_every", ctypes.c_int), ("warp_max_flops", ctypes.c_int),
                 ("block_max_flops", ctypes.c_int), ("dense_part_flops", ctypes.c_int),
                 ("predictor_margin", ctypes.c_float), ("range_table_slots", ctypes.c_int),
-                ("block_kernel", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+                ("block_kernel", ctypes.c_int), ("range_slab_rows", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
 
 
 def _sig(name, args, res=ctypes.c_int):

@@ -64,6 +64,43 @@ def test_tier_choice_does_not_change_result(ctx, sr):
         assert_matches(C, ref, sr, what=str(kw))
 
 
+@pytest.mark.parametrize("sr", [PT_F64, MP_F32])
+def test_slab_rows_do_not_change_result(ctx, sr):
+    """Long columns cut into row slabs of 4096 .. 16384 rows (up to the 16-slab limit,
+    which raises the slab size for 2^14 rows / 4096) give the same result."""
+    A = gen.rmat(14, 8, 0x1402, sr)
+    s = sp()
+    ref = oracle.spgemm(A, A, sr)
+    for rows in (4096, 8192, 1000, 16384, 0):
+        C = gpu_product(ctx, A, A, sr, s.default_opts(range_slab_rows=rows, dense_part_flops=1024))
+        assert_matches(C, ref, sr, what=f"slab rows {rows}")
+
+
+def test_long_column_over_slab_limit_is_unsupported(ctx):
+    """A long column of more than 16 * (2^20 - 32) rows is refused, not cut into slabs
+    wider than the shared-memory bitmap; short columns of such a matrix still work."""
+    s = sp()
+    m = 17 * (1 << 20)
+    rng = np.random.default_rng(17)
+    k = 64
+    rows = rng.choice(m, (k, 100), replace=True)
+    cp = np.zeros(k + 1, np.int64)
+    ir = []
+    for c in range(k):
+        u = np.unique(rows[c]).astype(np.int32)
+        ir.append(u)
+        cp[c + 1] = cp[c] + len(u)
+    A = CSC(m, k, cp, np.concatenate(ir), np.ones(int(cp[-1])))
+    dA = s.Matrix.from_host(ctx, A, PT_F64)
+    long_b = CSC(k, 1, np.array([0, k], np.int64), np.arange(k, dtype=np.int32), np.ones(k))   # ~6400 flops
+    with pytest.raises(s.SpGEMMError) as ei:
+        s.spgemm_multiply(ctx, dA, s.Matrix.from_host(ctx, long_b, PT_F64), PT_F64)
+    assert ei.value.status == 8, ei.value   # SPGEMM_ERR_UNSUPPORTED
+    short_b = CSC(k, 2, np.array([0, 2, 3], np.int64), np.array([1, 5, 9], np.int32), np.ones(3))
+    C = s.spgemm_multiply(ctx, dA, s.Matrix.from_host(ctx, short_b, PT_F64), PT_F64).to_host()
+    assert_matches(C, oracle.spgemm(A, short_b, PT_F64), PT_F64, what="short columns of a tall A")
+
+
 def test_dense_rows_multiple_chunks_and_ragged_tail(ctx):
     # m not a multiple of the dense chunk (8192 rows for FP64): several chunks and a short tail
     m = 3 * 8192 + 77
