@@ -326,8 +326,10 @@ __device__ __forceinline__ int rank_emit(uint32_t* bitmap, int nw, int32_t* keys
     return total;
 }
 
+// small CTA-group tables (one table per 2 or 4 warps) are latency-bound: their
+// registers are capped so that 48 warps fit an SM
 template <class SR, int GS, int TBL, bool NUM, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_hash(Items it, const int2* __restrict__ list, int64_t count,
+__global__ void __launch_bounds__(BLOCK, (GS == BLOCK && BLOCK <= 128) ? 1536 / BLOCK : 1) k_hash(Items it, const int2* __restrict__ list, int64_t count,
                                                 int64_t* __restrict__ nnz_item, const int64_t* __restrict__ Coff,
                                                 int32_t* __restrict__ Cir, typename SR::T* __restrict__ Cv,
                                                 int bm_words) {
@@ -545,7 +547,8 @@ static void run_hash(cudaStream_t st, const Items& it, const int2* list, int64_t
     using L = HashLayout<SR, GS, TBL, NUM>;
     constexpr int NG = BLOCK / GS;
     constexpr bool CAN_BM = NUM && (GS == BLOCK || (GS == 32 && TBL >= BM_WARP_MIN_TBL));
-    constexpr int64_t bm_rows = GS == 32 ? BM_WARP_MAX_ROWS : BM_MAX_ROWS;
+    // small groups keep the bitmap to the rows a warp would (its scan is per column)
+    constexpr int64_t bm_rows = GS < 256 ? BM_WARP_MAX_ROWS : BM_MAX_ROWS;
     const int bm_words = CAN_BM && it.max_m > 0 && it.max_m <= bm_rows ? (int)((it.max_m + 31) / 32) : 0;
     size_t smem = L::group * NG + (size_t)bm_words * 4 * NG;
     auto kern = k_hash<SR, GS, TBL, NUM, BLOCK>;
@@ -641,8 +644,15 @@ static void run_hash_bins(cudaStream_t st, const Items& it, const int2* list, co
     run_hash<SR, 32, 64, NUM, WARP_BLOCK>(st, it, list + off[W0], cnt[W0], nnz_item, Coff, Cir, Cv);
     run_hash<SR, 32, 128, NUM, WARP_BLOCK>(st, it, list + off[W0 + 1], cnt[W0 + 1], nnz_item, Coff, Cir, Cv);
     run_hash<SR, 32, 256, NUM, WARP_BLOCK>(st, it, list + off[W0 + 2], cnt[W0 + 2], nnz_item, Coff, Cir, Cv);
-    run_hash<SR, 32, 512, NUM, WARP_BLOCK>(st, it, list + off[W0 + 3], cnt[W0 + 3], nnz_item, Coff, Cir, Cv);
-    run_hash<SR, 32, 1024, NUM, 128>(st, it, list + off[W0 + 4], cnt[W0 + 4], nnz_item, Coff, Cir, Cv);
+    if constexpr (NUM) {
+        // numeric tables of 512 and 1024 slots: one table per 2 or 4 warps, so that
+        // shared memory admits more warps per SM (a warp each left a quarter of them)
+        run_hash<SR, 64, 512, NUM, 64>(st, it, list + off[W0 + 3], cnt[W0 + 3], nnz_item, Coff, Cir, Cv);
+        run_hash<SR, 128, 1024, NUM, 128>(st, it, list + off[W0 + 4], cnt[W0 + 4], nnz_item, Coff, Cir, Cv);
+    } else {
+        run_hash<SR, 32, 512, NUM, WARP_BLOCK>(st, it, list + off[W0 + 3], cnt[W0 + 3], nnz_item, Coff, Cir, Cv);
+        run_hash<SR, 32, 1024, NUM, 128>(st, it, list + off[W0 + 4], cnt[W0 + 4], nnz_item, Coff, Cir, Cv);
+    }
     run_hash<SR, 256, 2048, NUM, 256>(st, it, list + off[B0], cnt[B0], nnz_item, Coff, Cir, Cv);
     // 4096-slot tables: 256 threads per column when the row bitmap is small (more columns
     // in flight per SM), 512 when a large bitmap already limits the CTAs per SM
