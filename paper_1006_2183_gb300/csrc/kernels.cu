@@ -326,10 +326,15 @@ __device__ __forceinline__ int rank_emit(uint32_t* bitmap, int nw, int32_t* keys
     return total;
 }
 
-// small CTA-group tables (one table per 2 or 4 warps) are latency-bound: their
-// registers are capped so that 48 warps fit an SM
+// The hash tables are latency-bound: registers are capped so that they never admit
+// fewer CTAs per SM than shared memory does (48 warps for warp tables, tables of 2
+// or 4 warps and 2048-slot CTA tables; 4 CTAs of 4096 slots; 2 CTAs of 512 threads).
+constexpr int hash_min_blocks(int block, int tbl) {
+    return block <= 128 ? 1536 / block : block == 256 ? (tbl <= 2048 ? 6 : 4) : 2;
+}
+
 template <class SR, int GS, int TBL, bool NUM, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, (GS == BLOCK && BLOCK <= 128) ? 1536 / BLOCK : 1) k_hash(Items it, const int2* __restrict__ list, int64_t count,
+__global__ void __launch_bounds__(BLOCK, hash_min_blocks(BLOCK, TBL)) k_hash(Items it, const int2* __restrict__ list, int64_t count,
                                                 int64_t* __restrict__ nnz_item, const int64_t* __restrict__ Coff,
                                                 int32_t* __restrict__ Cir, typename SR::T* __restrict__ Cv,
                                                 int bm_words) {
