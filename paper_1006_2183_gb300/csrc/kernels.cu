@@ -77,8 +77,10 @@ __device__ __forceinline__ int find_prod(const int64_t* __restrict__ base, int64
 __device__ __forceinline__ int64_t out_col(const DMat& B, int64_t p) { return B.jc ? __ldg(B.jc + p) : p; }
 
 // ------------------------------------------------------------------ analysis
-// Groups of 8 lanes per item: flops = sum_k nnz(A(:,k)) (Section 1's flops),
-// the tier bin, the product id, and optionally the predictor inputs.
+// Groups of LPI lanes per item (8, or 1 where B columns are short, as in the
+// block products): flops = sum_k nnz(A(:,k)) (Section 1's flops), the tier bin,
+// the product id, and optionally the predictor inputs.
+template <int LPI>
 __global__ void __launch_bounds__(256) k_analyze(Items it, TierCfg cfg, int64_t* __restrict__ flops,
                                                  uint8_t* __restrict__ bin, int32_t* __restrict__ item_prod,
                                                  unsigned long long* bin_count, unsigned long long* flops_total,
@@ -90,8 +92,8 @@ __global__ void __launch_bounds__(256) k_analyze(Items it, TierCfg cfg, int64_t*
     if (threadIdx.x < NBIN) s_cnt[threadIdx.x] = 0;
     if (threadIdx.x == 0) s_fl = 0;
     __syncthreads();
-    const int sub = threadIdx.x & 7;
-    const int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+    const int sub = threadIdx.x & (LPI - 1);
+    const int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / LPI;
     long long f = 0, mx = 0;
     unsigned long long sk = 0;
     int64_t bs = 0, be = 0, am = 0;
@@ -105,7 +107,7 @@ __global__ void __launch_bounds__(256) k_analyze(Items it, TierCfg cfg, int64_t*
         am = pr->A.m;
         const uint64_t* skp = sketch ? sketch + sketch_base[prod] : nullptr;
         const int64_t b0 = it.acs ? pr->bnz_base - __ldg(pr->B.cp) : 0;
-        for (int64_t t = bs + sub; t < be; t += 8) {
+        for (int64_t t = bs + sub; t < be; t += LPI) {
             int32_t k = __ldg(pr->B.ir + t);
             int64_t cs, ce;
             col_range(pr->A, k, cs, ce);
@@ -120,11 +122,11 @@ __global__ void __launch_bounds__(256) k_analyze(Items it, TierCfg cfg, int64_t*
         }
     }
 #pragma unroll
-    for (int o = 4; o > 0; o >>= 1) {
-        f += __shfl_xor_sync(0xffffffffu, f, o, 8);
-        long long om = __shfl_xor_sync(0xffffffffu, mx, o, 8);
+    for (int o = LPI / 2; o > 0; o >>= 1) {
+        f += __shfl_xor_sync(0xffffffffu, f, o, LPI);
+        long long om = __shfl_xor_sync(0xffffffffu, mx, o, LPI);
         mx = om > mx ? om : mx;
-        sk |= __shfl_xor_sync(0xffffffffu, sk, o, 8);
+        sk |= __shfl_xor_sync(0xffffffffu, sk, o, LPI);
     }
     if (u < it.nitems && sub == 0) {
         flops[u] = f;
@@ -161,9 +163,15 @@ void launch_analyze(cudaStream_t st, const Items& it, TierCfg cfg, int64_t* flop
                     unsigned long long* bin_count, unsigned long long* flops_total, const uint64_t* sketch,
                     const int64_t* sketch_base, float* feat, int64_t* maxlen) {
     if (it.nitems == 0) return;
-    int grid = (int)ceil_div64(it.nitems * 8, 256);
-    k_analyze<<<grid, 256, 0, st>>>(it, cfg, flops, bin, item_prod, bin_count, flops_total, sketch, sketch_base,
-                                    feat, maxlen);
+    if (it.total_bnz < 4 * it.nitems) {   // about one B entry per item: one lane each
+        int grid = (int)ceil_div64(it.nitems, 256);
+        k_analyze<1><<<grid, 256, 0, st>>>(it, cfg, flops, bin, item_prod, bin_count, flops_total, sketch,
+                                           sketch_base, feat, maxlen);
+    } else {
+        int grid = (int)ceil_div64(it.nitems * 8, 256);
+        k_analyze<8><<<grid, 256, 0, st>>>(it, cfg, flops, bin, item_prod, bin_count, flops_total, sketch,
+                                           sketch_base, feat, maxlen);
+    }
     note_launch();
 }
 
@@ -879,7 +887,8 @@ __device__ __forceinline__ void rt_expand(const RangeSmem* sc, int ns, int T, F&
 }
 
 // Symbolic range kernel: slab bitmap, count, cut into ranges.
-__global__ void __launch_bounds__(RT_BLOCK) k_range_sym(Items it, DenseWork dw) {
+// registers capped for 3 CTAs per SM (shared memory admits up to 4 with slabs of 2^18 rows)
+__global__ void __launch_bounds__(RT_BLOCK, 3) k_range_sym(Items it, DenseWork dw) {
     extern __shared__ __align__(16) unsigned char smem[];
     RangeSmem* sc = reinterpret_cast<RangeSmem*>(smem);
     int* s_bw = reinterpret_cast<int*>(smem + sizeof(RangeSmem));          // boundary words
