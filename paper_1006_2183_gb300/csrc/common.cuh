@@ -124,7 +124,7 @@ __device__ __forceinline__ void col_range(const DMat& A, int32_t k, int64_t& s, 
         e = A.ce ? __ldg(A.ce + k) : __ldg(A.cp + k + 1);
         return;
     }
-    int64_t t = k / A.chunk;
+    const int64_t t = (uint32_t)k / (uint32_t)A.chunk;   // 0 <= k < n < 2^31 and 1 <= chunk <= n
     int32_t p0 = __ldg(A.aux + t), p1 = __ldg(A.aux + t + 1);
     for (int32_t p = p0; p < p1; ++p) {
         int32_t c = __ldg(A.jc + p);

@@ -32,14 +32,20 @@ using namespace sg;
 
 namespace {
 
-__global__ void k_block_keys(const int64_t* __restrict__ cp, const int32_t* __restrict__ ir, int64_t n, int64_t mb,
-                             int64_t nb, int g, uint32_t* __restrict__ keys, uint32_t* __restrict__ pay) {
+// Block key of every entry (32-bit divisions: rows, columns and block sizes are
+// below 2^31); a row outside [0, m) sets *bad and gets the key of block (0, J).
+__global__ void k_block_keys(const int64_t* __restrict__ cp, const int32_t* __restrict__ ir, int64_t n, int64_t m,
+                             int64_t mb, int64_t nb, int g, uint32_t* __restrict__ keys, uint32_t* __restrict__ pay,
+                             unsigned long long* __restrict__ bad) {
     const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
     const int sub = threadIdx.x & 7;
     if (j >= n) return;
-    const uint32_t J = (uint32_t)(j / nb);
+    const uint32_t J = (uint32_t)j / (uint32_t)nb;
     for (int64_t t = cp[j] + sub; t < cp[j + 1]; t += 8) {
-        const uint32_t I = (uint32_t)(ir[t] / mb);
+        const int32_t r = ir[t];
+        uint32_t I = 0;
+        if (r < 0 || (int64_t)r >= m) atomicAdd(bad, 1ull);
+        else I = (uint32_t)r / (uint32_t)mb;
         keys[t] = J * (uint32_t)g + I;   // block (I, J), column-block major
         pay[t] = (uint32_t)t;
     }
@@ -57,8 +63,7 @@ template <int W>
 __global__ void k_block_gather(const uint32_t* __restrict__ skey, const uint32_t* __restrict__ perm, int64_t nnz,
                                const int32_t* __restrict__ ir, const int32_t* __restrict__ colid,
                                const void* __restrict__ num, int64_t mb, int64_t nb, int g, int32_t* __restrict__ lir,
-                               int32_t* __restrict__ lcol, void* __restrict__ lnum, int64_t* __restrict__ flag,
-                               unsigned long long* __restrict__ bnnz, unsigned long long* __restrict__ bnzc) {
+                               int32_t* __restrict__ lcol, void* __restrict__ lnum, int64_t* __restrict__ flag) {
     using Wt = typename std::conditional<W == 1, uint8_t, typename std::conditional<W == 4, uint32_t, uint64_t>::type>::type;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nnz; t += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t key = skey[t];
@@ -69,11 +74,29 @@ __global__ void k_block_gather(const uint32_t* __restrict__ skey, const uint32_t
         const int32_t lc = (int32_t)(c - J * nb);
         lcol[t] = lc;
         if (num) reinterpret_cast<Wt*>(lnum)[t] = reinterpret_cast<const Wt*>(num)[src];
-        int f = t == 0 || skey[t - 1] != key || colid[perm[t - 1]] != c;
-        flag[t] = f;
-        atomicAdd(bnnz + key, 1ull);
-        if (f) atomicAdd(bnzc + key, 1ull);
+        flag[t] = t == 0 || skey[t - 1] != key || colid[perm[t - 1]] != c;
     }
+}
+
+// Entries and nonzero columns per block from the sorted keys: block b holds the
+// keys in [lower_bound(b), lower_bound(b + 1)), its column starts are the flags
+// there (pos = exclusive scan of the flags, nnz + 1 entries).
+__global__ void k_block_counts(const uint32_t* __restrict__ skey, int64_t nnz, const int64_t* __restrict__ pos,
+                               int nblk, unsigned long long* __restrict__ bnnz, unsigned long long* __restrict__ bnzc) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nblk) return;
+    auto lb = [&](uint32_t key) {
+        int64_t lo = 0, hi = nnz;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (skey[mid] < key) lo = mid + 1;
+            else hi = mid;
+        }
+        return lo;
+    };
+    const int64_t lo = lb((uint32_t)b), hi = lb((uint32_t)b + 1);
+    bnnz[b] = (unsigned long long)(hi - lo);
+    bnzc[b] = (unsigned long long)(pos[hi] - pos[lo]);
 }
 
 __global__ void k_block_dcsc(const uint32_t* __restrict__ skey, const int32_t* __restrict__ lcol,
@@ -206,7 +229,7 @@ spgemm_status_t partition(spgemm_ctx* ctx, const DMat& M, size_t w, int g, Block
     };
     size_t o_k0 = take(4 * nz1), o_v0 = take(4 * nz1), o_k1 = take(4 * nz1), o_v1 = take(4 * nz1);
     size_t o_col = take(4 * nz1), o_lcol = take(4 * nz1), o_flag = take(8 * nz1), o_pos = take(8 * (nz1 + 1));
-    size_t o_cnt = take(8 * 2 * nblk), o_boff = take(8 * (nblk + 1)), o_jcb = take(8 * (nblk + 1));
+    size_t o_cnt = take(8 * (2 * nblk + 1)), o_boff = take(8 * (nblk + 1)), o_jcb = take(8 * (nblk + 1));
     size_t o_rs = take(radix_tmp_bytes(nz1)), o_sc = take(scan_tmp_bytes(std::max<int64_t>(nz1, nblk)));
     auto tmp = ctx_buf(ctx, off);
     if (!tmp) return set_err(ctx, SPGEMM_ERR_OOM, "partition temporaries");
@@ -217,13 +240,14 @@ spgemm_status_t partition(spgemm_ctx* ctx, const DMat& M, size_t w, int g, Block
     int32_t* lcol = (int32_t*)(t + o_lcol);
     int64_t* flag = (int64_t*)(t + o_flag);
     int64_t* pos = (int64_t*)(t + o_pos);
-    unsigned long long* bcnt = (unsigned long long*)(t + o_cnt);   // bnnz[nblk], bnzc[nblk]
+    unsigned long long* bcnt = (unsigned long long*)(t + o_cnt);   // bnnz[nblk], bnzc[nblk], bad rows
     int64_t* boff = (int64_t*)(t + o_boff);
     int64_t* jcbase = (int64_t*)(t + o_jcb);
-    SG_CUDA(ctx, cudaMemsetAsync(bcnt, 0, 16 * nblk, st));
+    SG_CUDA(ctx, cudaMemsetAsync(bcnt, 0, 16 * nblk + 8, st));
     std::vector<int64_t> hnnz(nblk, 0), hnzc(nblk, 0);
     if (nnz > 0) {
-        k_block_keys<<<(int)ceil_div64(n * 8, 256) + 1, 256, 0, st>>>(M.cp, M.ir, n, mb, nb, g, k0, v0);
+        k_block_keys<<<(int)ceil_div64(n * 8, 256) + 1, 256, 0, st>>>(M.cp, M.ir, n, m, mb, nb, g, k0, v0,
+                                                                        bcnt + 2 * nblk);
         k_block_colid<<<(int)ceil_div64(n * 8, 256) + 1, 256, 0, st>>>(M.cp, n, colid);
         note_launch(2);
         int bits = 0;
@@ -233,17 +257,21 @@ spgemm_status_t partition(spgemm_ctx* ctx, const DMat& M, size_t w, int g, Block
         uint32_t* sk = second ? k1 : k0;
         uint32_t* sp = second ? v1 : v0;
         switch (w) {
-        case 1: k_block_gather<1><<<gridn(nnz), 256, 0, st>>>(sk, sp, nnz, M.ir, colid, M.num, mb, nb, g, (int32_t*)irb->p, lcol, vb->p, flag, bcnt, bcnt + nblk); break;
-        case 4: k_block_gather<4><<<gridn(nnz), 256, 0, st>>>(sk, sp, nnz, M.ir, colid, M.num, mb, nb, g, (int32_t*)irb->p, lcol, vb->p, flag, bcnt, bcnt + nblk); break;
-        default: k_block_gather<8><<<gridn(nnz), 256, 0, st>>>(sk, sp, nnz, M.ir, colid, M.num, mb, nb, g, (int32_t*)irb->p, lcol, vb->p, flag, bcnt, bcnt + nblk); break;
+        case 1: k_block_gather<1><<<gridn(nnz), 256, 0, st>>>(sk, sp, nnz, M.ir, colid, M.num, mb, nb, g, (int32_t*)irb->p, lcol, vb->p, flag); break;
+        case 4: k_block_gather<4><<<gridn(nnz), 256, 0, st>>>(sk, sp, nnz, M.ir, colid, M.num, mb, nb, g, (int32_t*)irb->p, lcol, vb->p, flag); break;
+        default: k_block_gather<8><<<gridn(nnz), 256, 0, st>>>(sk, sp, nnz, M.ir, colid, M.num, mb, nb, g, (int32_t*)irb->p, lcol, vb->p, flag); break;
         }
         note_launch();
         launch_exclusive_scan(st, flag, nnz, pos, t + o_sc);
         k_block_dcsc<<<gridn(nnz), 256, 0, st>>>(sk, lcol, flag, pos, nnz, (int32_t*)jcb->p, (int64_t*)cpb->p);
-        note_launch();
-        std::vector<unsigned long long> hc(2 * nblk);
-        SG_CUDA(ctx, cudaMemcpyAsync(hc.data(), bcnt, 16 * nblk, cudaMemcpyDeviceToHost, st));
+        k_block_counts<<<(int)ceil_div64(nblk, 256), 256, 0, st>>>(sk, nnz, pos, nblk, bcnt, bcnt + nblk);
+        note_launch(2);
+        std::vector<unsigned long long> hc(2 * nblk + 1);
+        SG_CUDA(ctx, cudaMemcpyAsync(hc.data(), bcnt, 16 * nblk + 8, cudaMemcpyDeviceToHost, st));
         SG_TRY(sync_ctx(ctx));
+        if (hc[2 * nblk])
+            return set_err(ctx, SPGEMM_ERR_BAD_FORMAT, "partition: %llu row indices outside [0, %lld)",
+                           (unsigned long long)hc[2 * nblk], (long long)m);
         for (int b = 0; b < nblk; ++b) {
             hnnz[b] = (int64_t)hc[b];
             hnzc[b] = (int64_t)hc[nblk + b];

@@ -76,6 +76,31 @@ def test_slab_rows_do_not_change_result(ctx, sr):
         assert_matches(C, ref, sr, what=f"slab rows {rows}")
 
 
+@pytest.mark.parametrize("sr", [PT_F64, OR_BOOL])
+def test_tall_long_columns_cut_into_slabs(ctx, sr):
+    """3,000,017 rows: long columns need at least 6 row slabs of 2^19 rows (ragged last
+    slab); columns of 1, 2 and 64 B entries cover the hash and range tiers."""
+    s = sp()
+    m, k = 3_000_017, 64
+    rng = np.random.default_rng(3)
+    cp = np.zeros(k + 1, np.int64)
+    ir = []
+    for c in range(k):
+        u = np.unique(rng.integers(0, m, 150 if c % 2 else 90)).astype(np.int32)
+        if c == 5:
+            u = np.unique(np.concatenate([u, np.array([0, m - 1], np.int32)]))   # first and last row
+        ir.append(u)
+        cp[c + 1] = cp[c] + len(u)
+    irs = np.concatenate(ir)
+    vals = rng.random(len(irs)) if sr == PT_F64 else np.ones(len(irs), np.uint8)
+    A = CSC(m, k, cp, irs, vals)
+    B = CSC(k, 4, np.array([0, 1, 3, 67, 131], np.int64),
+            np.concatenate([[5], [2, 9], np.arange(64), np.arange(64)]).astype(np.int32),
+            rng.random(131) if sr == PT_F64 else np.ones(131, np.uint8))
+    C = s.spgemm_multiply(ctx, s.Matrix.from_host(ctx, A, sr), s.Matrix.from_host(ctx, B, sr), sr).to_host()
+    assert_matches(C, oracle.spgemm(A, B, sr), sr, what="tall slabs")
+
+
 def test_long_column_over_slab_limit_is_unsupported(ctx):
     """A long column of more than 16 * (2^20 - 32) rows is refused, not cut into slabs
     wider than the shared-memory bitmap; short columns of such a matrix still work."""

@@ -104,6 +104,15 @@ def test_summa_empty_and_errors(ctx):
     dB = s.Matrix.from_host(ctx, B, PT_F64)
     with pytest.raises(s.SpGEMMError):
         s.spgemm_summa_blocked(ctx, dA, dB, 0, PT_F64)
+    # a row index past m: the block split reports it instead of writing past its blocks
+    bad = B.rowidx.copy()
+    bad[len(bad) // 2] = B.m + 5
+    dbad = s.Matrix.from_host(ctx, CSC(B.m, B.n, B.colptr, bad, B.vals), PT_F64)
+    with pytest.raises(s.SpGEMMError) as ei:
+        s.spgemm_summa_blocked(ctx, dbad, dB, 4, PT_F64)
+    assert ei.value.status == 3   # SPGEMM_ERR_BAD_FORMAT
+    C = blocked(ctx, B, B, PT_F64, 4)   # the context still works
+    assert_matches(C, oracle.spgemm(B, B, PT_F64), PT_F64, what="after bad format")
 
 
 def test_summa_scale18_sampled(ctx):
