@@ -572,6 +572,99 @@ static void run_hash(cudaStream_t st, const Items& it, const int2* list, int64_t
     note_launch();
 }
 
+// Symbolic count of columns whose rows fit a per-group bitmap (every A_i has at
+// most BM_WARP_MAX_ROWS rows, as the SUMMA merge columns): each product sets its
+// row's bit and nnz is the popcount; no keys, no probing, no table to clear.
+template <int GS, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 2048 / BLOCK) k_bitcount(Items it, const int2* __restrict__ list,
+                                                                  int64_t count, int64_t* __restrict__ nnz_item,
+                                                                  int bm_words) {
+    using G = Group<GS>;
+    constexpr int NG = BLOCK / GS;
+    constexpr size_t GROUP = ((size_t)GS * 12 + 34 * 4 + 15) / 16 * 16;   // incl, a0, scan
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = G::lane(), g = G::gid();
+    unsigned char* base = smem + (size_t)g * GROUP;
+    int64_t* s_a0 = reinterpret_cast<int64_t*>(base);
+    int* s_incl = reinterpret_cast<int*>(base + (size_t)GS * 8);
+    int* s_scan = s_incl + GS;
+    uint32_t* bitmap = reinterpret_cast<uint32_t*>(smem + (size_t)NG * GROUP) + (size_t)g * bm_words;
+    for (int x = lane; x < bm_words; x += GS) bitmap[x] = 0u;
+    G::sync();
+    for (int64_t w = (int64_t)blockIdx.x * NG + g; w < count; w += (int64_t)gridDim.x * NG) {
+        const int2 e = __ldg(list + w);
+        const Prod* pr = it.prods + e.x;
+        const int64_t u = __ldg(it.item_base + e.x) + e.y;
+        const int64_t bs = __ldg(pr->B.cp + e.y), be = __ldg(pr->B.cp + e.y + 1);
+        const int64_t mw = (pr->A.m + 31) >> 5;
+        const int nwc = mw < bm_words ? (int)mw : bm_words;
+        const uint32_t mrows = (uint32_t)(pr->A.m < (int64_t)bm_words * 32 ? pr->A.m : (int64_t)bm_words * 32);
+        const int32_t* __restrict__ air = pr->A.ir;
+        for (int64_t b0 = bs; b0 < be; b0 += GS) {
+            const int64_t t = b0 + lane;
+            int len = 0;
+            int64_t a0 = 0;
+            if (t < be) {
+                int64_t s, en;
+                a_col(it, pr, t, __ldg(pr->B.ir + t), s, en);
+                a0 = s;
+                len = (int)(en - s);
+            }
+            int total;
+            const int incl = group_incl_scan_open<GS>(len, s_scan, total);
+            s_incl[lane] = incl;
+            s_a0[lane] = a0;
+            G::sync();
+            constexpr int U = 4;
+            for (int q0 = 0; q0 < total; q0 += GS * U) {
+                int32_t row[U];
+#pragma unroll
+                for (int i = 0; i < U; ++i) {
+                    const int q = q0 + i * GS + lane;
+                    row[i] = -1;
+                    if (q < total) {
+                        int lo = 0, hi = GS - 1;
+                        while (lo < hi) {
+                            const int mid = (lo + hi) >> 1;
+                            if (s_incl[mid] > q) hi = mid;
+                            else lo = mid + 1;
+                        }
+                        row[i] = __ldg(air + s_a0[lo] + (q - (lo ? s_incl[lo - 1] : 0)));
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < U; ++i)
+                    if ((uint32_t)row[i] < mrows) atomicOr(&bitmap[row[i] >> 5], 1u << (row[i] & 31));
+            }
+            if constexpr (GS == 32) __syncwarp();
+        }
+        G::sync();
+        int c = 0;
+        for (int x = lane; x < nwc; x += GS) {
+            c += __popc(bitmap[x]);
+            bitmap[x] = 0u;
+        }
+        int tot;
+        group_incl_scan<GS>(c, s_scan, tot);
+        if (lane == 0) nnz_item[u] = tot;
+        G::sync();
+    }
+}
+
+template <int GS, int BLOCK>
+static void run_bitcount(cudaStream_t st, const Items& it, const int2* list, int64_t count, int64_t* nnz_item) {
+    if (count <= 0) return;
+    constexpr int NG = BLOCK / GS;
+    constexpr size_t GROUP = ((size_t)GS * 12 + 34 * 4 + 15) / 16 * 16;
+    const int bm_words = (int)((it.max_m + 31) / 32);
+    const size_t smem = (GROUP + (size_t)bm_words * 4) * NG;
+    auto kern = k_bitcount<GS, BLOCK>;
+    smem_at_least((const void*)kern, smem);
+    const int grid = (int)std::min<int64_t>(ceil_div64(count, NG), 152 * 32);
+    kern<<<grid, BLOCK, smem, st>>>(it, list, count, nnz_item, bm_words);
+    note_launch();
+}
+
 // Tiny columns (flops <= TINY_MAX): one thread gathers the products in
 // registers, insertion-sorts them by row (stable, so equal rows keep ascending
 // k order), sums duplicates and writes the column.  No table, no barrier.
@@ -656,6 +749,16 @@ static void run_hash_bins(cudaStream_t st, const Items& it, const int2* list, co
     run_tiny<SR, NUM>(st, it, list + off[BIN_TINY], cnt[BIN_TINY], nnz_item, Coff, Cir, Cv);
     run_hash<SR, 32, 64, NUM, WARP_BLOCK>(st, it, list + off[W0], cnt[W0], nnz_item, Coff, Cir, Cv);
     run_hash<SR, 32, 128, NUM, WARP_BLOCK>(st, it, list + off[W0 + 1], cnt[W0 + 1], nnz_item, Coff, Cir, Cv);
+    if constexpr (!NUM) {
+        if (it.max_m > 0 && it.max_m <= BM_WARP_MAX_ROWS) {
+            // rows fit a small bitmap: count the longer columns by bits (64 and 128
+            // slots hold so few rows that clearing a bitmap would cost more)
+            run_bitcount<32, WARP_BLOCK>(st, it, list + off[W0 + 2], cnt[W0 + 2] + cnt[W0 + 3] + cnt[W0 + 4],
+                                         nnz_item);
+            run_bitcount<256, 256>(st, it, list + off[B0], cnt[B0] + cnt[B0 + 1] + cnt[B0 + 2], nnz_item);
+            return;
+        }
+    }
     run_hash<SR, 32, 256, NUM, WARP_BLOCK>(st, it, list + off[W0 + 2], cnt[W0 + 2], nnz_item, Coff, Cir, Cv);
     if constexpr (NUM) {
         // numeric tables of 512 and 1024 slots: one table per 2 or 4 warps, so that
