@@ -299,16 +299,21 @@ __device__ __forceinline__ void bitonic_sort(int32_t* keys, Acc* vals, int P) {
 // and the bitmap.  Called by all GS members; returns the number of entries.  With
 // `pred`, nothing is written when the count exceeds capn.
 template <class SR, int TBL, int GS>
-__device__ __forceinline__ int rank_emit(uint32_t* bitmap, int nw, int32_t* keys, typename SR::Acc* vals, int* gp,
-                                         int* scratch, bool pred, int64_t capn, int64_t out0, int32_t rb,
-                                         int32_t* __restrict__ Cir, typename SR::T* __restrict__ Cv) {
+__device__ __forceinline__ int rank_emit(uint32_t* bitmap, uint16_t* wp, int nw, int32_t* keys,
+                                         typename SR::Acc* vals, int* gp, int* scratch, bool pred, int64_t capn,
+                                         int64_t out0, int32_t rb, int32_t* __restrict__ Cir,
+                                         typename SR::T* __restrict__ Cv) {
     using G = Group<GS>;
     const int lane = G::lane();
-    int lgw = 0;   // words per group: a power of two with GS groups covering nw words
+    int lgw = 0;   // words per member: a power of two with GS members covering nw words
     while ((GS << lgw) < nw) ++lgw;
     const int gw = 1 << lgw;
+    // wp[x]: set bits before word x within its member's words (< 2^16: gw <= 2^11)
     int c = 0;
-    for (int x = lane * gw; x < (lane + 1) * gw && x < nw; ++x) c += __popc(bitmap[x]);
+    for (int x = lane * gw; x < (lane + 1) * gw && x < nw; ++x) {
+        wp[x] = (uint16_t)c;
+        c += __popc(bitmap[x]);
+    }
     int total;
     const int incl = group_incl_scan<GS>(c, scratch, total);
     gp[lane] = incl - c;
@@ -319,9 +324,7 @@ __device__ __forceinline__ int rank_emit(uint32_t* bitmap, int nw, int32_t* keys
         if (kr < 0) continue;
         const int wd = kr >> 5;
         if (wd < nw && write) {   // rows past the bitmap occur only on malformed input
-            const int g = wd >> lgw;
-            int rank = gp[g] + __popc(bitmap[wd] & ((1u << (kr & 31)) - 1u));
-            for (int y = g << lgw; y < wd; ++y) rank += __popc(bitmap[y]);
+            const int rank = gp[wd >> lgw] + wp[wd] + __popc(bitmap[wd] & ((1u << (kr & 31)) - 1u));
             Cir[out0 + rank] = kr + rb;
             Cv[out0 + rank] = SR::out(vals[s]);
         }
@@ -367,6 +370,9 @@ __global__ void __launch_bounds__(BLOCK, hash_min_blocks(BLOCK, TBL)) k_hash(Ite
     // Numeric tables order their output through a row bitmap (one per group) when
     // the rows fit; otherwise they compact and sort.
     uint32_t* bitmap = reinterpret_cast<uint32_t*>(smem + (size_t)NG * L::group) + (size_t)g * bm_words;
+    // per-word prefixes of the bitmap, after the bitmaps of all groups
+    uint16_t* wp = reinterpret_cast<uint16_t*>(smem + (size_t)NG * L::group + (size_t)NG * bm_words * 4) +
+                   (size_t)g * bm_words;
     constexpr bool CAN_BM = NUM && (GS == BLOCK || (GS == 32 && TBL >= BM_WARP_MIN_TBL));
     if constexpr (CAN_BM) {
         for (int x = lane; x < bm_words; x += GS) bitmap[x] = 0u;
@@ -392,6 +398,12 @@ __global__ void __launch_bounds__(BLOCK, hash_min_blocks(BLOCK, TBL)) k_hash(Ite
             G::sync();
         }
         int mycnt = 0;
+        // numeric columns whose rows fit the bitmap mark a row when they claim its slot
+        int mark_nw = 0;
+        if constexpr (CAN_BM) {
+            const int64_t mw = (pr->A.m + 31) >> 5;
+            mark_nw = mw <= bm_words ? (int)mw : 0;
+        }
         for (int64_t b0 = bs; b0 < be; b0 += GS) {
             const int64_t t = b0 + lane;
             int len = 0;
@@ -448,7 +460,12 @@ __global__ void __launch_bounds__(BLOCK, hash_min_blocks(BLOCK, TBL)) k_hash(Ite
                         if (cur == r) break;
                         if (cur == -1) {
                             int32_t prev = atomicCAS(&keys[h], -1, r);
-                            if (prev == -1) { ++mycnt; break; }
+                            if (prev == -1) {
+                                ++mycnt;
+                                if constexpr (CAN_BM)
+                                    if ((r >> 5) < mark_nw) atomicOr(&bitmap[r >> 5], 1u << (r & 31));
+                                break;
+                            }
                             if (prev == r) break;
                         }
                         h = (h + 1) & (TBL - 1);
@@ -476,21 +493,17 @@ __global__ void __launch_bounds__(BLOCK, hash_min_blocks(BLOCK, TBL)) k_hash(Ite
             const int64_t capn = __ldg(Coff + u + 1) - out0;
             const int32_t rb = out_row_base(pr, e.y);
             if constexpr (CAN_BM) {
-                const int nwc = (int)((pr->A.m + 31) >> 5);
                 // a warp prefers the bitmap once sorting the entries would cost more than scanning it
-                bool use_bm = bm_words > 0;
-                if constexpr (GS == 32) use_bm = use_bm && nwc <= 8 * warp_sum(mycnt);
+                bool use_bm = mark_nw > 0;
+                if constexpr (GS == 32) use_bm = use_bm && mark_nw <= 8 * warp_sum(mycnt);
                 if (use_bm) {
-                    for (int s = lane; s < TBL; s += GS) {
-                        const int32_t kr = keys[s];
-                        if (kr >= 0 && (kr >> 5) < nwc) atomicOr(&bitmap[kr >> 5], 1u << (kr & 31));
-                    }
-                    G::sync();
-                    const int total = rank_emit<SR, TBL, GS>(bitmap, nwc, keys, vals, s_incl, s_scan,
+                    const int total = rank_emit<SR, TBL, GS>(bitmap, wp, mark_nw, keys, vals, s_incl, s_scan,
                                                              nnz_item != nullptr, capn, out0, rb, Cir, Cv);
                     if (nnz_item && lane == 0) nnz_item[u] = total;
                     continue;
                 }
+                // sorting instead: drop the marks
+                for (int x = lane; x < mark_nw; x += GS) bitmap[x] = 0u;
             }
             // in-place compaction toward the front: the i-th occupied slot moves to i <= its slot.
             // Each lane holds a contiguous run of S slots in registers; rounds go up the table, and
@@ -563,7 +576,7 @@ static void run_hash(cudaStream_t st, const Items& it, const int2* list, int64_t
     // small groups keep the bitmap to the rows a warp would (its scan is per column)
     constexpr int64_t bm_rows = GS < 256 ? BM_WARP_MAX_ROWS : BM_MAX_ROWS;
     const int bm_words = CAN_BM && it.max_m > 0 && it.max_m <= bm_rows ? (int)((it.max_m + 31) / 32) : 0;
-    size_t smem = L::group * NG + (size_t)bm_words * 4 * NG;
+    size_t smem = L::group * NG + (size_t)bm_words * 6 * NG;   // bitmap words and their 16-bit prefixes
     auto kern = k_hash<SR, GS, TBL, NUM, BLOCK>;
     smem_at_least((const void*)kern, smem);
     int64_t want = ceil_div64(count, NG);

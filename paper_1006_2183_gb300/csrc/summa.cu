@@ -179,10 +179,27 @@ __global__ void k_add_offset(const int64_t* __restrict__ in, int64_t n, int64_t 
         out[i] = in[i] + add;
 }
 
+// Flops per product: the items of a product are contiguous, so each thread sums
+// a run of PF_RUN items and adds once per product it meets.
+constexpr int PF_RUN = 32;
 __global__ void k_prod_flops(Items it, const int32_t* __restrict__ item_prod, const int64_t* __restrict__ flops,
                              unsigned long long* __restrict__ pf) {
-    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < it.nitems; u += (int64_t)gridDim.x * blockDim.x)
-        if (flops[u]) atomicAdd(pf + item_prod[u], (unsigned long long)flops[u]);
+    const int64_t nrun = (it.nitems + PF_RUN - 1) / PF_RUN;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nrun; c += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t u0 = c * PF_RUN, u1 = u0 + PF_RUN < it.nitems ? u0 + PF_RUN : it.nitems;
+        int cur = item_prod[u0];
+        unsigned long long acc = 0;
+        for (int64_t u = u0; u < u1; ++u) {
+            const int p = item_prod[u];
+            if (p != cur) {
+                if (acc) atomicAdd(pf + cur, acc);
+                cur = p;
+                acc = 0;
+            }
+            acc += (unsigned long long)flops[u];
+        }
+        if (acc) atomicAdd(pf + cur, acc);
+    }
 }
 
 int gridn(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div64(n, 256), 152 * 32)); }
@@ -437,7 +454,7 @@ spgemm_status_t stage_products(spgemm_ctx* ctx, spgemm_semiring_t sr, const spge
     auto pf = ctx_buf(ctx, 8 * grp.size());
     if (!pf) return set_err(ctx, SPGEMM_ERR_OOM, "stage flops");
     SG_CUDA(ctx, cudaMemsetAsync(pf->p, 0, 8 * grp.size(), ctx->stream));
-    k_prod_flops<<<gridn(G->U), 256, 0, ctx->stream>>>(E.it, E.item_prod, E.flops, (unsigned long long*)pf->p);
+    k_prod_flops<<<gridn(ceil_div64(G->U, PF_RUN)), 256, 0, ctx->stream>>>(E.it, E.item_prod, E.flops, (unsigned long long*)pf->p);
     note_launch();
     std::vector<unsigned long long> hpf(grp.size());
     SG_CUDA(ctx, cudaMemcpyAsync(hpf.data(), pf->p, 8 * grp.size(), cudaMemcpyDeviceToHost, ctx->stream));
@@ -748,7 +765,7 @@ spgemm_status_t spgemm_summa_block_flops(spgemm_ctx_t ctx, spgemm_mat_t A, spgem
     auto pf = ctx_buf(ctx, 8 * all.size());
     if (!pf) return set_err(ctx, SPGEMM_ERR_OOM, "block flops");
     SG_CUDA(ctx, cudaMemsetAsync(pf->p, 0, 8 * all.size(), ctx->stream));
-    k_prod_flops<<<gridn(E.it.nitems), 256, 0, ctx->stream>>>(E.it, E.item_prod, E.flops, (unsigned long long*)pf->p);
+    k_prod_flops<<<gridn(ceil_div64(E.it.nitems, PF_RUN)), 256, 0, ctx->stream>>>(E.it, E.item_prod, E.flops, (unsigned long long*)pf->p);
     note_launch();
     std::vector<unsigned long long> h(all.size());
     SG_CUDA(ctx, cudaMemcpyAsync(h.data(), pf->p, 8 * all.size(), cudaMemcpyDeviceToHost, ctx->stream));
