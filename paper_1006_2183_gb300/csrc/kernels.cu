@@ -586,8 +586,9 @@ static void run_hash(cudaStream_t st, const Items& it, const int2* list, int64_t
 }
 
 // Symbolic count of columns whose rows fit a per-group bitmap (every A_i has at
-// most BM_WARP_MAX_ROWS rows, as the SUMMA merge columns): each product sets its
+// most BM_COUNT_MAX_ROWS rows, as the SUMMA merge columns): each product sets its
 // row's bit and nnz is the popcount; no keys, no probing, no table to clear.
+constexpr int64_t BM_COUNT_MAX_ROWS = 32768;
 template <int GS, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK) k_bitcount(Items it, const int2* __restrict__ list,
                                                                   int64_t count, int64_t* __restrict__ nnz_item,
@@ -763,7 +764,7 @@ static void run_hash_bins(cudaStream_t st, const Items& it, const int2* list, co
     run_hash<SR, 32, 64, NUM, WARP_BLOCK>(st, it, list + off[W0], cnt[W0], nnz_item, Coff, Cir, Cv);
     run_hash<SR, 32, 128, NUM, WARP_BLOCK>(st, it, list + off[W0 + 1], cnt[W0 + 1], nnz_item, Coff, Cir, Cv);
     if constexpr (!NUM) {
-        if (it.max_m > 0 && it.max_m <= BM_WARP_MAX_ROWS) {
+        if (it.max_m > 0 && it.max_m <= BM_COUNT_MAX_ROWS) {
             // rows fit a small bitmap: count the longer columns by bits (64 and 128
             // slots hold so few rows that clearing a bitmap would cost more)
             run_bitcount<32, WARP_BLOCK>(st, it, list + off[W0 + 2], cnt[W0 + 2] + cnt[W0 + 3] + cnt[W0 + 4],

@@ -104,7 +104,7 @@ __device__ __forceinline__ void a_col(const Items& it, const Prod* pr, int64_t t
 // bitmap (instead of sorting) when every A_i has at most this many rows.
 constexpr int64_t BM_MAX_ROWS = 262144;
 // The same for warp tables (one bitmap per warp), and only where sorting costs more.
-constexpr int64_t BM_WARP_MAX_ROWS = 16384;
+constexpr int64_t BM_WARP_MAX_ROWS = 32768;
 constexpr int BM_WARP_MIN_TBL = 256;   // smaller tables hold too few rows to prefer the bitmap
 
 // flops and bin per item, product id per item, bin counts and total flops.

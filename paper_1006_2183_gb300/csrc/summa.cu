@@ -347,7 +347,20 @@ spgemm_status_t partition(spgemm_ctx* ctx, const DMat& M, size_t w, int g, Block
 // C (m x n) = merge of `ncols` sorted partial columns: column u of P (rows
 // global, colptr Pcp) is added into output column oc[u].
 // Stage partials go to upper-bound slots (no count pass) below this many slots.
-constexpr int64_t BOUNDED_MAX_SLOTS = int64_t(1) << 30;
+// Stage partials go to upper-bound slots (no count pass) when those slots, their
+// rows and values, take at most this share of the free device memory (the merge
+// that reads them needs about as much again).
+constexpr double BOUNDED_MEM_SHARE = 0.45;
+
+bool bounded_fits(const Engine& E) {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const double bytes = (double)E.flops_total * (4.0 + (double)sr_size(E.sr)) + 24.0 * (double)E.it.nitems;
+    return bytes <= BOUNDED_MEM_SHARE * (double)free_b;
+}
 
 // Merges the partial columns P (local rows < mb; column u goes to merge column
 // oc[u] = j * g + I) into the mb x (n g) matrix of merge columns, or, when
@@ -440,7 +453,7 @@ spgemm_status_t stage_products(spgemm_ctx* ctx, spgemm_semiring_t sr, const spge
     SG_TRY(engine_setup(&E, ctx, sr, o, grp, false));
     if (o.block_kernel == 1) {
         SG_TRY(engine_esc(&E, &G->rbuf, &G->vbuf));   // outer-product order, Section 2.4
-    } else if (single_merge && E.flops_total <= BOUNDED_MAX_SLOTS) {
+    } else if (single_merge && bounded_fits(E)) {
         // one merge reads the partials where they were written: no count pass for them
         SG_TRY(engine_numeric_bounded(&E, &G->rbuf, &G->vbuf, &G->colbuf, &G->pstart, &G->pend));
     } else {
