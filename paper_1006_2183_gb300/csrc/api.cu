@@ -318,7 +318,6 @@ spgemm_status_t engine_setup(Engine* E, spgemm_ctx* ctx, spgemm_semiring_t sr, c
     for (int64_t i = 0; i < np; ++i) {
         prods[i].item_base = E->hitem_base[i];
         prods[i].bnz_base = bnz;
-        prods[i].G = (int32_t)ceil_div64(std::max<int64_t>(prods[i].A.m, 1), E->cfg.dense_rows);
         E->hitem_base[i + 1] = E->hitem_base[i] + prods[i].B.nzc;
         bnz += prods[i].B.nnz;
         amax_n += prods[i].A.n;

@@ -90,7 +90,6 @@ struct Prod {
     int64_t item_base = 0;   // first global item of this product
     int64_t bnz_base = 0;    // sum of nnz(B) over earlier products (cursor addressing)
     int32_t row_base = 0;    // added to every output row id
-    int32_t G = 0;           // row slabs a long column needs at least: ceil(A.m / RB)
     int64_t col_base = 0;    // global column of B's column 0 (2D blocks)
     int32_t tag = 0;         // caller's label (SUMMA: the stage)
     int32_t blk = 0;         // caller's second label (SUMMA: the block row)
