@@ -417,11 +417,18 @@ spgemm_status_t engine_setup(Engine* E, spgemm_ctx* ctx, spgemm_semiring_t sr, c
     launch_bin_scatter(st, E->it, E->bin, E->item_prod, E->bin_off_dev, E->ctr + NBIN, E->list);
     const int64_t nd = E->bin_cnt[BIN_DENSE];
     E->dw = DenseWork();
-    if (nd > 0 && E->slab_rows_short)
+    if (nd > 0 && E->it.max_m <= dcol_rows(sr)) {
+        // operands of few rows: long columns go to the dense-column kernel
+        DenseWork& dw = E->dw;
+        dw.dlist = E->list + E->bin_off[BIN_DENSE];
+        dw.ndense = nd;
+        dw.dcol = true;
+        dw.mcap = (int)((E->it.max_m + 31) / 32 * 32);
+    } else if (nd > 0 && E->slab_rows_short)
         return set_err(ctx, SPGEMM_ERR_UNSUPPORTED,
                        "long columns of more than %d * (2^20 - 32) rows need more than %d row slabs", MAX_PARTS,
                        MAX_PARTS);
-    if (nd > 0) {
+    if (nd > 0 && !E->dw.dcol) {
         // slabs of the long columns, then the range buffers sized from their count
         off = 0;
         size_t o_items = take(sizeof(int2) * nd * MAX_PARTS);

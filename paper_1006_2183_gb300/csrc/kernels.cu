@@ -1426,6 +1426,148 @@ static void run_range(cudaStream_t st, const Items& it, const DenseWork& dw, boo
     note_launch();
 }
 
+// ------------------------------------------------------------------ dense-column tier
+// Long columns whose operands have few rows (every A_i has at most dcol_rows(SR)
+// rows, as the SUMMA stage blocks and merge columns): one CTA per column adds
+// every product into a dense row array in shared memory and marks a row bitmap,
+// then writes the column in row order from per-word ranks.  No row ranges, no
+// cursors, no hashing.
+int dcol_rows(spgemm_semiring_t sr) {
+    const int acc = sr == SPGEMM_PLUS_TIMES_F64 || sr == SPGEMM_PLUS_TIMES_I64 ? 8 : 4;
+    const int rows = (128 * 1024) / acc;
+    return rows < (int)BM_COUNT_MAX_ROWS ? rows : (int)BM_COUNT_MAX_ROWS;
+}
+static_assert(BM_COUNT_MAX_ROWS / 32 <= 2 * RT_BLOCK, "dense-column emit: two bitmap words per thread");
+
+template <class SR>
+__global__ void __launch_bounds__(RT_BLOCK) k_dcol(Items it, const int2* __restrict__ dlist, int64_t nd, int mcap,
+                                                   const int64_t* __restrict__ Coff, int32_t* __restrict__ Cir,
+                                                   typename SR::T* __restrict__ Cv) {
+    using Acc = typename SR::Acc;
+    using T = typename SR::T;
+    constexpr int NWARP = RT_BLOCK / 32;
+    extern __shared__ __align__(16) unsigned char smem[];
+    RangeSmem* sc = reinterpret_cast<RangeSmem*>(smem);
+    Acc* vals = reinterpret_cast<Acc*>(smem + sizeof(RangeSmem));   // mcap
+    uint32_t* bitmap = reinterpret_cast<uint32_t*>(vals + mcap);    // mcap / 32
+    int* s_scan = reinterpret_cast<int*>(bitmap + mcap / 32);       // 34
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int x = tid; x < mcap; x += RT_BLOCK) vals[x] = SR::zero();
+    for (int x = tid; x < mcap / 32; x += RT_BLOCK) bitmap[x] = 0u;
+    __syncthreads();
+    for (int64_t w = blockIdx.x; w < nd; w += gridDim.x) {
+        const int2 e = __ldg(dlist + w);
+        const Prod* pr = it.prods + e.x;
+        const int64_t u = __ldg(it.item_base + e.x) + e.y;
+        const int64_t bs = __ldg(pr->B.cp + e.y), be = __ldg(pr->B.cp + e.y + 1);
+        const int m = (int)(pr->A.m < (int64_t)mcap ? pr->A.m : (int64_t)mcap);
+        const int32_t* __restrict__ air = pr->A.ir;
+        for (int64_t b0 = bs; b0 < be; b0 += RT_BLOCK) {
+            const int64_t t = b0 + tid;
+            int len = 0;
+            int64_t a = 0;
+            T bv = T(0);
+            if (t < be) {
+                int64_t s, en;
+                a_col(it, pr, t, __ldg(pr->B.ir + t), s, en);
+                a = s;
+                len = (int)(en - s);
+                bv = load_val<SR>(pr->B, t);
+            }
+            int64_t bvbits = 0;
+            *reinterpret_cast<T*>(&bvbits) = bv;
+            int ns, Tn;
+            rt_compact(sc, t < be, len, a, bvbits, ns, Tn);
+            // warp slices of the products, 4 windows of 32 per step (as in the range tier)
+            constexpr int U = 4;
+            const int C = (Tn + NWARP * 32 - 1) / (NWARP * 32) * 32;
+            const int xb = warp * C, xe = min(Tn, xb + C);
+            if (xb < xe) {
+                int lo = 0, hi = ns;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (sc->end[mid] <= xb) lo = mid + 1;
+                    else hi = mid;
+                }
+                int o0 = lo;
+                for (int x0 = xb; x0 < xe; x0 += 32 * U) {
+                    int64_t idx[U];
+                    bool ok[U];
+                    int ob[U];
+#pragma unroll
+                    for (int uu = 0; uu < U; ++uu) {
+                        const int xw = x0 + 32 * uu;
+                        const int ej = o0 + lane < ns ? sc->end[o0 + lane] : INT_MAX;
+                        const unsigned bitv = (ej > xw && ej <= xw + 32) ? (1u << (ej - xw - 1)) : 0u;
+                        const unsigned mask = __reduce_or_sync(0xffffffffu, bitv);
+                        const int oi = o0 + __popc(mask & ((1u << lane) - 1u));
+                        const int pe0 = o0 > 0 ? sc->end[o0 - 1] : 0;
+                        const int src = oi - 1 - o0;
+                        const int pe = __shfl_sync(0xffffffffu, ej, src < 0 ? 0 : src);
+                        ok[uu] = xw + lane < xe;
+                        ob[uu] = oi;
+                        idx[uu] = ok[uu] ? sc->start[oi] + (xw + lane - (src < 0 ? pe0 : pe)) : 0;
+                        o0 += __popc(mask);
+                    }
+                    int32_t row[U];
+                    T av[U];
+#pragma unroll
+                    for (int uu = 0; uu < U; ++uu) {
+                        row[uu] = ok[uu] ? __ldg(air + idx[uu]) : -1;
+                        av[uu] = ok[uu] ? load_val<SR>(pr->A, idx[uu]) : T(0);
+                    }
+#pragma unroll
+                    for (int uu = 0; uu < U; ++uu) {
+                        const int r = row[uu];
+                        if ((unsigned)r >= (unsigned)m) continue;   // not taken, or malformed input
+                        const uint32_t bit = 1u << (r & 31);
+                        if (!(bitmap[r >> 5] & bit)) atomicOr(&bitmap[r >> 5], bit);
+                        SR::atomic_add(&vals[r], SR::mul(av[uu], *reinterpret_cast<const T*>(&sc->bv[ob[uu]])));
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        // row order: thread tid owns words 2 tid and 2 tid + 1 and writes their rows at their ranks
+        const int nw = (m + 31) >> 5;
+        const int x0 = 2 * tid;
+        const uint32_t w0 = x0 < nw ? bitmap[x0] : 0u, w1 = x0 + 1 < nw ? bitmap[x0 + 1] : 0u;
+        const int c = __popc(w0) + __popc(w1);
+        int total;
+        int rank = group_incl_scan<RT_BLOCK>(c, s_scan, total) - c;
+        const int64_t out0 = __ldg(Coff + u);
+        const int32_t rb = out_row_base(pr, e.y);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            uint32_t bits = h ? w1 : w0;
+            const int base = (x0 + h) * 32;
+            while (bits) {
+                const int r = base + __ffs(bits) - 1;
+                bits &= bits - 1;
+                Cir[out0 + rank] = r + rb;
+                Cv[out0 + rank] = SR::out(vals[r]);
+                vals[r] = SR::zero();
+                ++rank;
+            }
+            if (x0 + h < nw) bitmap[x0 + h] = 0u;
+        }
+        __syncthreads();
+    }
+}
+
+template <class SR>
+static void run_dcol(cudaStream_t st, const Items& it, const DenseWork& dw, const int64_t* Coff, int32_t* Cir,
+                     typename SR::T* Cv) {
+    if (dw.ndense <= 0) return;
+    const size_t smem = sizeof(RangeSmem) + (size_t)dw.mcap * sizeof(typename SR::Acc) + (size_t)(dw.mcap / 32) * 4 +
+                        34 * 4;
+    smem_at_least((const void*)k_dcol<SR>, smem);
+    const int per_sm = smem <= 72 * 1024 ? 3 : smem <= 110 * 1024 ? 2 : 1;
+    const int grid = (int)std::min<int64_t>(dw.ndense, 152 * per_sm);
+    k_dcol<SR><<<grid, RT_BLOCK, smem, st>>>(it, dw.dlist, dw.ndense, dw.mcap, Coff, Cir, Cv);
+    note_launch();
+}
+
 template <class SR>
 void launch_numeric_predicted(cudaStream_t st, const Items& it, const int2* list, const int64_t* bin_off,
                               const int64_t* bin_cnt, const int64_t* cap_off, int64_t* nnz_item, int32_t* Cir,
@@ -1438,7 +1580,10 @@ void launch_symbolic(cudaStream_t st, const Items& it, TierCfg cfg, const int2* 
                      const int64_t* bin_cnt, const DenseWork& dw, int64_t* nnz_item, int which) {
     (void)cfg;
     if (which & 1) run_hash_bins<SR, false>(st, it, list, bin_off, bin_cnt, nnz_item, nullptr, nullptr, nullptr);
-    if (which & 2) run_range<SR>(st, it, dw, false, nullptr, nullptr, nullptr);
+    if (which & 2) {
+        if (dw.dcol) run_bitcount<256, 256>(st, it, dw.dlist, dw.ndense, nnz_item);   // rows fit the bitmap
+        else run_range<SR>(st, it, dw, false, nullptr, nullptr, nullptr);
+    }
 }
 
 template <class SR>
@@ -1447,7 +1592,10 @@ void launch_numeric(cudaStream_t st, const Items& it, TierCfg cfg, const int2* l
                     typename SR::T* Cv, int which) {
     (void)cfg;
     if (which & 1) run_hash_bins<SR, true>(st, it, list, bin_off, bin_cnt, nullptr, Coff, Cir, Cv);
-    if (which & 2) run_range<SR>(st, it, dw, true, Coff, Cir, Cv);
+    if (which & 2) {
+        if (dw.dcol) run_dcol<SR>(st, it, dw, Coff, Cir, Cv);
+        else run_range<SR>(st, it, dw, true, Coff, Cir, Cv);
+    }
 }
 
 #define SG_INST(SR)                                                                                              \
@@ -1479,7 +1627,7 @@ __global__ void k_sum_parts(Items it, const int2* __restrict__ dlist, int64_t nd
 
 void launch_sum_parts(cudaStream_t st, const Items& it, const int2* dense_list, int64_t ndense, const int8_t* nparts,
                       const int32_t* part_count, int64_t* nnz_item) {
-    if (ndense == 0) return;
+    if (ndense == 0 || nparts == nullptr) return;   // no slabs: the dense-column mode counted directly
     k_sum_parts<<<(int)ceil_div64(ndense, 256), 256, 0, st>>>(it, dense_list, ndense, nparts, part_count, nnz_item);
     note_launch();
 }

@@ -72,7 +72,15 @@ struct DenseWork {   // state of the range tier shared by its kernels
     int H = RANGE_H;                      // cut a range once it holds this many entries (< tbl / 2)
     int WW = RANGE_W / 32;                // words per range window
     int tbl = RANGE_TBL;                  // hash slots per numeric range (4096 or 8192)
+    // dense-column mode (every A_i has at most dcol_rows rows): one CTA per long
+    // column with a dense row array; no slabs, ranges or cursors
+    bool dcol = false;
+    int mcap = 0;                         // rows of the dense array (multiple of 32)
 };
+
+// Most rows for the dense-column mode of a semiring: 128 KB of accumulators in
+// shared memory, and a row bitmap the bitmap count can hold.
+int dcol_rows(spgemm_semiring_t sr);
 
 struct Items {
     const Prod* prods = nullptr;        // device, nprod descriptors

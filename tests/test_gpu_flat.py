@@ -66,12 +66,13 @@ def test_tier_choice_does_not_change_result(ctx, sr):
 
 @pytest.mark.parametrize("sr", [PT_F64, MP_F32])
 def test_slab_rows_do_not_change_result(ctx, sr):
-    """Long columns cut into row slabs of 4096 .. 16384 rows (up to the 16-slab limit,
-    which raises the slab size for 2^14 rows / 4096) give the same result."""
-    A = gen.rmat(14, 8, 0x1402, sr)
+    """Long columns cut into row slabs of 4096 .. 65536 rows (up to the 16-slab limit,
+    which raises the slab size for 2^16 rows / 4096) give the same result; 2^16 rows
+    keep the long columns in the range tier."""
+    A = gen.rmat(16, 8, 0x1602, sr)
     s = sp()
     ref = oracle.spgemm(A, A, sr)
-    for rows in (4096, 8192, 1000, 16384, 0):
+    for rows in (4096, 8192, 1000, 65536, 0):
         C = gpu_product(ctx, A, A, sr, s.default_opts(range_slab_rows=rows, dense_part_flops=1024))
         assert_matches(C, ref, sr, what=f"slab rows {rows}")
 
@@ -99,6 +100,18 @@ def test_tall_long_columns_cut_into_slabs(ctx, sr):
             rng.random(131) if sr == PT_F64 else np.ones(131, np.uint8))
     C = s.spgemm_multiply(ctx, s.Matrix.from_host(ctx, A, sr), s.Matrix.from_host(ctx, B, sr), sr).to_host()
     assert_matches(C, oracle.spgemm(A, B, sr), sr, what="tall slabs")
+
+
+@pytest.mark.parametrize("sr", SEMIRINGS)
+def test_dense_column_tier_boundaries(ctx, sr):
+    """Long columns on both sides of the dense-column limit (16384 rows for 8-byte
+    accumulators, 32768 for 4-byte ones): the dense row array below, the range tier
+    above, the same result as the oracle either way."""
+    s = sp()
+    for m in (16384, 16385, 32768, 32769):
+        A = gen.erdos_renyi(m, 96, 120, 0xD0 + m % 7, sr)
+        B = gen.erdos_renyi(96, 24, 60, 0xD1 + m % 5, sr)   # 60 x 120 = 7200 products per column
+        check_product(ctx, A, B, sr, what=f"m = {m}")
 
 
 def test_long_column_over_slab_limit_is_unsupported(ctx):
