@@ -231,6 +231,26 @@ __device__ __forceinline__ int group_incl_scan_open(int v, int* scratch, int& to
     }
 }
 
+// 64-bit group_incl_scan_open for a group of several warps (GS == blockDim.x),
+// scratch of GS / 32 entries.
+template <int GS>
+__device__ __forceinline__ long long group_incl_scan64_open(long long v, long long* scratch, long long& total) {
+    static_assert(GS > 32 && GS % 32 == 0, "several warps");
+    constexpr int NW = GS / 32;
+    const int lane = threadIdx.x & 31, w = (threadIdx.x % GS) >> 5;
+    long long x = warp_incl_scan64(v);
+    if (lane == 31) scratch[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        long long s = lane < NW ? scratch[lane] : 0;
+        s = warp_incl_scan64(s);
+        if (lane < NW) scratch[lane] = s;
+    }
+    __syncthreads();
+    total = scratch[NW - 1];
+    return x + (w > 0 ? scratch[w - 1] : 0);
+}
+
 __host__ __device__ __forceinline__ int64_t ceil_div64(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 __device__ __forceinline__ uint32_t hash_row(int32_t r) { return (uint32_t)r * 0x9E3779B1u; }

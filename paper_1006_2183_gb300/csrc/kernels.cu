@@ -255,6 +255,21 @@ void launch_bin_scatter(cudaStream_t st, const Items& it, const uint8_t* bin, co
 }
 
 // ------------------------------------------------------------------ hash tiers
+// Segment of product xw + lane for a warp over compacted segments (ends[0, ns)
+// strictly increasing: no empty segment): bit b of the window mask marks the
+// segment that ends at xw + b + 1, so the lane's segment index is the count of
+// segments ending at or before its product.  o0 carries the segments that end at
+// or before the window start; windows must come in order.  All 32 lanes call it.
+__device__ __forceinline__ int warp_window_segment(const int* ends, int ns, int xw, int& o0) {
+    const int lane = threadIdx.x & 31;
+    const int ej = o0 + lane < ns ? ends[o0 + lane] : INT_MAX;
+    const unsigned bitv = (ej > xw && ej <= xw + 32) ? (1u << (ej - xw - 1)) : 0u;
+    const unsigned mask = __reduce_or_sync(0xffffffffu, bitv);
+    const int oi = o0 + __popc(mask & ((1u << lane) - 1u));
+    o0 += __popc(mask);
+    return oi;
+}
+
 template <class SR, int GS, int TBL, bool NUM>
 struct HashLayout {
     using T = typename SR::T;
@@ -421,33 +436,79 @@ __global__ void __launch_bounds__(BLOCK, hash_min_blocks(BLOCK, TBL)) k_hash(Ite
             // barrier (or the warp's shuffles), so the chunk arrays can be rewritten
             // after it without a closing barrier.
             int total;
-            int incl = group_incl_scan_open<GS>(len, s_scan, total);
-            s_incl[lane] = incl;
-            s_a0[lane] = a0;
-            if constexpr (NUM) s_bv[lane] = bv;
+            int ns = GS;   // segments in s_incl / s_a0 / s_bv
+            if constexpr (GS == 32) {
+                const int incl = group_incl_scan_open<GS>(len, s_scan, total);
+                s_incl[lane] = incl;
+                s_a0[lane] = a0;
+                if constexpr (NUM) s_bv[lane] = bv;
+            } else {
+                // several warps: keep the nonempty segments only (their ends are then
+                // distinct), so that a warp finds its products' segments by windows
+                long long tot64;
+                const long long inc64 = group_incl_scan64_open<GS>(len > 0 ? ((1ll << 32) | len) : 0ll,
+                                                                   reinterpret_cast<long long*>(s_scan), tot64);
+                if (len > 0) {
+                    const int p = (int)(inc64 >> 32) - 1;
+                    s_incl[p] = (int)(inc64 & 0xffffffffll);
+                    s_a0[p] = a0;
+                    if constexpr (NUM) s_bv[p] = bv;
+                }
+                ns = (int)(tot64 >> 32);
+                total = (int)(tot64 & 0xffffffffll);
+            }
             G::sync();
             const int32_t* __restrict__ air = pr->A.ir;
             // U products per lane per round: their loads are all issued before the first insert
             constexpr int U = 4;
-            for (int q0 = 0; q0 < total; q0 += GS * U) {
+            // several warps: each takes a contiguous slice of the products, in windows of 32
+            int q0 = 0, qend = total, o0 = 0;
+            constexpr int QSTEP = GS == 32 ? GS * U : 32 * U;
+            if constexpr (GS > 32) {
+                constexpr int NWG = GS / 32;
+                const int wg = (threadIdx.x % GS) >> 5;
+                const int C = (total + NWG * 32 - 1) / (NWG * 32) * 32;
+                q0 = wg * C;
+                qend = min(total, q0 + C);
+                int lo = 0, hi = ns;   // segments ending at or before the slice start
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (s_incl[mid] <= q0) lo = mid + 1;
+                    else hi = mid;
+                }
+                o0 = lo;
+            }
+            for (; q0 < qend; q0 += QSTEP) {
                 int32_t row[U];
                 T av[U];
                 int seg[U];
 #pragma unroll
                 for (int i = 0; i < U; ++i) {
-                    const int q = q0 + i * GS + lane;
                     row[i] = -1;
-                    if (q < total) {
-                        int lo = 0, hi = GS - 1;
-                        while (lo < hi) {
-                            int mid = (lo + hi) >> 1;
-                            if (s_incl[mid] > q) hi = mid;
-                            else lo = mid + 1;
+                    if constexpr (GS == 32) {
+                        const int q = q0 + i * GS + lane;
+                        if (q < total) {
+                            int lo = 0, hi = GS - 1;
+                            while (lo < hi) {
+                                int mid = (lo + hi) >> 1;
+                                if (s_incl[mid] > q) hi = mid;
+                                else lo = mid + 1;
+                            }
+                            const int64_t idx = s_a0[lo] + (q - (lo ? s_incl[lo - 1] : 0));
+                            row[i] = __ldg(air + idx);
+                            if constexpr (NUM) av[i] = load_val<SR>(pr->A, idx);
+                            seg[i] = lo;
                         }
-                        const int64_t idx = s_a0[lo] + (q - (lo ? s_incl[lo - 1] : 0));
-                        row[i] = __ldg(air + idx);
-                        if constexpr (NUM) av[i] = load_val<SR>(pr->A, idx);
-                        seg[i] = lo;
+                    } else {
+                        const int xw = q0 + 32 * i;
+                        const int oi = warp_window_segment(s_incl, ns, xw, o0);
+                        const int q = xw + (threadIdx.x & 31);   // this warp's lane, not the group's
+                        if (q < qend) {
+                            const int64_t idx = s_a0[oi] + (q - (oi ? s_incl[oi - 1] : 0));
+                            row[i] = __ldg(air + idx);
+                            if constexpr (NUM) av[i] = load_val<SR>(pr->A, idx);
+                            seg[i] = oi;
+                        }
                     }
                 }
 #pragma unroll
@@ -625,25 +686,62 @@ __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK) k_bitcount(Items it, cons
                 len = (int)(en - s);
             }
             int total;
-            const int incl = group_incl_scan_open<GS>(len, s_scan, total);
-            s_incl[lane] = incl;
-            s_a0[lane] = a0;
+            int ns = GS;
+            if constexpr (GS == 32) {
+                const int incl = group_incl_scan_open<GS>(len, s_scan, total);
+                s_incl[lane] = incl;
+                s_a0[lane] = a0;
+            } else {   // nonempty segments only, for the windowed walk below
+                long long tot64;
+                const long long inc64 = group_incl_scan64_open<GS>(len > 0 ? ((1ll << 32) | len) : 0ll,
+                                                                   reinterpret_cast<long long*>(s_scan), tot64);
+                if (len > 0) {
+                    const int p = (int)(inc64 >> 32) - 1;
+                    s_incl[p] = (int)(inc64 & 0xffffffffll);
+                    s_a0[p] = a0;
+                }
+                ns = (int)(tot64 >> 32);
+                total = (int)(tot64 & 0xffffffffll);
+            }
             G::sync();
             constexpr int U = 4;
-            for (int q0 = 0; q0 < total; q0 += GS * U) {
+            int q0 = 0, qend = total, o0 = 0;
+            constexpr int QSTEP = GS == 32 ? GS * U : 32 * U;
+            if constexpr (GS > 32) {   // a contiguous slice of the products per warp
+                constexpr int NWG = GS / 32;
+                const int wg = (threadIdx.x % GS) >> 5;
+                const int C = (total + NWG * 32 - 1) / (NWG * 32) * 32;
+                q0 = wg * C;
+                qend = min(total, q0 + C);
+                int lo = 0, hi = ns;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (s_incl[mid] <= q0) lo = mid + 1;
+                    else hi = mid;
+                }
+                o0 = lo;
+            }
+            for (; q0 < qend; q0 += QSTEP) {
                 int32_t row[U];
 #pragma unroll
                 for (int i = 0; i < U; ++i) {
-                    const int q = q0 + i * GS + lane;
                     row[i] = -1;
-                    if (q < total) {
-                        int lo = 0, hi = GS - 1;
-                        while (lo < hi) {
-                            const int mid = (lo + hi) >> 1;
-                            if (s_incl[mid] > q) hi = mid;
-                            else lo = mid + 1;
+                    if constexpr (GS == 32) {
+                        const int q = q0 + i * GS + lane;
+                        if (q < total) {
+                            int lo = 0, hi = GS - 1;
+                            while (lo < hi) {
+                                const int mid = (lo + hi) >> 1;
+                                if (s_incl[mid] > q) hi = mid;
+                                else lo = mid + 1;
+                            }
+                            row[i] = __ldg(air + s_a0[lo] + (q - (lo ? s_incl[lo - 1] : 0)));
                         }
-                        row[i] = __ldg(air + s_a0[lo] + (q - (lo ? s_incl[lo - 1] : 0)));
+                    } else {
+                        const int xw = q0 + 32 * i;
+                        const int oi = warp_window_segment(s_incl, ns, xw, o0);
+                        const int q = xw + (threadIdx.x & 31);   // this warp's lane, not the group's
+                        if (q < qend) row[i] = __ldg(air + s_a0[oi] + (q - (oi ? s_incl[oi - 1] : 0)));
                     }
                 }
 #pragma unroll
