@@ -1141,11 +1141,42 @@ __global__ void __launch_bounds__(RT_BLOCK, 3) k_range_sym(Items it, DenseWork d
             }
             int ns, T;
             rt_compact(sc, t < be, len, a, 0, ns, T);
-            rt_expand(sc, ns, T, [&](bool valid, int o, int off) {
-                if (!valid) return;
-                const int lr = (int)(__ldg(air + sc->start[o] + off) - R0);
-                if ((unsigned)lr < (unsigned)(R1 - R0)) atomicOr(&bitmap[lr >> 5], 1u << (lr & 31));
-            });
+            // warp slices, 4 windows of 32 products per step: all row loads issued before the marks
+            {
+                constexpr int U = 4, NWARP = RT_BLOCK / 32;
+                const int lane = tid & 31, warp = tid >> 5;
+                const int C = (T + NWARP * 32 - 1) / (NWARP * 32) * 32;
+                const int xb = warp * C, xe = min(T, xb + C);
+                if (xb < xe) {
+                    int lo = 0, hi = ns;
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (sc->end[mid] <= xb) lo = mid + 1;
+                        else hi = mid;
+                    }
+                    int o0 = lo;
+                    for (int x0 = xb; x0 < xe; x0 += 32 * U) {
+                        int64_t idx[U];
+                        bool ok[U];
+#pragma unroll
+                        for (int uu = 0; uu < U; ++uu) {
+                            const int xw = x0 + 32 * uu;
+                            const int oi = warp_window_segment(sc->end, ns, xw, o0);
+                            ok[uu] = xw + lane < xe;
+                            idx[uu] = ok[uu] ? sc->start[oi] + (xw + lane - (oi ? sc->end[oi - 1] : 0)) : 0;
+                        }
+                        int32_t row[U];
+#pragma unroll
+                        for (int uu = 0; uu < U; ++uu) row[uu] = ok[uu] ? __ldg(air + idx[uu]) : INT_MIN;
+#pragma unroll
+                        for (int uu = 0; uu < U; ++uu) {
+                            if (!ok[uu]) continue;
+                            const int lr = (int)(row[uu] - R0);
+                            if ((unsigned)lr < (unsigned)(R1 - R0)) atomicOr(&bitmap[lr >> 5], 1u << (lr & 31));
+                        }
+                    }
+                }
+            }
             __syncthreads();
         }
         // count per thread over a contiguous word range, then cut into ranges
