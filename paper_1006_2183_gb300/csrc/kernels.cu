@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(256) k_analyze(Items it, TierCfg cfg, int64_t*
     int64_t bs = 0, be = 0, am = 0;
     int prod = 0;
     if (u < it.nitems) {
-        prod = it.nprod == 1 ? 0 : find_prod(it.item_base, it.nprod, u);
+        prod = it.nprod == 1 ? 0 : __ldg(item_prod + u);   // filled per product beforehand
         const Prod* pr = it.prods + prod;
         const int64_t p = u - __ldg(it.item_base + prod);
         bs = __ldg(pr->B.cp + p);
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(256) k_analyze(Items it, TierCfg cfg, int64_t*
     }
     if (u < it.nitems && sub == 0) {
         flops[u] = f;
-        item_prod[u] = prod;
+        if (it.nprod == 1) item_prod[u] = 0;
         int64_t cap = f < am ? f : am;
         int b = bin_of(f, cap, cfg.warp_max, cfg.block_max);
         bin[u] = (uint8_t)b;
@@ -159,10 +159,21 @@ __global__ void __launch_bounds__(256) k_analyze(Items it, TierCfg cfg, int64_t*
     if (threadIdx.x == 0 && flops_total) atomicAdd(flops_total, s_fl);
 }
 
+// item_prod[u] = the product of item u: one CTA per product over its contiguous items.
+__global__ void k_item_prod(Items it, int32_t* __restrict__ item_prod) {
+    const int64_t p = blockIdx.x;
+    const int64_t u0 = __ldg(it.item_base + p), u1 = __ldg(it.item_base + p + 1);
+    for (int64_t u = u0 + threadIdx.x; u < u1; u += blockDim.x) item_prod[u] = (int32_t)p;
+}
+
 void launch_analyze(cudaStream_t st, const Items& it, TierCfg cfg, int64_t* flops, uint8_t* bin, int32_t* item_prod,
                     unsigned long long* bin_count, unsigned long long* flops_total, const uint64_t* sketch,
                     const int64_t* sketch_base, float* feat, int64_t* maxlen) {
     if (it.nitems == 0) return;
+    if (it.nprod > 1) {
+        k_item_prod<<<(unsigned)it.nprod, 256, 0, st>>>(it, item_prod);
+        note_launch();
+    }
     if (it.total_bnz < 4 * it.nitems) {   // about one B entry per item: one lane each
         int grid = (int)ceil_div64(it.nitems, 256);
         k_analyze<1><<<grid, 256, 0, st>>>(it, cfg, flops, bin, item_prod, bin_count, flops_total, sketch,
