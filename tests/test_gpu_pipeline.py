@@ -141,3 +141,23 @@ def test_pipeline_scale16_grid16(ctxs):
     np.testing.assert_array_equal(Hp.colptr, Hb.colptr)
     np.testing.assert_array_equal(Hp.rowidx, Hb.rowidx)
     np.testing.assert_allclose(Hp.vals, Hb.vals, rtol=2e-13, atol=0)
+
+
+@pytest.mark.parametrize("sr", [PT_I64, OR_BOOL])
+def test_pipeline_with_expand_sort_compress_stages(ctxs, sr):
+    """Stage products in the outer-product order (block_kernel = 1) feeding the
+    pipelined merges: the same C as the oracle."""
+    A = gen.rmat(11, 8, 0x110E, sr)
+    R = oracle.spgemm(A, A, sr)
+    for every in (1, 3):
+        C = pipelined(ctxs, A, A, sr, 8, summa_merge_every=every, block_kernel=1)
+        assert_matches(C.to_host(), R, sr, what=f"esc, every {every}")
+
+
+def test_pipeline_single_group_upper_bound_slots(ctxs):
+    """One group (merge after the last stage): its partials go to upper-bound slots
+    and the worker's single merge reads them with gaps."""
+    sr = MP_F32
+    A = gen.rmat(13, 8, 0x1313, sr)
+    R = oracle.spgemm(A, A, sr)
+    assert_matches(pipelined(ctxs, A, A, sr, 16).to_host(), R, sr, what="single group")
