@@ -13,9 +13,11 @@
  *     of the semiring's element type (double / float / uint8 / int64).
  *   - Every pointer passed in a matrix handle is a DEVICE pointer on the
  *     context's GPU, unless an entry point says otherwise.
- *   - All work is enqueued on the context's CUDA stream.  Only calls that must
- *     return a device-computed number to the host (spgemm_symbolic's nnz,
- *     spgemm_numeric's output size) synchronise that stream.
+ *   - All work is enqueued on the context's CUDA stream.  The product calls
+ *     synchronise that stream where a host decision needs a device count (tier
+ *     list sizes, output sizes, block layouts of the SUMMA split), so a product
+ *     call returns with its result complete; handle creation and export do not
+ *     synchronise.
  *   - Every function returns spgemm_status_t and never aborts; the message of
  *     the last failure is available from spgemm_last_error(ctx).
  *   - Results are structural: C(i,j) exists iff some k pairs a stored A(i,k)
@@ -30,8 +32,10 @@
  *     the handle is destroyed.
  *   - Handles returned by the library (products, conversions) OWN arrays
  *     allocated through the context allocator; spgemm_mat_destroy frees them.
- *   - Temporaries come from a per-context workspace that grows on demand and
- *     is released by spgemm_ctx_destroy.
+ *   - Temporaries are allocated through the context allocator for the
+ *     duration of one call (freed in stream order on the context stream before
+ *     it returns); the predictor's parameters live until spgemm_ctx_destroy.
+ *     spgemm_colptr_noalloc allocates nothing.
  */
 #ifndef SPGEMM_H
 #define SPGEMM_H
