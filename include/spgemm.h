@@ -178,10 +178,10 @@ spgemm_status_t spgemm_mat_destroy(spgemm_mat_t mat);
 typedef enum {
     SPGEMM_PHASE_ANALYZE = 0,        /* flops per column, binning, dense work items     */
     SPGEMM_PHASE_SYMBOLIC_HASH = 1,  /* symbolic pass, hash-table tiers                 */
-    SPGEMM_PHASE_SYMBOLIC_DENSE = 2, /* symbolic pass, row-chunked dense tier           */
+    SPGEMM_PHASE_SYMBOLIC_DENSE = 2, /* symbolic pass, long columns (ranges / dense)    */
     SPGEMM_PHASE_SCAN = 3,           /* column pointers of C                            */
     SPGEMM_PHASE_NUMERIC_HASH = 4,   /* numeric pass, hash-table tiers                  */
-    SPGEMM_PHASE_NUMERIC_DENSE = 5,  /* numeric pass, row-chunked dense tier            */
+    SPGEMM_PHASE_NUMERIC_DENSE = 5,  /* numeric pass, long columns (ranges / dense)     */
     SPGEMM_PHASE_PREDICT = 6,        /* predictor inference + overflow repair           */
     SPGEMM_PHASE_MERGE = 7           /* SUMMA stage merge                               */
 } spgemm_phase_t;
