@@ -216,6 +216,22 @@ def parse():
     return ap.parse_args()
 
 
+CPU_STRIDE_1T = 64   # the single-thread oracle sample: every 64th output column
+
+
+def cpu_single_thread(oracle, A) -> dict:
+    """The oracle on one host thread, over every CPU_STRIDE_1T-th output column of A*A
+    (plus-times FP64), for the single-thread figure beside the all-cores baseline."""
+    cols = np.arange(0, A.n, CPU_STRIDE_1T)
+    lens = np.diff(A.colptr)
+    fl = int(sum(lens[A.rowidx[A.colptr[j]:A.colptr[j + 1]]].sum() for j in cols))
+    t0 = time.perf_counter()
+    oracle.spgemm_columns(A, A, oracle.PT_F64, cols, nthreads=1)
+    dt = time.perf_counter() - t0
+    return {"value": 2.0 * fl / dt / 1e9, "unit": UNIT, "cores": 1,
+            "sample": f"every {CPU_STRIDE_1T}th output column ({len(cols)} columns, {fl} flops), {dt:.2f} s wall"}
+
+
 def flops_of(A) -> int:
     lens = np.diff(A.colptr)
     return int(lens[A.rowidx].sum())
@@ -633,7 +649,8 @@ def main():
         dt = time.perf_counter() - t0
         cpu = {"value": 2.0 * fl / dt / 1e9, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
                "sample": f"every {CPU_STRIDE}th output column ({len(cols)} columns, {fl} flops) of the flat "
-                         f"plus-times FP64 product, {dt:.2f} s wall on {oracle.max_threads()} threads"}
+                         f"plus-times FP64 product, {dt:.2f} s wall on {oracle.max_threads()} threads",
+               "single_thread": cpu_single_thread(oracle, A64)}
 
     imb = summa_imbalance(sp, ctx, mats[sp.PLUS_TIMES_F64], args.grid) if rank == 0 else None
     lvp = None

@@ -65,3 +65,17 @@ def test_imbalance_measure():
     assert r["overall"] == 2.5
     # Cannon stage 0 uses k = (I+J) mod 2: (0,0)->k=0: 4; (1,0)->k=1: 1; (0,1)->k=1: 1; (1,1)->k=0: 0
     assert abs(r["per_stage_max_cannon"] - 4.0 / 1.5) < 1e-12
+
+
+def test_single_thread_oracle_sample():
+    """The single-thread oracle figure: one thread, every 64th column, the flops of
+    exactly those columns (checked against the oracle's own flops count)."""
+    import bench
+    import oracle
+    from paper_1006_2183_gb300 import gen
+    A = gen.rmat(10, 8, 0x1010, gen.PLUS_TIMES_F64)
+    r = bench.cpu_single_thread(oracle, A)
+    assert r["cores"] == 1 and r["unit"] == "GFLOPS" and r["value"] > 0
+    cols = np.arange(0, A.n, bench.CPU_STRIDE_1T)
+    fl = int(oracle.flops_per_col(A, A)[cols].sum())
+    assert f"({len(cols)} columns, {fl} flops)" in r["sample"]
