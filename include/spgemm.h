@@ -97,22 +97,23 @@ typedef struct {
                                  the last stage, the paper's buffered triples).        */
     int warp_max_flops;       /* columns with flops <= this use warp-wide hash tables  */
     int block_max_flops;      /* columns with flops <= this use CTA-wide hash tables;
-                                 longer columns (the range tier) are cut into row ranges
-                                 of bounded output, each accumulated by one CTA          */
-    int dense_part_flops;     /* range tier: target flops per row slab of a long column */
+                                 longer columns (the slab tier) are cut into row slabs,
+                                 each counted and then accumulated by one CTA          */
+    int dense_part_flops;     /* slab tier: target flops per row slab of a long column
+                                 (default 32768); a column whose B column is long gets
+                                 fewer, larger slabs                                    */
     float predictor_margin;   /* capacity = (1 + margin) * prediction (+ slack)        */
-    int range_table_slots;    /* long columns: hash slots per row range, 2048, 4096 or
-                                 8192 (0 = default 4096); a range holds < slots/2 entries */
+    int range_table_slots;    /* ignored (kept for the layout of this struct)          */
     int block_kernel;         /* spgemm_summa_blocked stage products: 0 = the column
                                  tiers (default), 1 = expand-sort-compress, the
                                  data-parallel form of the outer-product multiply of
                                  Section 2.4 (needs < 2^32 products per merge group) */
-    int range_slab_rows;      /* long columns: most rows of one symbolic row slab (its
-                                 row bitmap lives in shared memory), rounded to a
+    int range_slab_rows;      /* long columns: most rows of one row slab (its row
+                                 bitmap lives in shared memory), rounded to a
                                  multiple of 32 and clamped to [4096, 2^20]; raised
-                                 where a column would need more than 16 slabs.
+                                 where a column would need more than 64 slabs.
                                  0 = default (2^19).  A long column of more than
-                                 16 * (2^20 - 32) rows is SPGEMM_ERR_UNSUPPORTED.   */
+                                 64 * (2^20 - 32) rows is SPGEMM_ERR_UNSUPPORTED.   */
     int reserved[5];
 } spgemm_opts_t;
 
@@ -312,11 +313,16 @@ spgemm_status_t spgemm_autotune(spgemm_ctx_t ctx, int count, const spgemm_mat_t*
  * cuda_stream (a cudaStream_t; NULL = legacy default stream) and the call does
  * not synchronise.  The first call on a device looks up the device address of
  * the scratch array (cudaGetSymbolAddress), so make that first call before any
- * stream capture.  All calls share the scratch array, which keeps the last
+ * stream capture; the address is kept for the life of the process and does not
+ * survive cudaDeviceReset (do not call this entry point on a device after
+ * resetting it).  All calls share the scratch array, which keeps the last
  * call's contents (each call overwrites what it reads); calls that overlap on
  * the GPU -- on different streams or from different threads -- race on it and
- * must be ordered by the caller.  Returns SPGEMM_ERR_INVALID_ARG for null or
- * negative arguments and SPGEMM_ERR_CUDA when a CUDA call fails. */
+ * must be ordered by the caller.  Work per column is O(flops_j + min(flops_j,
+ * m / 32)).  Returns SPGEMM_ERR_INVALID_ARG for a negative size or any null
+ * array (Arowidx and Browidx included: with no nonzeros pass a one-element
+ * array) and SPGEMM_ERR_CUDA when a CUDA call fails; an error already pending
+ * from earlier work on the thread is cleared on entry, not reported. */
 #define SPGEMM_NOALLOC_MAX_TILES 4096
 #define SPGEMM_NOALLOC_MAX_ROWS 1048576
 spgemm_status_t spgemm_colptr_noalloc(void* cuda_stream, int64_t m, int64_t k, int64_t n, const int64_t* Acolptr,

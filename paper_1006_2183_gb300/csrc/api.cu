@@ -112,7 +112,7 @@ void spgemm_opts_default(spgemm_opts_t* o) {
     o->summa_merge_every = 0;
     o->warp_max_flops = 512;
     o->block_max_flops = 4096;
-    o->dense_part_flops = 65536;
+    o->dense_part_flops = DEFAULT_PART_FLOPS;
     o->range_slab_rows = 0;
     o->predictor_margin = 0.25f;
 }
@@ -336,7 +336,7 @@ spgemm_status_t engine_setup(Engine* E, spgemm_ctx* ctx, spgemm_semiring_t sr, c
     size_t o_flops = take(8 * U1);
     size_t o_bin = take(U1);
     size_t o_iprod = take(4 * U1);
-    size_t o_ctr = take(8 * (2 * NBIN + 4));
+    size_t o_ctr = take(8 * (2 * NBIN + 8));
     size_t o_binoff = take(8 * NBIN);
     size_t o_list = take(sizeof(int2) * U1);
     size_t o_nnz = take(8 * U1);
@@ -399,7 +399,7 @@ spgemm_status_t engine_setup(Engine* E, spgemm_ctx* ctx, spgemm_semiring_t sr, c
         }
         SG_CUDA(ctx, cudaMemcpyAsync(skbase, hb.data(), 8 * (np + 1), cudaMemcpyHostToDevice, st));
     }
-    SG_CUDA(ctx, cudaMemsetAsync(E->ctr, 0, 8 * (2 * NBIN + 4), st));
+    SG_CUDA(ctx, cudaMemsetAsync(E->ctr, 0, 8 * (2 * NBIN + 8), st));
     launch_analyze(st, E->it, E->cfg, E->flops, E->bin, E->item_prod, E->ctr, E->ctr + 2 * NBIN, sketch, skbase,
                    E->feat, E->maxlen);
     unsigned long long hc[NBIN + 1];
@@ -429,47 +429,53 @@ spgemm_status_t engine_setup(Engine* E, spgemm_ctx* ctx, spgemm_semiring_t sr, c
                        "long columns of more than %d * (2^20 - 32) rows need more than %d row slabs", MAX_PARTS,
                        MAX_PARTS);
     if (nd > 0 && !E->dw.dcol) {
-        // slabs of the long columns, then the range buffers sized from their count
+        // slabs of the long columns, then the slab arrays and row-set storage sized from them
         off = 0;
         size_t o_items = take(sizeof(int2) * nd * MAX_PARTS);
         size_t o_np = take(nd);
-        size_t o_pc = take(4 * nd * MAX_PARTS);
-        size_t o_pb = take(8 * nd * MAX_PARTS);
-        size_t o_pn = take(4 * nd * MAX_PARTS);
-        size_t o_cur = take(sizeof(int2) * std::max<int64_t>(bnz, 1) * MAX_PARTS);
+        size_t o_sb = take(4 * nd);
         auto dbuf = ctx_buf(ctx, off);
-        if (!dbuf) return set_err(ctx, SPGEMM_ERR_OOM, "range-tier arena of %zu bytes", off);
+        if (!dbuf) return set_err(ctx, SPGEMM_ERR_OOM, "slab-tier arena of %zu bytes", off);
         E->bufs.push_back(dbuf);
         char* db = (char*)dbuf->p;
-        E->ditems = (int2*)(db + o_items);
-        E->nparts = (int8_t*)(db + o_np);
-        E->part_count = (int32_t*)(db + o_pc);
-        E->cursors = (int2*)(db + o_cur);
         DenseWork& dw = E->dw;
         dw.dlist = E->list + E->bin_off[BIN_DENSE];
         dw.ndense = nd;
-        dw.items = E->ditems;
+        dw.items = (int2*)(db + o_items);
         dw.nitems = E->ctr + 2 * NBIN + 1;
-        dw.nparts = E->nparts;
-        dw.cursors = E->cursors;
-        dw.part_count = E->part_count;
-        dw.parts_ctr = E->ctr + 2 * NBIN + 2;
+        dw.nparts = (int8_t*)(db + o_np);
+        dw.sbase = (int32_t*)(db + o_sb);
+        dw.store_ctr = E->ctr + 2 * NBIN + 2;
         dw.err = (int*)(E->ctr + 2 * NBIN + 3);
-        dw.pbase = (int64_t*)(db + o_pb);
-        dw.pcnt = (int32_t*)(db + o_pn);
+        unsigned long long* store_bound = E->ctr + 2 * NBIN + 4;
+        int* vals_zero = (int*)(E->ctr + 2 * NBIN + 5);
         dw.RB = E->cfg.dense_rows;
-        dw.tbl = opts.range_table_slots > 4096 ? 8192 : (opts.range_table_slots > 0 && opts.range_table_slots <= 2048 ? 2048 : 4096);
-        dw.H = dw.tbl / 2 - 32;
-        launch_dense_items(st, E->it, dw.dlist, nd, E->flops, E->cfg.part_flops, dw.RB, E->ditems,
-                           E->ctr + 2 * NBIN + 1, E->nparts);
-        unsigned long long nslabs = 0;
-        SG_CUDA(ctx, cudaMemcpyAsync(&nslabs, E->ctr + 2 * NBIN + 1, 8, cudaMemcpyDeviceToHost, st));
+        launch_dense_items(st, E->it, dw.dlist, nd, E->flops, E->cfg.part_flops, dw.RB, (int2*)dw.items,
+                           E->ctr + 2 * NBIN + 1, (int8_t*)dw.nparts, (int32_t*)dw.sbase, store_bound);
+        if (sr == SPGEMM_OR_AND_BOOL) {
+            launch_false_values(st, E->it, vals_zero);
+            dw.vals_zero = vals_zero;
+        }
+        unsigned long long hs[2] = {0, 0};
+        SG_CUDA(ctx, cudaMemcpyAsync(&hs[0], E->ctr + 2 * NBIN + 1, 8, cudaMemcpyDeviceToHost, st));
+        SG_CUDA(ctx, cudaMemcpyAsync(&hs[1], store_bound, 8, cudaMemcpyDeviceToHost, st));
         SG_TRY(sync_ctx(ctx));
-        dw.parts_cap = ceil_div64(E->flops_total, dw.H) + (int64_t)nslabs * (ceil_div64(dw.RB, RANGE_W) + 2) + 16;
-        auto pbuf = ctx_buf(ctx, sizeof(RangePart) * dw.parts_cap);
-        if (!pbuf) return set_err(ctx, SPGEMM_ERR_OOM, "range list of %lld entries", (long long)dw.parts_cap);
-        E->bufs.push_back(pbuf);
-        dw.parts = (RangePart*)pbuf->p;
+        dw.nslabs = (int64_t)hs[0];
+        dw.store_cap = (int64_t)hs[1];
+        off = 0;
+        const int64_t ns1 = std::max<int64_t>(dw.nslabs, 1);
+        size_t o_cnt = take(4 * ns1);
+        size_t o_pref = take(4 * ns1);
+        size_t o_soff = take(8 * ns1);
+        size_t o_store = take(4 * (size_t)std::max<int64_t>(dw.store_cap, 1));
+        auto sbuf = ctx_buf(ctx, off);
+        if (!sbuf) return set_err(ctx, SPGEMM_ERR_OOM, "slab row sets of %zu bytes", off);
+        E->bufs.push_back(sbuf);
+        char* sb = (char*)sbuf->p;
+        dw.scount = (int32_t*)(sb + o_cnt);
+        dw.spref = (int32_t*)(sb + o_pref);
+        dw.soff = (int64_t*)(sb + o_soff);
+        dw.store = (uint32_t*)(sb + o_store);
     }
     SG_CUDA(ctx, cudaGetLastError());
     return SPGEMM_OK;
@@ -507,8 +513,7 @@ spgemm_status_t engine_symbolic(Engine* E) {
     case SPGEMM_PLUS_TIMES_I64: dispatch_symbolic<PTI64>(E); break;
     }
     SG_CUDA(ctx, cudaGetLastError());   // launch errors of the symbolic kernels
-    launch_sum_parts(st, E->it, E->list + E->bin_off[BIN_DENSE], E->bin_cnt[BIN_DENSE], E->nparts, E->part_count,
-                     E->nnz_item);
+    launch_sum_parts(st, E->it, E->dw, E->nnz_item);
     E->Coff_buf = ctx_buf(ctx, 8 * (U + 1));
     if (!E->Coff_buf) return set_err(ctx, SPGEMM_ERR_OOM, "item offsets");
     E->Coff = (int64_t*)E->Coff_buf->p;
@@ -528,7 +533,7 @@ spgemm_status_t engine_symbolic(Engine* E) {
     SG_CUDA(ctx, cudaMemcpyAsync(&nnz, E->Coff + U, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     SG_CUDA(ctx, cudaMemcpyAsync(&err, E->ctr + 2 * NBIN + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
     SG_TRY(sync_ctx(ctx));
-    if (err) return set_err(ctx, SPGEMM_ERR_INDEX_OVERFLOW, "range tier capacity exceeded (code %d)", err);
+    if (err) return set_err(ctx, SPGEMM_ERR_INDEX_OVERFLOW, "slab tier capacity exceeded (code %d)", err);
     E->nnz_total = nnz;
     int64_t acc = 0;
     for (int b = 0; b < NBIN; ++b) {

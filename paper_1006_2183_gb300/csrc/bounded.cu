@@ -16,7 +16,7 @@ using namespace sg;
 
 namespace {
 
-int gridb(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div64(n, 256), 152 * 8)); }
+int gridb(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div64(n, 256), sm_count() * 8)); }
 
 // slots per item: min(flops, m) for the hash tiers, the exact count for the range tier
 __global__ void k_bound_capacity(Items it, const uint8_t* __restrict__ bin, const int32_t* __restrict__ item_prod,
@@ -75,8 +75,7 @@ spgemm_status_t engine_numeric_bounded(Engine* E, std::shared_ptr<DevBuf>* rbuf,
         case SPGEMM_OR_AND_BOOL: range_symbolic<BOOL8>(E); break;
         case SPGEMM_PLUS_TIMES_I64: range_symbolic<PTI64>(E); break;
         }
-        launch_sum_parts(st, E->it, E->list + E->bin_off[BIN_DENSE], E->bin_cnt[BIN_DENSE], E->nparts, E->part_count,
-                         E->nnz_item);
+        launch_sum_parts(st, E->it, E->dw, E->nnz_item);
     }
     // slot offsets (U + 1) and column ends (U) in one buffer
     auto cb = ctx_buf(ctx, 8 * (2 * U1 + 2) + scan_tmp_bytes(U1));
@@ -97,7 +96,7 @@ spgemm_status_t engine_numeric_bounded(Engine* E, std::shared_ptr<DevBuf>* rbuf,
         SG_CUDA(ctx, cudaMemcpyAsync(&err, E->ctr + 2 * NBIN + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
         SG_TRY(sync_ctx(ctx));
     }
-    if (err) return set_err(ctx, SPGEMM_ERR_INDEX_OVERFLOW, "range tier capacity exceeded (code %d)", err);
+    if (err) return set_err(ctx, SPGEMM_ERR_INDEX_OVERFLOW, "slab tier capacity exceeded (code %d)", err);
     auto r = ctx_buf(ctx, 4 * (size_t)std::max<int64_t>(total, 1));
     auto v = ctx_buf(ctx, w * (size_t)std::max<int64_t>(total, 1));
     if (!r || !v) return set_err(ctx, SPGEMM_ERR_OOM, "bounded output of %lld slots", (long long)total);

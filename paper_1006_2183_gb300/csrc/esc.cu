@@ -18,7 +18,7 @@ using namespace sg;
 
 namespace {
 
-int grid_esc(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div64(n, 256), 152 * 32)); }
+int grid_esc(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div64(n, 256), sm_count() * 32)); }
 
 int bits_for(int64_t n) {
     int b = 0;

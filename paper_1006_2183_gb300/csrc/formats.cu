@@ -113,7 +113,7 @@ __global__ void k_gather(const uint32_t* __restrict__ perm, const int32_t* __res
     }
 }
 
-int grid_for(int64_t n, int block = 256) { return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div64(n, block), 152 * 32)); }
+int grid_for(int64_t n, int block = 256) { return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div64(n, block), sm_count() * 32)); }
 
 // ---------------------------------------------------------------- DCSC
 __global__ void k_nonempty(const int64_t* __restrict__ cp, int64_t n, int64_t* __restrict__ flag) {

@@ -75,14 +75,11 @@ struct Engine {
     int64_t* flops = nullptr;
     uint8_t* bin = nullptr;
     int32_t* item_prod = nullptr;
-    unsigned long long* ctr = nullptr;   // bin_count[NBIN], bin_cursor[NBIN], flops_total, slabs, ranges, err
+    unsigned long long* ctr = nullptr;   // bin_count[NBIN], bin_cursor[NBIN], flops_total, slabs, store use, err,
+                                         // store bound, false-value flag
     int64_t* bin_off_dev = nullptr;
     int2* list = nullptr;
-    int2* ditems = nullptr;
-    int8_t* nparts = nullptr;
-    int2* cursors = nullptr;
-    int32_t* part_count = nullptr;
-    sg::DenseWork dw;                    // range-tier state
+    sg::DenseWork dw;                    // slab-tier state
     int64_t* nnz_item = nullptr;
     void* scan_tmp = nullptr;
     float* feat = nullptr;               // predictor inputs (items x 8) when requested

@@ -29,6 +29,23 @@ static std::atomic<int64_t> g_launches{0};
 void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 int64_t launches() { return g_launches.load(std::memory_order_relaxed); }
 
+int sm_count() {
+    static std::mutex mu;
+    static std::map<int, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    auto f = cache.find(dev);
+    if (f != cache.end()) return f->second;
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        return 1;   // not cached: asked again next time
+    }
+    cache[dev] = n;
+    return n;
+}
+
 // Raises a kernel's dynamic shared-memory limit on the current device to at least
 // `bytes`; never lowers it (the limit belongs to the kernel, whichever launcher
 // asks).  A refused request is not remembered, so the launch reports the error.
@@ -234,7 +251,7 @@ __global__ void k_numeric_bins(Items it, TierCfg cfg, const uint8_t* __restrict_
 void launch_numeric_bins(cudaStream_t st, const Items& it, TierCfg cfg, const uint8_t* bin, const int64_t* flops,
                          const int64_t* nnz_item, uint8_t* nbin, unsigned long long* cnt) {
     if (it.nitems == 0) return;
-    const int grid = (int)std::min<int64_t>(ceil_div64(it.nitems, 256), 152 * 8);
+    const int grid = (int)std::min<int64_t>(ceil_div64(it.nitems, 256), sm_count() * 8);
     k_numeric_bins<<<grid, 256, 0, st>>>(it, cfg, bin, flops, nnz_item, nbin, cnt);
     note_launch();
 }
@@ -652,7 +669,7 @@ static void run_hash(cudaStream_t st, const Items& it, const int2* list, int64_t
     auto kern = k_hash<SR, GS, TBL, NUM, BLOCK>;
     smem_at_least((const void*)kern, smem);
     int64_t want = ceil_div64(count, NG);
-    int grid = (int)std::min<int64_t>(want, 152 * 32);
+    int grid = (int)std::min<int64_t>(want, sm_count() * 32);
     kern<<<grid, BLOCK, smem, st>>>(it, list, count, nnz_item, Coff, Cir, Cv, bm_words);
     note_launch();
 }
@@ -783,7 +800,7 @@ static void run_bitcount(cudaStream_t st, const Items& it, const int2* list, int
     const size_t smem = (GROUP + (size_t)bm_words * 4) * NG;
     auto kern = k_bitcount<GS, BLOCK>;
     smem_at_least((const void*)kern, smem);
-    const int grid = (int)std::min<int64_t>(ceil_div64(count, NG), 152 * 32);
+    const int grid = (int)std::min<int64_t>(ceil_div64(count, NG), sm_count() * 32);
     kern<<<grid, BLOCK, smem, st>>>(it, list, count, nnz_item, bm_words);
     note_launch();
 }
@@ -860,7 +877,7 @@ template <class SR, bool NUM>
 static void run_tiny(cudaStream_t st, const Items& it, const int2* list, int64_t count, int64_t* nnz_item,
                      const int64_t* Coff, int32_t* Cir, typename SR::T* Cv) {
     if (count <= 0) return;
-    const int grid = (int)std::min<int64_t>(ceil_div64(count, 256), 152 * 16);
+    const int grid = (int)std::min<int64_t>(ceil_div64(count, 256), sm_count() * 16);
     k_tiny<SR, NUM><<<grid, 256, 0, st>>>(it, list, count, nnz_item, Coff, Cir, Cv);
     note_launch();
 }
@@ -902,23 +919,21 @@ static void run_hash_bins(cudaStream_t st, const Items& it, const int2* list, co
     run_hash<SR, 512, 8192, NUM, 512>(st, it, list + off[B0 + 2], cnt[B0 + 2], nnz_item, Coff, Cir, Cv);
 }
 
-// ------------------------------------------------------------------ range tier (long columns)
-// A long output column is first split into at most MAX_PARTS row slabs of
-// at most RB rows ("symbolic items", balanced by flops).  The symbolic kernel
-// marks the rows of its slab in a shared-memory bitmap with a balanced,
-// flattened walk over the products, counts them, and cuts the slab into
-// "ranges" of at most H entries and W rows.  The numeric kernel walks the
-// ranges of a slab in row order with one cursor per k: a galloping search
-// finds where A(:,k) leaves the range, the products of the range are
-// accumulated in a shared-memory hash table (values) plus a bitmap of the
-// range's rows (order), and the bitmap is read back in row order, so each
-// range is written already sorted.
+// ------------------------------------------------------------------ slab tier (long columns)
+// A long output column is split into P row slabs of at most RB rows (balanced by
+// flops, at most MAX_PARTS, fewer where B(:,j) is long: every slab repeats two
+// binary searches per entry of B(:,j)).  The symbolic kernel marks the rows of a
+// slab in a shared-memory bitmap with one flattened walk over the slab's products,
+// counts them and stores the slab's row set for the numeric pass: its bitmap words
+// when the slab holds at least one row per word, else its rows in ascending order,
+// whichever is smaller.  The numeric kernel reloads the row set into a
+// shared-memory bitmap, ranks rows by per-group prefix counts (4 words = 128 rows
+// per group), writes C's rows for the slab, sets the slab's values to the
+// semiring zero and walks the products again, adding each one into C at its row's
+// rank with an L2 reduction.  There is no shared-memory accumulator (FP64 shared
+// atomics are the slow path on this part), no hashing and no sort, and a slab's
+// products are spread evenly over the CTA's warps.
 constexpr int RT_BLOCK = 512;
-constexpr int RT_MAXB = 1024;
-constexpr int RT_NEXT = 512;
-static_assert(RANGE_W / 32 <= 4 * RT_BLOCK, "range emit: one 4-word group of the row bitmap per thread");
-// the rank order of a range (< TBL / 2 entries of 2 bytes) lives in RangeSmem.start and .bv
-static_assert(RANGE_TBL / 2 * 2 <= 2 * RT_BLOCK * 8, "range emit: the rank order of a range fits start + bv");    // k's per column whose cursor state lives in shared memory
 
 __device__ __forceinline__ int32_t lower_bound_rows(const int32_t* __restrict__ r, int64_t len, int64_t v) {
     int64_t lo = 0, hi = len;
@@ -930,61 +945,16 @@ __device__ __forceinline__ int32_t lower_bound_rows(const int32_t* __restrict__ 
     return (int32_t)lo;
 }
 
-// rows [R0, R1) of symbolic item q of P over m rows (32-aligned cuts)
-__device__ __forceinline__ void slab_rows(int64_t m, int q, int P, int64_t& R0, int64_t& R1) {
+// rows [R0, R1) of slab q of P over m rows (32-aligned cuts)
+__host__ __device__ __forceinline__ void slab_rows(int64_t m, int q, int P, int64_t& R0, int64_t& R1) {
     R0 = ((int64_t)q * m / P) & ~int64_t(31);
     R1 = q == P - 1 ? m : (((int64_t)(q + 1) * m / P) & ~int64_t(31));
 }
 
-// number of positions in [pos, en) whose row is < lim (rows ascending)
-__device__ __forceinline__ int64_t gallop_count(const int32_t* __restrict__ r, int64_t pos, int64_t en, int64_t lim) {
-    if (pos >= en || (int64_t)__ldg(r + pos) >= lim) return 0;
-    int64_t lo = pos, step = 1;   // r[lo] < lim
-    while (lo + step < en && (int64_t)__ldg(r + lo + step) < lim) {
-        lo += step;
-        step <<= 1;
-    }
-    int64_t hi = lo + step < en ? lo + step : en;   // r[hi] >= lim or hi == en
-    ++lo;
-    while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        if ((int64_t)__ldg(r + mid) < lim) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo - pos;
-}
-
-// gallop_count, plus the row at pos + count (INT_MAX past en).  The first 8
-// positions are read with independent loads, so the common short run costs one
-// memory round trip; longer runs continue with the gallop.
-__device__ __forceinline__ int64_t count_below(const int32_t* __restrict__ r, int64_t pos, int64_t en, int64_t lim,
-                                               int32_t& next) {
-    constexpr int F = 8;
-    int32_t v[F];
-#pragma unroll
-    for (int i = 0; i < F; ++i) v[i] = pos + i < en ? __ldg(r + pos + i) : INT_MAX;
-    int c = 0;
-#pragma unroll
-    for (int i = 0; i < F; ++i) c += (int64_t)v[i] < lim;   // a prefix, rows ascending
-    if (c < F) {
-        next = v[0];
-#pragma unroll
-        for (int i = 1; i < F; ++i)
-            if (i == c) next = v[i];
-        return c;
-    }
-    const int64_t p = pos + F - 1;   // r[p] < lim
-    const int64_t cnt = F - 1 + gallop_count(r, p, en, lim);
-    next = pos + cnt < en ? __ldg(r + pos + cnt) : INT_MAX;
-    return cnt;
-}
-
 // bitmap[wd] |= bit for every lane with wd >= 0; lanes that hit the same word
-// combine their bits first, so each word takes one shared atomic per warp.
+// combine their bits first, so each run of equal words takes one shared atomic.
 // Called by all 32 lanes of the warp.
 __device__ __forceinline__ void or_bits_warp(uint32_t* bitmap, int wd, uint32_t bit) {
-    // lanes usually walk one segment in row order, so neighbours often share a word:
-    // fold runs of equal words with a shuffle before the shared atomic
     const int lane = threadIdx.x & 31;
     const int wprev = __shfl_up_sync(0xffffffffu, wd, 1);
     const bool head = lane == 0 || wprev != wd;
@@ -998,30 +968,79 @@ __device__ __forceinline__ void or_bits_warp(uint32_t* bitmap, int wd, uint32_t 
     if (wd >= 0 && head) atomicOr(&bitmap[wd], acc);
 }
 
+// Slabs of the long columns: P per column, items[sbase[d] + q] = (d, q); the
+// storage bound of the slab row sets, sum over columns of min(flops, words),
+// accumulates in *store_bound (a slab stores min(words, rows) 4-byte entries and
+// rows <= flops).
 __global__ void k_dense_items(Items it, const int2* __restrict__ dlist, int64_t nd, const int64_t* __restrict__ flops,
-                              int part_flops, int RB, int2* items, unsigned long long* nitems, int8_t* nparts) {
+                              int part_flops, int RB, int2* items, unsigned long long* nitems, int8_t* nparts,
+                              int32_t* sbase, unsigned long long* store_bound) {
     int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (d >= nd) return;
     const int2 e = dlist[d];
     const Prod* pr = it.prods + e.x;
     const int64_t f = flops[__ldg(it.item_base + e.x) + e.y];
+    const int64_t deg = __ldg(pr->B.cp + e.y + 1) - __ldg(pr->B.cp + e.y);
     const int64_t m = pr->A.m;
     // slab rows stay <= RB: one slab when m fits, else cuts of at most RB - 32 rows plus alignment
-    int64_t pmin = m <= RB ? 1 : ceil_div64(m, (int64_t)RB - 32);
+    const int64_t pmin = m <= RB ? 1 : ceil_div64(m, (int64_t)RB - 32);
     int64_t P = ceil_div64(f, part_flops);
+    const int64_t pdeg = f / (32 * (deg > 0 ? deg : 1));   // about 32 products per (slab, B entry) at least
+    P = P < pdeg ? P : pdeg;
     P = P < pmin ? pmin : P;
     P = P > MAX_PARTS ? MAX_PARTS : P;
     P = P < 1 ? 1 : P;
     nparts[d] = (int8_t)P;
+    int64_t words = 0;
+    for (int q = 0; q < P; ++q) {
+        int64_t R0, R1;
+        slab_rows(m, q, (int)P, R0, R1);
+        words += (R1 - R0 + 31) >> 5;
+    }
+    atomicAdd(store_bound, (unsigned long long)(f < words ? f : words));
     unsigned long long base = atomicAdd(nitems, (unsigned long long)P);
+    sbase[d] = (int32_t)base;
     for (int q = 0; q < P; ++q) items[base + q] = make_int2((int)d, q);
 }
 
 void launch_dense_items(cudaStream_t st, const Items& it, const int2* dense_list, int64_t ndense, const int64_t* flops,
-                        int part_flops, int RB, int2* items, unsigned long long* nitems, int8_t* nparts) {
+                        int part_flops, int RB, int2* items, unsigned long long* nitems, int8_t* nparts,
+                        int32_t* sbase, unsigned long long* store_bound) {
     if (ndense == 0) return;
     k_dense_items<<<(int)ceil_div64(ndense, 256), 256, 0, st>>>(it, dense_list, ndense, flops, part_flops, RB, items,
-                                                               nitems, nparts);
+                                                               nitems, nparts, sbase, store_bound);
+    note_launch();
+}
+
+// flag = 1 when some stored value of an operand is false (boolean semiring): then
+// the numeric pass must evaluate the products; else every output value is true.
+__global__ void k_false_values(Items it, int* flag) {
+    for (int64_t p = blockIdx.y; p < it.nprod; p += gridDim.y) {
+        const Prod* pr = it.prods + p;
+        for (int side = 0; side < 2; ++side) {
+            const DMat& M = side ? pr->B : pr->A;
+            if (M.num == nullptr || M.nzc <= 0) continue;
+            const uint8_t* __restrict__ v = reinterpret_cast<const uint8_t*>(M.num);
+            const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+            const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+            bool f = false;
+            if (M.ce) {   // a CSC with gaps: only the stored part of every column
+                for (int64_t c = t0; c < M.nzc; c += stride)
+                    for (int64_t i = __ldg(M.cp + c); i < __ldg(M.ce + c); ++i) f |= __ldg(v + i) == 0;
+            } else {
+                const int64_t s = __ldg(M.cp), e = __ldg(M.cp + M.nzc);
+                for (int64_t i = s + t0; i < e; i += stride) f |= __ldg(v + i) == 0;
+            }
+            if (f) *flag = 1;
+        }
+    }
+}
+
+void launch_false_values(cudaStream_t st, const Items& it, int* flag) {
+    if (it.nprod <= 0) return;
+    const int gy = (int)std::min<int64_t>(it.nprod, 65535);
+    const int gx = std::max(1, std::min(256, 4096 / gy));
+    k_false_values<<<dim3(gx, gy), 256, 0, st>>>(it, flag);
     note_launch();
 }
 
@@ -1060,6 +1079,8 @@ struct RangeSmem {   // per-batch segments of the flattened expansion (compacted
     unsigned long long ws[32];
     int wc[RT_BLOCK / 32 + 1];
 };
+// shared-memory offset of what follows a RangeSmem (16-byte aligned for vector access)
+constexpr size_t RS_BYTES = (sizeof(RangeSmem) + 15) / 16 * 16;
 
 // Compacts the active (k, segment) pairs of this batch into sc and returns
 // (number of segments, number of products).  Called by all threads.
@@ -1079,49 +1100,82 @@ __device__ __forceinline__ void rt_compact(RangeSmem* sc, bool active, int len, 
     __syncthreads();
 }
 
-// Walks products x in [0, T) of the compacted segments: each warp takes a
-// contiguous slice; a lane finds its segment from the boundary mask of its
-// 32-product window.  f(valid, segment, offset) is called by all 32 lanes.
-template <class F>
-__device__ __forceinline__ void rt_expand(const RangeSmem* sc, int ns, int T, F&& f) {
-    constexpr int NW = RT_BLOCK / 32;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int C = (T + NW * 32 - 1) / (NW * 32) * 32;
-    const int xb = warp * C, xe = min(T, xb + C);
-    if (xb >= xe) return;
-    // o0 = number of segment ends <= xb
-    int lo = 0, hi = ns;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (sc->end[mid] <= xb) lo = mid + 1;
-        else hi = mid;
-    }
-    int o0 = lo;
-    for (int x0 = xb; x0 < xe; x0 += 32) {
-        const int ej = o0 + lane < ns ? sc->end[o0 + lane] : INT_MAX;
-        const unsigned bitv = (ej > x0 && ej <= x0 + 32) ? (1u << (ej - x0 - 1)) : 0u;
-        const unsigned mask = __reduce_or_sync(0xffffffffu, bitv);
-        const int oi = o0 + __popc(mask & ((1u << lane) - 1u));
-        const int pe0 = o0 > 0 ? sc->end[o0 - 1] : 0;
-        const int src = oi - 1 - o0;
-        const int pe = __shfl_sync(0xffffffffu, ej, src < 0 ? 0 : src);
-        const int prev_end = src < 0 ? pe0 : pe;
-        const int x = x0 + lane;
-        f(x < xe, oi, x - prev_end);
-        o0 += __popc(mask);
+// Flattened walk over the products of rows [R0, R1) of column bs..be of B: B's
+// entries in chunks of RT_BLOCK; per entry the part of A(:,k) inside the rows
+// (two binary searches), compacted into segments; each warp takes a contiguous
+// slice of the chunk's products, four 32-product windows per step with every load
+// issued before the updates.  f(row, a, b) is called for each product (a and b,
+// the A and B values, only when NUM).  Ends with a CTA barrier.
+template <class SR, bool NUM, class F>
+__device__ __forceinline__ void slab_walk(const Items& it, const Prod* pr, int64_t bs, int64_t be, int64_t R0,
+                                          int64_t R1, int64_t m, RangeSmem* sc, F&& f) {
+    using T = typename SR::T;
+    constexpr int U = 4, NWARP = RT_BLOCK / 32;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int32_t* __restrict__ air = pr->A.ir;
+    for (int64_t b0 = bs; b0 < be; b0 += RT_BLOCK) {
+        const int64_t t = b0 + tid;
+        int len = 0;
+        int64_t a = 0, bvbits = 0;
+        if (t < be) {
+            const int32_t k = __ldg(pr->B.ir + t);
+            int64_t s, en;
+            a_col(it, pr, t, k, s, en);
+            a = R0 == 0 ? s : s + lower_bound_rows(air + s, en - s, R0);
+            const int64_t b = R1 == m ? en : s + lower_bound_rows(air + s, en - s, R1);
+            len = (int)(b - a);
+            if constexpr (NUM) *reinterpret_cast<T*>(&bvbits) = load_val<SR>(pr->B, t);
+        }
+        int ns, Tn;
+        rt_compact(sc, t < be, len, a, bvbits, ns, Tn);
+        const int C = (Tn + NWARP * 32 - 1) / (NWARP * 32) * 32;
+        const int xb = warp * C, xe = min(Tn, xb + C);
+        if (xb < xe) {
+            int lo = 0, hi = ns;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (sc->end[mid] <= xb) lo = mid + 1;
+                else hi = mid;
+            }
+            int o0 = lo;
+            for (int x0 = xb; x0 < xe; x0 += 32 * U) {
+                int64_t idx[U];
+                bool ok[U];
+                int ob[U];
+#pragma unroll
+                for (int uu = 0; uu < U; ++uu) {
+                    const int xw = x0 + 32 * uu;
+                    const int oi = warp_window_segment(sc->end, ns, xw, o0);
+                    ok[uu] = xw + lane < xe;
+                    ob[uu] = oi;
+                    idx[uu] = ok[uu] ? sc->start[oi] + (xw + lane - (oi ? sc->end[oi - 1] : 0)) : 0;
+                }
+                int32_t row[U];
+                T av[U];
+#pragma unroll
+                for (int uu = 0; uu < U; ++uu) {
+                    row[uu] = ok[uu] ? __ldg(air + idx[uu]) : INT_MIN;
+                    if constexpr (NUM) av[uu] = ok[uu] ? load_val<SR>(pr->A, idx[uu]) : T(0);
+                }
+#pragma unroll
+                for (int uu = 0; uu < U; ++uu) {
+                    if (!ok[uu]) continue;
+                    if constexpr (NUM) f(row[uu], av[uu], *reinterpret_cast<const T*>(&sc->bv[ob[uu]]));
+                    else f(row[uu], T(0), T(0));
+                }
+            }
+        }
+        __syncthreads();
     }
 }
 
-// Symbolic range kernel: slab bitmap, count, cut into ranges.
-// registers capped for 3 CTAs per SM (shared memory admits up to 4 with slabs of 2^18 rows)
-__global__ void __launch_bounds__(RT_BLOCK, 3) k_range_sym(Items it, DenseWork dw) {
+// Symbolic slab kernel: mark, count, store the row set.
+__global__ void __launch_bounds__(RT_BLOCK, 2) k_slab_sym(Items it, DenseWork dw) {
     extern __shared__ __align__(16) unsigned char smem[];
     RangeSmem* sc = reinterpret_cast<RangeSmem*>(smem);
-    int* s_bw = reinterpret_cast<int*>(smem + sizeof(RangeSmem));          // boundary words
-    int* s_bp = s_bw + RT_MAXB + 1;                                           // set bits before them
-    int* s_misc = s_bp + RT_MAXB + 1;
-    uint32_t* bitmap = reinterpret_cast<uint32_t*>(s_misc + 4);
-    int* s_scan = reinterpret_cast<int*>(sc->wc);
+    uint32_t* bitmap = reinterpret_cast<uint32_t*>(smem + RS_BYTES);
+    int* s_scan = sc->wc;
+    __shared__ long long s_off;
     const int tid = threadIdx.x;
     const int64_t nsym = (int64_t)*dw.nitems;
     for (int64_t w = blockIdx.x; w < nsym; w += gridDim.x) {
@@ -1135,160 +1189,46 @@ __global__ void __launch_bounds__(RT_BLOCK, 3) k_range_sym(Items it, DenseWork d
         slab_rows(m, q, P, R0, R1);
         const int nw = (int)((R1 - R0 + 31) >> 5);
         const int64_t bs = __ldg(pr->B.cp + e.y), be = __ldg(pr->B.cp + e.y + 1);
-        const int32_t* __restrict__ air = pr->A.ir;
         for (int x = tid; x < nw; x += RT_BLOCK) bitmap[x] = 0u;
         __syncthreads();
-        for (int64_t b0 = bs; b0 < be; b0 += RT_BLOCK) {
-            const int64_t t = b0 + tid;
-            int len = 0;
-            int64_t a = 0;
-            if (t < be) {
-                const int32_t k = __ldg(pr->B.ir + t);
-                int64_t s, en;
-                a_col(it, pr, t, k, s, en);
-                a = R0 == 0 ? s : s + lower_bound_rows(air + s, en - s, R0);
-                const int64_t b = R1 == m ? en : s + lower_bound_rows(air + s, en - s, R1);
-                len = (int)(b - a);
-            }
-            int ns, T;
-            rt_compact(sc, t < be, len, a, 0, ns, T);
-            // warp slices, 4 windows of 32 products per step: all row loads issued before the marks
-            {
-                constexpr int U = 4, NWARP = RT_BLOCK / 32;
-                const int lane = tid & 31, warp = tid >> 5;
-                const int C = (T + NWARP * 32 - 1) / (NWARP * 32) * 32;
-                const int xb = warp * C, xe = min(T, xb + C);
-                if (xb < xe) {
-                    int lo = 0, hi = ns;
-                    while (lo < hi) {
-                        const int mid = (lo + hi) >> 1;
-                        if (sc->end[mid] <= xb) lo = mid + 1;
-                        else hi = mid;
-                    }
-                    int o0 = lo;
-                    for (int x0 = xb; x0 < xe; x0 += 32 * U) {
-                        int64_t idx[U];
-                        bool ok[U];
-#pragma unroll
-                        for (int uu = 0; uu < U; ++uu) {
-                            const int xw = x0 + 32 * uu;
-                            const int oi = warp_window_segment(sc->end, ns, xw, o0);
-                            ok[uu] = xw + lane < xe;
-                            idx[uu] = ok[uu] ? sc->start[oi] + (xw + lane - (oi ? sc->end[oi - 1] : 0)) : 0;
-                        }
-                        int32_t row[U];
-#pragma unroll
-                        for (int uu = 0; uu < U; ++uu) row[uu] = ok[uu] ? __ldg(air + idx[uu]) : INT_MIN;
-#pragma unroll
-                        for (int uu = 0; uu < U; ++uu) {
-                            if (!ok[uu]) continue;
-                            const int lr = (int)(row[uu] - R0);
-                            if ((unsigned)lr < (unsigned)(R1 - R0)) atomicOr(&bitmap[lr >> 5], 1u << (lr & 31));
-                        }
-                    }
-                }
-            }
-            __syncthreads();
-        }
-        // count per thread over a contiguous word range, then cut into ranges
+        const int span = (int)(R1 - R0);
+        slab_walk<BOOL8, false>(it, pr, bs, be, R0, R1, m, sc, [&](int32_t row, uint8_t, uint8_t) {
+            const int lr = (int)(row - R0);
+            if ((unsigned)lr < (unsigned)span) atomicOr(&bitmap[lr >> 5], 1u << (lr & 31));
+        });
+        // count over contiguous word ranges, then store the row set
         const int wpt = (nw + RT_BLOCK - 1) / RT_BLOCK;
         const int w0 = min(tid * wpt, nw), w1 = min(w0 + wpt, nw);
         int cnt = 0;
         for (int x = w0; x < w1; ++x) cnt += __popc(bitmap[x]);
         int total;
         const int excl = group_incl_scan<RT_BLOCK>(cnt, s_scan, total) - cnt;
-        // Entries before each window of WW words (the numeric bitmap's reach): every
-        // window is cut into the fewest ranges of < H entries, of equal size, so a
-        // window never leaves a small remainder range.
-        int* s_win = reinterpret_cast<int*>(sc->ws);   // <= 33 windows per slab (RB <= 2^20 rows)
-        {
-            int bp = excl;
-            for (int x = w0; x < w1; ++x) {
-                if (x % dw.WW == 0) s_win[x / dw.WW] = bp;
-                bp += __popc(bitmap[x]);
+        const bool dense = total >= nw;
+        const int64_t size = dense ? nw : total;
+        if (tid == 0) {
+            long long off = size > 0 ? (long long)atomicAdd(dw.store_ctr, (unsigned long long)size) : 0;
+            if (off + size > dw.store_cap) {
+                atomicExch(dw.err, 3);
+                off = -1;
             }
-            if (tid == 0) s_win[(nw + dw.WW - 1) / dw.WW] = total;
+            dw.soff[w] = off;
+            dw.scount[w] = total;
+            s_off = off;
         }
         __syncthreads();
-        // cut words of this thread's word range, as a mask (wpt <= 64 words): a window
-        // start, or the first word at or past the window's next multiple of `size`
-        uint64_t cuts = 0;
-        {
-            int bp = excl, base = 0, size = 1, next = INT_MAX;
-            for (int x = w0; x < w1; ++x) {
-                const bool wstart = x % dw.WW == 0;
-                if (wstart || x == w0) {
-                    base = s_win[x / dw.WW];
-                    const int e = s_win[x / dw.WW + 1] - base;
-                    const int nr = (e + dw.H - 1) / dw.H;
-                    size = nr > 0 ? (e + nr - 1) / nr : 1;
-                    // the next multiple of size above the entries before word x - 1
-                    const int prev = wstart ? bp : bp - __popc(bitmap[x - 1]);
-                    next = base + ((prev - base) / size + 1) * size;
-                }
-                if (wstart || bp >= next) {
-                    cuts |= 1ull << (x - w0);
-                    if (!wstart) next = base + ((bp - base) / size + 1) * size;
-                }
-                bp += __popc(bitmap[x]);
-            }
-        }
-        const int nb = __popcll(cuts);
-        int nbt;
-        const int bexcl = group_incl_scan<RT_BLOCK>(nb, s_scan, nbt) - nb;
-        {
-            int bp = excl, o = bexcl;
-            for (int x = w0; x < w1; ++x) {
-                if ((cuts >> (x - w0)) & 1) {
-                    if (o < RT_MAXB) {
-                        s_bw[o] = x;
-                        s_bp[o] = bp;
+        const long long off = s_off;
+        if (off >= 0 && size > 0) {
+            uint32_t* __restrict__ out = dw.store + off;
+            if (dense) {
+                for (int x = tid; x < nw; x += RT_BLOCK) out[x] = bitmap[x];
+            } else {
+                int r = excl;
+                for (int x = w0; x < w1; ++x) {
+                    uint32_t bits = bitmap[x];
+                    while (bits) {
+                        out[r++] = (uint32_t)(R0 + x * 32 + __ffs(bits) - 1);
+                        bits &= bits - 1;
                     }
-                    ++o;
-                }
-                bp += __popc(bitmap[x]);
-            }
-        }
-        if (tid == 0) {
-            const int nbc = nbt < RT_MAXB ? nbt : RT_MAXB;
-            s_bw[nbc] = nw;
-            s_bp[nbc] = total;
-            if (nbt > RT_MAXB) atomicExch(dw.err, 1);
-        }
-        __syncthreads();
-        const int nbc = nbt < RT_MAXB ? nbt : RT_MAXB;
-        // nonempty ranges in row order: thread tid owns ranges [i0, i1)
-        const int ipt = (nbc + RT_BLOCK - 1) / RT_BLOCK;
-        const int i0 = min(tid * ipt, nbc), i1 = min(i0 + ipt, nbc);
-        int ne = 0;
-        for (int i = i0; i < i1; ++i) ne += s_bp[i + 1] > s_bp[i];
-        int net;
-        const int neexcl = group_incl_scan<RT_BLOCK>(ne, s_scan, net) - ne;
-        if (tid == 0) {
-            unsigned long long base = net ? atomicAdd(dw.parts_ctr, (unsigned long long)net) : 0ull;
-            const bool over = base + (unsigned long long)net > (unsigned long long)dw.parts_cap;
-            if (over) atomicExch(dw.err, 2);
-            s_misc[0] = over ? 1 : 0;
-            dw.pbase[w] = over ? 0 : (int64_t)base;
-            dw.pcnt[w] = over ? 0 : net;
-            dw.part_count[(int64_t)q * dw.ndense + d] = total;
-        }
-        __syncthreads();
-        if (!s_misc[0]) {
-            const int64_t base = dw.pbase[w];
-            int o = neexcl;
-            for (int i = i0; i < i1; ++i) {
-                if (s_bp[i + 1] > s_bp[i]) {
-                    RangePart rp;
-                    rp.d = d;
-                    rp.q = q;
-                    rp.r0 = (int32_t)(R0 + (int64_t)s_bw[i] * 32);
-                    const int64_t r1 = R0 + (int64_t)s_bw[i + 1] * 32;
-                    rp.r1 = (int32_t)(r1 < R1 ? r1 : R1);
-                    rp.off = s_bp[i];
-                    rp.nnz = s_bp[i + 1] - s_bp[i];
-                    dw.parts[base + o] = rp;
-                    ++o;
                 }
             }
         }
@@ -1296,272 +1236,153 @@ __global__ void __launch_bounds__(RT_BLOCK, 3) k_range_sym(Items it, DenseWork d
     }
 }
 
-// Numeric range kernel: walk the ranges of a slab with per-k cursors.
-template <class SR, int TBL>
-__global__ void __launch_bounds__(RT_BLOCK) k_range_num(Items it, DenseWork dw, const int64_t* __restrict__ Coff,
-                                                        int32_t* __restrict__ Cir, typename SR::T* __restrict__ Cv) {
-    using Acc = typename SR::Acc;
+// C[pos] = C[pos] (+) v in global memory (an L2 reduction; the return value is unused).
+template <class SR>
+__device__ __forceinline__ void red_out(typename SR::T* Cv, int64_t pos, typename SR::Acc v) {
+    if constexpr (SR::id == SPGEMM_OR_AND_BOOL) {
+        if (v) {
+            const uintptr_t a = reinterpret_cast<uintptr_t>(Cv + pos);
+            atomicOr(reinterpret_cast<unsigned int*>(a & ~uintptr_t(3)), 1u << ((a & 3) * 8));
+        }
+    } else if constexpr (SR::id == SPGEMM_PLUS_TIMES_I64) {
+        atomicAdd(reinterpret_cast<unsigned long long*>(Cv + pos), v);
+    } else {
+        SR::atomic_add(Cv + pos, v);   // double add; float min through integer min / max
+    }
+}
+
+// Numeric slab kernel: row set -> ranks -> C's rows, zero values, L2 reductions.
+template <class SR>
+__global__ void __launch_bounds__(RT_BLOCK, 2) k_slab_num(Items it, DenseWork dw, const int64_t* __restrict__ Coff,
+                                                          int32_t* __restrict__ Cir, typename SR::T* __restrict__ Cv) {
     using T = typename SR::T;
-    constexpr int LOG2 = __builtin_ctz(TBL);
-    constexpr int NWARP = RT_BLOCK / 32;
     extern __shared__ __align__(16) unsigned char smem[];
     RangeSmem* sc = reinterpret_cast<RangeSmem*>(smem);
-    int32_t* keys = reinterpret_cast<int32_t*>(smem + sizeof(RangeSmem));
-    Acc* vals = reinterpret_cast<Acc*>(smem + sizeof(RangeSmem) + (size_t)TBL * 4);
-    uint32_t* bitmap = reinterpret_cast<uint32_t*>(smem + sizeof(RangeSmem) + (size_t)TBL * (4 + sizeof(Acc)));
-    // next row of A(:,k) at the cursor, for the first RT_NEXT k's: a range that ends at or
-    // before it gets nothing from that k, which is then skipped without touching memory
-    int32_t* s_next = reinterpret_cast<int32_t*>(bitmap + dw.WW);
-    // cursor state of the first RT_NEXT k's: position in A.ir and entries left in A(:,k)
-    int32_t* s_rem = s_next + RT_NEXT;
-    int64_t* s_pos = reinterpret_cast<int64_t*>(s_rem + RT_NEXT);
-    volatile int32_t* vkeys = keys;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t* bitmap = reinterpret_cast<uint32_t*>(smem + RS_BYTES);              // groups * 4 words
+    int* gp = reinterpret_cast<int*>(bitmap + (size_t)(dw.RB / 128 + 1) * 4);    // rows before each group
+    int* s_scan = sc->wc;
+    const int tid = threadIdx.x;
+    // boolean products whose operands hold no false value: every output is true
+    const bool walk = SR::id != SPGEMM_OR_AND_BOOL || dw.vals_zero == nullptr || *dw.vals_zero != 0;
+    const T init = walk ? SR::out(SR::zero()) : T(1);
     const int64_t nsym = (int64_t)*dw.nitems;
-    for (int x = tid; x < TBL; x += RT_BLOCK) {
-        keys[x] = -1;
-        vals[x] = SR::zero();
-    }
-    __syncthreads();
     for (int64_t w = blockIdx.x; w < nsym; w += gridDim.x) {
+        const int cnt = dw.scount[w];
+        // the same for every thread of the CTA; a row set that found no room (possible
+        // only with malformed input, reported by the symbolic pass) is skipped
+        if (cnt == 0 || dw.soff[w] < 0) continue;
         const int2 itm = dw.items[w];
         const int d = itm.x, q = itm.y;
         const int2 e = __ldg(dw.dlist + d);
         const Prod* pr = it.prods + e.x;
         const int P = dw.nparts[d];
         const int64_t m = pr->A.m;
-        const int64_t u = __ldg(it.item_base + e.x) + e.y;
-        const int32_t rb = out_row_base(pr, e.y);
         int64_t R0, R1;
         slab_rows(m, q, P, R0, R1);
-        const int64_t bs = __ldg(pr->B.cp + e.y), be = __ldg(pr->B.cp + e.y + 1);
-        const int64_t deg = be - bs;
-        const int32_t* __restrict__ air = pr->A.ir;
-        // cursor slots are indexed relative to the product's first B position (blocks share arrays)
-        // beyond the first RT_NEXT k's: (cursor offset in A(:,k), row at the cursor) in global memory
-        int2* cur = dw.cursors + (int64_t)q * it.total_bnz + pr->bnz_base + (bs - __ldg(pr->B.cp));
-        for (int64_t t = tid; t < deg; t += RT_BLOCK) {
-            const int32_t k = __ldg(pr->B.ir + bs + t);
-            int64_t s, en;
-            a_col(it, pr, bs + t, k, s, en);
-            const int32_t c0 = R0 == 0 ? 0 : lower_bound_rows(air + s, en - s, R0);
-            const int32_t nx = s + c0 < en ? __ldg(air + s + c0) : INT_MAX;
-            if (t < RT_NEXT) {
-                s_pos[t] = s + c0;
-                s_rem[t] = (int32_t)(en - s - c0);
-                s_next[t] = nx;
-            } else {
-                cur[t] = make_int2(c0, nx);
+        const int nw = (int)((R1 - R0 + 31) >> 5);
+        const int ng = (nw + 3) >> 2;
+        const int64_t u = __ldg(it.item_base + e.x) + e.y;
+        const int32_t rb = out_row_base(pr, e.y);
+        const int64_t ob = __ldg(Coff + u) + dw.spref[w];
+        const uint32_t* __restrict__ rs = dw.store + dw.soff[w];
+        const bool dense = cnt >= nw;
+        // 1. the slab's row bitmap (padded to whole groups)
+        if (dense) {
+            for (int x = tid; x < ng * 4; x += RT_BLOCK) bitmap[x] = x < nw ? __ldg(rs + x) : 0u;
+        } else {
+            for (int x = tid; x < ng * 4; x += RT_BLOCK) bitmap[x] = 0u;
+            __syncthreads();
+            for (int i0 = 0; i0 < cnt; i0 += RT_BLOCK) {   // every thread of a warp takes part
+                const int i = i0 + tid;
+                const int32_t r = i < cnt ? (int32_t)__ldg(rs + i) : -1;
+                const int lr = (int)(r - R0);
+                if (i < cnt) Cir[ob + i] = r + rb;    // C's rows: the row list itself
+                or_bits_warp(bitmap, i < cnt ? (lr >> 5) : -1, 1u << (lr & 31));
             }
         }
-        int64_t outbase = __ldg(Coff + u);
-        for (int qq = 0; qq < q; ++qq) outbase += dw.part_count[(int64_t)qq * dw.ndense + d];
-        const int64_t pb = dw.pbase[w];
-        const int np = dw.pcnt[w];
         __syncthreads();
-        for (int ip = 0; ip < np; ++ip) {
-            const RangePart rp = dw.parts[pb + ip];
-            const int64_t r0 = rp.r0, r1 = rp.r1;
-            const int nw = (int)((r1 - r0 + 31) >> 5);
-            const bool direct = r1 - r0 <= TBL;
-            for (int x = tid; x < nw; x += RT_BLOCK) bitmap[x] = 0u;
-            __syncthreads();
-            for (int64_t b0 = 0; b0 < deg; b0 += RT_BLOCK) {
-                const int64_t t = b0 + tid;
-                int len = 0;
-                int64_t a = 0;
-                T bv = T(0);
-                // a k whose next row lies at or past r1 gives nothing to this range
-                int2 cv = make_int2(0, INT_MAX);
-                if (t < deg && t >= RT_NEXT) cv = cur[t];
-                const bool act = t < deg && (t < RT_NEXT ? s_next[t] < r1 : cv.y < r1);
-                if (b0 >= RT_NEXT && !__syncthreads_or(act)) continue;   // a chunk with nothing for the range
-                if (act) {
-                    bv = load_val<SR>(pr->B, bs + t);
-                    if (t < RT_NEXT) {
-                        a = s_pos[t];
-                        const int64_t en = a + s_rem[t];
-                        int32_t nx;
-                        const int64_t c = count_below(air, a, en, r1, nx);
-                        s_pos[t] = a + c;
-                        s_rem[t] -= (int32_t)c;
-                        s_next[t] = nx;
-                        len = (int)c;
-                    } else {
-                        const int32_t k = __ldg(pr->B.ir + bs + t);
-                        int64_t s, en;
-                        a_col(it, pr, bs + t, k, s, en);
-                        a = s + cv.x;
-                        int32_t nx;
-                        const int64_t c = count_below(air, a, en, r1, nx);
-                        cur[t] = make_int2(cv.x + (int32_t)c, nx);
-                        len = (int)c;
-                    }
-                }
-                int64_t bvbits = 0;
-                *reinterpret_cast<T*>(&bvbits) = bv;
-                int ns, Tn;
-                rt_compact(sc, act, len, a, bvbits, ns, Tn);
-                // warp slices of the products, 4 windows of 32 per step: owners first, then all
-                // loads, then the accumulations, so each warp keeps several loads in flight
-                {
-                    constexpr int U = 4;
-                    const int C = (Tn + NWARP * 32 - 1) / (NWARP * 32) * 32;
-                    const int xb = warp * C, xe = min(Tn, xb + C);
-                    if (xb < xe) {
-                        int lo = 0, hi = ns;
-                        while (lo < hi) {
-                            const int mid = (lo + hi) >> 1;
-                            if (sc->end[mid] <= xb) lo = mid + 1;
-                            else hi = mid;
-                        }
-                        int o0 = lo;
-                        for (int x0 = xb; x0 < xe; x0 += 32 * U) {
-                            int64_t idx[U];
-                            bool ok[U];
-                            int ob[U];
+        // 2. rows before every group: thread tid owns groups [g0, g1)
+        {
+            const int gpt = (ng + RT_BLOCK - 1) / RT_BLOCK;
+            const int g0 = min(tid * gpt, ng), g1 = min(g0 + gpt, ng);
+            int c = 0;
+            for (int x = g0 * 4; x < g1 * 4; ++x) c += __popc(bitmap[x]);
+            int total;
+            int r = group_incl_scan<RT_BLOCK>(c, s_scan, total) - c;
+            for (int g = g0; g < g1; ++g) {
+                gp[g] = r;
+                r += __popc(bitmap[4 * g]) + __popc(bitmap[4 * g + 1]) + __popc(bitmap[4 * g + 2]) +
+                     __popc(bitmap[4 * g + 3]);
+            }
+        }
+        __syncthreads();
+        // 3. C's rows of a bitmap slab (one group per thread: consecutive threads, consecutive ranks)
+        if (dense) {
+            for (int g = tid; g < ng; g += RT_BLOCK) {
+                int r = gp[g];
+                const uint4 grp = reinterpret_cast<const uint4*>(bitmap)[g];
+                const uint32_t wv[4] = {grp.x, grp.y, grp.z, grp.w};
 #pragma unroll
-                            for (int uu = 0; uu < U; ++uu) {
-                                const int xw = x0 + 32 * uu;
-                                const int ej = o0 + lane < ns ? sc->end[o0 + lane] : INT_MAX;
-                                const unsigned bitv = (ej > xw && ej <= xw + 32) ? (1u << (ej - xw - 1)) : 0u;
-                                const unsigned mask = __reduce_or_sync(0xffffffffu, bitv);
-                                const int oi = o0 + __popc(mask & ((1u << lane) - 1u));
-                                const int pe0 = o0 > 0 ? sc->end[o0 - 1] : 0;
-                                const int src = oi - 1 - o0;
-                                const int pe = __shfl_sync(0xffffffffu, ej, src < 0 ? 0 : src);
-                                ok[uu] = xw + lane < xe;
-                                ob[uu] = oi;
-                                idx[uu] = ok[uu] ? sc->start[oi] + (xw + lane - (src < 0 ? pe0 : pe)) : 0;
-                                o0 += __popc(mask);
-                            }
-                            int32_t row[U];
-                            T av[U];
-#pragma unroll
-                            for (int uu = 0; uu < U; ++uu) {
-                                row[uu] = ok[uu] ? __ldg(air + idx[uu]) : 0;
-                                av[uu] = ok[uu] ? load_val<SR>(pr->A, idx[uu]) : T(0);
-                            }
-#pragma unroll
-                            for (int uu = 0; uu < U; ++uu) {
-                                if (!ok[uu]) continue;
-                                const int lr = (int)(row[uu] - r0);
-                                if ((unsigned)lr >= (unsigned)(r1 - r0)) continue;   // only on malformed input
-                                uint32_t h;
-                                if (direct) {
-                                    h = (uint32_t)lr;      // narrow range: the table is a dense row array,
-                                    keys[h] = row[uu];     // keys[] only marks occupancy
-                                } else {
-                                    h = hash_row(row[uu]) >> (32 - LOG2);
-                                    while (true) {
-                                        int32_t cu = vkeys[h];
-                                        if (cu == row[uu]) break;
-                                        if (cu == -1) {
-                                            int32_t prev = atomicCAS(&keys[h], -1, row[uu]);
-                                            if (prev == -1 || prev == row[uu]) break;
-                                        }
-                                        h = (h + 1) & (TBL - 1);
-                                    }
-                                }
-                                SR::atomic_add(&vals[h], SR::mul(av[uu], *reinterpret_cast<const T*>(&sc->bv[ob[uu]])));
-                            }
-                        }
-                    }
-                }
-                __syncthreads();
-            }
-            // the range's row bitmap, built once from the occupied table slots
-            if (direct) {
-                for (int wd = warp; wd < nw; wd += NWARP) {
-                    const unsigned occ = __ballot_sync(0xffffffffu, keys[wd * 32 + lane] != -1);
-                    if (lane == 0) bitmap[wd] = occ;
-                }
-            } else {
-                for (int x = tid; x < TBL; x += RT_BLOCK) {
-                    const int32_t kr = keys[x];
-                    if (kr != -1) {
-                        const int lr = (int)(kr - r0);
-                        atomicOr(&bitmap[lr >> 5], 1u << (lr & 31));
+                for (int y = 0; y < 4; ++y) {
+                    uint32_t bits = wv[y];
+                    const int32_t base = (int32_t)(R0 + (int64_t)(4 * g + y) * 32) + rb;
+                    while (bits) {
+                        Cir[ob + r++] = base + __ffs(bits) - 1;
+                        bits &= bits - 1;
                     }
                 }
             }
-            __syncthreads();
-            // Output in row order without sorting: the rank of row lr in the range is the
-            // number of bitmap bits below it, from per-group prefixes (4 words = 128 rows
-            // per group, one group per thread) plus at most 4 words of popcounts.  Each
-            // occupied slot writes its entry at that rank and empties itself.
-            int* s_gp = sc->end;   // free once the range's products are accumulated
-            int marked;            // rows in the range's bitmap
-            {
-                const int x0 = tid * 4;
-                int c = 0;
-                for (int x = x0; x < x0 + 4 && x < nw; ++x) c += __popc(bitmap[x]);
-                s_gp[tid] = group_incl_scan<RT_BLOCK>(c, sc->wc, marked) - c;
-            }
-            __syncthreads();
-            {
-                const int64_t ob = outbase + rp.off;
-                if (direct) {
-                    // slots are rows: ranks grow with the slot, so the stores are nearly coalesced
-                    const int nslots = (int)(r1 - r0);
-                    for (int x = tid; x < nslots; x += RT_BLOCK) {
-                        const int32_t kr = keys[x];
-                        if (kr == -1) continue;
-                        const int wd = x >> 5;
-                        int rank = s_gp[wd >> 2] + __popc(bitmap[wd] & ((1u << (x & 31)) - 1u));
-                        for (int y = wd & ~3; y < wd; ++y) rank += __popc(bitmap[y]);
-                        Cir[ob + rank] = kr + rb;
-                        Cv[ob + rank] = SR::out(vals[x]);
-                        keys[x] = -1;
-                        vals[x] = SR::zero();
-                    }
-                } else {
-                    // hashed slots: record the slot of every rank first, then store in rank
-                    // order, so consecutive threads write consecutive entries
-                    uint16_t* order = reinterpret_cast<uint16_t*>(sc->start);   // spans start and bv
-                    for (int x = tid; x < TBL; x += RT_BLOCK) {
-                        const int32_t kr = keys[x];
-                        if (kr == -1) continue;
-                        const int lr = (int)(kr - r0);
-                        const int wd = lr >> 5;
-                        int rank = s_gp[wd >> 2] + __popc(bitmap[wd] & ((1u << (lr & 31)) - 1u));
-                        for (int y = wd & ~3; y < wd; ++y) rank += __popc(bitmap[y]);
-                        order[rank] = (uint16_t)x;
-                    }
-                    __syncthreads();
-                    for (int i = tid; i < marked; i += RT_BLOCK) {
-                        const int x = order[i];
-                        Cir[ob + i] = keys[x] + rb;
-                        Cv[ob + i] = SR::out(vals[x]);
-                        keys[x] = -1;
-                        vals[x] = SR::zero();
-                    }
-                }
-            }
+        }
+        // 4. values: the semiring zero (all true for the boolean shortcut)
+        for (int i = tid; i < cnt; i += RT_BLOCK) Cv[ob + i] = init;
+        __syncthreads();   // the stores above come before this CTA's reductions
+        // 5. every product, added at its row's rank
+        if (walk) {
+            const int span = (int)(R1 - R0);
+            slab_walk<SR, true>(it, pr, __ldg(pr->B.cp + e.y), __ldg(pr->B.cp + e.y + 1), R0, R1, m, sc,
+                                [&](int32_t row, T a, T b) {
+                                    const int lr = (int)(row - R0);
+                                    if ((unsigned)lr >= (unsigned)span) return;   // malformed input only
+                                    const int wd = lr >> 5, g = wd >> 2, y = wd & 3;
+                                    const uint4 grp = reinterpret_cast<const uint4*>(bitmap)[g];
+                                    const uint32_t wv = y == 0 ? grp.x : y == 1 ? grp.y : y == 2 ? grp.z : grp.w;
+                                    const uint32_t bit = 1u << (lr & 31);
+                                    if (!(wv & bit)) return;                      // malformed input only
+                                    const int rank = gp[g] + __popc(wv & (bit - 1u)) + (y > 0 ? __popc(grp.x) : 0) +
+                                                     (y > 1 ? __popc(grp.y) : 0) + (y > 2 ? __popc(grp.z) : 0);
+                                    red_out<SR>(Cv, ob + rank, SR::mul(a, b));
+                                });
+        } else {
             __syncthreads();
         }
     }
 }
 
+// CTAs per SM the kernel can keep resident with `smem` bytes, times the SM count
+static int resident_grid(const void* fn, int block, size_t smem) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, smem) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    return per_sm * sm_count();
+}
+
 template <class SR>
-static void run_range(cudaStream_t st, const Items& it, const DenseWork& dw, bool numeric, const int64_t* Coff,
+static void run_slabs(cudaStream_t st, const Items& it, const DenseWork& dw, bool numeric, const int64_t* Coff,
                       int32_t* Cir, typename SR::T* Cv) {
     if (dw.ndense <= 0) return;
-    const int grid = (int)std::min<int64_t>(dw.ndense * MAX_PARTS, 152 * 8);
+    const int64_t nslab_max = dw.nslabs > 0 ? dw.nslabs : dw.ndense * MAX_PARTS;
     if (!numeric) {
-        const size_t smem = sizeof(RangeSmem) + 2 * (RT_MAXB + 1) * 4 + 16 + (size_t)(dw.RB / 32) * 4;
-        smem_at_least((const void*)k_range_sym, smem);
-        k_range_sym<<<grid, RT_BLOCK, smem, st>>>(it, dw);
+        const size_t smem = RS_BYTES + (size_t)(dw.RB / 32) * 4;
+        smem_at_least((const void*)k_slab_sym, smem);
+        const int grid = (int)std::min<int64_t>(nslab_max, resident_grid((const void*)k_slab_sym, RT_BLOCK, smem));
+        k_slab_sym<<<grid, RT_BLOCK, smem, st>>>(it, dw);
     } else {
-        auto go = [&](auto kern, int tbl) {
-            const size_t smem = sizeof(RangeSmem) + (size_t)tbl * (4 + sizeof(typename SR::Acc)) + (size_t)(dw.WW) * 4 +
-                                (size_t)RT_NEXT * 16;
-            smem_at_least((const void*)kern, smem);
-            kern<<<grid, RT_BLOCK, smem, st>>>(it, dw, Coff, Cir, Cv);
-        };
-        if (dw.tbl <= 2048) go(k_range_num<SR, 2048>, 2048);
-        else if (dw.tbl <= 4096) go(k_range_num<SR, 4096>, 4096);
-        else go(k_range_num<SR, 8192>, 8192);
+        const size_t smem = RS_BYTES + (size_t)(dw.RB / 128 + 1) * 16 + (size_t)(dw.RB / 128 + 1) * 4;
+        smem_at_least((const void*)k_slab_num<SR>, smem);
+        const int grid = (int)std::min<int64_t>(nslab_max, resident_grid((const void*)k_slab_num<SR>, RT_BLOCK, smem));
+        k_slab_num<SR><<<grid, RT_BLOCK, smem, st>>>(it, dw, Coff, Cir, Cv);
     }
     note_launch();
 }
@@ -1588,7 +1409,7 @@ __global__ void __launch_bounds__(RT_BLOCK) k_dcol(Items it, const int2* __restr
     constexpr int NWARP = RT_BLOCK / 32;
     extern __shared__ __align__(16) unsigned char smem[];
     RangeSmem* sc = reinterpret_cast<RangeSmem*>(smem);
-    Acc* vals = reinterpret_cast<Acc*>(smem + sizeof(RangeSmem));   // mcap
+    Acc* vals = reinterpret_cast<Acc*>(smem + RS_BYTES);   // mcap
     uint32_t* bitmap = reinterpret_cast<uint32_t*>(vals + mcap);    // mcap / 32
     int* s_scan = reinterpret_cast<int*>(bitmap + mcap / 32);       // 34
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1699,11 +1520,10 @@ template <class SR>
 static void run_dcol(cudaStream_t st, const Items& it, const DenseWork& dw, const int64_t* Coff, int32_t* Cir,
                      typename SR::T* Cv) {
     if (dw.ndense <= 0) return;
-    const size_t smem = sizeof(RangeSmem) + (size_t)dw.mcap * sizeof(typename SR::Acc) + (size_t)(dw.mcap / 32) * 4 +
-                        34 * 4;
+    const size_t smem = RS_BYTES + (size_t)dw.mcap * sizeof(typename SR::Acc) + (size_t)(dw.mcap / 32) * 4 + 34 * 4;
     smem_at_least((const void*)k_dcol<SR>, smem);
     const int per_sm = smem <= 72 * 1024 ? 3 : smem <= 110 * 1024 ? 2 : 1;
-    const int grid = (int)std::min<int64_t>(dw.ndense, 152 * per_sm);
+    const int grid = (int)std::min<int64_t>(dw.ndense, sm_count() * per_sm);
     k_dcol<SR><<<grid, RT_BLOCK, smem, st>>>(it, dw.dlist, dw.ndense, dw.mcap, Coff, Cir, Cv);
     note_launch();
 }
@@ -1722,7 +1542,7 @@ void launch_symbolic(cudaStream_t st, const Items& it, TierCfg cfg, const int2* 
     if (which & 1) run_hash_bins<SR, false>(st, it, list, bin_off, bin_cnt, nnz_item, nullptr, nullptr, nullptr);
     if (which & 2) {
         if (dw.dcol) run_bitcount<256, 256>(st, it, dw.dlist, dw.ndense, nnz_item);   // rows fit the bitmap
-        else run_range<SR>(st, it, dw, false, nullptr, nullptr, nullptr);
+        else run_slabs<SR>(st, it, dw, false, nullptr, nullptr, nullptr);
     }
 }
 
@@ -1734,7 +1554,7 @@ void launch_numeric(cudaStream_t st, const Items& it, TierCfg cfg, const int2* l
     if (which & 1) run_hash_bins<SR, true>(st, it, list, bin_off, bin_cnt, nullptr, Coff, Cir, Cv);
     if (which & 2) {
         if (dw.dcol) run_dcol<SR>(st, it, dw, Coff, Cir, Cv);
-        else run_range<SR>(st, it, dw, true, Coff, Cir, Cv);
+        else run_slabs<SR>(st, it, dw, true, Coff, Cir, Cv);
     }
 }
 
@@ -1754,21 +1574,25 @@ SG_INST(PTI64)
 
 
 // ------------------------------------------------------------------ part sums, colptrs, stats
-__global__ void k_sum_parts(Items it, const int2* __restrict__ dlist, int64_t nd, const int8_t* __restrict__ nparts,
-                            const int32_t* __restrict__ pc, int64_t* __restrict__ nnz_item) {
-    int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (d >= nd) return;
-    int P = nparts[d];
-    int64_t s = 0;
-    for (int q = 0; q < P; ++q) s += pc[(int64_t)q * nd + d];
-    int2 e = dlist[d];
-    nnz_item[__ldg(it.item_base + e.x) + e.y] = s;
+// nnz of a long column = the sum of its slab counts; spref[s] = rows of the
+// column's earlier slabs (where slab s starts inside the column)
+__global__ void k_sum_parts(Items it, DenseWork dw, int64_t* __restrict__ nnz_item) {
+    const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= dw.ndense) return;
+    const int P = dw.nparts[d];
+    const int64_t s0 = dw.sbase[d];
+    int32_t acc = 0;
+    for (int q = 0; q < P; ++q) {
+        dw.spref[s0 + q] = acc;
+        acc += dw.scount[s0 + q];
+    }
+    const int2 e = dw.dlist[d];
+    nnz_item[__ldg(it.item_base + e.x) + e.y] = acc;
 }
 
-void launch_sum_parts(cudaStream_t st, const Items& it, const int2* dense_list, int64_t ndense, const int8_t* nparts,
-                      const int32_t* part_count, int64_t* nnz_item) {
-    if (ndense == 0 || nparts == nullptr) return;   // no slabs: the dense-column mode counted directly
-    k_sum_parts<<<(int)ceil_div64(ndense, 256), 256, 0, st>>>(it, dense_list, ndense, nparts, part_count, nnz_item);
+void launch_sum_parts(cudaStream_t st, const Items& it, const DenseWork& dw, int64_t* nnz_item) {
+    if (dw.ndense == 0 || dw.dcol) return;   // the dense-column mode counted directly
+    k_sum_parts<<<(int)ceil_div64(dw.ndense, 256), 256, 0, st>>>(it, dw, nnz_item);
     note_launch();
 }
 
@@ -1800,7 +1624,7 @@ __global__ void k_colptrs(Items it, const int64_t* __restrict__ colbase, int64_t
 void launch_colptrs(cudaStream_t st, const Items& it, const int64_t* colbase, int64_t total_cols, const int64_t* Coff,
                     int64_t* out) {
     if (total_cols <= 0) return;
-    int grid = (int)std::min<int64_t>(ceil_div64(total_cols, 256), 152 * 16);
+    int grid = (int)std::min<int64_t>(ceil_div64(total_cols, 256), sm_count() * 16);
     k_colptrs<<<grid, 256, 0, st>>>(it, colbase, total_cols, Coff, out);
     note_launch();
 }
@@ -1812,7 +1636,7 @@ __global__ void k_fill_i64(int64_t* p, int64_t n, int64_t v) {
 
 void launch_fill_i64(cudaStream_t st, int64_t* p, int64_t n, int64_t v) {
     if (n <= 0) return;
-    int grid = (int)std::min<int64_t>(ceil_div64(n, 256), 152 * 16);
+    int grid = (int)std::min<int64_t>(ceil_div64(n, 256), sm_count() * 16);
     k_fill_i64<<<grid, 256, 0, st>>>(p, n, v);
     note_launch();
 }
@@ -1842,7 +1666,7 @@ __global__ void k_tier_stats(Items it, const uint8_t* __restrict__ bin, const in
 void launch_tier_stats(cudaStream_t st, const Items& it, const uint8_t* bin, const int32_t* item_prod,
                        const int64_t* flops, const int64_t* nnz_item, unsigned long long* out) {
     if (it.nitems <= 0) return;
-    int grid = (int)std::min<int64_t>(ceil_div64(it.nitems, 256), 152 * 4);
+    int grid = (int)std::min<int64_t>(ceil_div64(it.nitems, 256), sm_count() * 4);
     k_tier_stats<<<grid, 256, 0, st>>>(it, bin, item_prod, flops, nnz_item, out);
     note_launch();
 }

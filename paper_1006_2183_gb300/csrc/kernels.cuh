@@ -18,7 +18,7 @@ namespace sg {
 //   bin 1                  : flops <= TINY_MAX: one thread, products sorted in registers
 //   bins 2 .. NWARP+1      : warp-wide hash tables of 64 .. 1024 slots (>= 2 cap)
 //   bins NWARP+2 .. +NBLK  : CTA-wide hash tables of 2048 .. 8192 slots (>= 2 cap)
-//   bin NBIN-1             : range tier (row slabs cut into ranges)
+//   bin NBIN-1             : slab tier (long columns cut into row slabs)
 constexpr int NWARP = 5;
 constexpr int NBLK = 3;
 constexpr int NBIN = 2 + NWARP + NBLK + 1;
@@ -29,51 +29,42 @@ constexpr int BIN_DENSE = NBIN - 1;
 constexpr int TINY_MAX = 16;
 constexpr int WARP_TBL0 = 64;
 constexpr int BLK_TBL0 = 2048;
-constexpr int MAX_PARTS = 16;
-// default most rows of one symbolic slab: a 64 KB row bitmap keeps two symbolic CTAs
-// per SM (a 2^20-row slab holds one)
+// most row slabs of one long column
+constexpr int MAX_PARTS = 64;
+// default most rows of one slab: a 64 KB row bitmap keeps two CTAs per SM
 constexpr int DEFAULT_SLAB_ROWS = 1 << 19;
+// default target flops per slab: keeps the output regions that the numeric pass
+// reduces into, for every resident CTA at once, well inside L2
+constexpr int DEFAULT_PART_FLOPS = 32768;
 
 struct TierCfg {
     int warp_max;     // cap <= warp_max -> warp tables (<= 512)
     int block_max;    // cap <= block_max -> CTA tables (<= 4096)
-    int dense_rows;   // RB, most rows of one symbolic slab (bitmap bits in shared memory)
-    int part_flops;   // target flops per symbolic slab of a long column
+    int dense_rows;   // RB, most rows of one slab (bitmap bits in shared memory)
+    int part_flops;   // target flops per slab of a long column
 };
 
-// Range tier: hash-table slots per numeric range (default; 4096 also built), so a
-// range holds < RANGE_TBL / 2 entries.
-constexpr int RANGE_TBL = 8192;
-constexpr int RANGE_H = RANGE_TBL / 2 - 32;   // cut a range once it holds this many entries
-constexpr int RANGE_W = 65536;                // and at most this many rows
-
-struct RangePart {   // one numeric range of a slab
-    int32_t d, q;    // dense-list position, slab
-    int32_t r0, r1;  // rows [r0, r1)
-    int32_t off;     // entries of the slab before this range
-    int32_t nnz;
-};
-
-struct DenseWork {   // state of the range tier shared by its kernels
-    const int2* dlist = nullptr;          // dense items (product, stored column)
+// State of the slab tier shared by its kernels.  Slab s = sbase[d] + q is slab q
+// of long column d (position d in the dense list); items[s] = (d, q).
+struct DenseWork {
+    const int2* dlist = nullptr;          // long columns (product, stored column)
     int64_t ndense = 0;
     const int2* items = nullptr;          // slabs (d, q)
     const unsigned long long* nitems = nullptr;   // device count of slabs
-    const int8_t* nparts = nullptr;       // slabs per dense item
-    int2* cursors = nullptr;              // per slab and k: (position inside A(:,k), row there)
-    int32_t* part_count = nullptr;        // [q][d] entries per slab
-    RangePart* parts = nullptr;
-    unsigned long long* parts_ctr = nullptr;
-    int64_t parts_cap = 0;
-    int64_t* pbase = nullptr;             // per slab: first range
-    int32_t* pcnt = nullptr;              // per slab: number of ranges
+    int64_t nslabs = 0;                   // host copy of the count (0 before it is known)
+    const int8_t* nparts = nullptr;       // slabs per long column
+    const int32_t* sbase = nullptr;       // first slab of each long column
+    int32_t* scount = nullptr;            // rows per slab (symbolic pass)
+    int32_t* spref = nullptr;             // rows of the column's earlier slabs
+    int64_t* soff = nullptr;              // where each slab's row set is stored
+    uint32_t* store = nullptr;            // row sets: bitmap words, or rows ascending
+    int64_t store_cap = 0;                // entries of store
+    unsigned long long* store_ctr = nullptr;
+    const int* vals_zero = nullptr;       // boolean semiring: some operand value is false
     int* err = nullptr;                   // nonzero: a capacity was exceeded
-    int RB = 1 << 20;                     // most rows per slab
-    int H = RANGE_H;                      // cut a range once it holds this many entries (< tbl / 2)
-    int WW = RANGE_W / 32;                // words per range window
-    int tbl = RANGE_TBL;                  // hash slots per numeric range (4096 or 8192)
+    int RB = 1 << 19;                     // most rows per slab
     // dense-column mode (every A_i has at most dcol_rows rows): one CTA per long
-    // column with a dense row array; no slabs, ranges or cursors
+    // column with a dense row array; no slabs
     bool dcol = false;
     int mcap = 0;                         // rows of the dense array (multiple of 32)
 };
@@ -128,12 +119,15 @@ void launch_bin_scatter(cudaStream_t st, const Items& it, const uint8_t* bin, co
 // hash-tier bins from exact counts (after the symbolic pass); cnt[NBIN] accumulates
 void launch_numeric_bins(cudaStream_t st, const Items& it, TierCfg cfg, const uint8_t* bin, const int64_t* flops,
                          const int64_t* nnz_item, uint8_t* nbin, unsigned long long* cnt);
-// range-tier slabs (position d in the dense list, slab q); P_d slabs of at most RB rows each
+// slabs of the long columns (position d in the dense list, slab q); P_d slabs of at
+// most RB rows each; *store_bound accumulates the entries their row sets can need
 void launch_dense_items(cudaStream_t st, const Items& it, const int2* dense_list, int64_t ndense,
                         const int64_t* flops, int part_flops, int RB, int2* items, unsigned long long* nitems,
-                        int8_t* nparts);
+                        int8_t* nparts, int32_t* sbase, unsigned long long* store_bound);
+// *flag = 1 when an operand of some product stores a false value (boolean semiring)
+void launch_false_values(cudaStream_t st, const Items& it, int* flag);
 
-// which: 1 = hash-table tiers, 2 = range tier, 3 = both
+// which: 1 = hash-table tiers, 2 = long columns (slab or dense-column tier), 3 = both
 template <class SR>
 void launch_symbolic(cudaStream_t st, const Items& it, TierCfg cfg, const int2* list, const int64_t* bin_off,
                      const int64_t* bin_cnt, const DenseWork& dw, int64_t* nnz_item, int which = 3);
@@ -149,9 +143,8 @@ void launch_numeric_predicted(cudaStream_t st, const Items& it, const int2* list
                               const int64_t* bin_cnt, const int64_t* cap_off, int64_t* nnz_item, int32_t* Cir,
                               typename SR::T* Cv);
 
-// nnz of dense items = sum of their part counts
-void launch_sum_parts(cudaStream_t st, const Items& it, const int2* dense_list, int64_t ndense, const int8_t* nparts,
-                      const int32_t* part_count, int64_t* nnz_item);
+// nnz of long columns = sum of their slab counts (and each slab's start in its column)
+void launch_sum_parts(cudaStream_t st, const Items& it, const DenseWork& dw, int64_t* nnz_item);
 // per-product column pointers from item offsets: out[colbase_i + j] for j in [0, n_i]
 void launch_colptrs(cudaStream_t st, const Items& it, const int64_t* colbase, int64_t total_cols, const int64_t* Coff,
                     int64_t* out);
@@ -163,6 +156,9 @@ void launch_fill_i64(cudaStream_t st, int64_t* p, int64_t n, int64_t v);
 void launch_tier_stats(cudaStream_t st, const Items& it, const uint8_t* bin, const int32_t* item_prod,
                        const int64_t* flops, const int64_t* nnz_item, unsigned long long* out);
 
+
+// streaming multiprocessors of the current device (queried once per device)
+int sm_count();
 
 // process-wide count of kernel launches made by this library
 void note_launch(int n = 1);

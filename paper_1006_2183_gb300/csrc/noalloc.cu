@@ -38,37 +38,68 @@ std::mutex g_mu;
 long long* g_ptr[64] = {nullptr};
 
 // nnz(C(:,j)) = number of distinct rows over A(:,k), k in B(:,j): rows marked in
-// a shared-memory bitmap of m bits (one CTA per column), then counted.
+// a shared-memory bitmap of m bits (one CTA per column).  A column with fewer
+// products than bitmap words counts the bits its own atomics set and clears only
+// the words it touched, so it costs O(flops_j); a denser column counts and clears
+// the whole bitmap, O(m / 32) <= O(flops_j).  The bitmap is cleared once at start.
 __global__ void __launch_bounds__(NA_COUNT_BLOCK) k_count_bitmap(int64_t m, int64_t na, const int64_t* __restrict__ Acp,
                                                                  const int32_t* __restrict__ Air,
                                                                  const int64_t* __restrict__ Bcp,
                                                                  const int32_t* __restrict__ Bir, int64_t n,
                                                                  int64_t* __restrict__ cnt_out) {
     extern __shared__ __align__(16) uint32_t bm[];
-    __shared__ unsigned long long s_tot;
+    __shared__ unsigned long long s_tot, s_flops;
     const int nw = (int)((m + 31) >> 5);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = NA_COUNT_BLOCK / 32;
+    for (int w = threadIdx.x; w < nw; w += NA_COUNT_BLOCK) bm[w] = 0u;
     for (int64_t j = blockIdx.x; j < n; j += gridDim.x) {
-        for (int w = threadIdx.x; w < nw; w += NA_COUNT_BLOCK) bm[w] = 0u;
-        if (threadIdx.x == 0) s_tot = 0;
+        if (threadIdx.x == 0) s_tot = s_flops = 0;
         __syncthreads();
+        const int64_t b0 = Bcp[j], b1 = Bcp[j + 1];
+        unsigned long long f = 0;
+        for (int64_t t = b0 + threadIdx.x; t < b1; t += NA_COUNT_BLOCK) {
+            const int32_t k = Bir[t];
+            if (k >= 0 && k < na) f += (unsigned long long)(Acp[k + 1] - Acp[k]);
+        }
+        for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+        if (lane == 0 && f) atomicAdd(&s_flops, f);
+        __syncthreads();
+        const bool sparse = s_flops < (unsigned long long)nw;
+        unsigned long long c = 0;
         // one warp per entry of B(:,j), lanes walk A(:,k)
-        for (int64_t t = Bcp[j] + warp; t < Bcp[j + 1]; t += nwarp) {
+        for (int64_t t = b0 + warp; t < b1; t += nwarp) {
             const int32_t k = Bir[t];
             if (k < 0 || k >= na) continue;
             for (int64_t q = Acp[k] + lane; q < Acp[k + 1]; q += 32) {
                 const int32_t r = Air[q];
-                if (r >= 0 && r < m) atomicOr(&bm[r >> 5], 1u << (r & 31));
+                if (r < 0 || r >= m) continue;
+                const uint32_t bit = 1u << (r & 31);
+                const uint32_t old = atomicOr(&bm[r >> 5], bit);
+                c += (old & bit) == 0;   // a row seen for the first time in this column
             }
         }
+        if (!sparse) c = 0;
         __syncthreads();
-        unsigned long long c = 0;
-        for (int w = threadIdx.x; w < nw; w += NA_COUNT_BLOCK) c += __popc(bm[w]);
+        if (sparse) {
+            // clear exactly the words this column touched
+            for (int64_t t = b0 + warp; t < b1; t += nwarp) {
+                const int32_t k = Bir[t];
+                if (k < 0 || k >= na) continue;
+                for (int64_t q = Acp[k] + lane; q < Acp[k + 1]; q += 32) {
+                    const int32_t r = Air[q];
+                    if (r >= 0 && r < m) bm[r >> 5] = 0u;
+                }
+            }
+        } else {
+            for (int w = threadIdx.x; w < nw; w += NA_COUNT_BLOCK) {
+                c += __popc(bm[w]);
+                bm[w] = 0u;
+            }
+        }
         for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-        if (lane == 0) atomicAdd(&s_tot, c);
+        if (lane == 0 && c) atomicAdd(&s_tot, c);
         __syncthreads();
         if (threadIdx.x == 0) cnt_out[j] = (int64_t)s_tot;
-        __syncthreads();
     }
 }
 
@@ -152,7 +183,10 @@ __global__ void __launch_bounds__(NA_BLOCK) k_na_inclusive_apply(int64_t* __rest
 extern "C" spgemm_status_t spgemm_colptr_noalloc(void* cuda_stream, int64_t m, int64_t k, int64_t n,
                                                  const int64_t* Acolptr, const int32_t* Arowidx,
                                                  const int64_t* Bcolptr, const int32_t* Browidx, int64_t* Ccolptr) {
-    if (m < 0 || k < 0 || n < 0 || !Acolptr || !Bcolptr || !Ccolptr) return SPGEMM_ERR_INVALID_ARG;
+    // every array must be a real device pointer: a caller with no nonzeros still passes
+    // a one-element row array
+    if (m < 0 || k < 0 || n < 0 || !Acolptr || !Arowidx || !Bcolptr || !Browidx || !Ccolptr)
+        return SPGEMM_ERR_INVALID_ARG;
     if (m > NA_MAX_ROWS) return SPGEMM_ERR_UNSUPPORTED;                        // bitmap must fit shared memory
     if (sg::ceil_div64(std::max<int64_t>(n, 1), NA_TILE) > NA_MAX_TILES) return SPGEMM_ERR_UNSUPPORTED;
     cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -172,6 +206,10 @@ extern "C" spgemm_status_t spgemm_colptr_noalloc(void* cuda_stream, int64_t m, i
         }
         part = g_ptr[dev];
     }
+    // an error left pending by earlier, unrelated work would otherwise be reported
+    // as this call's failure by the check after the launches; a sticky error
+    // (a lost context) is reported by the first call below
+    cudaGetLastError();
     if (cudaMemsetAsync(Ccolptr, 0, sizeof(int64_t), st) != cudaSuccess) return SPGEMM_ERR_CUDA;
     if (n == 0) return SPGEMM_OK;
     int64_t* cnt = Ccolptr + 1;   // counts land in Ccolptr[1..n], then are scanned in place
@@ -179,7 +217,7 @@ extern "C" spgemm_status_t spgemm_colptr_noalloc(void* cuda_stream, int64_t m, i
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(k_count_bitmap, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return SPGEMM_ERR_CUDA;
-    const int grid = (int)std::min<int64_t>(n, 152 * 8);
+    const int grid = (int)std::min<int64_t>(n, sg::sm_count() * 8);
     k_count_bitmap<<<grid, NA_COUNT_BLOCK, smem, st>>>(m, k, Acolptr, Arowidx, Bcolptr, Browidx, n, cnt);
     const int64_t ntiles = sg::ceil_div64(n, NA_TILE);
     k_na_tile_sums<<<(int)ntiles, NA_BLOCK, 0, st>>>(cnt, n, part);

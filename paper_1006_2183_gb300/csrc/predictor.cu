@@ -236,7 +236,7 @@ spgemm_status_t ensure_pred(spgemm_ctx* ctx) {
     return SPGEMM_OK;
 }
 
-int gridp(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div64(n, 256), 152 * 8)); }
+int gridp(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div64(n, 256), sm_count() * 8)); }
 
 }  // namespace
 
@@ -258,8 +258,7 @@ spgemm_status_t engine_numeric_predicted(Engine* E, std::shared_ptr<DevBuf>* rbu
         case SPGEMM_OR_AND_BOOL: launch_symbolic<BOOL8>(st, E->it, E->cfg, E->list, E->bin_off, E->bin_cnt, E->dw, E->nnz_item, 2); break;
         case SPGEMM_PLUS_TIMES_I64: launch_symbolic<PTI64>(st, E->it, E->cfg, E->list, E->bin_off, E->bin_cnt, E->dw, E->nnz_item, 2); break;
         }
-        launch_sum_parts(st, E->it, E->list + E->bin_off[BIN_DENSE], E->bin_cnt[BIN_DENSE], E->nparts, E->part_count,
-                         E->nnz_item);
+        launch_sum_parts(st, E->it, E->dw, E->nnz_item);
     }
     // capacities: predicted for the hash tiers, exact for the range tier, 0 for empty columns
     auto capb = ctx_buf(ctx, 8 * (2 * (U + 1)) + 8 * (2 * NBIN + 2));
@@ -337,7 +336,7 @@ spgemm_status_t engine_numeric_predicted(Engine* E, std::shared_ptr<DevBuf>* rbu
     {
         PhaseTimer t(ctx, SPGEMM_PHASE_PREDICT, E->sr);
         if (U > 0) {
-            const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div64(U * 32, 256), 152 * 16));
+            const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div64(U * 32, 256), sm_count() * 16));
             switch (w) {
             case 1: k_move_items<1><<<grid, 256, 0, st>>>(U, E->nnz_item, cap_off, E->Coff, (int32_t*)trb->p, tvb->p, (int32_t*)rbuf->p, vbuf->p); break;
             case 4: k_move_items<4><<<grid, 256, 0, st>>>(U, E->nnz_item, cap_off, E->Coff, (int32_t*)trb->p, tvb->p, (int32_t*)rbuf->p, vbuf->p); break;

@@ -202,7 +202,7 @@ __global__ void k_prod_flops(Items it, const int32_t* __restrict__ item_prod, co
     }
 }
 
-int gridn(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div64(n, 256), 152 * 32)); }
+int gridn(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div64(n, 256), sm_count() * 32)); }
 
 // A matrix split into g x g DCSC+AUX blocks (all blocks share the arrays).
 struct Blocked {

@@ -81,5 +81,18 @@ def test_product_entry_points_check_their_handles(lib, ctx):
 def test_default_options():
     from paper_1006_2183_gb300 import spgemm as sp
     o = sp.default_opts()
-    assert (o.warp_max_flops, o.block_max_flops, o.dense_part_flops) == (512, 4096, 65536)
+    assert (o.warp_max_flops, o.block_max_flops, o.dense_part_flops) == (512, 4096, 32768)
     assert (o.use_predictor, o.summa_fused, o.summa_merge_every, o.block_kernel, o.range_slab_rows) == (0, 0, 0, 0, 0)
+
+
+def test_colptr_noalloc_rejects_null_arrays_before_any_cuda_call(lib):
+    """A null row-index array is refused by the argument checks, so no kernel can
+    read through it; those checks run before the first CUDA call (no GPU here)."""
+    lib.spgemm_colptr_noalloc.argtypes = [P, I64, I64, I64, P, P, P, P, P]
+    fake = P(256)
+    args = [None, 8, 8, 8, fake, fake, fake, fake, fake]
+    assert lib.spgemm_colptr_noalloc(*args[:5], None, *args[6:]) == INVALID_ARG      # Arowidx
+    assert lib.spgemm_colptr_noalloc(*args[:7], None, args[8]) == INVALID_ARG        # Browidx
+    assert lib.spgemm_colptr_noalloc(*args[:4], None, *args[5:]) == INVALID_ARG      # Acolptr
+    assert lib.spgemm_colptr_noalloc(*args[:8], None) == INVALID_ARG                 # Ccolptr
+    assert lib.spgemm_colptr_noalloc(None, -1, 8, 8, fake, fake, fake, fake, fake) == INVALID_ARG

@@ -51,6 +51,21 @@ def test_rmat_all_tiers(ctx, sr):
     assert st["flops"] == int(oracle.flops_per_col(A, A).sum())
 
 
+def test_bool_with_stored_false_values(ctx):
+    """Boolean operands that store false entries (0 bytes) and other true bytes (2):
+    stored false entries still make structural entries of C, whose values are
+    the OR of the ANDs; long columns then evaluate every product instead of
+    taking every output as true."""
+    A = gen.rmat(13, 8, 0x1303, OR_BOOL)
+    v = np.where(np.arange(A.nnz) % 3 == 0, 0, np.where(np.arange(A.nnz) % 3 == 1, 1, 2)).astype(np.uint8)
+    A = A.with_vals(v)
+    C = check_product(ctx, A, A, OR_BOOL)
+    s = sp()
+    dA = s.Matrix.from_host(ctx, A, OR_BOOL)
+    assert s.spgemm_plan(ctx, dA, dA, OR_BOOL).stats()["tiers"][3] > 0   # long columns present
+    assert (C.vals == 0).any() and (C.vals == 1).any()
+
+
 @pytest.mark.parametrize("sr", [PT_F64, PT_I64])
 def test_tier_choice_does_not_change_result(ctx, sr):
     A = gen.rmat(12, 8, 0x1202, sr)
@@ -114,13 +129,8 @@ def test_dense_column_tier_boundaries(ctx, sr):
         check_product(ctx, A, B, sr, what=f"m = {m}")
 
 
-def test_long_column_over_slab_limit_is_unsupported(ctx):
-    """A long column of more than 16 * (2^20 - 32) rows is refused, not cut into slabs
-    wider than the shared-memory bitmap; short columns of such a matrix still work."""
-    s = sp()
-    m = 17 * (1 << 20)
-    rng = np.random.default_rng(17)
-    k = 64
+def _tall_a(m, k=64, seed=17):
+    rng = np.random.default_rng(seed)
     rows = rng.choice(m, (k, 100), replace=True)
     cp = np.zeros(k + 1, np.int64)
     ir = []
@@ -128,15 +138,36 @@ def test_long_column_over_slab_limit_is_unsupported(ctx):
         u = np.unique(rows[c]).astype(np.int32)
         ir.append(u)
         cp[c + 1] = cp[c] + len(u)
-    A = CSC(m, k, cp, np.concatenate(ir), np.ones(int(cp[-1])))
+    return CSC(m, k, cp, np.concatenate(ir), np.ones(int(cp[-1])))
+
+
+def test_long_column_of_many_slabs_matches_oracle(ctx):
+    """A long column of 17 * 2^20 rows needs 35 row slabs of at most 2^19 rows (the
+    slab count stays under its limit of 64); it matches the oracle, as do short
+    columns of the same tall A."""
+    s = sp()
+    A = _tall_a(17 * (1 << 20))
+    k = A.n
     dA = s.Matrix.from_host(ctx, A, PT_F64)
     long_b = CSC(k, 1, np.array([0, k], np.int64), np.arange(k, dtype=np.int32), np.ones(k))   # ~6400 flops
-    with pytest.raises(s.SpGEMMError) as ei:
-        s.spgemm_multiply(ctx, dA, s.Matrix.from_host(ctx, long_b, PT_F64), PT_F64)
-    assert ei.value.status == 8, ei.value   # SPGEMM_ERR_UNSUPPORTED
+    C = s.spgemm_multiply(ctx, dA, s.Matrix.from_host(ctx, long_b, PT_F64), PT_F64).to_host()
+    assert_matches(C, oracle.spgemm(A, long_b, PT_F64), PT_F64, what="one long column over 35 slabs")
     short_b = CSC(k, 2, np.array([0, 2, 3], np.int64), np.array([1, 5, 9], np.int32), np.ones(3))
     C = s.spgemm_multiply(ctx, dA, s.Matrix.from_host(ctx, short_b, PT_F64), PT_F64).to_host()
     assert_matches(C, oracle.spgemm(A, short_b, PT_F64), PT_F64, what="short columns of a tall A")
+
+
+def test_long_column_over_slab_limit_is_unsupported(ctx):
+    """A long column of more than 64 * (2^20 - 32) rows is refused, not cut into slabs
+    wider than the shared-memory bitmap."""
+    s = sp()
+    A = _tall_a(65 * (1 << 20))
+    k = A.n
+    dA = s.Matrix.from_host(ctx, A, PT_F64)
+    long_b = CSC(k, 1, np.array([0, k], np.int64), np.arange(k, dtype=np.int32), np.ones(k))
+    with pytest.raises(s.SpGEMMError) as ei:
+        s.spgemm_multiply(ctx, dA, s.Matrix.from_host(ctx, long_b, PT_F64), PT_F64)
+    assert ei.value.status == 8, ei.value   # SPGEMM_ERR_UNSUPPORTED
 
 
 def test_dense_rows_multiple_chunks_and_ragged_tail(ctx):
