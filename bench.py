@@ -1,11 +1,13 @@
 #!/usr/bin/env python
 """SpGEMM benchmark on one or more GB300s (one process per GPU).
 
-Workload (default): C = A*A with A an R-MAT matrix of scale 18 (262,144
+Workload (default): C = A*A with A an R-MAT matrix of scale 20 (1,048,576
 vertices), edge factor 8, (a, b, c, d) = (0.57, 0.19, 0.19, 0.05), duplicates
 merged, self-loops kept, values uniform(0, 1).  One step runs every product
-of the workload once: the flat product in plus-times FP64 and in min-plus
-FP32, and the same two on a 16 x 16 virtual 2D Sparse SUMMA grid.
+of the workload once: the flat product in plus-times FP64 and in boolean
+or-and, and the same two on a 32 x 32 virtual 2D Sparse SUMMA grid.  The
+smaller R-MAT scale-18 workload (flat and 16 x 16 grid, plus-times FP64 and
+min-plus FP32) is timed after it and reported under "secondary".
 Metric: GFLOPS = 2 * flops / time, flops = sum_j sum_{k in B(:,j)} nnz(A(:,k)).
 
 Multi-GPU: every rank computes its own copy of the workload (independent
@@ -36,15 +38,19 @@ from paper_1006_2183_gb300 import gen  # noqa: E402
 
 METRIC = "SpGEMM GFLOPS (2*flops/s)"
 UNIT = "GFLOPS"
-SCALE, EF, SEED = 18, 8, 0x1802
-GRID = 16
+SCALE, EF, SEED = 20, 8, 0x2005
+GRID = 32
+SEMIRINGS = "pt64,bool"
+# the secondary workload: R-MAT scale 18, 16 x 16 grid, plus-times FP64 and min-plus FP32
+SECONDARY = (18, 16, "pt64,mp32")
 # R-MAT seeds of the A*A workloads by scale (scale 20 is the larger flat + 32 x 32 grid configuration)
 SEED_OF_SCALE = {18: 0x1802, 20: 0x2005}
 # semiring ids of the C ABI: name and value width in bytes
 SR_NAME = {0: "pt64", 1: "mp32", 2: "bool", 3: "pti64"}
 SR_WIDTH = {0: 8, 1: 4, 2: 1, 3: 8}
 L2_FLUSH_BYTES = 512 << 20
-CPU_STRIDE = 4   # oracle sample: every 4th output column (~25 core-seconds on the flat scale-18 product)
+# oracle sample: every CPU_STRIDE[scale]-th output column (a few seconds on the host cores)
+CPU_STRIDE = {18: 4, 20: 8}
 
 
 def _train_predictor(sp, ctx):
@@ -207,8 +213,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned+batched vs plain comparison on the batched workloads")
-    ap.add_argument("--semirings", default="pt64,mp32",
+    ap.add_argument("--semirings", default=SEMIRINGS,
                     help="comma list of pt64 (plus-times FP64), mp32 (min-plus FP32), bool (or-and)")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the secondary R-MAT scale-18 workload")
     ap.add_argument("--products", default="flat,summa",
                     help="comma list of product kinds in a step: flat, summa")
     ap.add_argument("--opt", action="append", default=[],
@@ -249,7 +257,7 @@ def kernel_source_hash() -> str:
 def profiled_traffic(scale: int):
     """DRAM bytes per launch of the dominant kernel from the committed ncu summary,
     or None when the kernels changed since it was captured (or no capture exists)."""
-    path = os.path.join(ROOT, "profiles", f"k_range_num_pt64_rmat{scale}.md")
+    path = os.path.join(ROOT, "profiles", f"k_slab_num_pt64_rmat{scale}.md")
     if not os.path.exists(path):
         return None
     kv = {}
@@ -342,7 +350,8 @@ def run_reference(args, rank, world):
     A = gen.rmat(args.scale, EF, seed, gen.PLUS_TIMES_F64)
     n = A.n
     # bounded sample: every 4th output column of the flat plus-times FP64 product
-    cols = np.arange(0, n, CPU_STRIDE)
+    stride = CPU_STRIDE.get(args.scale, 4)
+    cols = np.arange(0, n, stride)
     lens = np.diff(A.colptr)
     fl_cols = np.array([lens[A.rowidx[A.colptr[j]:A.colptr[j + 1]]].sum() for j in cols], np.int64)
     flops = int(fl_cols.sum())
@@ -356,7 +365,7 @@ def run_reference(args, rank, world):
             times.append(dt)
     tot = sum(times)
     value = 2.0 * flops * len(times) / tot / 1e9
-    sample = (f"every {CPU_STRIDE}th output column ({len(cols)} columns, {flops} flops) of the flat plus-times "
+    sample = (f"every {stride}th output column ({len(cols)} columns, {flops} flops) of the flat plus-times "
               f"FP64 product")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / len(times),
@@ -465,6 +474,177 @@ def run_sweep(args) -> None:
 
 
 # ---------------------------------------------------------------- our arm
+SRS = {"pt64": 0, "mp32": 1, "bool": 2}
+
+
+def run_workload(sp, ctx, scale, grid, semirings, kinds, steps, warmup, lib_opts, flush, world, local, sample=True):
+    """R-MAT(scale) A*A: every (product kind, semiring) once per step.  W warm-up steps,
+    then `steps` steps timed with CUDA events on the context stream, L2 flushed before
+    each; every product's result is freed once its nnz is read (inside the step).
+    Returns the measurement and the objects the other legs reuse."""
+    import torch
+    import torch.distributed as dist
+    seed = SEED_OF_SCALE.get(scale, SEED)
+    A64 = gen.rmat(scale, EF, seed, gen.PLUS_TIMES_F64)
+    wanted = [x for x in semirings.split(",") if x]
+    # the same pattern in every semiring: FP64 values, their FP32 rounding, boolean ones
+    host = {sp.PLUS_TIMES_F64: A64, sp.MIN_PLUS_F32: A64.with_vals(A64.vals.astype(np.float32)),
+            sp.OR_AND_BOOL: A64.with_vals(np.ones(A64.nnz, dtype=np.uint8))}
+    mats = {SRS[nm]: sp.Matrix.from_host(ctx, host[SRS[nm]], SRS[nm]) for nm in wanted}
+    products = [(k, SRS[nm]) for k in kinds for nm in wanted]
+
+    def run_product(kind, sr, M):
+        if kind == "flat":
+            ctx.timing_group(0)
+            plan = sp.spgemm_plan(ctx, M, M, sr, lib_opts)
+            return sp.spgemm_numeric(plan), plan
+        ctx.timing_group(1)
+        return sp.spgemm_summa_blocked(ctx, M, M, grid, sr, lib_opts), None
+
+    def step():
+        nz = []
+        for kind, sr in products:
+            C, plan = run_product(kind, sr, mats[sr])
+            nz.append(C.shape()[2])
+            del C, plan
+        return nz
+
+    step()   # one untimed run of every product first (errors surface here, before any timing)
+    for _ in range(max(3, warmup)):
+        step()
+    torch.cuda.synchronize()
+    st = ctx.stream
+    ctx.timing(True)
+    l0 = sp.launch_count()
+    times = []
+    nz = None
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) if sample else _NoClock() as clk:
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            nz = step()
+            e1.record(st)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    launches = sp.launch_count() - l0
+    phases = ctx.phase_ms()
+    ctx.timing(False)
+    flops1 = flops_of(A64)
+    nnz_seen = dict(zip(products, nz))
+    tot_ms, value = aggregate_ranks(sum(times), flops1 * len(products), steps, world, ctx.device)
+    hbm, _ = peaks()
+    pipe = {}
+    for (kind, sr) in products:
+        w = SR_WIDTH[sr]
+        byt = (A64.n + 1) * 8 + A64.nnz * (4 + w) + (A64.n + 1) * 8 + nnz_seen[(kind, sr)] * (4 + w)
+        pipe[f"{kind}_{SR_NAME[sr]}"] = {"compulsory_bytes": byt, "nnz_C": nnz_seen[(kind, sr)]}
+    byt_step = sum(v["compulsory_bytes"] for v in pipe.values())
+    return {"A64": A64, "host": host, "mats": mats, "products": products, "run_product": run_product,
+            "seed": seed, "flops1": flops1, "value": value, "tot_ms": tot_ms, "ms_per_step": tot_ms / steps,
+            "phases": phases, "launches": launches, "clocks": clk.summary(), "nnz_seen": nnz_seen, "pipe": pipe,
+            "pipeline_frac": byt_step / (tot_ms / steps / 1e3) / 1e9 / hbm,
+            "phase_tab": {f"{['flat', 'summa', 'g2', 'g3'][g]}:{SR_NAME[s_]}:{p_}": round(v[0] / max(1, steps), 4)
+                          for (g, s_, p_), v in phases.items() if v[1]}}
+
+
+class _NoClock:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        return False
+
+    def summary(self):
+        return None
+
+
+def slab_roofline(sp, ctx, W, lib_opts, scale):
+    """Roofline of the slab-tier numeric kernel of the flat plus-times FP64 product:
+    its compulsory bytes (C's entries of the tier written once, the tier's B columns
+    and A read once, column pointers) over its mean CUDA-event time in the timed
+    region (the numeric_dense phase brackets exactly its one launch)."""
+    A64 = W["A64"]
+    M = W["mats"][sp.PLUS_TIMES_F64]
+    ms, cnt = W["phases"].get((0, sp.PLUS_TIMES_F64, "numeric_dense"), (0.0, 0))
+    if not cnt:
+        return None
+    plan = sp.spgemm_plan(ctx, M, M, sp.PLUS_TIMES_F64, lib_opts)
+    sp.spgemm_symbolic(plan)
+    ts = plan.tier_stats()
+    del plan
+    nnz_d, bnnz_d, cols_d = ts["nnz"][3], ts["bnnz"][3], ts["cols"][3]
+    alg = nnz_d * 12 + bnnz_d * 12 + cols_d * 16 + A64.nnz * 12 + 8 * (A64.n + 1)
+    per_launch_ms = ms / cnt
+    hbm, peak_kind = peaks()
+    ach = alg / (per_launch_ms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+            "traffic": profiled_traffic(scale), "kernel": "k_slab_num<PT64>", "peak_kind": peak_kind,
+            "alg_bytes_per_launch": alg, "ms_per_launch": per_launch_ms, "launches_timed": cnt}
+
+
+def e2e_leg(sp, ctx, W, steps, warmup, flush, world):
+    """The step's products through the public API with host buffers: every step copies A
+    from pinned host memory to the device and every C back into one reused pinned
+    buffer, inside the timed region (wall clock, synchronised per product)."""
+    import torch as _t
+    A64, host, products, run_product = W["A64"], W["host"], W["products"], W["run_product"]
+    dev = ctx.device
+    st = ctx.stream
+    pinned = {}
+    for sr in {sr for _, sr in products}:
+        H = host[sr]
+        pinned[sr] = (_t.from_numpy(H.colptr).pin_memory(), _t.from_numpy(H.rowidx).pin_memory(),
+                      _t.from_numpy(np.ascontiguousarray(H.vals)).pin_memory())
+    h2d = sum(sum(t.numel() * t.element_size() for t in pinned[sr]) for _, sr in products)
+    nzmax = max(W["nnz_seen"].values())
+    out_cp = _t.empty(A64.n + 1, dtype=_t.int64).pin_memory()
+    out_ir = _t.empty(nzmax, dtype=_t.int32).pin_memory()
+    out_v = _t.empty(nzmax * 8, dtype=_t.uint8).pin_memory()   # viewed per semiring
+    d2h = sum((A64.n + 1) * 8 + nz * (4 + SR_WIDTH[sr]) for (kind, sr), nz in W["nnz_seen"].items())
+    et = []
+    for it in range(warmup + steps):
+        flush.fill_(1.0)
+        _t.cuda.synchronize()
+        t0 = time.perf_counter()
+        for (kind, sr) in products:
+            cp, ir, v = (x.to(dev, non_blocking=True) for x in pinned[sr])
+            M = sp.Matrix.csc(ctx, A64.m, A64.n, cp, ir, v, sr)
+            C, plan = run_product(kind, sr, M)
+            _, _, nz, ccp, cir, cv = C.export()
+            out_cp.copy_(ccp, non_blocking=True)
+            out_ir[:nz].copy_(cir, non_blocking=True)
+            out_v[:nz * SR_WIDTH[sr]].view(sp.TORCH_DTYPE[sr]).copy_(cv, non_blocking=True)
+            st.synchronize()
+            del C, plan, M
+        dt = time.perf_counter() - t0
+        if it >= warmup:
+            et.append(dt)
+    value = 2.0 * W["flops1"] * len(products) * len(et) * world / sum(et) / 1e9
+    return {"value": value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "steps": len(et), "warmup": warmup}
+
+
+def cpu_leg(A64, scale):
+    import oracle
+    stride = CPU_STRIDE.get(scale, 4)
+    cols = np.arange(0, A64.n, stride)
+    lens = np.diff(A64.colptr)
+    fl = int(sum(lens[A64.rowidx[A64.colptr[j]:A64.colptr[j + 1]]].sum() for j in cols))
+    t0 = time.perf_counter()
+    oracle.spgemm_columns(A64, A64, oracle.PT_F64, cols)
+    dt = time.perf_counter() - t0
+    return {"value": 2.0 * fl / dt / 1e9, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"every {stride}th output column ({len(cols)} columns, {fl} flops) of the flat "
+                      f"plus-times FP64 product, {dt:.2f} s wall on {oracle.max_threads()} threads",
+            "single_thread": cpu_single_thread(oracle, A64)}
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -490,185 +670,56 @@ def main():
     from paper_1006_2183_gb300 import spgemm as sp
 
     kinds = [k for k in args.products.split(",") if k]
-    seed = SEED_OF_SCALE.get(args.scale, SEED)
-    A64 = gen.rmat(args.scale, EF, seed, gen.PLUS_TIMES_F64)
-    flops1 = flops_of(A64)
     ctx = sp.Context()
-    dev = ctx.device
-    srs = {"pt64": sp.PLUS_TIMES_F64, "mp32": sp.MIN_PLUS_F32, "bool": sp.OR_AND_BOOL}
-    wanted = [x for x in args.semirings.split(",") if x]
-    # the same pattern in every semiring: FP64 values, their FP32 rounding, boolean ones
-    host = {sp.PLUS_TIMES_F64: A64, sp.MIN_PLUS_F32: A64.with_vals(A64.vals.astype(np.float32)),
-            sp.OR_AND_BOOL: A64.with_vals(np.ones(A64.nnz, dtype=np.uint8))}
-    mats = {srs[nm]: sp.Matrix.from_host(ctx, host[srs[nm]], srs[nm]) for nm in wanted}
-    if sp.PLUS_TIMES_F64 not in mats:
-        mats[sp.PLUS_TIMES_F64] = sp.Matrix.from_host(ctx, A64, sp.PLUS_TIMES_F64)   # imbalance report
-    products = []
-    for k in kinds:
-        for name in wanted:
-            products.append((k, srs[name]))
-
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=ctx.device)
     lib_opts = sp.default_opts(**{k: float(v) if k == "predictor_margin" else int(v)
                                   for k, v in (o.split("=", 1) for o in args.opt)})
-
-    def run_product(kind, sr, M):
-        if kind == "flat":
-            ctx.timing_group(0)
-            plan = sp.spgemm_plan(ctx, M, M, sr, lib_opts)
-            C = sp.spgemm_numeric(plan)
-            return C, plan
-        ctx.timing_group(1)
-        C = sp.spgemm_summa_blocked(ctx, M, M, args.grid, sr, lib_opts)
-        return C, None
-
-    # one untimed run of every product first (errors surface here, before any timing)
-    for kind, sr in products:
-        C, plan = run_product(kind, sr, mats[sr])
-        del C, plan
-    flops_step = flops1 * len(products)
-
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-
-    def step():
-        outs = []
-        for kind, sr in products:
-            outs.append(run_product(kind, sr, mats[sr]))
-        return outs
-
-    for _ in range(max(3, args.warmup)):
-        step()
-    torch.cuda.synchronize()
-
-    # timed region: per-step CUDA events on the context stream, L2 flushed between steps
-    st = ctx.stream
-    ctx.timing(True)
-    l0 = sp.launch_count()
-    times = []
-    nnz_seen = {}
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        for _ in range(args.steps):
-            flush.fill_(1.0)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(st)
-            outs = step()
-            e1.record(st)
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1))
-            for (kind, sr), (C, plan) in zip(products, outs):
-                nnz_seen[(kind, sr)] = C.shape()[2]
-            del outs
-    torch.cuda.synchronize()
-    launches = sp.launch_count() - l0
-    phases = ctx.phase_ms()
-    ctx.timing(False)
-    clocks = clk.summary()
-    tot_ms, value = aggregate_ranks(sum(times), flops_step, args.steps, world, dev)
-
-    # dominant kernel: numeric dense tier of the flat plus-times FP64 product
-    hbm, peak_kind = peaks()
-    roof = None
-    if ("flat", sp.PLUS_TIMES_F64) in products:
-        plan = sp.spgemm_plan(ctx, mats[sp.PLUS_TIMES_F64], mats[sp.PLUS_TIMES_F64], sp.PLUS_TIMES_F64, lib_opts)
-        sp.spgemm_symbolic(plan)
-        ts = plan.tier_stats()
-        ms, cnt = phases[(0, sp.PLUS_TIMES_F64, "numeric_dense")]
-        if cnt:
-            nnz_d, bnnz_d, cols_d = ts["nnz"][3], ts["bnnz"][3], ts["cols"][3]
-            alg = nnz_d * 12 + bnnz_d * 12 + cols_d * 16 + A64.nnz * 12 + 8 * (A64.n + 1)
-            per_launch_ms = ms / cnt
-            ach = alg / (per_launch_ms / 1e3) / 1e9
-            roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                    "traffic": profiled_traffic(args.scale), "kernel": "k_range_num<PT64,4096>",
-                    "peak_kind": peak_kind, "alg_bytes_per_launch": alg, "ms_per_launch": per_launch_ms,
-                    "launches_timed": cnt}
-        del plan
-    # whole-product roofline on compulsory bytes (A read once, C written once)
-    pipe = {}
-    for (kind, sr) in products:
-        w = SR_WIDTH[sr]
-        byt = (A64.n + 1) * 8 + A64.nnz * (4 + w) + (A64.n + 1) * 8 + nnz_seen[(kind, sr)] * (4 + w)
-        pipe[f"{kind}_{SR_NAME[sr]}"] = {"compulsory_bytes": byt, "nnz_C": nnz_seen[(kind, sr)]}
-    phase_tab = {f"{['flat', 'summa', 'g2', 'g3'][g]}:{SR_NAME[s]}:{p}":
-                 round(v[0] / max(1, args.steps), 4) for (g, s, p), v in phases.items() if v[1]}
-    byt_step = sum(v["compulsory_bytes"] for v in pipe.values())
-    pipeline_frac = byt_step / (tot_ms / args.steps / 1e3) / 1e9 / hbm
-
-    # end to end through the public API with host buffers
+    W = run_workload(sp, ctx, args.scale, args.grid, args.semirings, kinds, args.steps, args.warmup, lib_opts,
+                     flush, world, local)
+    roof = slab_roofline(sp, ctx, W, lib_opts, args.scale) if sp.PLUS_TIMES_F64 in W["mats"] and "flat" in kinds \
+        else None
     e2e = None
     if not args.no_e2e:
-        import torch as _t
-        pinned = {}
-        for sr in {sr for _, sr in products}:
-            H = host[sr]
-            pinned[sr] = (_t.from_numpy(H.colptr).pin_memory(), _t.from_numpy(H.rowidx).pin_memory(),
-                          _t.from_numpy(np.ascontiguousarray(H.vals)).pin_memory())
-        h2d = sum(sum(t.numel() * t.element_size() for t in pinned[sr]) for _, sr in products)
-        outbuf = {}
-        d2h = 0
-        for (kind, sr) in products:
-            nz = nnz_seen[(kind, sr)]
-            w = SR_WIDTH[sr]
-            outbuf[(kind, sr)] = (_t.empty(A64.n + 1, dtype=_t.int64).pin_memory(),
-                                  _t.empty(nz, dtype=_t.int32).pin_memory(),
-                                  _t.empty(nz, dtype=sp.TORCH_DTYPE[sr]).pin_memory())
-            d2h += (A64.n + 1) * 8 + nz * (4 + w)
-        et = []
-        for it in range(args.warmup + args.steps):
-            flush.fill_(1.0)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            for (kind, sr) in products:
-                cp, ir, v = (x.to(dev, non_blocking=True) for x in pinned[sr])
-                M = sp.Matrix.csc(ctx, A64.m, A64.n, cp, ir, v, sr)
-                C, plan = run_product(kind, sr, M)
-                _, _, nz, ccp, cir, cv = C.export()
-                ob = outbuf[(kind, sr)]
-                ob[0].copy_(ccp, non_blocking=True)
-                ob[1][:nz].copy_(cir, non_blocking=True)
-                ob[2][:nz].copy_(cv, non_blocking=True)
-                st.synchronize()
-                del C, plan, M
-            dt = time.perf_counter() - t0
-            if it >= args.warmup:
-                et.append(dt)
-        e2e_val = 2.0 * flops_step * len(et) * world / sum(et) / 1e9
-        e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import oracle
-        cols = np.arange(0, A64.n, CPU_STRIDE)
-        lens = np.diff(A64.colptr)
-        fl = int(sum(lens[A64.rowidx[A64.colptr[j]:A64.colptr[j + 1]]].sum() for j in cols))
-        t0 = time.perf_counter()
-        oracle.spgemm_columns(A64, A64, oracle.PT_F64, cols)
-        dt = time.perf_counter() - t0
-        cpu = {"value": 2.0 * fl / dt / 1e9, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
-               "sample": f"every {CPU_STRIDE}th output column ({len(cols)} columns, {fl} flops) of the flat "
-                         f"plus-times FP64 product, {dt:.2f} s wall on {oracle.max_threads()} threads",
-               "single_thread": cpu_single_thread(oracle, A64)}
-
-    imb = summa_imbalance(sp, ctx, mats[sp.PLUS_TIMES_F64], args.grid) if rank == 0 else None
+        e2e = e2e_leg(sp, ctx, W, min(args.steps, 5), 3, flush, world)
+    cpu = cpu_leg(W["A64"], args.scale) if rank == 0 and world == 1 and not args.no_cpu_baseline else None
+    imb = None
+    if rank == 0:
+        Mimb = W["mats"].get(sp.PLUS_TIMES_F64) or sp.Matrix.from_host(ctx, W["A64"], sp.PLUS_TIMES_F64)
+        imb = summa_imbalance(sp, ctx, Mimb, args.grid)
+    secondary = None
+    if not args.no_secondary and (args.scale, args.grid) != SECONDARY[:2]:
+        sc2, g2, srs2 = SECONDARY
+        del W["mats"], W["run_product"]
+        torch.cuda.empty_cache()
+        W2 = run_workload(sp, ctx, sc2, g2, srs2, ["flat", "summa"], 10, 3, lib_opts, flush, world, local,
+                          sample=False)
+        secondary = {"workload": f"rmat{sc2}_AxA", "scale": sc2, "grid": g2, "seed": W2["seed"],
+                     "products": [f"{k}_{SR_NAME[s_]}" for k, s_ in W2["products"]], "value": W2["value"],
+                     "unit": UNIT, "ms_per_step": W2["ms_per_step"], "steps": 10, "warmup": 3,
+                     "flops_per_product": W2["flops1"], "pipeline_hbm_frac": W2["pipeline_frac"],
+                     "phase_ms_per_step": W2["phase_tab"]}
+        del W2
     lvp = None
     if rank == 0 and world == 1 and not args.no_learned:
-        lvp = learned_vs_plain(sp, ctx, steps=2, warmup=1)
+        torch.cuda.empty_cache()
+        lvp = learned_vs_plain(sp, ctx, steps=10, warmup=3)
 
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+        A64, products = W["A64"], W["products"]
+        line = {"metric": METRIC, "value": W["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": W["ms_per_step"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": f"rmat{args.scale}_AxA", "scale": args.scale, "edge_factor": EF,
-                           "abcd": [0.57, 0.19, 0.19, 0.05], "seed": seed, "grid": args.grid,
-                           "products": [f"{k}_{SR_NAME[s]}" for k, s in products],
-                           "flops_per_product": flops1, "nnz_A": A64.nnz, "l2": "flushed between steps (512 MiB write)",
-                           "pipeline_hbm_frac": pipeline_frac, "pipeline": pipe, "phase_ms_per_step": phase_tab,
+                           "abcd": [0.57, 0.19, 0.19, 0.05], "seed": W["seed"], "grid": args.grid,
+                           "products": [f"{k}_{SR_NAME[s_]}" for k, s_ in products],
+                           "flops_per_product": W["flops1"], "nnz_A": A64.nnz,
+                           "l2": "flushed between steps (512 MiB write)",
+                           "pipeline_hbm_frac": W["pipeline_frac"], "pipeline": W["pipe"],
+                           "phase_ms_per_step": W["phase_tab"],
                            "lib_opts": {k: v for k, v in (o.split("=", 1) for o in args.opt)}},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
-                "learned_batched_vs_plain": lvp, "summa_imbalance": imb}
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": W["clocks"],
+                "gpu_launches": W["launches"], "secondary": secondary, "learned_batched_vs_plain": lvp,
+                "summa_imbalance": imb}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -417,13 +417,12 @@ spgemm_status_t engine_setup(Engine* E, spgemm_ctx* ctx, spgemm_semiring_t sr, c
     launch_bin_scatter(st, E->it, E->bin, E->item_prod, E->bin_off_dev, E->ctr + NBIN, E->list);
     const int64_t nd = E->bin_cnt[BIN_DENSE];
     E->dw = DenseWork();
-    if (nd > 0 && E->it.max_m <= dcol_rows(sr)) {
-        // operands of few rows: long columns go to the dense-column kernel
+    if (nd > 0 && E->it.max_m <= BLOCK_TIER_MAX_ROWS) {
+        // operands of few rows: long columns are counted with row bitmaps and computed by the block tier
         DenseWork& dw = E->dw;
         dw.dlist = E->list + E->bin_off[BIN_DENSE];
         dw.ndense = nd;
         dw.dcol = true;
-        dw.mcap = (int)((E->it.max_m + 31) / 32 * 32);
     } else if (nd > 0 && E->slab_rows_short)
         return set_err(ctx, SPGEMM_ERR_UNSUPPORTED,
                        "long columns of more than %d * (2^20 - 32) rows need more than %d row slabs", MAX_PARTS,
@@ -448,14 +447,9 @@ spgemm_status_t engine_setup(Engine* E, spgemm_ctx* ctx, spgemm_semiring_t sr, c
         dw.store_ctr = E->ctr + 2 * NBIN + 2;
         dw.err = (int*)(E->ctr + 2 * NBIN + 3);
         unsigned long long* store_bound = E->ctr + 2 * NBIN + 4;
-        int* vals_zero = (int*)(E->ctr + 2 * NBIN + 5);
         dw.RB = E->cfg.dense_rows;
         launch_dense_items(st, E->it, dw.dlist, nd, E->flops, E->cfg.part_flops, dw.RB, (int2*)dw.items,
                            E->ctr + 2 * NBIN + 1, (int8_t*)dw.nparts, (int32_t*)dw.sbase, store_bound);
-        if (sr == SPGEMM_OR_AND_BOOL) {
-            launch_false_values(st, E->it, vals_zero);
-            dw.vals_zero = vals_zero;
-        }
         unsigned long long hs[2] = {0, 0};
         SG_CUDA(ctx, cudaMemcpyAsync(&hs[0], E->ctr + 2 * NBIN + 1, 8, cudaMemcpyDeviceToHost, st));
         SG_CUDA(ctx, cudaMemcpyAsync(&hs[1], store_bound, 8, cudaMemcpyDeviceToHost, st));
@@ -476,6 +470,12 @@ spgemm_status_t engine_setup(Engine* E, spgemm_ctx* ctx, spgemm_semiring_t sr, c
         dw.spref = (int32_t*)(sb + o_pref);
         dw.soff = (int64_t*)(sb + o_soff);
         dw.store = (uint32_t*)(sb + o_store);
+    }
+    if (sr == SPGEMM_OR_AND_BOOL) {
+        // boolean operands without a stored false value: the long-column tiers take every output as true
+        int* vals_zero = (int*)(E->ctr + 2 * NBIN + 5);
+        launch_false_values(st, E->it, vals_zero);
+        E->dw.vals_zero = vals_zero;
     }
     SG_CUDA(ctx, cudaGetLastError());
     return SPGEMM_OK;

@@ -1,0 +1,372 @@
+// Block tier: the numeric pass of every column whose operand A has at most
+// BLOCK_TIER_MAX_ROWS rows (the 2D Sparse SUMMA blocks of Section 3.2 and the
+// stage merges of Section 6.1 on the virtual grid, and any other short operand).
+//
+// A group of GS threads (a warp, or a CTA for long columns) takes one output
+// column C(:,j) = (+)_{k in B(:,j)} A(:,k) (x) B(k,j) (Section 2.1):
+//   1. every product marks its row in a two-level row bitmap in shared memory:
+//      L2 holds one bit per row (1024 words for 32768 rows), L1 one bit per
+//      nonempty L2 word; lanes that hit the same word combine their bits first;
+//   2. one warp turns the bitmap into ranks: per L1 word, the rows before each
+//      nonempty L2 word (16-bit) and before the L1 word (int), so the rank of a
+//      row is gp + wp + the bits below it in its word;
+//   3. C's rows are written at their ranks and C's values set to the semiring zero;
+//   4. every product is added into C at its row's rank with an L2 reduction.
+// There is no hash table, no sort and no shared-memory accumulator, and the
+// bitmap work is proportional to the column's entries, not to the row count.
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace sg {
+namespace {
+
+constexpr int L2W = BLOCK_TIER_MAX_ROWS / 32;   // row-bitmap words
+constexpr int L1W = L2W / 32;                   // words of the bitmap of nonempty L2 words
+static_assert(L1W == 32, "one warp owns the first-level bitmap");
+
+template <class SR, int GS>
+struct BtLayout {
+    using T = typename SR::T;
+    static constexpr size_t l2 = (size_t)L2W * 4;
+    static constexpr size_t l1 = (size_t)L1W * 4;
+    static constexpr size_t wp = (size_t)L2W * 2;
+    static constexpr size_t gp = (size_t)L1W * 4;
+    static constexpr size_t incl = (size_t)GS * 4;
+    static constexpr size_t a0 = (size_t)GS * 8;
+    static constexpr size_t bv = (size_t)GS * 8;
+    static constexpr size_t ws = 32 * 8;
+    static constexpr size_t group = (l2 + l1 + wp + gp + incl + a0 + bv + ws + 15) / 16 * 16;
+};
+
+template <int GS>
+__device__ __forceinline__ void gsync() {
+    if constexpr (GS == 32) __syncwarp();
+    else __syncthreads();
+}
+
+// Inclusive scan of a 64-bit value over the group, total in `total`.  For a
+// multi-warp group `ws` holds one partial per warp; the closing barrier is left
+// to the caller (the next gsync).
+template <int GS>
+__device__ __forceinline__ long long group_scan64(long long v, long long* ws, long long& total) {
+    long long x = warp_incl_scan64(v);
+    if constexpr (GS == 32) {
+        total = __shfl_sync(0xffffffffu, x, 31);
+        return x;
+    } else {
+        constexpr int NW = GS / 32;
+        const int lane = threadIdx.x & 31, w = (threadIdx.x % GS) >> 5;
+        if (lane == 31) ws[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            long long s = lane < NW ? ws[lane] : 0;
+            s = warp_incl_scan64(s);
+            if (lane < NW) ws[lane] = s;
+        }
+        __syncthreads();
+        total = ws[NW - 1];
+        return x + (w > 0 ? ws[w - 1] : 0);
+    }
+}
+
+// Sets bit `bit` of L2 word wd (wd < 0: nothing) for every lane of the warp;
+// runs of lanes with the same word combine their bits into one atomic, and the
+// lane that turns a word nonzero marks it in L1.  Called by all 32 lanes.
+__device__ __forceinline__ void mark_rows(uint32_t* l2, uint32_t* l1, int wd, uint32_t bit) {
+    const int lane = threadIdx.x & 31;
+    const int wprev = __shfl_up_sync(0xffffffffu, wd, 1);
+    const bool head = lane == 0 || wprev != wd;
+    uint32_t acc = bit;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t b2 = __shfl_down_sync(0xffffffffu, acc, o);
+        const int w2 = __shfl_down_sync(0xffffffffu, wd, o);
+        if (lane + o < 32 && w2 == wd) acc |= b2;
+    }
+    if (wd >= 0 && head) {
+        const uint32_t old = atomicOr(&l2[wd], acc);
+        if (old == 0u) atomicOr(&l1[wd >> 5], 1u << (wd & 31));
+    }
+}
+
+// The products of one chunk of at most GS entries of B(:,j): per entry the
+// segment A(:,k), compacted (nonempty segments only); returns the number of
+// segments and of products.  Ends with a group barrier.
+template <class SR, int GS, bool NUM>
+__device__ __forceinline__ void chunk_segments(const Items& it, const Prod* pr, int64_t t, int64_t be, int* s_incl,
+                                               int64_t* s_a0, typename SR::T* s_bv, long long* ws, int& ns,
+                                               int& total) {
+    using T = typename SR::T;
+    int len = 0;
+    int64_t a0 = 0;
+    T bv = T(0);
+    if (t < be) {
+        const int32_t k = __ldg(pr->B.ir + t);
+        int64_t s, e;
+        a_col(it, pr, t, k, s, e);
+        a0 = s;
+        len = (int)(e - s);
+        if constexpr (NUM) bv = load_val<SR>(pr->B, t);
+    }
+    long long tot;
+    const long long inc = group_scan64<GS>(len > 0 ? ((1ll << 32) | (unsigned)len) : 0ll, ws, tot);
+    if (len > 0) {
+        const int p = (int)(inc >> 32) - 1;
+        s_incl[p] = (int)(inc & 0xffffffffll);
+        s_a0[p] = a0;
+        if constexpr (NUM) s_bv[p] = bv;
+    }
+    ns = (int)(tot >> 32);
+    total = (int)(tot & 0xffffffffll);
+    gsync<GS>();
+}
+
+// Walks the products [0, total) of the current chunk: each warp of the group
+// takes a contiguous slice, four 32-product windows per step with every load
+// issued first.  f(valid, row, a, b) is called by all 32 lanes of each warp.
+template <class SR, int GS, bool NUM, class F>
+__device__ __forceinline__ void chunk_walk(const Prod* pr, const int* s_incl, const int64_t* s_a0,
+                                           const typename SR::T* s_bv, int ns, int total, F&& f) {
+    using T = typename SR::T;
+    constexpr int U = 4, NWG = GS / 32;
+    const int lane = threadIdx.x & 31, wg = (threadIdx.x % GS) >> 5;
+    const int C = (total + NWG * 32 - 1) / (NWG * 32) * 32;
+    const int xb = wg * C, xe = min(total, xb + C);
+    if (xb >= xe) return;
+    int lo = 0, hi = ns;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (s_incl[mid] <= xb) lo = mid + 1;
+        else hi = mid;
+    }
+    int o0 = lo;
+    const int32_t* __restrict__ air = pr->A.ir;
+    for (int x0 = xb; x0 < xe; x0 += 32 * U) {
+        int64_t idx[U];
+        bool ok[U];
+        int ob[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int xw = x0 + 32 * u;
+            const int oi = warp_window_segment(s_incl, ns, xw, o0);
+            ok[u] = xw + lane < xe;
+            ob[u] = oi;
+            idx[u] = ok[u] ? s_a0[oi] + (xw + lane - (oi ? s_incl[oi - 1] : 0)) : 0;
+        }
+        int32_t row[U];
+        T av[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            row[u] = ok[u] ? __ldg(air + idx[u]) : -1;
+            if constexpr (NUM) av[u] = ok[u] ? load_val<SR>(pr->A, idx[u]) : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if constexpr (NUM) f(ok[u], row[u], av[u], ok[u] ? s_bv[ob[u]] : T(0));
+            else f(ok[u], row[u], T(0), T(0));
+        }
+    }
+}
+
+// Rows of the operand: an out-of-range row (malformed input) is skipped.
+__device__ __forceinline__ int row_word(bool ok, int32_t r, int m) { return ok && (unsigned)r < (unsigned)m ? r >> 5 : -1; }
+
+// One column per group.  Coff[u] is where column u starts.  Without nnz_item the
+// offsets are exact.  With nnz_item the column's count is recorded there and the
+// column is written only when it fits its capacity Coff[u+1] - Coff[u] (the
+// predicted and the upper-bound layouts).
+template <class SR, int GS, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_block_tier(Items it, const int2* __restrict__ list, int64_t count,
+                                                     int64_t* __restrict__ nnz_item, const int64_t* __restrict__ Coff,
+                                                     int32_t* __restrict__ Cir, typename SR::T* __restrict__ Cv,
+                                                     const int* __restrict__ vals_zero) {
+    using T = typename SR::T;
+    using L = BtLayout<SR, GS>;
+    constexpr int NG = BLOCK / GS;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int g = (threadIdx.x / GS), lane = threadIdx.x % GS;
+    unsigned char* base = smem + (size_t)g * L::group;
+    uint32_t* l2 = reinterpret_cast<uint32_t*>(base);
+    uint32_t* l1 = reinterpret_cast<uint32_t*>(base + L::l2);
+    uint16_t* wp = reinterpret_cast<uint16_t*>(base + L::l2 + L::l1);
+    int* gp = reinterpret_cast<int*>(base + L::l2 + L::l1 + L::wp);
+    int* s_incl = reinterpret_cast<int*>(base + L::l2 + L::l1 + L::wp + L::gp);
+    int64_t* s_a0 = reinterpret_cast<int64_t*>(base + L::l2 + L::l1 + L::wp + L::gp + L::incl);
+    T* s_bv = reinterpret_cast<T*>(base + L::l2 + L::l1 + L::wp + L::gp + L::incl + L::a0);
+    long long* ws = reinterpret_cast<long long*>(base + L::l2 + L::l1 + L::wp + L::gp + L::incl + L::a0 + L::bv);
+    // boolean products whose operands hold no false value: every output value is true
+    const bool walk = SR::id != SPGEMM_OR_AND_BOOL || vals_zero == nullptr || *vals_zero != 0;
+    const T init = walk ? SR::out(SR::zero()) : T(1);
+    for (int x = lane; x < L2W; x += GS) l2[x] = 0u;
+    for (int x = lane; x < L1W; x += GS) l1[x] = 0u;
+    gsync<GS>();
+    for (int64_t w = (int64_t)blockIdx.x * NG + g; w < count; w += (int64_t)gridDim.x * NG) {
+        const int2 e = __ldg(list + w);
+        const Prod* pr = it.prods + e.x;
+        const int64_t u = __ldg(it.item_base + e.x) + e.y;
+        const int64_t bs = __ldg(pr->B.cp + e.y), be = __ldg(pr->B.cp + e.y + 1);
+        const int m = (int)pr->A.m;   // <= BLOCK_TIER_MAX_ROWS
+        const int nw = (m + 31) >> 5;
+        const bool one_chunk = be - bs <= GS;
+        int ns = 0, total = 0;
+        // 1. marks
+        for (int64_t b0 = bs; b0 < be; b0 += GS) {
+            // the B values too: a single chunk's segments serve the value pass as they are
+            chunk_segments<SR, GS, true>(it, pr, b0 + lane, be, s_incl, s_a0, s_bv, ws, ns, total);
+            chunk_walk<SR, GS, false>(pr, s_incl, s_a0, s_bv, ns, total, [&](bool ok, int32_t r, T, T) {
+                mark_rows(l2, l1, row_word(ok, r, m), 1u << (r & 31));
+            });
+            if (!one_chunk) gsync<GS>();   // the next chunk rewrites the segment arrays
+        }
+        gsync<GS>();
+        // 2. ranks: warp 0 of the group; lane l owns L1 word l (L2 words 32 l .. 32 l + 31)
+        if (lane < 32) {
+            uint32_t bits = l1[lane];
+            int c = 0;
+            while (bits) {
+                const int wd = lane * 32 + __ffs(bits) - 1;
+                bits &= bits - 1;
+                wp[wd] = (uint16_t)c;
+                c += __popc(l2[wd]);
+            }
+            const int incl = warp_incl_scan(c);
+            gp[lane] = incl - c;
+            if (lane == 31) ws[0] = incl;   // the column's entries
+        }
+        gsync<GS>();
+        const int cnt = (int)ws[0];
+        const int64_t out0 = __ldg(Coff + u);
+        const int64_t capn = __ldg(Coff + u + 1) - out0;
+        // exact offsets always fit (the counting pass marks the same rows); the check
+        // keeps an inconsistent input from writing past the column
+        const bool write = cnt <= capn;
+        if (nnz_item && lane == 0) nnz_item[u] = cnt;
+        const int32_t rb = out_row_base(pr, e.y);
+        if (write) {
+            // 3. rows at their ranks, values set to the semiring zero
+            if constexpr (GS == 32) {
+                uint32_t bits = l1[lane];
+                while (bits) {
+                    const int wd = lane * 32 + __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    uint32_t wv = l2[wd];
+                    int r = gp[lane] + wp[wd];
+                    while (wv) {
+                        Cir[out0 + r++] = wd * 32 + __ffs(wv) - 1 + rb;
+                        wv &= wv - 1;
+                    }
+                }
+            } else {
+                for (int wd = lane; wd < nw; wd += GS) {
+                    uint32_t wv = l2[wd];
+                    if (!wv) continue;
+                    int r = gp[wd >> 5] + wp[wd];
+                    while (wv) {
+                        Cir[out0 + r++] = wd * 32 + __ffs(wv) - 1 + rb;
+                        wv &= wv - 1;
+                    }
+                }
+            }
+            for (int i = lane; i < cnt; i += GS) Cv[out0 + i] = init;
+            gsync<GS>();   // this group's stores come before its reductions
+            // 4. every product added at its row's rank
+            if (walk) {
+                for (int64_t b0 = bs; b0 < be; b0 += GS) {
+                    if (!one_chunk) chunk_segments<SR, GS, true>(it, pr, b0 + lane, be, s_incl, s_a0, s_bv, ws, ns, total);
+                    chunk_walk<SR, GS, true>(pr, s_incl, s_a0, s_bv, ns, total, [&](bool ok, int32_t r, T a, T b) {
+                        if (!ok || (unsigned)r >= (unsigned)m) return;
+                        const int wd = r >> 5;
+                        const uint32_t wv = l2[wd];
+                        const uint32_t bit = 1u << (r & 31);
+                        const int rank = gp[wd >> 5] + wp[wd] + __popc(wv & (bit - 1u));
+                        red_out<SR>(Cv, out0 + rank, SR::mul(a, b));
+                    });
+                    if (!one_chunk) gsync<GS>();
+                }
+            }
+        }
+        gsync<GS>();
+        // 5. clear the touched words
+        if constexpr (GS == 32) {
+            uint32_t bits = l1[lane];
+            while (bits) {
+                l2[lane * 32 + __ffs(bits) - 1] = 0u;
+                bits &= bits - 1;
+            }
+            l1[lane] = 0u;
+        } else {
+            for (int wd = lane; wd < nw; wd += GS) l2[wd] = 0u;
+            if (lane < L1W) l1[lane] = 0u;
+        }
+        gsync<GS>();
+    }
+}
+
+template <class SR, int GS, int BLOCK>
+void run_bt(cudaStream_t st, const Items& it, const int2* list, int64_t count, int64_t* nnz_item, const int64_t* Coff,
+            int32_t* Cir, typename SR::T* Cv, const int* vals_zero) {
+    if (count <= 0) return;
+    constexpr int NG = BLOCK / GS;
+    const size_t smem = BtLayout<SR, GS>::group * NG;
+    auto kern = k_block_tier<SR, GS, BLOCK>;
+    static bool attr = false;   // per process: the limit belongs to the kernel
+    if (!attr) {
+        cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLOCK, smem) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    const int grid = (int)std::min<int64_t>(ceil_div64(count, NG), (int64_t)per_sm * sm_count());
+    kern<<<grid, BLOCK, smem, st>>>(it, list, count, nnz_item, Coff, Cir, Cv, vals_zero);
+    note_launch();
+}
+
+}  // namespace
+
+template <class SR>
+void launch_block_tier(cudaStream_t st, const Items& it, const int2* list, const int64_t* bin_off,
+                       const int64_t* bin_cnt, const DenseWork& dw, int64_t* nnz_item, const int64_t* Coff,
+                       int32_t* Cir, typename SR::T* Cv, int which) {
+    if (which & 1) {
+        // Bins [b0, b1) as one launch per contiguous run: the lists of the exact and
+        // predicted passes are contiguous, but a repair list keeps every bin at its
+        // full-list offset with fewer entries, which leaves gaps between bins.
+        auto runs = [&](int b0, int b1, auto launch) {
+            int b = b0;
+            while (b < b1) {
+                const int64_t start = bin_off[b];
+                int64_t n = 0;
+                int e = b;
+                while (e < b1 && bin_off[e] == start + n) n += bin_cnt[e++];
+                if (e == b) {   // bin b starts after a gap: a run of its own
+                    n = bin_cnt[b];
+                    e = b + 1;
+                }
+                launch(list + start, n);
+                b = e;
+            }
+        };
+        runs(BIN_WARP0, BIN_BLK0, [&](const int2* l, int64_t n) {
+            run_bt<SR, 32, 256>(st, it, l, n, nnz_item, Coff, Cir, Cv, dw.vals_zero);
+        });
+        runs(BIN_BLK0, BIN_DENSE, [&](const int2* l, int64_t n) {
+            run_bt<SR, 256, 256>(st, it, l, n, nnz_item, Coff, Cir, Cv, dw.vals_zero);
+        });
+    }
+    if (which & 2) run_bt<SR, 512, 512>(st, it, dw.dlist, dw.ndense, nnz_item, Coff, Cir, Cv, dw.vals_zero);
+}
+
+#define SG_INST(SR)                                                                                               \
+    template void launch_block_tier<SR>(cudaStream_t, const Items&, const int2*, const int64_t*, const int64_t*, \
+                                        const DenseWork&, int64_t*, const int64_t*, int32_t*, typename SR::T*, int);
+SG_INST(PT64)
+SG_INST(MP32)
+SG_INST(BOOL8)
+SG_INST(PTI64)
+#undef SG_INST
+
+}  // namespace sg

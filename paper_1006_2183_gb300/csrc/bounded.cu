@@ -41,7 +41,7 @@ void numeric_launches(Engine* E, const int64_t* cap_off, int32_t* rows, void* va
     cudaStream_t st = E->ctx->stream;
     {
         PhaseTimer t(E->ctx, SPGEMM_PHASE_NUMERIC_HASH, E->sr);
-        launch_numeric_predicted<SR>(st, E->it, E->list, E->bin_off, E->bin_cnt, cap_off, E->nnz_item, rows,
+        launch_numeric_predicted<SR>(st, E->it, E->list, E->bin_off, E->bin_cnt, E->dw, cap_off, E->nnz_item, rows,
                                      (typename SR::T*)vals);
     }
     {

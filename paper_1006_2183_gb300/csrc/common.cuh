@@ -1,6 +1,7 @@
 // Shared device-side definitions of the SpGEMM library: semiring traits,
 // matrix views (CSC / DCSC with AUX), and thread-group primitives.
 #pragma once
+#include <climits>
 #include <cstdint>
 #include <cuda_runtime.h>
 #include <math_constants.h>
@@ -249,6 +250,36 @@ __device__ __forceinline__ long long group_incl_scan64_open(long long v, long lo
     __syncthreads();
     total = scratch[NW - 1];
     return x + (w > 0 ? scratch[w - 1] : 0);
+}
+
+// Segment of product xw + lane for a warp over compacted segments (ends[0, ns)
+// strictly increasing: no empty segment): bit b of the window mask marks the
+// segment that ends at xw + b + 1, so the lane's segment index is the count of
+// segments ending at or before its product.  o0 carries the segments that end at
+// or before the window start; windows must come in order.  All 32 lanes call it.
+__device__ __forceinline__ int warp_window_segment(const int* ends, int ns, int xw, int& o0) {
+    const int lane = threadIdx.x & 31;
+    const int ej = o0 + lane < ns ? ends[o0 + lane] : INT_MAX;
+    const unsigned bitv = (ej > xw && ej <= xw + 32) ? (1u << (ej - xw - 1)) : 0u;
+    const unsigned mask = __reduce_or_sync(0xffffffffu, bitv);
+    const int oi = o0 + __popc(mask & ((1u << lane) - 1u));
+    o0 += __popc(mask);
+    return oi;
+}
+
+// C[pos] = C[pos] (+) v in global memory (an L2 reduction; the return value is unused).
+template <class SR>
+__device__ __forceinline__ void red_out(typename SR::T* Cv, int64_t pos, typename SR::Acc v) {
+    if constexpr (SR::id == SPGEMM_OR_AND_BOOL) {
+        if (v) {
+            const uintptr_t a = reinterpret_cast<uintptr_t>(Cv + pos);
+            atomicOr(reinterpret_cast<unsigned int*>(a & ~uintptr_t(3)), 1u << ((a & 3) * 8));
+        }
+    } else if constexpr (SR::id == SPGEMM_PLUS_TIMES_I64) {
+        atomicAdd(reinterpret_cast<unsigned long long*>(Cv + pos), v);
+    } else {
+        SR::atomic_add(Cv + pos, v);   // double add; float min through integer min / max
+    }
 }
 
 __host__ __device__ __forceinline__ int64_t ceil_div64(int64_t a, int64_t b) { return (a + b - 1) / b; }

@@ -283,21 +283,6 @@ void launch_bin_scatter(cudaStream_t st, const Items& it, const uint8_t* bin, co
 }
 
 // ------------------------------------------------------------------ hash tiers
-// Segment of product xw + lane for a warp over compacted segments (ends[0, ns)
-// strictly increasing: no empty segment): bit b of the window mask marks the
-// segment that ends at xw + b + 1, so the lane's segment index is the count of
-// segments ending at or before its product.  o0 carries the segments that end at
-// or before the window start; windows must come in order.  All 32 lanes call it.
-__device__ __forceinline__ int warp_window_segment(const int* ends, int ns, int xw, int& o0) {
-    const int lane = threadIdx.x & 31;
-    const int ej = o0 + lane < ns ? ends[o0 + lane] : INT_MAX;
-    const unsigned bitv = (ej > xw && ej <= xw + 32) ? (1u << (ej - xw - 1)) : 0u;
-    const unsigned mask = __reduce_or_sync(0xffffffffu, bitv);
-    const int oi = o0 + __popc(mask & ((1u << lane) - 1u));
-    o0 += __popc(mask);
-    return oi;
-}
-
 template <class SR, int GS, int TBL, bool NUM>
 struct HashLayout {
     using T = typename SR::T;
@@ -882,6 +867,9 @@ static void run_tiny(cudaStream_t st, const Items& it, const int2* list, int64_t
     note_launch();
 }
 
+// every A_i has at most BLOCK_TIER_MAX_ROWS rows: numeric passes run in the block tier
+static bool block_mode(const Items& it) { return it.max_m > 0 && it.max_m <= BLOCK_TIER_MAX_ROWS; }
+
 template <class SR, bool NUM>
 static void run_hash_bins(cudaStream_t st, const Items& it, const int2* list, const int64_t* off, const int64_t* cnt,
                           int64_t* nnz_item, const int64_t* Coff, int32_t* Cir, typename SR::T* Cv) {
@@ -1236,21 +1224,6 @@ __global__ void __launch_bounds__(RT_BLOCK, 2) k_slab_sym(Items it, DenseWork dw
     }
 }
 
-// C[pos] = C[pos] (+) v in global memory (an L2 reduction; the return value is unused).
-template <class SR>
-__device__ __forceinline__ void red_out(typename SR::T* Cv, int64_t pos, typename SR::Acc v) {
-    if constexpr (SR::id == SPGEMM_OR_AND_BOOL) {
-        if (v) {
-            const uintptr_t a = reinterpret_cast<uintptr_t>(Cv + pos);
-            atomicOr(reinterpret_cast<unsigned int*>(a & ~uintptr_t(3)), 1u << ((a & 3) * 8));
-        }
-    } else if constexpr (SR::id == SPGEMM_PLUS_TIMES_I64) {
-        atomicAdd(reinterpret_cast<unsigned long long*>(Cv + pos), v);
-    } else {
-        SR::atomic_add(Cv + pos, v);   // double add; float min through integer min / max
-    }
-}
-
 // Numeric slab kernel: row set -> ranks -> C's rows, zero values, L2 reductions.
 template <class SR>
 __global__ void __launch_bounds__(RT_BLOCK, 2) k_slab_num(Items it, DenseWork dw, const int64_t* __restrict__ Coff,
@@ -1387,151 +1360,15 @@ static void run_slabs(cudaStream_t st, const Items& it, const DenseWork& dw, boo
     note_launch();
 }
 
-// ------------------------------------------------------------------ dense-column tier
-// Long columns whose operands have few rows (every A_i has at most dcol_rows(SR)
-// rows, as the SUMMA stage blocks and merge columns): one CTA per column adds
-// every product into a dense row array in shared memory and marks a row bitmap,
-// then writes the column in row order from per-word ranks.  No row ranges, no
-// cursors, no hashing.
-int dcol_rows(spgemm_semiring_t sr) {
-    const int acc = sr == SPGEMM_PLUS_TIMES_F64 || sr == SPGEMM_PLUS_TIMES_I64 ? 8 : 4;
-    const int rows = (128 * 1024) / acc;
-    return rows < (int)BM_COUNT_MAX_ROWS ? rows : (int)BM_COUNT_MAX_ROWS;
-}
-static_assert(BM_COUNT_MAX_ROWS / 32 <= 2 * RT_BLOCK, "dense-column emit: two bitmap words per thread");
-
-template <class SR>
-__global__ void __launch_bounds__(RT_BLOCK) k_dcol(Items it, const int2* __restrict__ dlist, int64_t nd, int mcap,
-                                                   const int64_t* __restrict__ Coff, int32_t* __restrict__ Cir,
-                                                   typename SR::T* __restrict__ Cv) {
-    using Acc = typename SR::Acc;
-    using T = typename SR::T;
-    constexpr int NWARP = RT_BLOCK / 32;
-    extern __shared__ __align__(16) unsigned char smem[];
-    RangeSmem* sc = reinterpret_cast<RangeSmem*>(smem);
-    Acc* vals = reinterpret_cast<Acc*>(smem + RS_BYTES);   // mcap
-    uint32_t* bitmap = reinterpret_cast<uint32_t*>(vals + mcap);    // mcap / 32
-    int* s_scan = reinterpret_cast<int*>(bitmap + mcap / 32);       // 34
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int x = tid; x < mcap; x += RT_BLOCK) vals[x] = SR::zero();
-    for (int x = tid; x < mcap / 32; x += RT_BLOCK) bitmap[x] = 0u;
-    __syncthreads();
-    for (int64_t w = blockIdx.x; w < nd; w += gridDim.x) {
-        const int2 e = __ldg(dlist + w);
-        const Prod* pr = it.prods + e.x;
-        const int64_t u = __ldg(it.item_base + e.x) + e.y;
-        const int64_t bs = __ldg(pr->B.cp + e.y), be = __ldg(pr->B.cp + e.y + 1);
-        const int m = (int)(pr->A.m < (int64_t)mcap ? pr->A.m : (int64_t)mcap);
-        const int32_t* __restrict__ air = pr->A.ir;
-        for (int64_t b0 = bs; b0 < be; b0 += RT_BLOCK) {
-            const int64_t t = b0 + tid;
-            int len = 0;
-            int64_t a = 0;
-            T bv = T(0);
-            if (t < be) {
-                int64_t s, en;
-                a_col(it, pr, t, __ldg(pr->B.ir + t), s, en);
-                a = s;
-                len = (int)(en - s);
-                bv = load_val<SR>(pr->B, t);
-            }
-            int64_t bvbits = 0;
-            *reinterpret_cast<T*>(&bvbits) = bv;
-            int ns, Tn;
-            rt_compact(sc, t < be, len, a, bvbits, ns, Tn);
-            // warp slices of the products, 4 windows of 32 per step (as in the range tier)
-            constexpr int U = 4;
-            const int C = (Tn + NWARP * 32 - 1) / (NWARP * 32) * 32;
-            const int xb = warp * C, xe = min(Tn, xb + C);
-            if (xb < xe) {
-                int lo = 0, hi = ns;
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (sc->end[mid] <= xb) lo = mid + 1;
-                    else hi = mid;
-                }
-                int o0 = lo;
-                for (int x0 = xb; x0 < xe; x0 += 32 * U) {
-                    int64_t idx[U];
-                    bool ok[U];
-                    int ob[U];
-#pragma unroll
-                    for (int uu = 0; uu < U; ++uu) {
-                        const int xw = x0 + 32 * uu;
-                        const int ej = o0 + lane < ns ? sc->end[o0 + lane] : INT_MAX;
-                        const unsigned bitv = (ej > xw && ej <= xw + 32) ? (1u << (ej - xw - 1)) : 0u;
-                        const unsigned mask = __reduce_or_sync(0xffffffffu, bitv);
-                        const int oi = o0 + __popc(mask & ((1u << lane) - 1u));
-                        const int pe0 = o0 > 0 ? sc->end[o0 - 1] : 0;
-                        const int src = oi - 1 - o0;
-                        const int pe = __shfl_sync(0xffffffffu, ej, src < 0 ? 0 : src);
-                        ok[uu] = xw + lane < xe;
-                        ob[uu] = oi;
-                        idx[uu] = ok[uu] ? sc->start[oi] + (xw + lane - (src < 0 ? pe0 : pe)) : 0;
-                        o0 += __popc(mask);
-                    }
-                    int32_t row[U];
-                    T av[U];
-#pragma unroll
-                    for (int uu = 0; uu < U; ++uu) {
-                        row[uu] = ok[uu] ? __ldg(air + idx[uu]) : -1;
-                        av[uu] = ok[uu] ? load_val<SR>(pr->A, idx[uu]) : T(0);
-                    }
-#pragma unroll
-                    for (int uu = 0; uu < U; ++uu) {
-                        const int r = row[uu];
-                        if ((unsigned)r >= (unsigned)m) continue;   // not taken, or malformed input
-                        const uint32_t bit = 1u << (r & 31);
-                        if (!(bitmap[r >> 5] & bit)) atomicOr(&bitmap[r >> 5], bit);
-                        SR::atomic_add(&vals[r], SR::mul(av[uu], *reinterpret_cast<const T*>(&sc->bv[ob[uu]])));
-                    }
-                }
-            }
-            __syncthreads();
-        }
-        // row order: thread tid owns words 2 tid and 2 tid + 1 and writes their rows at their ranks
-        const int nw = (m + 31) >> 5;
-        const int x0 = 2 * tid;
-        const uint32_t w0 = x0 < nw ? bitmap[x0] : 0u, w1 = x0 + 1 < nw ? bitmap[x0 + 1] : 0u;
-        const int c = __popc(w0) + __popc(w1);
-        int total;
-        int rank = group_incl_scan<RT_BLOCK>(c, s_scan, total) - c;
-        const int64_t out0 = __ldg(Coff + u);
-        const int32_t rb = out_row_base(pr, e.y);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            uint32_t bits = h ? w1 : w0;
-            const int base = (x0 + h) * 32;
-            while (bits) {
-                const int r = base + __ffs(bits) - 1;
-                bits &= bits - 1;
-                Cir[out0 + rank] = r + rb;
-                Cv[out0 + rank] = SR::out(vals[r]);
-                vals[r] = SR::zero();
-                ++rank;
-            }
-            if (x0 + h < nw) bitmap[x0 + h] = 0u;
-        }
-        __syncthreads();
-    }
-}
-
-template <class SR>
-static void run_dcol(cudaStream_t st, const Items& it, const DenseWork& dw, const int64_t* Coff, int32_t* Cir,
-                     typename SR::T* Cv) {
-    if (dw.ndense <= 0) return;
-    const size_t smem = RS_BYTES + (size_t)dw.mcap * sizeof(typename SR::Acc) + (size_t)(dw.mcap / 32) * 4 + 34 * 4;
-    smem_at_least((const void*)k_dcol<SR>, smem);
-    const int per_sm = smem <= 72 * 1024 ? 3 : smem <= 110 * 1024 ? 2 : 1;
-    const int grid = (int)std::min<int64_t>(dw.ndense, sm_count() * per_sm);
-    k_dcol<SR><<<grid, RT_BLOCK, smem, st>>>(it, dw.dlist, dw.ndense, dw.mcap, Coff, Cir, Cv);
-    note_launch();
-}
-
 template <class SR>
 void launch_numeric_predicted(cudaStream_t st, const Items& it, const int2* list, const int64_t* bin_off,
-                              const int64_t* bin_cnt, const int64_t* cap_off, int64_t* nnz_item, int32_t* Cir,
-                              typename SR::T* Cv) {
+                              const int64_t* bin_cnt, const DenseWork& dw, const int64_t* cap_off, int64_t* nnz_item,
+                              int32_t* Cir, typename SR::T* Cv) {
+    if (block_mode(it)) {
+        run_tiny<SR, true>(st, it, list + bin_off[BIN_TINY], bin_cnt[BIN_TINY], nnz_item, cap_off, Cir, Cv);
+        launch_block_tier<SR>(st, it, list, bin_off, bin_cnt, dw, nnz_item, cap_off, Cir, Cv, 1);
+        return;
+    }
     run_hash_bins<SR, true>(st, it, list, bin_off, bin_cnt, nnz_item, cap_off, Cir, Cv);
 }
 
@@ -1551,11 +1388,13 @@ void launch_numeric(cudaStream_t st, const Items& it, TierCfg cfg, const int2* l
                     const int64_t* bin_cnt, const DenseWork& dw, const int64_t* Coff, int32_t* Cir,
                     typename SR::T* Cv, int which) {
     (void)cfg;
-    if (which & 1) run_hash_bins<SR, true>(st, it, list, bin_off, bin_cnt, nullptr, Coff, Cir, Cv);
-    if (which & 2) {
-        if (dw.dcol) run_dcol<SR>(st, it, dw, Coff, Cir, Cv);
-        else run_slabs<SR>(st, it, dw, true, Coff, Cir, Cv);
+    if (block_mode(it)) {
+        if (which & 1) run_tiny<SR, true>(st, it, list + bin_off[BIN_TINY], bin_cnt[BIN_TINY], nullptr, Coff, Cir, Cv);
+        launch_block_tier<SR>(st, it, list, bin_off, bin_cnt, dw, nullptr, Coff, Cir, Cv, which);
+        return;
     }
+    if (which & 1) run_hash_bins<SR, true>(st, it, list, bin_off, bin_cnt, nullptr, Coff, Cir, Cv);
+    if (which & 2) run_slabs<SR>(st, it, dw, true, Coff, Cir, Cv);
 }
 
 #define SG_INST(SR)                                                                                              \
@@ -1565,7 +1404,8 @@ void launch_numeric(cudaStream_t st, const Items& it, TierCfg cfg, const int2* l
                                      const int64_t*, const DenseWork&, const int64_t*, int32_t*, typename SR::T*, \
                                      int);                                                                       \
     template void launch_numeric_predicted<SR>(cudaStream_t, const Items&, const int2*, const int64_t*,          \
-                                               const int64_t*, const int64_t*, int64_t*, int32_t*, typename SR::T*);
+                                               const int64_t*, const DenseWork&, const int64_t*, int64_t*, int32_t*, \
+                                               typename SR::T*);
 SG_INST(PT64)
 SG_INST(MP32)
 SG_INST(BOOL8)

@@ -63,15 +63,15 @@ struct DenseWork {
     const int* vals_zero = nullptr;       // boolean semiring: some operand value is false
     int* err = nullptr;                   // nonzero: a capacity was exceeded
     int RB = 1 << 19;                     // most rows per slab
-    // dense-column mode (every A_i has at most dcol_rows rows): one CTA per long
-    // column with a dense row array; no slabs
+    // block mode (every A_i has at most BLOCK_TIER_MAX_ROWS rows): long columns
+    // are counted with row bitmaps and computed by the block tier; no slabs
     bool dcol = false;
-    int mcap = 0;                         // rows of the dense array (multiple of 32)
 };
 
-// Most rows for the dense-column mode of a semiring: 128 KB of accumulators in
-// shared memory, and a row bitmap the bitmap count can hold.
-int dcol_rows(spgemm_semiring_t sr);
+// Products whose every A_i has at most this many rows run their numeric pass in
+// the block tier (two-level row bitmap per column, L2 reductions; blocktier.cu)
+// and count their columns with row bitmaps.
+constexpr int BLOCK_TIER_MAX_ROWS = 32768;
 
 struct Items {
     const Prod* prods = nullptr;        // device, nprod descriptors
@@ -127,7 +127,7 @@ void launch_dense_items(cudaStream_t st, const Items& it, const int2* dense_list
 // *flag = 1 when an operand of some product stores a false value (boolean semiring)
 void launch_false_values(cudaStream_t st, const Items& it, int* flag);
 
-// which: 1 = hash-table tiers, 2 = long columns (slab or dense-column tier), 3 = both
+// which: 1 = hash-table tiers, 2 = long columns (slab tier, or the block tier in block mode), 3 = both
 template <class SR>
 void launch_symbolic(cudaStream_t st, const Items& it, TierCfg cfg, const int2* list, const int64_t* bin_off,
                      const int64_t* bin_cnt, const DenseWork& dw, int64_t* nnz_item, int which = 3);
@@ -140,9 +140,15 @@ void launch_numeric(cudaStream_t st, const Items& it, TierCfg cfg, const int2* l
 // every item's exact count goes to nnz_item, items that do not fit are not written
 template <class SR>
 void launch_numeric_predicted(cudaStream_t st, const Items& it, const int2* list, const int64_t* bin_off,
-                              const int64_t* bin_cnt, const int64_t* cap_off, int64_t* nnz_item, int32_t* Cir,
-                              typename SR::T* Cv);
+                              const int64_t* bin_cnt, const DenseWork& dw, const int64_t* cap_off, int64_t* nnz_item,
+                              int32_t* Cir, typename SR::T* Cv);
 
+// numeric pass of the block tier (blocktier.cu); with nnz_item the counts are recorded and
+// a column is written only when it fits its slots Coff[u+1] - Coff[u]
+template <class SR>
+void launch_block_tier(cudaStream_t st, const Items& it, const int2* list, const int64_t* bin_off,
+                       const int64_t* bin_cnt, const DenseWork& dw, int64_t* nnz_item, const int64_t* Coff,
+                       int32_t* Cir, typename SR::T* Cv, int which);
 // nnz of long columns = sum of their slab counts (and each slab's start in its column)
 void launch_sum_parts(cudaStream_t st, const Items& it, const DenseWork& dw, int64_t* nnz_item);
 // per-product column pointers from item offsets: out[colbase_i + j] for j in [0, n_i]

@@ -286,10 +286,10 @@ spgemm_status_t engine_numeric_predicted(Engine* E, std::shared_ptr<DevBuf>* rbu
     {
         PhaseTimer t(ctx, SPGEMM_PHASE_NUMERIC_HASH, E->sr);
         switch (E->sr) {
-        case SPGEMM_PLUS_TIMES_F64: launch_numeric_predicted<PT64>(st, E->it, E->list, E->bin_off, E->bin_cnt, cap_off, E->nnz_item, (int32_t*)trb->p, (double*)tvb->p); break;
-        case SPGEMM_MIN_PLUS_F32: launch_numeric_predicted<MP32>(st, E->it, E->list, E->bin_off, E->bin_cnt, cap_off, E->nnz_item, (int32_t*)trb->p, (float*)tvb->p); break;
-        case SPGEMM_OR_AND_BOOL: launch_numeric_predicted<BOOL8>(st, E->it, E->list, E->bin_off, E->bin_cnt, cap_off, E->nnz_item, (int32_t*)trb->p, (uint8_t*)tvb->p); break;
-        case SPGEMM_PLUS_TIMES_I64: launch_numeric_predicted<PTI64>(st, E->it, E->list, E->bin_off, E->bin_cnt, cap_off, E->nnz_item, (int32_t*)trb->p, (int64_t*)tvb->p); break;
+        case SPGEMM_PLUS_TIMES_F64: launch_numeric_predicted<PT64>(st, E->it, E->list, E->bin_off, E->bin_cnt, E->dw, cap_off, E->nnz_item, (int32_t*)trb->p, (double*)tvb->p); break;
+        case SPGEMM_MIN_PLUS_F32: launch_numeric_predicted<MP32>(st, E->it, E->list, E->bin_off, E->bin_cnt, E->dw, cap_off, E->nnz_item, (int32_t*)trb->p, (float*)tvb->p); break;
+        case SPGEMM_OR_AND_BOOL: launch_numeric_predicted<BOOL8>(st, E->it, E->list, E->bin_off, E->bin_cnt, E->dw, cap_off, E->nnz_item, (int32_t*)trb->p, (uint8_t*)tvb->p); break;
+        case SPGEMM_PLUS_TIMES_I64: launch_numeric_predicted<PTI64>(st, E->it, E->list, E->bin_off, E->bin_cnt, E->dw, cap_off, E->nnz_item, (int32_t*)trb->p, (int64_t*)tvb->p); break;
         }
     }
     {
