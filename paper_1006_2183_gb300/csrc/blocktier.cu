@@ -70,24 +70,13 @@ __device__ __forceinline__ long long group_scan64(long long v, long long* ws, lo
     }
 }
 
-// Sets bit `bit` of L2 word wd (wd < 0: nothing) for every lane of the warp;
-// runs of lanes with the same word combine their bits into one atomic, and the
-// lane that turns a word nonzero marks it in L1.  Called by all 32 lanes.
+// Sets bit `bit` of L2 word wd (wd < 0: nothing); the lane that turns a word
+// nonzero marks it in L1.  One shared atomic per product: rows of one window
+// mostly fall in different words, so folding lanes per word first measured slower.
 __device__ __forceinline__ void mark_rows(uint32_t* l2, uint32_t* l1, int wd, uint32_t bit) {
-    const int lane = threadIdx.x & 31;
-    const int wprev = __shfl_up_sync(0xffffffffu, wd, 1);
-    const bool head = lane == 0 || wprev != wd;
-    uint32_t acc = bit;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t b2 = __shfl_down_sync(0xffffffffu, acc, o);
-        const int w2 = __shfl_down_sync(0xffffffffu, wd, o);
-        if (lane + o < 32 && w2 == wd) acc |= b2;
-    }
-    if (wd >= 0 && head) {
-        const uint32_t old = atomicOr(&l2[wd], acc);
-        if (old == 0u) atomicOr(&l1[wd >> 5], 1u << (wd & 31));
-    }
+    if (wd < 0) return;
+    const uint32_t old = atomicOr(&l2[wd], bit);
+    if (old == 0u) atomicOr(&l1[wd >> 5], 1u << (wd & 31));
 }
 
 // The products of one chunk of at most GS entries of B(:,j): per entry the

@@ -282,6 +282,23 @@ __device__ __forceinline__ void red_out(typename SR::T* Cv, int64_t pos, typenam
     }
 }
 
+// bitmap[wd] |= bit for every lane with wd >= 0; lanes that hit the same word
+// combine their bits first, so each run of equal words takes one shared atomic.
+// Called by all 32 lanes of the warp.
+__device__ __forceinline__ void or_bits_warp(uint32_t* bitmap, int wd, uint32_t bit) {
+    const int lane = threadIdx.x & 31;
+    const int wprev = __shfl_up_sync(0xffffffffu, wd, 1);
+    const bool head = lane == 0 || wprev != wd;
+    uint32_t acc = bit;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t b2 = __shfl_down_sync(0xffffffffu, acc, o);
+        const int w2 = __shfl_down_sync(0xffffffffu, wd, o);
+        if (lane + o < 32 && w2 == wd) acc |= b2;
+    }
+    if (wd >= 0 && head) atomicOr(&bitmap[wd], acc);
+}
+
 __host__ __device__ __forceinline__ int64_t ceil_div64(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 __device__ __forceinline__ uint32_t hash_row(int32_t r) { return (uint32_t)r * 0x9E3779B1u; }

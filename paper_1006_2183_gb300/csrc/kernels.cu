@@ -663,21 +663,26 @@ static void run_hash(cudaStream_t st, const Items& it, const int2* list, int64_t
 // most BM_COUNT_MAX_ROWS rows, as the SUMMA merge columns): each product sets its
 // row's bit and nnz is the popcount; no keys, no probing, no table to clear.
 constexpr int64_t BM_COUNT_MAX_ROWS = 32768;
+// shared memory of one counting group before the bitmaps: a0, incl, scan (34), l1 (32)
+template <int GS>
+constexpr size_t bitcount_group_bytes() { return ((size_t)GS * 12 + 34 * 4 + 32 * 4 + 15) / 16 * 16; }
 template <int GS, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK) k_bitcount(Items it, const int2* __restrict__ list,
                                                                   int64_t count, int64_t* __restrict__ nnz_item,
                                                                   int bm_words) {
     using G = Group<GS>;
     constexpr int NG = BLOCK / GS;
-    constexpr size_t GROUP = ((size_t)GS * 12 + 34 * 4 + 15) / 16 * 16;   // incl, a0, scan
+    constexpr size_t GROUP = bitcount_group_bytes<GS>();
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = G::lane(), g = G::gid();
     unsigned char* base = smem + (size_t)g * GROUP;
     int64_t* s_a0 = reinterpret_cast<int64_t*>(base);
     int* s_incl = reinterpret_cast<int*>(base + (size_t)GS * 8);
     int* s_scan = s_incl + GS;
+    uint32_t* l1 = reinterpret_cast<uint32_t*>(s_scan + 34);   // nonempty bitmap words (bm_words <= 1024)
     uint32_t* bitmap = reinterpret_cast<uint32_t*>(smem + (size_t)NG * GROUP) + (size_t)g * bm_words;
     for (int x = lane; x < bm_words; x += GS) bitmap[x] = 0u;
+    for (int x = lane; x < 32; x += GS) l1[x] = 0u;
     G::sync();
     for (int64_t w = (int64_t)blockIdx.x * NG + g; w < count; w += (int64_t)gridDim.x * NG) {
         const int2 e = __ldg(list + w);
@@ -685,9 +690,9 @@ __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK) k_bitcount(Items it, cons
         const int64_t u = __ldg(it.item_base + e.x) + e.y;
         const int64_t bs = __ldg(pr->B.cp + e.y), be = __ldg(pr->B.cp + e.y + 1);
         const int64_t mw = (pr->A.m + 31) >> 5;
-        const int nwc = mw < bm_words ? (int)mw : bm_words;
         const uint32_t mrows = (uint32_t)(pr->A.m < (int64_t)bm_words * 32 ? pr->A.m : (int64_t)bm_words * 32);
         const int32_t* __restrict__ air = pr->A.ir;
+        int c = 0;   // rows this lane marked first
         for (int64_t b0 = bs; b0 < be; b0 += GS) {
             const int64_t t = b0 + lane;
             int len = 0;
@@ -757,21 +762,33 @@ __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK) k_bitcount(Items it, cons
                         if (q < qend) row[i] = __ldg(air + s_a0[oi] + (q - (oi ? s_incl[oi - 1] : 0)));
                     }
                 }
+            // the atomic's return value says whether the row is new; a word that becomes
+            // nonempty is marked in l1, so only touched words are cleared afterwards
 #pragma unroll
-                for (int i = 0; i < U; ++i)
-                    if ((uint32_t)row[i] < mrows) atomicOr(&bitmap[row[i] >> 5], 1u << (row[i] & 31));
+                for (int i = 0; i < U; ++i) {
+                    if ((uint32_t)row[i] >= mrows) continue;
+                    const int wd = row[i] >> 5;
+                    const uint32_t bit = 1u << (row[i] & 31);
+                    const uint32_t old = atomicOr(&bitmap[wd], bit);
+                    c += (old & bit) == 0u;
+                    if (old == 0u) atomicOr(&l1[wd >> 5], 1u << (wd & 31));
+                }
             }
             if constexpr (GS == 32) __syncwarp();
         }
         G::sync();
-        int c = 0;
-        for (int x = lane; x < nwc; x += GS) {
-            c += __popc(bitmap[x]);
-            bitmap[x] = 0u;
-        }
         int tot;
         group_incl_scan<GS>(c, s_scan, tot);
         if (lane == 0) nnz_item[u] = tot;
+        // empty the words this column touched (through the first-level bitmap)
+        for (int x = lane; x < 32; x += GS) {
+            uint32_t bits = l1[x];
+            while (bits) {
+                bitmap[x * 32 + __ffs(bits) - 1] = 0u;
+                bits &= bits - 1;
+            }
+            l1[x] = 0u;
+        }
         G::sync();
     }
 }
@@ -780,7 +797,7 @@ template <int GS, int BLOCK>
 static void run_bitcount(cudaStream_t st, const Items& it, const int2* list, int64_t count, int64_t* nnz_item) {
     if (count <= 0) return;
     constexpr int NG = BLOCK / GS;
-    constexpr size_t GROUP = ((size_t)GS * 12 + 34 * 4 + 15) / 16 * 16;
+    constexpr size_t GROUP = bitcount_group_bytes<GS>();
     const int bm_words = (int)((it.max_m + 31) / 32);
     const size_t smem = (GROUP + (size_t)bm_words * 4) * NG;
     auto kern = k_bitcount<GS, BLOCK>;
@@ -939,23 +956,6 @@ __host__ __device__ __forceinline__ void slab_rows(int64_t m, int q, int P, int6
     R1 = q == P - 1 ? m : (((int64_t)(q + 1) * m / P) & ~int64_t(31));
 }
 
-// bitmap[wd] |= bit for every lane with wd >= 0; lanes that hit the same word
-// combine their bits first, so each run of equal words takes one shared atomic.
-// Called by all 32 lanes of the warp.
-__device__ __forceinline__ void or_bits_warp(uint32_t* bitmap, int wd, uint32_t bit) {
-    const int lane = threadIdx.x & 31;
-    const int wprev = __shfl_up_sync(0xffffffffu, wd, 1);
-    const bool head = lane == 0 || wprev != wd;
-    uint32_t acc = bit;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t b2 = __shfl_down_sync(0xffffffffu, acc, o);
-        const int w2 = __shfl_down_sync(0xffffffffu, wd, o);
-        if (lane + o < 32 && w2 == wd) acc |= b2;
-    }
-    if (wd >= 0 && head) atomicOr(&bitmap[wd], acc);
-}
-
 // Slabs of the long columns: P per column, items[sbase[d] + q] = (d, q); the
 // storage bound of the slab row sets, sum over columns of min(flops, words),
 // accumulates in *store_bound (a slab stores min(words, rows) 4-byte entries and
@@ -1092,8 +1092,9 @@ __device__ __forceinline__ void rt_compact(RangeSmem* sc, bool active, int len, 
 // entries in chunks of RT_BLOCK; per entry the part of A(:,k) inside the rows
 // (two binary searches), compacted into segments; each warp takes a contiguous
 // slice of the chunk's products, four 32-product windows per step with every load
-// issued before the updates.  f(row, a, b) is called for each product (a and b,
-// the A and B values, only when NUM).  Ends with a CTA barrier.
+// issued before the updates.  f(valid, row, a, b) is called by all 32 lanes of a
+// warp for each window of products (a and b, the A and B values, only when NUM;
+// row is INT_MIN on lanes without a product).  Ends with a CTA barrier.
 template <class SR, bool NUM, class F>
 __device__ __forceinline__ void slab_walk(const Items& it, const Prod* pr, int64_t bs, int64_t be, int64_t R0,
                                           int64_t R1, int64_t m, RangeSmem* sc, F&& f) {
@@ -1147,9 +1148,8 @@ __device__ __forceinline__ void slab_walk(const Items& it, const Prod* pr, int64
                 }
 #pragma unroll
                 for (int uu = 0; uu < U; ++uu) {
-                    if (!ok[uu]) continue;
-                    if constexpr (NUM) f(row[uu], av[uu], *reinterpret_cast<const T*>(&sc->bv[ob[uu]]));
-                    else f(row[uu], T(0), T(0));
+                    if constexpr (NUM) f(ok[uu], row[uu], av[uu], ok[uu] ? *reinterpret_cast<const T*>(&sc->bv[ob[uu]]) : T(0));
+                    else f(ok[uu], row[uu], T(0), T(0));
                 }
             }
         }
@@ -1180,9 +1180,11 @@ __global__ void __launch_bounds__(RT_BLOCK, 2) k_slab_sym(Items it, DenseWork dw
         for (int x = tid; x < nw; x += RT_BLOCK) bitmap[x] = 0u;
         __syncthreads();
         const int span = (int)(R1 - R0);
-        slab_walk<BOOL8, false>(it, pr, bs, be, R0, R1, m, sc, [&](int32_t row, uint8_t, uint8_t) {
+        // one shared atomic per product: R-MAT rows of one window mostly fall in different
+        // words, so folding lanes per word first (shuffles) measured slower
+        slab_walk<BOOL8, false>(it, pr, bs, be, R0, R1, m, sc, [&](bool ok, int32_t row, uint8_t, uint8_t) {
             const int lr = (int)(row - R0);
-            if ((unsigned)lr < (unsigned)span) atomicOr(&bitmap[lr >> 5], 1u << (lr & 31));
+            if (ok && (unsigned)lr < (unsigned)span) atomicOr(&bitmap[lr >> 5], 1u << (lr & 31));
         });
         // count over contiguous word ranges, then store the row set
         const int wpt = (nw + RT_BLOCK - 1) / RT_BLOCK;
@@ -1265,12 +1267,14 @@ __global__ void __launch_bounds__(RT_BLOCK, 2) k_slab_num(Items it, DenseWork dw
         } else {
             for (int x = tid; x < ng * 4; x += RT_BLOCK) bitmap[x] = 0u;
             __syncthreads();
-            for (int i0 = 0; i0 < cnt; i0 += RT_BLOCK) {   // every thread of a warp takes part
+            for (int i0 = 0; i0 < cnt; i0 += RT_BLOCK) {
                 const int i = i0 + tid;
                 const int32_t r = i < cnt ? (int32_t)__ldg(rs + i) : -1;
                 const int lr = (int)(r - R0);
-                if (i < cnt) Cir[ob + i] = r + rb;    // C's rows: the row list itself
-                or_bits_warp(bitmap, i < cnt ? (lr >> 5) : -1, 1u << (lr & 31));
+                if (i < cnt) {
+                    Cir[ob + i] = r + rb;    // C's rows: the row list itself
+                    atomicOr(&bitmap[lr >> 5], 1u << (lr & 31));
+                }
             }
         }
         __syncthreads();
@@ -1313,7 +1317,8 @@ __global__ void __launch_bounds__(RT_BLOCK, 2) k_slab_num(Items it, DenseWork dw
         if (walk) {
             const int span = (int)(R1 - R0);
             slab_walk<SR, true>(it, pr, __ldg(pr->B.cp + e.y), __ldg(pr->B.cp + e.y + 1), R0, R1, m, sc,
-                                [&](int32_t row, T a, T b) {
+                                [&](bool ok, int32_t row, T a, T b) {
+                                    if (!ok) return;
                                     const int lr = (int)(row - R0);
                                     if ((unsigned)lr >= (unsigned)span) return;   // malformed input only
                                     const int wd = lr >> 5, g = wd >> 2, y = wd & 3;
