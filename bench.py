@@ -54,12 +54,13 @@ CPU_STRIDE = {18: 4, 20: 8}
 
 
 def _train_predictor(sp, ctx):
-    """Predictor trained on exact symbolic counts of R-MAT and ER squares (scales 14-16)
+    """Predictor trained on exact symbolic counts of R-MAT and ER squares of scales 14-18,
     drawn from seeds disjoint from the measured workloads."""
     import torch
     Xs, ys = [], []
     for M in (gen.rmat(14, 8, 0x7000), gen.erdos_renyi(16384, 16384, 8, 0x7100), gen.rmat(16, 4, 0x7200),
-              gen.rmat(15, 16, 0x7300)):
+              gen.rmat(15, 16, 0x7300), gen.rmat(17, 8, 0x7400), gen.rmat(18, 8, 0x7500),
+              gen.erdos_renyi(65536, 65536, 16, 0x7600)):
         d = sp.Matrix.from_host(ctx, M, sp.PLUS_TIMES_F64)
         X, y = sp.spgemm_predictor_features(ctx, d, d)
         keep = y > 0
@@ -69,18 +70,67 @@ def _train_predictor(sp, ctx):
     sp.spgemm_predictor_set(ctx, np.random.default_rng(11).normal(0, 0.2, sp.NPARAM).astype(np.float32))
     for _ in range(400):
         loss, _ = sp.spgemm_predictor_train_step(ctx, X, y, 3e-3)
-    return loss
+    return {"loss": loss, "samples": int(X.shape[0]),
+            "matrices": "R-MAT scales 14-18 and ER 2^14, 2^16 squares, seeds 0x7000-0x7600"}
 
 
-def learned_vs_plain(sp, ctx, steps: int, warmup: int) -> dict:
-    """The batched workloads, plain (one plan -> symbolic -> numeric per product, in
-    sequence) against learned+batched (all products of the workload in one batched
-    execution, the predictor sizing the output instead of the symbolic pass, bins from
-    the autotuner).  Wall time on the device, synchronised on both sides; outputs
-    compared by nnz."""
+def _same_outputs(ctx, Xs, Ys, sr) -> bool:
+    """Exact equality of two lists of device products: column pointers, rows, and values
+    (bit-exact for int64, boolean and min-plus; within 1e-13 relative for plus-times FP64)."""
     import torch
+    torch.cuda.current_stream().wait_stream(ctx.stream)
+    for X, Y in zip(Xs, Ys):
+        mx, nx, zx, cpx, irx, vx = X.export()
+        my, ny, zy, cpy, iry, vy = Y.export()
+        if (mx, nx, zx) != (my, ny, zy) or not torch.equal(cpx, cpy) or not torch.equal(irx, iry):
+            return False
+        if sr == 0:
+            if not bool(((vx - vy).abs() <= 1e-13 * vy.abs()).all()):
+                return False
+        elif not torch.equal(vx, vy):
+            return False
+    return True
+
+
+def _timed_arm(ctx, fn, steps, warmup, flush):
+    """Median device time of fn() (CUDA events on the context stream, L2 flushed before
+    each run) over `steps` runs after `warmup` untimed runs; returns (ms, last result)."""
+    import torch
+    st = ctx.stream
+    for _ in range(warmup):
+        r = fn()
+        del r
+    ts = []
+    r = None
+    for _ in range(steps):
+        del r
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        r = fn()
+        e1.record(st)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts), r
+
+
+def learned_vs_plain(sp, ctx, steps: int, warmup: int, flush, c5=None) -> dict:
+    """The a9 + a10 comparison.  Per batched workload five arms, each timed on the device
+    (CUDA events, L2 flushed, median of `steps` after `warmup`) and checked against the
+    plain arm's output, exactly:
+      plain            one spgemm_multiply per product, in sequence;
+      batched          spgemm_batch, exact symbolic pass, autotuned thresholds;
+      learned_batched  spgemm_batch with the predictor sizing the output (no symbolic
+                       pass for the hash tiers), autotuned thresholds;
+      auto             spgemm_batch with what the autotuner chose, predictor included;
+      graph_replay     spgemm_batch_plan once, then one spgemm_batch_execute per call: the
+                       numeric pass replayed from a CUDA graph (same structure, new values).
+    A speedup is reported only where the outputs are identical."""
     import oracle
-    loss = _train_predictor(sp, ctx)
+    train = _train_predictor(sp, ctx)
+    out = {"predictor": train, "timing": f"CUDA events, median of {steps} after {warmup} warm-up runs, "
+                                          "L2 flushed before each"}
     work = {}
     pairs = gen.batch_pairs(512, 0x4004)
     As = [sp.Matrix.from_host(ctx, a, sp.PLUS_TIMES_I64) for a, _ in pairs]
@@ -93,59 +143,72 @@ def learned_vs_plain(sp, ctx, steps: int, warmup: int) -> dict:
     work["bfs_step_bool"] = ([sp.Matrix.from_host(ctx, Ab, sp.OR_AND_BOOL)], [sp.Matrix.from_host(ctx, F, sp.OR_AND_BOOL)],
                              sp.OR_AND_BOOL, int(oracle.flops_per_col(Ab, F).sum()),
                              "boolean R-MAT scale 20 (edge factor 16) times a 2^20 x 128 frontier")
+    for name, (As_, Bs_, sr, flops, desc) in work.items():
+        tuned = sp.default_opts(use_predictor=1)
+        tuned = sp.spgemm_autotune(ctx, As_, Bs_, sr, tuned)
+        thr = dict(warp_max_flops=tuned.warp_max_flops, block_max_flops=tuned.block_max_flops,
+                   dense_part_flops=tuned.dense_part_flops)
+        o_b, o_l = sp.default_opts(use_predictor=0, **thr), sp.default_opts(use_predictor=1, **thr)
+        t_p, Cp = _timed_arm(ctx, lambda: [sp.spgemm_multiply(ctx, a, b, sr) for a, b in zip(As_, Bs_)], steps,
+                             warmup, flush)
+        rec = {"workload": desc, "flops": flops, "tuned": {**thr, "use_predictor": tuned.use_predictor},
+               "plain_ms": t_p}
+        for arm, fn in (("batched", lambda: sp.spgemm_batch(ctx, As_, Bs_, sr, o_b)),
+                        ("learned_batched", lambda: sp.spgemm_batch(ctx, As_, Bs_, sr, o_l)),
+                        ("auto", lambda: sp.spgemm_batch(ctx, As_, Bs_, sr, tuned))):
+            t, C = _timed_arm(ctx, fn, steps, warmup, flush)
+            same = _same_outputs(ctx, C, Cp, sr)
+            rec[arm] = {"ms": t, "identical": same, "speedup": t_p / t if same else None}
+            del C
+        plan = sp.spgemm_batch_plan(ctx, As_, Bs_, sr, o_b)
+        t, _ = _timed_arm(ctx, lambda: plan.execute(), steps, warmup, flush)
+        same = _same_outputs(ctx, plan.outputs(), Cp, sr)
+        rec["graph_replay"] = {"ms": t, "identical": same, "speedup": t_p / t if same else None,
+                               "note": "numeric pass only, replayed from a CUDA graph on a fixed structure"}
+        del plan, Cp
+        rec["predictor_gain"] = rec["batched"]["ms"] / rec["learned_batched"]["ms"]
+        out[name] = rec
+    # Galerkin triple product R*(A*P), FP64: two dependent products
     N = 128
     A, P = gen.grid3d_laplacian(N), gen.aggregation_2x2x2(N)
     R = gen.transpose_host(P)
     dA, dP, dR = (sp.Matrix.from_host(ctx, M, sp.PLUS_TIMES_F64) for M in (A, P, R))
-    out = {"predictor_train_loss": loss}
-
-    def timed(fn):
-        for _ in range(max(1, warmup)):
-            fn()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(steps):
-            r = fn()
-        torch.cuda.synchronize()
-        return (time.perf_counter() - t0) / steps * 1e3, r
-
-    def nnz_of(Cs):
-        return sum(C.shape()[2] for C in Cs)
-
-    for name, (As_, Bs_, sr, flops, desc) in work.items():
-        tuned = sp.spgemm_autotune(ctx, As_, Bs_, sr)
-        lo = sp.default_opts(use_predictor=1, warp_max_flops=tuned.warp_max_flops,
-                             block_max_flops=tuned.block_max_flops, dense_part_flops=tuned.dense_part_flops)
-        t_plain, Cp = timed(lambda: [sp.spgemm_multiply(ctx, a, b, sr) for a, b in zip(As_, Bs_)])
-        nz_plain = nnz_of(Cp)
-        del Cp
-        t_lb, Cl = timed(lambda: sp.spgemm_batch(ctx, As_, Bs_, sr, lo))
-        nz_lb = nnz_of(Cl)
-        del Cl
-        out[name] = {"workload": desc, "flops": flops, "plain_ms": t_plain, "learned_batched_ms": t_lb,
-                     "speedup": t_plain / t_lb, "plain_gflops": 2 * flops / t_plain / 1e6,
-                     "learned_batched_gflops": 2 * flops / t_lb / 1e6, "same_nnz": nz_plain == nz_lb,
-                     "tuned": [tuned.warp_max_flops, tuned.block_max_flops, tuned.dense_part_flops]}
-        torch.cuda.empty_cache()
-    # Galerkin triple product R*(A*P), FP64: plain products vs the learned+autotuned batch form
-    tuned = sp.spgemm_autotune(ctx, [dA], [dP], sp.PLUS_TIMES_F64)
-    lo = sp.default_opts(use_predictor=1, warp_max_flops=tuned.warp_max_flops,
-                         block_max_flops=tuned.block_max_flops, dense_part_flops=tuned.dense_part_flops)
-
-    def rap_plain():
-        AP = sp.spgemm_multiply(ctx, dA, dP, sp.PLUS_TIMES_F64)
-        return sp.spgemm_multiply(ctx, dR, AP, sp.PLUS_TIMES_F64)
-
-    def rap_learned():
-        AP = sp.spgemm_batch(ctx, [dA], [dP], sp.PLUS_TIMES_F64, lo)[0]
-        return sp.spgemm_batch(ctx, [dR], [AP], sp.PLUS_TIMES_F64, lo)[0]
-
+    sr = sp.PLUS_TIMES_F64
+    tuned = sp.spgemm_autotune(ctx, [dA], [dP], sr, sp.default_opts(use_predictor=1))
+    thr = dict(warp_max_flops=tuned.warp_max_flops, block_max_flops=tuned.block_max_flops,
+               dense_part_flops=tuned.dense_part_flops)
     fl = A.nnz + 32 * 64 ** 3 - 24 * 64 ** 2   # flops(A*P) = nnz(A), flops(R*(AP)) = nnz(AP)
-    t_plain, C1 = timed(rap_plain)
-    t_lb, C2 = timed(rap_learned)
-    out["galerkin128_fp64"] = {"workload": "R*(A*P), 7-point Laplacian on 128^3, 2x2x2 aggregation",
-                               "flops": fl, "plain_ms": t_plain, "learned_batched_ms": t_lb,
-                               "speedup": t_plain / t_lb, "same_nnz": C1.shape()[2] == C2.shape()[2]}
+    t_p, Cp = _timed_arm(ctx, lambda: [sp.spgemm_multiply(ctx, dR, sp.spgemm_multiply(ctx, dA, dP, sr), sr)],
+                         steps, warmup, flush)
+    rec = {"workload": "R*(A*P), 7-point Laplacian on 128^3, 2x2x2 aggregation", "flops": fl,
+           "tuned": {**thr, "use_predictor": tuned.use_predictor}, "plain_ms": t_p}
+    for arm, o in (("batched", sp.default_opts(use_predictor=0, **thr)),
+                   ("learned_batched", sp.default_opts(use_predictor=1, **thr)), ("auto", tuned)):
+        t, C = _timed_arm(ctx, lambda o=o: [sp.spgemm_batch(ctx, [dR], sp.spgemm_batch(ctx, [dA], [dP], sr, o), sr, o)[0]],
+                          steps, warmup, flush)
+        same = _same_outputs(ctx, C, Cp, sr)
+        rec[arm] = {"ms": t, "identical": same, "speedup": t_p / t if same else None}
+        del C
+    p1 = sp.spgemm_batch_plan(ctx, [dA], [dP], sr, sp.default_opts(**thr))
+    p1.execute()
+    p2 = sp.spgemm_batch_plan(ctx, [dR], p1.outputs(), sr, sp.default_opts(**thr))
+    t, _ = _timed_arm(ctx, lambda: (p1.execute(), p2.execute()), steps, warmup, flush)
+    same = _same_outputs(ctx, p2.outputs(), Cp, sr)
+    rec["graph_replay"] = {"ms": t, "identical": same, "speedup": t_p / t if same else None,
+                           "note": "numeric passes only, replayed from CUDA graphs on a fixed structure"}
+    rec["predictor_gain"] = rec["batched"]["ms"] / rec["learned_batched"]["ms"]
+    out["galerkin128_fp64"] = rec
+    del p1, p2, Cp
+    # the large skewed squaring (R-MAT scale 20 flat A*A): predictor on vs off
+    if c5 is not None:
+        for sr, M in c5:
+            t_p, Cp = _timed_arm(ctx, lambda: [sp.spgemm_multiply(ctx, M, M, sr)], max(3, steps // 2), 3, flush)
+            t_l, Cl = _timed_arm(ctx, lambda: [sp.spgemm_multiply(ctx, M, M, sr, sp.default_opts(use_predictor=1))],
+                                 max(3, steps // 2), 3, flush)
+            same = _same_outputs(ctx, Cl, Cp, sr)
+            out[f"rmat20_flat_{SR_NAME[sr]}"] = {"plain_ms": t_p, "learned_ms": t_l, "identical": same,
+                                                 "speedup": t_p / t_l if same else None}
+            del Cp, Cl
     return out
 
 
@@ -686,10 +749,12 @@ def main():
     if rank == 0:
         Mimb = W["mats"].get(sp.PLUS_TIMES_F64) or sp.Matrix.from_host(ctx, W["A64"], sp.PLUS_TIMES_F64)
         imb = summa_imbalance(sp, ctx, Mimb, args.grid)
+    c5_mats = [(sr, W["mats"][sr]) for sr in (sp.PLUS_TIMES_F64, sp.OR_AND_BOOL) if sr in W["mats"]] \
+        if args.scale == 20 else None
     secondary = None
     if not args.no_secondary and (args.scale, args.grid) != SECONDARY[:2]:
         sc2, g2, srs2 = SECONDARY
-        del W["mats"], W["run_product"]
+        del W["run_product"]
         torch.cuda.empty_cache()
         W2 = run_workload(sp, ctx, sc2, g2, srs2, ["flat", "summa"], 10, 3, lib_opts, flush, world, local,
                           sample=False)
@@ -702,7 +767,7 @@ def main():
     lvp = None
     if rank == 0 and world == 1 and not args.no_learned:
         torch.cuda.empty_cache()
-        lvp = learned_vs_plain(sp, ctx, steps=10, warmup=3)
+        lvp = learned_vs_plain(sp, ctx, steps=10, warmup=3, flush=flush, c5=c5_mats)
 
     if rank == 0:
         A64, products = W["A64"], W["products"]

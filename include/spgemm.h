@@ -14,10 +14,14 @@
  *   - Every pointer passed in a matrix handle is a DEVICE pointer on the
  *     context's GPU, unless an entry point says otherwise.
  *   - All work is enqueued on the context's CUDA stream.  The product calls
- *     synchronise that stream where a host decision needs a device count (tier
- *     list sizes, output sizes, block layouts of the SUMMA split), so a product
- *     call returns with its result complete; handle creation and export do not
- *     synchronise.
+ *     synchronise that stream where a host decision needs a device count, so a
+ *     product call returns with its result complete; handle creation and export
+ *     do not synchronise.  The counts a flat product waits for: the input check
+ *     (once per borrowed handle), the column count of every accumulator tier
+ *     (launch sizes and list offsets), the slab count and row-set bound of the
+ *     long columns (their arrays), the output size nnz(C) (the allocation of
+ *     C), and, with the predictor, the predicted capacity and the overflowed
+ *     columns.  SUMMA adds the block layouts of the split and of every merge.
  *   - Every function returns spgemm_status_t and never aborts; the message of
  *     the last failure is available from spgemm_last_error(ctx).
  *   - Results are structural: C(i,j) exists iff some k pairs a stored A(i,k)
@@ -114,7 +118,13 @@ typedef struct {
                                  where a column would need more than 64 slabs.
                                  0 = default (2^19).  A long column of more than
                                  64 * (2^20 - 32) rows is SPGEMM_ERR_UNSUPPORTED.   */
-    int reserved[5];
+    int check_inputs;         /* 1 (default): every product call first checks, on the
+                                 device, each borrowed CSC/CSR operand it has not checked
+                                 before (the spgemm_mat_validate invariants) and returns
+                                 SPGEMM_ERR_BAD_FORMAT before any product kernel runs; a
+                                 handle passes once and is then trusted (re-check arrays
+                                 changed in place with spgemm_mat_validate).  0: skip. */
+    int reserved[4];
 } spgemm_opts_t;
 
 void spgemm_opts_default(spgemm_opts_t* opts);
@@ -133,7 +143,8 @@ const char* spgemm_status_string(spgemm_status_t s);
 /* Borrowing CSC handle over device arrays (Section 2.2, Fig. 5): colptr[n+1]
  * int64, rowidx[nnz] int32, vals[nnz] of the semiring type (vals may be NULL
  * for a pattern-only matrix, read as all-ones / all-true / zero for min-plus).
- * No check is run here; see spgemm_mat_validate. */
+ * No device work is done here: the arrays are checked by the first product
+ * call that uses the handle (check_inputs) or by spgemm_mat_validate. */
 spgemm_status_t spgemm_mat_csc(spgemm_ctx_t ctx, spgemm_mat_t* out, int64_t m, int64_t n, int64_t nnz,
                                const int64_t* colptr, const int32_t* rowidx, const void* vals,
                                spgemm_semiring_t semiring);
@@ -143,7 +154,8 @@ spgemm_status_t spgemm_mat_csr(spgemm_ctx_t ctx, spgemm_mat_t* out, int64_t m, i
                                spgemm_semiring_t semiring);
 /* Checks the CSC/CSR invariants on the device: colptr[0] == 0, colptr
  * monotone, colptr[n] == nnz, rows in [0, m) and strictly ascending per column.
- * Returns SPGEMM_ERR_BAD_FORMAT on the first violation found (synchronises). */
+ * Returns SPGEMM_ERR_BAD_FORMAT on a violation (synchronises); on success the
+ * handle is marked checked (see spgemm_opts_t.check_inputs). */
 spgemm_status_t spgemm_mat_validate(spgemm_mat_t mat);
 /* CSC -> DCSC (Section 2.3): JC = ids of the nzc nonempty columns, CP = their
  * pointers (nzc+1), IR/NUM shared with the source (the result borrows them, so
@@ -290,8 +302,13 @@ spgemm_status_t spgemm_batch_execute(spgemm_plan_t plan);
 spgemm_status_t spgemm_batch_outputs(spgemm_plan_t plan, spgemm_mat_t* C);
 /* Autotuner: times the numeric phase of the batch for a small set of tier
  * thresholds (warp_max_flops, block_max_flops, dense_part_flops) and writes the
- * fastest into *opts (other fields kept).  Results are cached in the context
- * per (semiring, number of products, total flops rounded to a power of two). */
+ * fastest into *opts.  When opts->use_predictor is set and the context holds
+ * predictor parameters, it then times whole spgemm_batch calls with and
+ * without the predictor (at the chosen thresholds) and leaves use_predictor at
+ * 1 only if the predictor measured faster, so the tuned call never loses to
+ * the exact symbolic pass.  Other fields are kept.  Results are cached in the
+ * context per (semiring, predictor tried, number of products, total flops
+ * rounded to a power of two). */
 spgemm_status_t spgemm_autotune(spgemm_ctx_t ctx, int count, const spgemm_mat_t* A, const spgemm_mat_t* B,
                                 spgemm_semiring_t semiring, spgemm_opts_t* opts);
 

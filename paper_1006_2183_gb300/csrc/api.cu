@@ -115,6 +115,7 @@ void spgemm_opts_default(spgemm_opts_t* o) {
     o->dense_part_flops = DEFAULT_PART_FLOPS;
     o->range_slab_rows = 0;
     o->predictor_margin = 0.25f;
+    o->check_inputs = 1;
 }
 
 spgemm_status_t spgemm_ctx_create(spgemm_ctx_t* out, void* stream, spgemm_alloc_fn alloc, spgemm_free_fn free_fn,
@@ -266,6 +267,7 @@ spgemm_mat_t new_owned_csc(spgemm_ctx* ctx, spgemm_semiring_t sr, int64_t m, int
     M->ir = ir;
     M->num = num;
     M->owned = std::move(owned);
+    M->checked = true;
     return M;
 }
 
@@ -610,6 +612,7 @@ spgemm_status_t spgemm_plan(spgemm_ctx_t ctx, spgemm_mat_t A, spgemm_mat_t B, sp
     spgemm_opts_t o;
     spgemm_opts_default(&o);
     if (opts) o = *opts;
+    if (o.check_inputs) SG_TRY(check_handles(ctx, {A, B}));
     auto* P = new struct spgemm_plan();
     P->ctx = ctx;
     P->sr = sr;

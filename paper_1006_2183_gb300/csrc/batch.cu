@@ -22,8 +22,18 @@ __global__ void k_gather_offsets(const int64_t* __restrict__ Coff, const int64_t
 }
 
 spgemm_status_t collect_prods(spgemm_ctx* ctx, int count, const spgemm_mat_t* A, const spgemm_mat_t* B,
-                              spgemm_semiring_t sr, std::vector<Prod>* prods, std::vector<spgemm_mat_t>* convs) {
+                              spgemm_semiring_t sr, std::vector<Prod>* prods, std::vector<spgemm_mat_t>* convs,
+                              bool check = false) {
     if (count < 0 || (count > 0 && (!A || !B))) return set_err(ctx, SPGEMM_ERR_INVALID_ARG, "bad batch arrays");
+    if (check) {
+        std::vector<spgemm_mat*> ops;
+        for (int i = 0; i < count; ++i) {
+            if (!A[i] || !B[i]) return set_err(ctx, SPGEMM_ERR_INVALID_ARG, "null operand %d", i);
+            ops.push_back(A[i]);
+            ops.push_back(B[i]);
+        }
+        SG_TRY(check_handles(ctx, ops));
+    }
     for (int i = 0; i < count; ++i) {
         if (!A[i] || !B[i]) return set_err(ctx, SPGEMM_ERR_INVALID_ARG, "null operand %d", i);
         if (A[i]->sr != sr || B[i]->sr != sr) return set_err(ctx, SPGEMM_ERR_INVALID_ARG, "semiring of pair %d", i);
@@ -85,7 +95,7 @@ spgemm_status_t batch_plan_build(spgemm_ctx* ctx, int count, const spgemm_mat_t*
     P->opts = o;
     P->is_batch = true;
     std::vector<Prod> prods;
-    SG_TRY(collect_prods(ctx, count, A, B, sr, &prods, &P->convs));
+    SG_TRY(collect_prods(ctx, count, A, B, sr, &prods, &P->convs, o.check_inputs != 0));
     Engine& E = P->E;
     const bool learned = o.use_predictor && ctx->pred_ready && run_numeric;
     SG_TRY(engine_setup(&E, ctx, sr, o, prods, learned));
@@ -125,7 +135,32 @@ struct TuneKey {
         return std::tie(sr, count, lgflops) < std::tie(o.sr, o.count, o.lgflops);
     }
 };
-std::map<std::pair<spgemm_ctx*, TuneKey>, std::tuple<int, int, int>> g_tune_cache;
+std::map<std::pair<spgemm_ctx*, TuneKey>, std::tuple<int, int, int, int>> g_tune_cache;
+
+// Device time of whole spgemm_batch calls with opts o (one warm-up, then the best of two).
+float time_batch_calls(spgemm_ctx* ctx, int count, const spgemm_mat_t* A, const spgemm_mat_t* B,
+                       spgemm_semiring_t sr, const spgemm_opts_t& o, spgemm_status_t* st) {
+    std::vector<spgemm_mat_t> C(std::max(count, 1), nullptr);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    *st = SPGEMM_OK;
+    for (int r = 0; r < 3 && *st == SPGEMM_OK; ++r) {
+        cudaEventRecord(e0, ctx->stream);
+        *st = spgemm_batch(ctx, count, A, B, sr, &o, C.data());
+        cudaEventRecord(e1, ctx->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (r > 0) best = std::min(best, ms);
+        if (*st == SPGEMM_OK)
+            for (int i = 0; i < count; ++i) spgemm_mat_destroy(C[i]);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return best;
+}
 
 }  // namespace
 
@@ -216,14 +251,15 @@ spgemm_status_t spgemm_autotune(spgemm_ctx_t ctx, int count, const spgemm_mat_t*
     }
     int lg = 0;
     while ((int64_t(1) << lg) < fl && lg < 62) ++lg;
-    TuneKey key{(int)sr, count, lg};
+    const bool try_pred = opts->use_predictor != 0 && ctx->pred_ready;
+    TuneKey key{(int)sr * 2 + (try_pred ? 1 : 0), count, lg};
     auto hit = g_tune_cache.find({ctx, key});
     if (hit == g_tune_cache.end()) {
         const int warp_c[] = {128, 512};
         const int block_c[] = {1024, 4096};
         const int part_c[] = {32768, 262144};
         double best = 1e30;
-        std::tuple<int, int, int> pick{opts->warp_max_flops, opts->block_max_flops, opts->dense_part_flops};
+        std::tuple<int, int, int, int> pick{opts->warp_max_flops, opts->block_max_flops, opts->dense_part_flops, 0};
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
@@ -249,16 +285,33 @@ spgemm_status_t spgemm_autotune(spgemm_ctx_t ctx, int count, const spgemm_mat_t*
                     }
                     if (tot < best) {
                         best = tot;
-                        pick = {wm, bm, pf};
+                        pick = {wm, bm, pf, 0};
                     }
                 }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
+        if (try_pred) {
+            // the predictor replaces the symbolic pass of the hash tiers but adds its own launches
+            // and a move of C: keep it only where the whole batched call measured faster with it
+            spgemm_opts_t o = *opts;
+            o.warp_max_flops = std::get<0>(pick);
+            o.block_max_flops = std::get<1>(pick);
+            o.dense_part_flops = std::get<2>(pick);
+            spgemm_status_t s1, s0;
+            o.use_predictor = 1;
+            const float t1 = time_batch_calls(ctx, count, A, B, sr, o, &s1);
+            SG_TRY(s1);
+            o.use_predictor = 0;
+            const float t0 = time_batch_calls(ctx, count, A, B, sr, o, &s0);
+            SG_TRY(s0);
+            std::get<3>(pick) = t1 < t0 ? 1 : 0;
+        }
         hit = g_tune_cache.emplace(std::make_pair(ctx, key), pick).first;
     }
     opts->warp_max_flops = std::get<0>(hit->second);
     opts->block_max_flops = std::get<1>(hit->second);
     opts->dense_part_flops = std::get<2>(hit->second);
+    if (try_pred) opts->use_predictor = std::get<3>(hit->second);
     return SPGEMM_OK;
 }
 

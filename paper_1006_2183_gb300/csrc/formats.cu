@@ -168,7 +168,97 @@ __global__ void k_validate(const int64_t* __restrict__ cp, const int32_t* __rest
     }
 }
 
+// Format check of several stored CSC arrays at once: one warp per column of the
+// concatenated column space (handle h owns columns [cbase[h], cbase[h+1])); the
+// first lane checks the column's pointers, all lanes its rows.  bad[h] gets the
+// largest violation code seen.
+struct VDesc {
+    const int64_t* cp;
+    const int32_t* ir;
+    int64_t m, n, nnz;
+};
+__global__ void k_validate_many(const VDesc* __restrict__ d, const int64_t* __restrict__ cbase, int nh,
+                                int* __restrict__ bad) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t total = cbase[nh];
+    for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < total; c += nwarps) {
+        int lo = 0, hi = nh - 1;   // the handle h with cbase[h] <= c < cbase[h+1]
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (cbase[mid] <= c) lo = mid;
+            else hi = mid - 1;
+        }
+        const VDesc D = d[lo];
+        const int64_t j = c - cbase[lo];
+        const int64_t s = D.cp[j], e = D.cp[j + 1];
+        int code = 0;
+        if (j == 0 && s != 0) code = 1;
+        else if (j == D.n - 1 && e != D.nnz) code = 2;
+        else if (e < s || s < 0 || e > D.nnz) code = 3;
+        if (code == 0) {
+            for (int64_t t = s + lane; t < e; t += 32) {
+                const int32_t r = D.ir[t];
+                if (r < 0 || r >= D.m) code = code > 4 ? code : 4;
+                else if (t > s && D.ir[t - 1] >= r) code = 5;
+            }
+        }
+        if (code) atomicMax(bad + lo, code);
+    }
+}
+
 }  // namespace
+
+spgemm_status_t check_handles(spgemm_ctx* ctx, const std::vector<spgemm_mat*>& mats) {
+    std::vector<spgemm_mat*> todo;
+    for (spgemm_mat* M : mats)
+        if (M && !M->checked && M->fmt != SPGEMM_FMT_DCSC && std::find(todo.begin(), todo.end(), M) == todo.end())
+            todo.push_back(M);
+    if (todo.empty()) return SPGEMM_OK;
+    const int nh = (int)todo.size();
+    std::vector<VDesc> hd(nh);
+    std::vector<int64_t> hb(nh + 1, 0);
+    for (int h = 0; h < nh; ++h) {
+        spgemm_mat* M = todo[h];
+        // stored arrays: CSC of (rows = stored m) x (cols = stored n)
+        const int64_t sm = M->fmt == SPGEMM_FMT_CSR ? M->n : M->m;
+        const int64_t sn = M->fmt == SPGEMM_FMT_CSR ? M->m : M->n;
+        hd[h] = VDesc{M->cp, M->ir, sm, sn, M->nnz};
+        hb[h + 1] = hb[h] + sn;
+    }
+    const size_t bytes = sizeof(VDesc) * nh + 8 * (nh + 1) + 4 * nh;
+    auto buf = ctx_buf(ctx, bytes);
+    if (!buf) return set_err(ctx, SPGEMM_ERR_OOM, "input check");
+    VDesc* dd = (VDesc*)buf->p;
+    int64_t* db = (int64_t*)(dd + nh);
+    int* dbad = (int*)(db + nh + 1);
+    cudaStream_t st = ctx->stream;
+    SG_CUDA(ctx, cudaMemcpyAsync(dd, hd.data(), sizeof(VDesc) * nh, cudaMemcpyHostToDevice, st));
+    SG_CUDA(ctx, cudaMemcpyAsync(db, hb.data(), 8 * (nh + 1), cudaMemcpyHostToDevice, st));
+    SG_CUDA(ctx, cudaMemsetAsync(dbad, 0, 4 * nh, st));
+    std::vector<int> hbad(nh, 0);
+    if (hb[nh] > 0) {
+        k_validate_many<<<grid_for(hb[nh] * 32), 256, 0, st>>>(dd, db, nh, dbad);
+        note_launch();
+    }
+    SG_CUDA(ctx, cudaMemcpyAsync(hbad.data(), dbad, 4 * nh, cudaMemcpyDeviceToHost, st));
+    // a matrix without columns: its (single) column pointer must be 0 and nnz 0
+    std::vector<int64_t> c0(nh, 0);
+    for (int h = 0; h < nh; ++h)
+        if (hb[h + 1] == hb[h]) SG_CUDA(ctx, cudaMemcpyAsync(&c0[h], todo[h]->cp, 8, cudaMemcpyDeviceToHost, st));
+    SG_TRY(sync_ctx(ctx));
+    static const char* why[] = {"", "colptr[0] != 0", "colptr[n] != nnz", "colptr not monotone",
+                                "row index out of range", "rows not strictly ascending in a column"};
+    for (int h = 0; h < nh; ++h) {
+        int code = hbad[h];
+        if (hb[h + 1] == hb[h] && (c0[h] != 0 || todo[h]->nnz != 0)) code = 1;
+        if (code)
+            return set_err(ctx, SPGEMM_ERR_BAD_FORMAT, "operand %d of this call (%lld x %lld): %s", h,
+                           (long long)todo[h]->m, (long long)todo[h]->n, why[code < 6 ? code : 0]);
+    }
+    for (spgemm_mat* M : todo) M->checked = true;
+    return SPGEMM_OK;
+}
 
 // Stable sort of (key, payload) pairs by the low `bits` bits of key, LSD with
 // 8-bit digits.  Buffers (k0, v0) hold the input; the result ends in (k0, v0)
@@ -478,6 +568,7 @@ spgemm_status_t spgemm_mat_permute(spgemm_ctx_t ctx, spgemm_mat_t a, const int32
     if (a->fmt == SPGEMM_FMT_DCSC) return set_err(ctx, SPGEMM_ERR_UNSUPPORTED, "permute of a DCSC handle");
     SG_TRY(check_perm(ctx, row_perm, a->m, "row_perm"));
     SG_TRY(check_perm(ctx, col_perm, a->n, "col_perm"));
+    SG_TRY(check_handles(ctx, {a}));
     spgemm_mat_t conv = nullptr;
     DMat d;
     SG_TRY(to_csc_operand(ctx, a, &conv, &d));
@@ -489,6 +580,7 @@ spgemm_status_t spgemm_mat_permute(spgemm_ctx_t ctx, spgemm_mat_t a, const int32
         return s;
     }
     P->sr = a->sr;
+    P->checked = true;
     *out = P;
     return SPGEMM_OK;
 }
@@ -496,7 +588,9 @@ spgemm_status_t spgemm_mat_permute(spgemm_ctx_t ctx, spgemm_mat_t a, const int32
 spgemm_status_t spgemm_mat_transpose(spgemm_ctx_t ctx, spgemm_mat_t a, spgemm_mat_t* out) {
     if (!ctx || !a || !out) return SPGEMM_ERR_INVALID_ARG;
     if (a->fmt == SPGEMM_FMT_DCSC) return set_err(ctx, SPGEMM_ERR_UNSUPPORTED, "transpose of a DCSC handle");
+    SG_TRY(check_handles(ctx, {a}));
     auto* T = new spgemm_mat();
+    T->checked = true;
     spgemm_status_t s;
     if (a->fmt == SPGEMM_FMT_CSR) {
         // CSR(A) stores CSC(A^T): its arrays already are A^T in CSC; copy nothing, borrow
@@ -526,7 +620,9 @@ spgemm_status_t spgemm_mat_transpose(spgemm_ctx_t ctx, spgemm_mat_t a, spgemm_ma
 spgemm_status_t spgemm_mat_to_dcsc(spgemm_ctx_t ctx, spgemm_mat_t csc, int build_aux, spgemm_mat_t* out) {
     if (!ctx || !csc || !out) return SPGEMM_ERR_INVALID_ARG;
     if (csc->fmt != SPGEMM_FMT_CSC) return set_err(ctx, SPGEMM_ERR_INVALID_ARG, "to_dcsc expects a CSC handle");
+    SG_TRY(check_handles(ctx, {csc}));
     auto* D = new spgemm_mat();
+    D->checked = true;
     spgemm_status_t s = make_dcsc(ctx, csc, build_aux != 0, D);
     if (s != SPGEMM_OK) {
         delete D;
@@ -563,6 +659,7 @@ spgemm_status_t spgemm_mat_validate(spgemm_mat_t M) {
     static const char* why[] = {"", "colptr[0] != 0", "colptr[n] != nnz", "colptr not monotone",
                                 "row index out of range", "rows not strictly ascending in a column"};
     if (h) return set_err(ctx, SPGEMM_ERR_BAD_FORMAT, "%s", why[h < 6 ? h : 0]);
+    M->checked = true;
     return SPGEMM_OK;
 }
 

@@ -59,6 +59,7 @@ struct spgemm_mat {
     const int32_t* aux = nullptr;
     int64_t naux = 0, chunk = 1;
     std::vector<std::shared_ptr<DevBuf>> owned;
+    bool checked = false;   // arrays passed the format check (library-made handles are born checked)
 };
 
 // One batched execution of products C_i = A_i * B_i over the item space
@@ -151,6 +152,10 @@ spgemm_status_t check_cuda(spgemm_ctx* ctx, cudaError_t e, const char* what);
 spgemm_status_t sync_ctx(spgemm_ctx* ctx);
 
 // formats.cu
+// Checks, in one launch and one synchronisation, every handle of `mats` that is a
+// borrowed CSC/CSR not checked before (null entries and duplicates are skipped);
+// SPGEMM_ERR_BAD_FORMAT names the first failing handle.  Passing handles are marked.
+spgemm_status_t check_handles(spgemm_ctx* ctx, const std::vector<spgemm_mat*>& mats);
 spgemm_status_t transpose_csc(spgemm_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const int64_t* cp,
                               const int32_t* ir, const void* num, size_t w, spgemm_mat_t out_handle);
 spgemm_status_t make_dcsc(spgemm_ctx* ctx, const spgemm_mat* csc, bool aux, spgemm_mat* out);

@@ -387,6 +387,7 @@ spgemm_status_t spgemm_predictor_features(spgemm_ctx_t ctx, spgemm_mat_t A, spge
     if (A->n != B->m) return set_err(ctx, SPGEMM_ERR_DIM_MISMATCH, "inner dimensions differ");
     if (B->fmt != SPGEMM_FMT_CSC || A->fmt == SPGEMM_FMT_CSR)
         return set_err(ctx, SPGEMM_ERR_UNSUPPORTED, "features need CSC or DCSC A and CSC B");
+    SG_TRY(check_handles(ctx, {A, B}));
     spgemm_opts_t o;
     spgemm_opts_default(&o);
     Prod pr;

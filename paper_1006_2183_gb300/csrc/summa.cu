@@ -615,6 +615,7 @@ spgemm_status_t summa_run(spgemm_ctx_t ctx, spgemm_ctx_t mctx, spgemm_mat_t A, s
     if (o.block_kernel != 0 && o.block_kernel != 1)
         return set_err(ctx, SPGEMM_ERR_INVALID_ARG, "block_kernel %d: 0 (column tiers) or 1 (expand-sort-compress)",
                        o.block_kernel);
+    if (o.check_inputs) SG_TRY(check_handles(ctx, {A, B}));
     spgemm_mat_t Ac = nullptr, Bc = nullptr;
     DMat dA, dB;
     SG_TRY(to_csc_operand(ctx, A, &Ac, &dA));
@@ -743,6 +744,7 @@ spgemm_status_t spgemm_summa_block_flops(spgemm_ctx_t ctx, spgemm_mat_t A, spgem
     if (A->n != B->m) return set_err(ctx, SPGEMM_ERR_DIM_MISMATCH, "inner dimensions differ");
     if (A->fmt == SPGEMM_FMT_DCSC || B->fmt == SPGEMM_FMT_DCSC)
         return set_err(ctx, SPGEMM_ERR_UNSUPPORTED, "summa takes CSC or CSR operands");
+    SG_TRY(check_handles(ctx, {A, B}));
     spgemm_mat_t Ac = nullptr, Bc = nullptr;
     DMat dA, dB;
     SG_TRY(to_csc_operand(ctx, A, &Ac, &dA));

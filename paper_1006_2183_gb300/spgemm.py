@@ -55,7 +55,7 @@ class Opts(ctypes.Structure):
                 ("block_max_flops", ctypes.c_int), ("dense_part_flops", ctypes.c_int),
                 ("predictor_margin", ctypes.c_float), ("range_table_slots", ctypes.c_int),
                 ("block_kernel", ctypes.c_int), ("range_slab_rows", ctypes.c_int),
-                ("reserved", ctypes.c_int * 5)]
+                ("check_inputs", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 def _sig(name, args, res=ctypes.c_int):

@@ -331,3 +331,41 @@ def test_repeatable_exact_semirings(ctx):
     C1 = gpu_product(ctx, A, A, PT_I64)
     C2 = gpu_product(ctx, A, A, PT_I64)
     np.testing.assert_array_equal(C1.vals, C2.vals)
+
+
+def test_malformed_operands_are_refused_before_any_product_kernel(ctx):
+    """Section 8(b) preconditions: a non-monotone colptr, rows out of order and a
+    row past m are reported as SPGEMM_ERR_BAD_FORMAT by the input check of the
+    product call (the default), so no product kernel reads the arrays; a valid
+    operand then works on the same context, and check_inputs = 0 skips the check."""
+    s = sp()
+    A = gen.random_csc(50, 40, 0.1, 77)
+    good = s.Matrix.from_host(ctx, A, PT_F64)
+    cp = A.colptr.copy()
+    cp[10], cp[11] = cp[11], cp[10] - 1                       # colptr decreases
+    rows = A.rowidx.copy()
+    j = int(np.argmax(np.diff(A.colptr) >= 2))
+    s0 = A.colptr[j]
+    rows[s0], rows[s0 + 1] = rows[s0 + 1], rows[s0]           # two rows of one column swapped
+    past = A.rowidx.copy()
+    past[-1] = A.m + 3                                         # a row past m
+    for name, M in (("non-monotone colptr", CSC(A.m, A.n, cp, A.rowidx, A.vals)),
+                    ("unsorted rows", CSC(A.m, A.n, A.colptr, rows, A.vals)),
+                    ("row past m", CSC(A.m, A.n, A.colptr, past, A.vals))):
+        bad = s.Matrix.from_host(ctx, M, PT_F64)
+        At = s.Matrix.from_host(ctx, gen.transpose_host(A), PT_F64)   # 40 x 50: At * bad is defined
+        with pytest.raises(s.SpGEMMError) as ei:
+            s.spgemm_multiply(ctx, At, bad, PT_F64)
+        assert ei.value.status == 3, (name, ei.value)
+        with pytest.raises(s.SpGEMMError) as ei:
+            s.spgemm_summa_blocked(ctx, At, bad, 4, PT_F64)
+        assert ei.value.status == 3, (name, ei.value)
+        with pytest.raises(s.SpGEMMError) as ei:
+            s.spgemm_batch(ctx, [At], [bad], PT_F64)
+        assert ei.value.status == 3, (name, ei.value)
+    # the context still works, and a checked handle is not checked again
+    At = s.Matrix.from_host(ctx, gen.transpose_host(A), PT_F64)
+    C = s.spgemm_multiply(ctx, At, good, PT_F64).to_host()
+    assert_matches(C, oracle.spgemm(gen.transpose_host(A), A, PT_F64), PT_F64, what="after refused operands")
+    C = s.spgemm_multiply(ctx, At, good, PT_F64, s.default_opts(check_inputs=0)).to_host()
+    assert_matches(C, oracle.spgemm(gen.transpose_host(A), A, PT_F64), PT_F64, what="check_inputs = 0")

@@ -115,11 +115,14 @@ def test_summa_empty_and_errors(ctx):
     assert_matches(C, oracle.spgemm(B, B, PT_F64), PT_F64, what="after bad format")
 
 
-def test_summa_scale18_sampled(ctx):
-    """The benchmark's blocked workload: R-MAT scale 18 on a 16 x 16 grid, PT64;
-    column counts vs the oracle's symbolic pass and sampled columns vs the oracle."""
-    sr = PT_F64
-    A = gen.rmat(18, 8, 0x1802, sr)
+@pytest.mark.parametrize("sr", [PT_F64, MP_F32])
+def test_summa_scale18_sampled(ctx, sr):
+    """The secondary benchmark workload: R-MAT scale 18 on a 16 x 16 grid in plus-times
+    FP64 and min-plus FP32 (the bench's two semirings there); all column counts vs the
+    oracle's symbolic pass and sampled columns vs the oracle (min-plus bit-exact)."""
+    A = gen.rmat(18, 8, 0x1802, PT_F64)
+    if sr == MP_F32:
+        A = A.with_vals(A.vals.astype(np.float32))   # the bench's FP32 rounding of the same values
     C = blocked(ctx, A, A, sr, 16)
     np.testing.assert_array_equal(np.diff(C.colptr), oracle.symbolic(A, A))
     rng = np.random.default_rng(3)
@@ -130,7 +133,10 @@ def test_summa_scale18_sampled(ctx):
         np.testing.assert_array_equal(C.rowidx[C.colptr[j]:C.colptr[j + 1]], R.rowidx[R.colptr[t]:R.colptr[t + 1]])
         got = C.vals[C.colptr[j]:C.colptr[j + 1]]
         ref = R.vals[R.colptr[t]:R.colptr[t + 1]]
-        assert np.all(np.abs(got - ref) <= 1e-13 * np.abs(ref)), j
+        if sr == PT_F64:
+            assert np.all(np.abs(got - ref) <= 1e-13 * np.abs(ref)), j
+        else:
+            np.testing.assert_array_equal(got, ref, err_msg=f"column {j}")
 
 
 @pytest.mark.parametrize("g", [4, 7, 16])
