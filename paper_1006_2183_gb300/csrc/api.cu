@@ -474,9 +474,10 @@ spgemm_status_t engine_setup(Engine* E, spgemm_ctx* ctx, spgemm_semiring_t sr, c
         dw.store = (uint32_t*)(sb + o_store);
     }
     if (sr == SPGEMM_OR_AND_BOOL) {
-        // boolean operands without a stored false value: the long-column tiers take every output as true
+        // boolean operands without a stored false value: the bitmap tiers take every output as true
         int* vals_zero = (int*)(E->ctr + 2 * NBIN + 5);
-        launch_false_values(st, E->it, vals_zero);
+        if (ctx->bool_hint >= 0) SG_CUDA(ctx, cudaMemsetAsync(vals_zero, ctx->bool_hint ? 1 : 0, 4, st));
+        else launch_false_values(st, E->it, vals_zero);
         E->dw.vals_zero = vals_zero;
     }
     SG_CUDA(ctx, cudaGetLastError());

@@ -123,7 +123,7 @@ __device__ __forceinline__ void chunk_walk(const Prod* pr, const int* s_incl, co
     const int C = (total + NWG * 32 - 1) / (NWG * 32) * 32;
     const int xb = wg * C, xe = min(total, xb + C);
     if (xb >= xe) return;
-    int lo = 0, hi = ns;
+    int lo = 0, hi = xb > 0 ? ns : 0;   // segments ending at or before the slice start
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
         if (s_incl[mid] <= xb) lo = mid + 1;
@@ -131,7 +131,8 @@ __device__ __forceinline__ void chunk_walk(const Prod* pr, const int* s_incl, co
     }
     int o0 = lo;
     const int32_t* __restrict__ air = pr->A.ir;
-    for (int x0 = xb; x0 < xe; x0 += 32 * U) {
+    int x0 = xb;
+    for (; x0 + 32 * (U - 1) < xe; x0 += 32 * U) {   // steps of four full or nearly full windows
         int64_t idx[U];
         bool ok[U];
         int ob[U];
@@ -154,6 +155,18 @@ __device__ __forceinline__ void chunk_walk(const Prod* pr, const int* s_incl, co
         for (int u = 0; u < U; ++u) {
             if constexpr (NUM) f(ok[u], row[u], av[u], ok[u] ? s_bv[ob[u]] : T(0));
             else f(ok[u], row[u], T(0), T(0));
+        }
+    }
+    for (; x0 < xe; x0 += 32) {   // the last windows one at a time (short columns end here)
+        const int oi = warp_window_segment(s_incl, ns, x0, o0);
+        const bool ok = x0 + lane < xe;
+        const int64_t idx = ok ? s_a0[oi] + (x0 + lane - (oi ? s_incl[oi - 1] : 0)) : 0;
+        const int32_t row = ok ? __ldg(air + idx) : -1;
+        if constexpr (NUM) {
+            const T av = ok ? load_val<SR>(pr->A, idx) : T(0);
+            f(ok, row, av, ok ? s_bv[oi] : T(0));
+        } else {
+            f(ok, row, T(0), T(0));
         }
     }
 }

@@ -31,6 +31,9 @@ struct spgemm_ctx {
     int group = 0;
     double phase_ms[SPGEMM_NGROUP * 4 * SPGEMM_NPHASE] = {0};
     int64_t phase_cnt[SPGEMM_NGROUP * 4 * SPGEMM_NPHASE] = {0};
+    // boolean semiring, set by a call that already knows it for every product it runs
+    // (SUMMA checks its two operands once): -1 unknown, 0 no stored false value, 1 some
+    int bool_hint = -1;
     // statistics of the last SUMMA call
     std::vector<int64_t> summa_stage_flops;
     int64_t summa_nonempty = 0;

@@ -1024,6 +1024,20 @@ __global__ void k_false_values(Items it, int* flag) {
     }
 }
 
+__global__ void k_any_false(const uint8_t* __restrict__ v, int64_t n, int* flag) {
+    bool f = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        f |= __ldg(v + i) == 0;
+    if (f) *flag = 1;
+}
+
+void launch_any_false(cudaStream_t st, const void* vals, int64_t n, int* flag) {
+    if (!vals || n <= 0) return;
+    k_any_false<<<(int)std::min<int64_t>(ceil_div64(n, 256), sm_count() * 8), 256, 0, st>>>((const uint8_t*)vals, n,
+                                                                                          flag);
+    note_launch();
+}
+
 void launch_false_values(cudaStream_t st, const Items& it, int* flag) {
     if (it.nprod <= 0) return;
     const int gy = (int)std::min<int64_t>(it.nprod, 65535);

@@ -126,6 +126,8 @@ void launch_dense_items(cudaStream_t st, const Items& it, const int2* dense_list
                         int8_t* nparts, int32_t* sbase, unsigned long long* store_bound);
 // *flag = 1 when an operand of some product stores a false value (boolean semiring)
 void launch_false_values(cudaStream_t st, const Items& it, int* flag);
+// *flag = 1 when one of the n bytes at vals is 0 (vals == nullptr: nothing)
+void launch_any_false(cudaStream_t st, const void* vals, int64_t n, int* flag);
 
 // which: 1 = hash-table tiers, 2 = long columns (slab tier, or the block tier in block mode), 3 = both
 template <class SR>

@@ -616,6 +616,27 @@ spgemm_status_t summa_run(spgemm_ctx_t ctx, spgemm_ctx_t mctx, spgemm_mat_t A, s
         return set_err(ctx, SPGEMM_ERR_INVALID_ARG, "block_kernel %d: 0 (column tiers) or 1 (expand-sort-compress)",
                        o.block_kernel);
     if (o.check_inputs) SG_TRY(check_handles(ctx, {A, B}));
+    // boolean: whether the two operands store a false value, checked once for every stage
+    // product and merge of this call (their values all come from A and B)
+    struct HintGuard {
+        spgemm_ctx *c, *mc;
+        ~HintGuard() {
+            c->bool_hint = -1;
+            if (mc) mc->bool_hint = -1;
+        }
+    } hint_guard{ctx, mctx};
+    if (sr == SPGEMM_OR_AND_BOOL) {
+        auto fb = ctx_buf(ctx, 16);
+        if (!fb) return set_err(ctx, SPGEMM_ERR_OOM, "false-value flag");
+        SG_CUDA(ctx, cudaMemsetAsync(fb->p, 0, 4, ctx->stream));
+        launch_any_false(ctx->stream, A->num, A->nnz, (int*)fb->p);
+        launch_any_false(ctx->stream, B->num, B->nnz, (int*)fb->p);
+        int hf = 0;
+        SG_CUDA(ctx, cudaMemcpyAsync(&hf, fb->p, 4, cudaMemcpyDeviceToHost, ctx->stream));
+        SG_TRY(sync_ctx(ctx));
+        ctx->bool_hint = hf ? 1 : 0;
+        if (mctx) mctx->bool_hint = ctx->bool_hint;
+    }
     spgemm_mat_t Ac = nullptr, Bc = nullptr;
     DMat dA, dB;
     SG_TRY(to_csc_operand(ctx, A, &Ac, &dA));
