@@ -352,13 +352,13 @@ void launch_block_tier(cudaStream_t st, const Items& it, const int2* list, const
                 b = e;
             }
         };
-        runs(BIN_WARP0, BIN_BLK0, [&](const int2* l, int64_t n) {
+        // one warp per column for the CTA-table bins too (cap <= 4096): without the CTA's
+        // barrier chain per column, measured faster than 256-thread groups
+        runs(BIN_WARP0, BIN_DENSE, [&](const int2* l, int64_t n) {
             run_bt<SR, 32, 256>(st, it, l, n, nnz_item, Coff, Cir, Cv, dw.vals_zero);
         });
-        runs(BIN_BLK0, BIN_DENSE, [&](const int2* l, int64_t n) {
-            run_bt<SR, 256, 256>(st, it, l, n, nnz_item, Coff, Cir, Cv, dw.vals_zero);
-        });
     }
+    // long columns (cap > 4096): a 512-thread group each (one warp each measured slower)
     if (which & 2) run_bt<SR, 512, 512>(st, it, dw.dlist, dw.ndense, nnz_item, Coff, Cir, Cv, dw.vals_zero);
 }
 

@@ -898,9 +898,11 @@ static void run_hash_bins(cudaStream_t st, const Items& it, const int2* list, co
         if (it.max_m > 0 && it.max_m <= BM_COUNT_MAX_ROWS) {
             // rows fit a small bitmap: count the longer columns by bits (64 and 128
             // slots hold so few rows that clearing a bitmap would cost more)
-            run_bitcount<32, WARP_BLOCK>(st, it, list + off[W0 + 2], cnt[W0 + 2] + cnt[W0 + 3] + cnt[W0 + 4],
+            // one warp per column for the CTA-table bins too: a column of a few thousand
+            // products has no barrier chain to wait on, and its bitmap is the same size
+            run_bitcount<32, WARP_BLOCK>(st, it, list + off[W0 + 2],
+                                         cnt[W0 + 2] + cnt[W0 + 3] + cnt[W0 + 4] + cnt[B0] + cnt[B0 + 1] + cnt[B0 + 2],
                                          nnz_item);
-            run_bitcount<256, 256>(st, it, list + off[B0], cnt[B0] + cnt[B0 + 1] + cnt[B0 + 2], nnz_item);
             return;
         }
     }
