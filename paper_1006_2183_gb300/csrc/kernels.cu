@@ -1080,6 +1080,7 @@ struct RangeSmem {   // per-batch segments of the flattened expansion (compacted
     int end[RT_BLOCK];        // inclusive prefix of segment lengths (exclusive end in flattened space)
     int64_t start[RT_BLOCK];  // first position of the segment in A.ir
     int64_t bv[RT_BLOCK];     // B value bits (read back as SR::T)
+    int64_t stop[RT_BLOCK];   // one past the segment's last position (quad walks)
     unsigned long long ws[32];
     int wc[RT_BLOCK / 32 + 1];
 };
@@ -1089,7 +1090,7 @@ constexpr size_t RS_BYTES = (sizeof(RangeSmem) + 15) / 16 * 16;
 // Compacts the active (k, segment) pairs of this batch into sc and returns
 // (number of segments, number of products).  Called by all threads.
 __device__ __forceinline__ void rt_compact(RangeSmem* sc, bool active, int len, int64_t a, int64_t bvbits, int& ns,
-                                           int& T) {
+                                           int& T, int64_t stop = 0) {
     const unsigned long long packed = active && len > 0 ? ((1ull << 32) | (unsigned)len) : 0ull;
     unsigned long long tot;
     const unsigned long long inc = rt_block_incl_scan64(packed, sc->ws, tot);
@@ -1098,6 +1099,7 @@ __device__ __forceinline__ void rt_compact(RangeSmem* sc, bool active, int len, 
         sc->end[pos] = (int)(inc & 0xffffffffull);
         sc->start[pos] = a;
         sc->bv[pos] = bvbits;
+        sc->stop[pos] = stop;
     }
     ns = (int)(tot >> 32);
     T = (int)(tot & 0xffffffffull);
@@ -1173,6 +1175,116 @@ __device__ __forceinline__ void slab_walk(const Items& it, const Prod* pr, int64
     }
 }
 
+// Four consecutive values of A at an aligned position p (16-byte loads: one for
+// 4- and 1-byte types, two for 8-byte types).
+template <class T>
+__device__ __forceinline__ void load4(const T* __restrict__ p, T v[4]) {
+    if constexpr (sizeof(T) == 8) {
+        const ulonglong2 x = __ldg(reinterpret_cast<const ulonglong2*>(p));
+        const ulonglong2 y = __ldg(reinterpret_cast<const ulonglong2*>(p) + 1);
+        const unsigned long long w[4] = {x.x, x.y, y.x, y.y};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[j] = *reinterpret_cast<const T*>(&w[j]);
+    } else if constexpr (sizeof(T) == 4) {
+        const uint4 x = __ldg(reinterpret_cast<const uint4*>(p));
+        const unsigned w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[j] = *reinterpret_cast<const T*>(&w[j]);
+    } else {
+        const unsigned x = __ldg(reinterpret_cast<const unsigned*>(p));
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[j] = (T)((x >> (8 * j)) & 0xffu);
+    }
+}
+
+// slab_walk over aligned quads: a segment [a, b) of A(:,k) covers the quads
+// q = a/4 .. (b-1)/4, and each lane takes one quad per window, loading its four
+// rows with one 16-byte load (and its values with one or two) and masking the
+// positions outside [a, b).  Needs A.ir and A.num 16-byte aligned and A a CSC
+// whose arrays hold nnz_end entries (a quad past the end is read one by one).
+// f(valid, row, a, b) as in slab_walk, four times per window.
+template <class SR, bool NUM, class F>
+__device__ __forceinline__ void slab_walk_quads(const Items& it, const Prod* pr, int64_t bs, int64_t be, int64_t R0,
+                                                int64_t R1, int64_t m, int64_t nnz_end, RangeSmem* sc, F&& f) {
+    using T = typename SR::T;
+    constexpr int NWARP = RT_BLOCK / 32;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int32_t* __restrict__ air = pr->A.ir;
+    const T* __restrict__ anum = reinterpret_cast<const T*>(pr->A.num);
+    for (int64_t b0 = bs; b0 < be; b0 += RT_BLOCK) {
+        const int64_t t = b0 + tid;
+        int nq = 0;
+        int64_t a = 0, b = 0, bvbits = 0;
+        if (t < be) {
+            const int32_t k = __ldg(pr->B.ir + t);
+            int64_t s, en;
+            a_col(it, pr, t, k, s, en);
+            a = R0 == 0 ? s : s + lower_bound_rows(air + s, en - s, R0);
+            b = R1 == m ? en : s + lower_bound_rows(air + s, en - s, R1);
+            nq = b > a ? (int)(((b - 1) >> 2) - (a >> 2) + 1) : 0;
+            if constexpr (NUM) *reinterpret_cast<T*>(&bvbits) = load_val<SR>(pr->B, t);
+        }
+        int ns, Tq;
+        rt_compact(sc, t < be, nq, a, bvbits, ns, Tq, b);
+        const int C = (Tq + NWARP * 32 - 1) / (NWARP * 32) * 32;
+        const int xb = warp * C, xe = min(Tq, xb + C);
+        if (xb < xe) {
+            int lo = 0, hi = xb > 0 ? ns : 0;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (sc->end[mid] <= xb) lo = mid + 1;
+                else hi = mid;
+            }
+            int o0 = lo;
+            for (int xw = xb; xw < xe; xw += 32) {
+                const int oi = warp_window_segment(sc->end, ns, xw, o0);
+                const bool ok = xw + lane < xe;
+                int32_t row[4] = {INT_MIN, INT_MIN, INT_MIN, INT_MIN};
+                T av[4] = {T(0), T(0), T(0), T(0)};
+                int64_t sa = 0, sb = 0, p0 = 0;
+                T bv = T(0);
+                if (ok) {
+                    sa = sc->start[oi];
+                    sb = sc->stop[oi];
+                    p0 = ((sa >> 2) + (xw + lane - (oi ? sc->end[oi - 1] : 0))) << 2;
+                    if (p0 + 4 <= nnz_end) {
+                        const int4 r = __ldg(reinterpret_cast<const int4*>(air + p0));
+                        row[0] = r.x;
+                        row[1] = r.y;
+                        row[2] = r.z;
+                        row[3] = r.w;
+                        if constexpr (NUM) {
+                            if (anum) load4<T>(anum + p0, av);
+                            else av[0] = av[1] = av[2] = av[3] = (T)SR::one();
+                        }
+                    } else {   // the array's last, partial quad
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            if (p0 + j < nnz_end) {
+                                row[j] = __ldg(air + p0 + j);
+                                if constexpr (NUM) av[j] = load_val<SR>(pr->A, p0 + j);
+                            }
+                    }
+                    if constexpr (NUM) bv = *reinterpret_cast<const T*>(&sc->bv[oi]);
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const bool v = ok && p0 + j >= sa && p0 + j < sb;
+                    f(v, v ? row[j] : INT_MIN, av[j], bv);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// the quad walk applies to a product whose A is a CSC (no DCSC index, no gaps) with
+// 16-byte aligned row and value arrays
+__device__ __forceinline__ bool quads_ok(const Prod* pr) {
+    return pr->A.jc == nullptr && pr->A.ce == nullptr && ((uintptr_t)pr->A.ir & 15) == 0 &&
+           ((uintptr_t)pr->A.num & 15) == 0;
+}
+
 // Symbolic slab kernel: mark, count, store the row set.
 __global__ void __launch_bounds__(RT_BLOCK, 2) k_slab_sym(Items it, DenseWork dw) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1198,10 +1310,12 @@ __global__ void __launch_bounds__(RT_BLOCK, 2) k_slab_sym(Items it, DenseWork dw
         const int span = (int)(R1 - R0);
         // one shared atomic per product: R-MAT rows of one window mostly fall in different
         // words, so folding lanes per word first (shuffles) measured slower
-        slab_walk<BOOL8, false>(it, pr, bs, be, R0, R1, m, sc, [&](bool ok, int32_t row, uint8_t, uint8_t) {
+        auto mark = [&](bool ok, int32_t row, uint8_t, uint8_t) {
             const int lr = (int)(row - R0);
             if (ok && (unsigned)lr < (unsigned)span) atomicOr(&bitmap[lr >> 5], 1u << (lr & 31));
-        });
+        };
+        if (quads_ok(pr)) slab_walk_quads<BOOL8, false>(it, pr, bs, be, R0, R1, m, pr->A.nnz, sc, mark);
+        else slab_walk<BOOL8, false>(it, pr, bs, be, R0, R1, m, sc, mark);
         // count over contiguous word ranges, then store the row set
         const int wpt = (nw + RT_BLOCK - 1) / RT_BLOCK;
         const int w0 = min(tid * wpt, nw), w1 = min(w0 + wpt, nw);
@@ -1332,20 +1446,22 @@ __global__ void __launch_bounds__(RT_BLOCK, 2) k_slab_num(Items it, DenseWork dw
         // 5. every product, added at its row's rank
         if (walk) {
             const int span = (int)(R1 - R0);
-            slab_walk<SR, true>(it, pr, __ldg(pr->B.cp + e.y), __ldg(pr->B.cp + e.y + 1), R0, R1, m, sc,
-                                [&](bool ok, int32_t row, T a, T b) {
-                                    if (!ok) return;
-                                    const int lr = (int)(row - R0);
-                                    if ((unsigned)lr >= (unsigned)span) return;   // malformed input only
-                                    const int wd = lr >> 5, g = wd >> 2, y = wd & 3;
-                                    const uint4 grp = reinterpret_cast<const uint4*>(bitmap)[g];
-                                    const uint32_t wv = y == 0 ? grp.x : y == 1 ? grp.y : y == 2 ? grp.z : grp.w;
-                                    const uint32_t bit = 1u << (lr & 31);
-                                    if (!(wv & bit)) return;                      // malformed input only
-                                    const int rank = gp[g] + __popc(wv & (bit - 1u)) + (y > 0 ? __popc(grp.x) : 0) +
-                                                     (y > 1 ? __popc(grp.y) : 0) + (y > 2 ? __popc(grp.z) : 0);
-                                    red_out<SR>(Cv, ob + rank, SR::mul(a, b));
-                                });
+            auto add = [&](bool ok, int32_t row, T a, T b) {
+                if (!ok) return;
+                const int lr = (int)(row - R0);
+                if ((unsigned)lr >= (unsigned)span) return;   // malformed input only
+                const int wd = lr >> 5, g = wd >> 2, y = wd & 3;
+                const uint4 grp = reinterpret_cast<const uint4*>(bitmap)[g];
+                const uint32_t wv = y == 0 ? grp.x : y == 1 ? grp.y : y == 2 ? grp.z : grp.w;
+                const uint32_t bit = 1u << (lr & 31);
+                if (!(wv & bit)) return;                      // malformed input only
+                const int rank = gp[g] + __popc(wv & (bit - 1u)) + (y > 0 ? __popc(grp.x) : 0) +
+                                 (y > 1 ? __popc(grp.y) : 0) + (y > 2 ? __popc(grp.z) : 0);
+                red_out<SR>(Cv, ob + rank, SR::mul(a, b));
+            };
+            const int64_t bs = __ldg(pr->B.cp + e.y), be = __ldg(pr->B.cp + e.y + 1);
+            if (quads_ok(pr)) slab_walk_quads<SR, true>(it, pr, bs, be, R0, R1, m, pr->A.nnz, sc, add);
+            else slab_walk<SR, true>(it, pr, bs, be, R0, R1, m, sc, add);
         } else {
             __syncthreads();
         }

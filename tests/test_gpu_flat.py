@@ -369,3 +369,49 @@ def test_malformed_operands_are_refused_before_any_product_kernel(ctx):
     assert_matches(C, oracle.spgemm(gen.transpose_host(A), A, PT_F64), PT_F64, what="after refused operands")
     C = s.spgemm_multiply(ctx, At, good, PT_F64, s.default_opts(check_inputs=0)).to_host()
     assert_matches(C, oracle.spgemm(gen.transpose_host(A), A, PT_F64), PT_F64, what="check_inputs = 0")
+
+
+def _quad_edge_case(seed):
+    """A of 40000 rows (slab tier) whose last column holds the array's last entries,
+    nnz = 3 mod 4, and one long B column over every column of A (the quad walk's
+    partial last quad); plus a short B column."""
+    rng = np.random.default_rng(seed)
+    m, k = 40000, 300
+    cols = [np.sort(rng.choice(m, int(rng.integers(20, 80)), replace=False)).astype(np.int32) for _ in range(k)]
+    while sum(len(c) for c in cols) % 4 != 3:
+        cols[-1] = np.sort(np.unique(np.append(cols[-1], rng.integers(0, m)))).astype(np.int32)
+    cp = np.zeros(k + 1, np.int64)
+    np.cumsum([len(c) for c in cols], out=cp[1:])
+    A = CSC(m, k, cp, np.concatenate(cols), rng.uniform(0, 1, int(cp[-1])))
+    B = CSC(k, 2, np.array([0, k, k + 2], np.int64), np.concatenate([np.arange(k), [k - 2, k - 1]]).astype(np.int32),
+            rng.uniform(0, 1, k + 2))
+    return A, B
+
+
+@pytest.mark.parametrize("sr", [PT_F64, OR_BOOL, PT_I64])
+def test_slab_quads_partial_last_quad(ctx, sr):
+    A, B = _quad_edge_case(91)
+    A = A.with_vals(gen.values_for(sr, 5, A.nnz)) if sr != PT_F64 else A
+    B = B.with_vals(gen.values_for(sr, 6, B.nnz)) if sr != PT_F64 else B
+    s = sp()
+    dA = s.Matrix.from_host(ctx, A, sr)
+    assert s.spgemm_plan(ctx, dA, s.Matrix.from_host(ctx, B, sr), sr).stats()["tiers"][3] == 1
+    check_product(ctx, A, B, sr, what="partial last quad")
+
+
+def test_slab_misaligned_arrays_take_the_scalar_walk(ctx):
+    """Row and value arrays that start 4 and 8 bytes past a 16-byte boundary (views
+    into larger tensors): the long column is walked one product per lane."""
+    import torch
+    A, B = _quad_edge_case(92)
+    s = sp()
+    dev = ctx.device
+    ir = torch.zeros(A.nnz + 1, dtype=torch.int32, device=dev)
+    ir[1:] = torch.from_numpy(A.rowidx).to(dev)
+    v = torch.zeros(A.nnz + 1, dtype=torch.float64, device=dev)
+    v[1:] = torch.from_numpy(A.vals).to(dev)
+    cp = torch.from_numpy(A.colptr).to(dev)
+    assert ir[1:].data_ptr() % 16 == 4 and v[1:].data_ptr() % 16 == 8
+    dA = s.Matrix.csc(ctx, A.m, A.n, cp, ir[1:], v[1:], PT_F64)
+    C = s.spgemm_multiply(ctx, dA, s.Matrix.from_host(ctx, B, PT_F64), PT_F64).to_host()
+    assert_matches(C, oracle.spgemm(A, B, PT_F64), PT_F64, what="misaligned A")
