@@ -246,7 +246,8 @@ __global__ void __launch_bounds__(BLOCK) k_block_tier(Items it, const int2* __re
         if (nnz_item && lane == 0) nnz_item[u] = cnt;
         const int32_t rb = out_row_base(pr, e.y);
         if (write) {
-            // 3. rows at their ranks, values set to the semiring zero
+            // 3. rows at their ranks (evict-first: written once), values set to the semiring
+            //    zero (kept in L2 for the reductions that follow)
             if constexpr (GS == 32) {
                 uint32_t bits = l1[lane];
                 while (bits) {
@@ -255,7 +256,7 @@ __global__ void __launch_bounds__(BLOCK) k_block_tier(Items it, const int2* __re
                     uint32_t wv = l2[wd];
                     int r = gp[lane] + wp[wd];
                     while (wv) {
-                        Cir[out0 + r++] = wd * 32 + __ffs(wv) - 1 + rb;
+                        __stcs(Cir + out0 + r++, wd * 32 + __ffs(wv) - 1 + rb);
                         wv &= wv - 1;
                     }
                 }
@@ -265,7 +266,7 @@ __global__ void __launch_bounds__(BLOCK) k_block_tier(Items it, const int2* __re
                     if (!wv) continue;
                     int r = gp[wd >> 5] + wp[wd];
                     while (wv) {
-                        Cir[out0 + r++] = wd * 32 + __ffs(wv) - 1 + rb;
+                        __stcs(Cir + out0 + r++, wd * 32 + __ffs(wv) - 1 + rb);
                         wv &= wv - 1;
                     }
                 }

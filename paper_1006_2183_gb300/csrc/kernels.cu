@@ -1340,13 +1340,13 @@ __global__ void __launch_bounds__(RT_BLOCK, 2) k_slab_sym(Items it, DenseWork dw
         if (off >= 0 && size > 0) {
             uint32_t* __restrict__ out = dw.store + off;
             if (dense) {
-                for (int x = tid; x < nw; x += RT_BLOCK) out[x] = bitmap[x];
+                for (int x = tid; x < nw; x += RT_BLOCK) __stcs(out + x, bitmap[x]);
             } else {
                 int r = excl;
                 for (int x = w0; x < w1; ++x) {
                     uint32_t bits = bitmap[x];
                     while (bits) {
-                        out[r++] = (uint32_t)(R0 + x * 32 + __ffs(bits) - 1);
+                        __stcs(out + r++, (uint32_t)(R0 + x * 32 + __ffs(bits) - 1));
                         bits &= bits - 1;
                     }
                 }
@@ -1391,18 +1391,21 @@ __global__ void __launch_bounds__(RT_BLOCK, 2) k_slab_num(Items it, DenseWork dw
         const int64_t ob = __ldg(Coff + u) + dw.spref[w];
         const uint32_t* __restrict__ rs = dw.store + dw.soff[w];
         const bool dense = cnt >= nw;
+        // Streaming data (the stored row sets, read once; C's rows, written once) use
+        // evict-first loads and stores, so that the slab's value region, zeroed below and
+        // then reduced into, stays in L2 instead of coming back from DRAM.
         // 1. the slab's row bitmap (padded to whole groups)
         if (dense) {
-            for (int x = tid; x < ng * 4; x += RT_BLOCK) bitmap[x] = x < nw ? __ldg(rs + x) : 0u;
+            for (int x = tid; x < ng * 4; x += RT_BLOCK) bitmap[x] = x < nw ? __ldcs(rs + x) : 0u;
         } else {
             for (int x = tid; x < ng * 4; x += RT_BLOCK) bitmap[x] = 0u;
             __syncthreads();
             for (int i0 = 0; i0 < cnt; i0 += RT_BLOCK) {
                 const int i = i0 + tid;
-                const int32_t r = i < cnt ? (int32_t)__ldg(rs + i) : -1;
+                const int32_t r = i < cnt ? (int32_t)__ldcs(rs + i) : -1;
                 const int lr = (int)(r - R0);
                 if (i < cnt) {
-                    Cir[ob + i] = r + rb;    // C's rows: the row list itself
+                    __stcs(Cir + ob + i, r + rb);    // C's rows: the row list itself
                     atomicOr(&bitmap[lr >> 5], 1u << (lr & 31));
                 }
             }
@@ -1434,7 +1437,7 @@ __global__ void __launch_bounds__(RT_BLOCK, 2) k_slab_num(Items it, DenseWork dw
                     uint32_t bits = wv[y];
                     const int32_t base = (int32_t)(R0 + (int64_t)(4 * g + y) * 32) + rb;
                     while (bits) {
-                        Cir[ob + r++] = base + __ffs(bits) - 1;
+                        __stcs(Cir + ob + r++, base + __ffs(bits) - 1);
                         bits &= bits - 1;
                     }
                 }
