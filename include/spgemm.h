@@ -104,7 +104,7 @@ typedef struct {
                                  longer columns (the slab tier) are cut into row slabs,
                                  each counted and then accumulated by one CTA          */
     int dense_part_flops;     /* slab tier: target flops per row slab of a long column
-                                 (default 32768); a column whose B column is long gets
+                                 (default 65536); a column whose B column is long gets
                                  fewer, larger slabs                                    */
     float predictor_margin;   /* capacity = (1 + margin) * prediction (+ slack)        */
     int range_table_slots;    /* ignored (kept for the layout of this struct)          */

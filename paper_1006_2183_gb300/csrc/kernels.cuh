@@ -33,9 +33,11 @@ constexpr int BLK_TBL0 = 2048;
 constexpr int MAX_PARTS = 64;
 // default most rows of one slab: a 64 KB row bitmap keeps two CTAs per SM
 constexpr int DEFAULT_SLAB_ROWS = 1 << 19;
-// default target flops per slab: keeps the output regions that the numeric pass
-// reduces into, for every resident CTA at once, well inside L2
-constexpr int DEFAULT_PART_FLOPS = 32768;
+// default target flops per slab: every slab repeats its binary searches per entry of
+// B(:,j) and its bitmap set-up, so larger slabs pay up to about this size (R-MAT
+// scale 20 flat: 8192 / 16384 / 32768 / 65536 / 131072 flops per slab give 74.8 /
+// 67.9 / 64.5 / 62.3 / 62.1 ms for the FP64 numeric pass)
+constexpr int DEFAULT_PART_FLOPS = 65536;
 
 struct TierCfg {
     int warp_max;     // cap <= warp_max -> warp tables (<= 512)
