@@ -30,8 +30,8 @@ struct BtLayout {
     using T = typename SR::T;
     static constexpr size_t l2 = (size_t)L2W * 4;
     static constexpr size_t l1 = (size_t)L1W * 4;
-    static constexpr size_t wp = (size_t)L2W * 2;
-    static constexpr size_t gp = (size_t)L1W * 4;
+    static constexpr size_t wp = (size_t)L2W * 2;   // rows before each nonempty word (< 2^16)
+    static constexpr size_t gp = (size_t)L2W * 2;   // the nonempty words, ascending
     static constexpr size_t incl = (size_t)GS * 4;
     static constexpr size_t a0 = (size_t)GS * 8;
     static constexpr size_t bv = (size_t)GS * 8;
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(BLOCK) k_block_tier(Items it, const int2* __re
     uint32_t* l2 = reinterpret_cast<uint32_t*>(base);
     uint32_t* l1 = reinterpret_cast<uint32_t*>(base + L::l2);
     uint16_t* wp = reinterpret_cast<uint16_t*>(base + L::l2 + L::l1);
-    int* gp = reinterpret_cast<int*>(base + L::l2 + L::l1 + L::wp);
+    uint16_t* wl = reinterpret_cast<uint16_t*>(base + L::l2 + L::l1 + L::wp);
     int* s_incl = reinterpret_cast<int*>(base + L::l2 + L::l1 + L::wp + L::gp);
     int64_t* s_a0 = reinterpret_cast<int64_t*>(base + L::l2 + L::l1 + L::wp + L::gp + L::incl);
     T* s_bv = reinterpret_cast<T*>(base + L::l2 + L::l1 + L::wp + L::gp + L::incl + L::a0);
@@ -222,22 +222,37 @@ __global__ void __launch_bounds__(BLOCK) k_block_tier(Items it, const int2* __re
             if (!one_chunk) gsync<GS>();   // the next chunk rewrites the segment arrays
         }
         gsync<GS>();
-        // 2. ranks: warp 0 of the group; lane l owns L1 word l (L2 words 32 l .. 32 l + 31)
+        // 2. ranks, by warp 0 of the group: the nonempty words in ascending order (from L1,
+        //    by a warp scan of the per-word counts), then the rows before each of them
+        //    (32 words per step).  A row's rank is wp[its word] + the bits below it there.
         if (lane < 32) {
-            uint32_t bits = l1[lane];
-            int c = 0;
-            while (bits) {
-                const int wd = lane * 32 + __ffs(bits) - 1;
+            const uint32_t lb = l1[lane];
+            const int nl = __popc(lb);
+            const int off = warp_incl_scan(nl) - nl;
+            const int nwords = __shfl_sync(0xffffffffu, off + nl, 31);
+            uint32_t bits = lb;
+            for (int i = 0; bits; ++i) {   // lane l lists the words of L1 word l
+                wl[off + i] = (uint16_t)(lane * 32 + __ffs(bits) - 1);
                 bits &= bits - 1;
-                wp[wd] = (uint16_t)c;
-                c += __popc(l2[wd]);
             }
-            const int incl = warp_incl_scan(c);
-            gp[lane] = incl - c;
-            if (lane == 31) ws[0] = incl;   // the column's entries
+            __syncwarp();
+            int carry = 0;
+            for (int i0 = 0; i0 < nwords; i0 += 32) {
+                const int i = i0 + lane;
+                const int wd = i < nwords ? wl[i] : 0;
+                const int c = i < nwords ? __popc(l2[wd]) : 0;
+                const int incl = warp_incl_scan(c);
+                if (i < nwords) wp[wd] = (uint16_t)(carry + incl - c);
+                carry += __shfl_sync(0xffffffffu, incl, 31);
+            }
+            if (lane == 0) {
+                ws[0] = carry;    // the column's entries
+                ws[1] = nwords;   // its nonempty words
+            }
         }
         gsync<GS>();
         const int cnt = (int)ws[0];
+        const int nwords = (int)ws[1];
         const int64_t out0 = __ldg(Coff + u);
         const int64_t capn = __ldg(Coff + u + 1) - out0;
         // exact offsets always fit (the counting pass marks the same rows); the check
@@ -247,27 +262,32 @@ __global__ void __launch_bounds__(BLOCK) k_block_tier(Items it, const int2* __re
         const int32_t rb = out_row_base(pr, e.y);
         if (write) {
             // 3. rows at their ranks (evict-first: written once), values set to the semiring
-            //    zero (kept in L2 for the reductions that follow)
-            if constexpr (GS == 32) {
-                uint32_t bits = l1[lane];
-                while (bits) {
-                    const int wd = lane * 32 + __ffs(bits) - 1;
-                    bits &= bits - 1;
-                    uint32_t wv = l2[wd];
-                    int r = gp[lane] + wp[wd];
-                    while (wv) {
-                        __stcs(Cir + out0 + r++, wd * 32 + __ffs(wv) - 1 + rb);
-                        wv &= wv - 1;
-                    }
-                }
-            } else {
-                for (int wd = lane; wd < nw; wd += GS) {
-                    uint32_t wv = l2[wd];
-                    if (!wv) continue;
-                    int r = gp[wd >> 5] + wp[wd];
-                    while (wv) {
-                        __stcs(Cir + out0 + r++, wd * 32 + __ffs(wv) - 1 + rb);
-                        wv &= wv - 1;
+            //    zero (kept in L2 for the reductions that follow).  Each warp of the group
+            //    takes 32 nonempty words at a time: one word per lane, bit by bit, when the
+            //    words are sparse; word by word with the whole warp (one coalesced store per
+            //    word) when they are dense.
+            {
+                const int wlane = threadIdx.x & 31, wgi = (threadIdx.x % GS) >> 5;
+                for (int i0 = wgi * 32; i0 < nwords; i0 += GS) {
+                    const int i = i0 + wlane;
+                    const int wd = i < nwords ? wl[i] : 0;
+                    uint32_t wv = i < nwords ? l2[wd] : 0u;
+                    const int r0 = i < nwords ? wp[wd] : 0;
+                    const int pc = __popc(wv);
+                    if (__reduce_add_sync(0xffffffffu, pc) >= 16 * 32) {
+                        for (int j = 0; j < 32; ++j) {
+                            const int wdj = __shfl_sync(0xffffffffu, wd, j);
+                            const uint32_t wvj = __shfl_sync(0xffffffffu, wv, j);
+                            const int rj = __shfl_sync(0xffffffffu, r0, j);
+                            if (i0 + j < nwords && ((wvj >> wlane) & 1u))
+                                __stcs(Cir + out0 + rj + __popc(wvj & ((1u << wlane) - 1u)), wdj * 32 + wlane + rb);
+                        }
+                    } else {
+                        int r = r0;
+                        while (wv) {
+                            __stcs(Cir + out0 + r++, wd * 32 + __ffs(wv) - 1 + rb);
+                            wv &= wv - 1;
+                        }
                     }
                 }
             }
@@ -282,7 +302,7 @@ __global__ void __launch_bounds__(BLOCK) k_block_tier(Items it, const int2* __re
                         const int wd = r >> 5;
                         const uint32_t wv = l2[wd];
                         const uint32_t bit = 1u << (r & 31);
-                        const int rank = gp[wd >> 5] + wp[wd] + __popc(wv & (bit - 1u));
+                        const int rank = wp[wd] + __popc(wv & (bit - 1u));
                         red_out<SR>(Cv, out0 + rank, SR::mul(a, b));
                     });
                     if (!one_chunk) gsync<GS>();
@@ -290,18 +310,9 @@ __global__ void __launch_bounds__(BLOCK) k_block_tier(Items it, const int2* __re
             }
         }
         gsync<GS>();
-        // 5. clear the touched words
-        if constexpr (GS == 32) {
-            uint32_t bits = l1[lane];
-            while (bits) {
-                l2[lane * 32 + __ffs(bits) - 1] = 0u;
-                bits &= bits - 1;
-            }
-            l1[lane] = 0u;
-        } else {
-            for (int wd = lane; wd < nw; wd += GS) l2[wd] = 0u;
-            if (lane < L1W) l1[lane] = 0u;
-        }
+        // 5. clear the touched words (through the word list)
+        for (int i = lane; i < nwords; i += GS) l2[wl[i]] = 0u;
+        if (lane < L1W) l1[lane] = 0u;
         gsync<GS>();
     }
 }
