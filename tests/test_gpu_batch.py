@@ -108,3 +108,41 @@ def test_galerkin_triple_product(ctx, N):
     np.testing.assert_array_equal(RAP.colptr, coarse.colptr)
     np.testing.assert_array_equal(RAP.rowidx, coarse.rowidx)
     np.testing.assert_array_equal(RAP.vals, 4.0 * coarse.vals)
+
+
+def test_autotuned_batch_is_never_slower_than_either_predictor_choice(ctx):
+    """The autotuner times whole batched calls with and without the learned predictor
+    and keeps the faster: the tuned call is no slower (beyond timing noise) than either
+    fixed choice at the same thresholds, and its output equals the exact path's."""
+    import time
+    import torch
+    s = sp()
+    pairs = gen.batch_pairs(96, 0x4104, 9, 13)
+    As = [_up(ctx, a, PT_I64) for a, _ in pairs]
+    Bs = [_up(ctx, b, PT_I64) for _, b in pairs]
+    rng = np.random.default_rng(5)
+    s.spgemm_predictor_set(ctx, rng.normal(0, 0.2, s.NPARAM).astype(np.float32))
+    tuned = s.spgemm_autotune(ctx, As, Bs, PT_I64, s.default_opts(use_predictor=1))
+    thr = dict(warp_max_flops=tuned.warp_max_flops, block_max_flops=tuned.block_max_flops,
+               dense_part_flops=tuned.dense_part_flops)
+
+    def best_of(opts, reps=7):
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            Cs = s.spgemm_batch(ctx, As, Bs, PT_I64, opts)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+            del Cs
+        return min(ts)
+    t_auto = best_of(tuned)
+    t_on = best_of(s.default_opts(use_predictor=1, **thr))
+    t_off = best_of(s.default_opts(use_predictor=0, **thr))
+    assert t_auto <= 1.25 * min(t_on, t_off), (t_auto, t_on, t_off, tuned.use_predictor)
+    ref = [C.to_host() for C in s.spgemm_batch(ctx, As, Bs, PT_I64, s.default_opts(use_predictor=0, **thr))]
+    for C, R in zip(s.spgemm_batch(ctx, As, Bs, PT_I64, tuned), ref):
+        H = C.to_host()
+        np.testing.assert_array_equal(H.colptr, R.colptr)
+        np.testing.assert_array_equal(H.rowidx, R.rowidx)
+        np.testing.assert_array_equal(H.vals, R.vals)

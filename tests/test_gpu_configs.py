@@ -9,9 +9,10 @@ run and against closed forms where the result has one:
   forms identical;
 * the tall-skinny BFS step, boolean R-MAT scale 20 (edge factor 16) times a 2^20 x 128
   frontier, every column against the oracle;
-* R-MAT scale 20 A*A (edge factor 8), plus-times FP64 and or-and, flat and on a
-  32 x 32 virtual SUMMA grid: every column count against the oracle, sampled columns
-  against the oracle, and flat and blocked structure identical.
+* R-MAT scale 20 A*A (edge factor 8), plus-times FP64 and or-and, flat, on a
+  32 x 32 virtual SUMMA grid and flat with the learned predictor: every column count
+  against the oracle, sampled columns against the oracle, and the three structures
+  identical (boolean values too).
 """
 import numpy as np
 import pytest
@@ -141,12 +142,26 @@ def test_rmat20_flat_and_summa32(ctx, sr):
     C = s.spgemm_multiply(ctx, dA, dA, sr)
     cp = assert_sampled(C, A, A, sr, cols, what="flat")
     np.testing.assert_array_equal(np.diff(cp), counts)
-    flat_rows = _checksums(C)[:4]
+    fl = _checksums(C)
+    flat_rows, flat_vals = fl[:4], fl[4]
     del C
     _release()
     C = s.spgemm_summa_blocked(ctx, dA, dA, 32, sr)
     cp = assert_sampled(C, A, A, sr, cols, what="summa 32")
     np.testing.assert_array_equal(np.diff(cp), counts)
     assert _checksums(C)[:4] == flat_rows, "flat and blocked structure differ"
+    del C
+    _release()
+    # the large skewed squaring with the learned predictor sizing the output (trained on
+    # R-MAT scales 14-15 and ER 2^13 here; every overflowed column is redone exactly): the same counts,
+    # sampled columns and structure as the exact path, values exact for the boolean semiring
+    _train_predictor(ctx, steps=200)
+    C = s.spgemm_multiply(ctx, dA, dA, sr, s.default_opts(use_predictor=1))
+    cp = assert_sampled(C, A, A, sr, cols, what="flat, predictor on")
+    np.testing.assert_array_equal(np.diff(cp), counts)
+    got = _checksums(C)
+    assert got[:4] == flat_rows, "predicted and exact structure differ"
+    if sr == OR_BOOL:
+        assert got[4] == flat_vals, "predicted and exact boolean values differ"
     del C
     _release()
