@@ -435,6 +435,7 @@ spgemm_status_t engine_setup(Engine* E, spgemm_ctx* ctx, spgemm_semiring_t sr, c
         size_t o_items = take(sizeof(int2) * nd * MAX_PARTS);
         size_t o_np = take(nd);
         size_t o_sb = take(4 * nd);
+        size_t o_bb = take(8 * nd);
         auto dbuf = ctx_buf(ctx, off);
         if (!dbuf) return set_err(ctx, SPGEMM_ERR_OOM, "slab-tier arena of %zu bytes", off);
         E->bufs.push_back(dbuf);
@@ -446,15 +447,19 @@ spgemm_status_t engine_setup(Engine* E, spgemm_ctx* ctx, spgemm_semiring_t sr, c
         dw.nitems = E->ctr + 2 * NBIN + 1;
         dw.nparts = (int8_t*)(db + o_np);
         dw.sbase = (int32_t*)(db + o_sb);
+        dw.bbase = (int64_t*)(db + o_bb);
+        unsigned long long* bnd_total = E->ctr + 2 * NBIN + 6;
         dw.store_ctr = E->ctr + 2 * NBIN + 2;
         dw.err = (int*)(E->ctr + 2 * NBIN + 3);
         unsigned long long* store_bound = E->ctr + 2 * NBIN + 4;
         dw.RB = E->cfg.dense_rows;
         launch_dense_items(st, E->it, dw.dlist, nd, E->flops, E->cfg.part_flops, dw.RB, (int2*)dw.items,
-                           E->ctr + 2 * NBIN + 1, (int8_t*)dw.nparts, (int32_t*)dw.sbase, store_bound);
-        unsigned long long hs[2] = {0, 0};
+                           E->ctr + 2 * NBIN + 1, (int8_t*)dw.nparts, (int32_t*)dw.sbase, store_bound,
+                           (int64_t*)dw.bbase, bnd_total);
+        unsigned long long hs[3] = {0, 0, 0};
         SG_CUDA(ctx, cudaMemcpyAsync(&hs[0], E->ctr + 2 * NBIN + 1, 8, cudaMemcpyDeviceToHost, st));
         SG_CUDA(ctx, cudaMemcpyAsync(&hs[1], store_bound, 8, cudaMemcpyDeviceToHost, st));
+        SG_CUDA(ctx, cudaMemcpyAsync(&hs[2], bnd_total, 8, cudaMemcpyDeviceToHost, st));
         SG_TRY(sync_ctx(ctx));
         dw.nslabs = (int64_t)hs[0];
         dw.store_cap = (int64_t)hs[1];
@@ -464,6 +469,7 @@ spgemm_status_t engine_setup(Engine* E, spgemm_ctx* ctx, spgemm_semiring_t sr, c
         size_t o_pref = take(4 * ns1);
         size_t o_soff = take(8 * ns1);
         size_t o_store = take(4 * (size_t)std::max<int64_t>(dw.store_cap, 1));
+        size_t o_bnd = take(4 * (size_t)std::max<unsigned long long>(hs[2], 1));
         auto sbuf = ctx_buf(ctx, off);
         if (!sbuf) return set_err(ctx, SPGEMM_ERR_OOM, "slab row sets of %zu bytes", off);
         E->bufs.push_back(sbuf);
@@ -472,6 +478,7 @@ spgemm_status_t engine_setup(Engine* E, spgemm_ctx* ctx, spgemm_semiring_t sr, c
         dw.spref = (int32_t*)(sb + o_pref);
         dw.soff = (int64_t*)(sb + o_soff);
         dw.store = (uint32_t*)(sb + o_store);
+        dw.bnd = (int32_t*)(sb + o_bnd);
     }
     if (sr == SPGEMM_OR_AND_BOOL) {
         // boolean operands without a stored false value: the bitmap tiers take every output as true

@@ -964,7 +964,8 @@ __host__ __device__ __forceinline__ void slab_rows(int64_t m, int q, int P, int6
 // rows <= flops).
 __global__ void k_dense_items(Items it, const int2* __restrict__ dlist, int64_t nd, const int64_t* __restrict__ flops,
                               int part_flops, int RB, int2* items, unsigned long long* nitems, int8_t* nparts,
-                              int32_t* sbase, unsigned long long* store_bound) {
+                              int32_t* sbase, unsigned long long* store_bound, int64_t* bbase,
+                              unsigned long long* bnd_total) {
     int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (d >= nd) return;
     const int2 e = dlist[d];
@@ -988,6 +989,8 @@ __global__ void k_dense_items(Items it, const int2* __restrict__ dlist, int64_t 
         words += (R1 - R0 + 31) >> 5;
     }
     atomicAdd(store_bound, (unsigned long long)(f < words ? f : words));
+    // boundary table: P + 1 rows of deg positions (where each slab starts in every A(:,k))
+    bbase[d] = (int64_t)atomicAdd(bnd_total, (unsigned long long)((P + 1) * deg));
     unsigned long long base = atomicAdd(nitems, (unsigned long long)P);
     sbase[d] = (int32_t)base;
     for (int q = 0; q < P; ++q) items[base + q] = make_int2((int)d, q);
@@ -995,11 +998,42 @@ __global__ void k_dense_items(Items it, const int2* __restrict__ dlist, int64_t 
 
 void launch_dense_items(cudaStream_t st, const Items& it, const int2* dense_list, int64_t ndense, const int64_t* flops,
                         int part_flops, int RB, int2* items, unsigned long long* nitems, int8_t* nparts,
-                        int32_t* sbase, unsigned long long* store_bound) {
+                        int32_t* sbase, unsigned long long* store_bound, int64_t* bbase,
+                        unsigned long long* bnd_total) {
     if (ndense == 0) return;
     k_dense_items<<<(int)ceil_div64(ndense, 256), 256, 0, st>>>(it, dense_list, ndense, flops, part_flops, RB, items,
-                                                               nitems, nparts, sbase, store_bound);
+                                                               nitems, nparts, sbase, store_bound, bbase, bnd_total);
     note_launch();
+}
+
+// Slab boundaries, once for both passes: row q of column d's table holds, for every
+// entry t of B(:,j), where slab q starts inside A(:,k) (relative to the column's
+// start); row P holds A(:,k)'s length.  One CTA per slab, every search of the slab
+// in flight at once (the passes that read them no longer wait on search chains at
+// their barriers).
+__global__ void __launch_bounds__(256) k_slab_bounds(Items it, DenseWork dw) {
+    const int64_t nsym = (int64_t)*dw.nitems;
+    for (int64_t w = blockIdx.x; w < nsym; w += gridDim.x) {
+        const int2 itm = dw.items[w];
+        const int d = itm.x, q = itm.y;
+        const int2 e = __ldg(dw.dlist + d);
+        const Prod* pr = it.prods + e.x;
+        const int P = dw.nparts[d];
+        const int64_t m = pr->A.m;
+        int64_t R0, R1;
+        slab_rows(m, q, P, R0, R1);
+        const int64_t bs = __ldg(pr->B.cp + e.y), be = __ldg(pr->B.cp + e.y + 1);
+        const int64_t deg = be - bs;
+        int32_t* __restrict__ row = dw.bnd + dw.bbase[d] + (int64_t)q * deg;
+        const int32_t* __restrict__ air = pr->A.ir;
+        for (int64_t t = threadIdx.x; t < deg; t += blockDim.x) {
+            const int32_t k = __ldg(pr->B.ir + bs + t);
+            int64_t s, en;
+            a_col(it, pr, bs + t, k, s, en);
+            row[t] = q == 0 ? 0 : lower_bound_rows(air + s, en - s, R0);
+            if (q == P - 1) row[t + deg] = (int32_t)(en - s);
+        }
+    }
 }
 
 // flag = 1 when some stored value of an operand is false (boolean semiring): then
@@ -1114,8 +1148,9 @@ __device__ __forceinline__ void rt_compact(RangeSmem* sc, bool active, int len, 
 // warp for each window of products (a and b, the A and B values, only when NUM;
 // row is INT_MIN on lanes without a product).  Ends with a CTA barrier.
 template <class SR, bool NUM, class F>
-__device__ __forceinline__ void slab_walk(const Items& it, const Prod* pr, int64_t bs, int64_t be, int64_t R0,
-                                          int64_t R1, int64_t m, RangeSmem* sc, F&& f) {
+__device__ __forceinline__ void slab_walk(const Items& it, const Prod* pr, int64_t bs, int64_t be,
+                                          const int32_t* __restrict__ brow0, const int32_t* __restrict__ brow1,
+                                          RangeSmem* sc, F&& f) {
     using T = typename SR::T;
     constexpr int U = 4, NWARP = RT_BLOCK / 32;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1128,8 +1163,8 @@ __device__ __forceinline__ void slab_walk(const Items& it, const Prod* pr, int64
             const int32_t k = __ldg(pr->B.ir + t);
             int64_t s, en;
             a_col(it, pr, t, k, s, en);
-            a = R0 == 0 ? s : s + lower_bound_rows(air + s, en - s, R0);
-            const int64_t b = R1 == m ? en : s + lower_bound_rows(air + s, en - s, R1);
+            a = s + __ldg(brow0 + (t - bs));
+            const int64_t b = s + __ldg(brow1 + (t - bs));
             len = (int)(b - a);
             if constexpr (NUM) *reinterpret_cast<T*>(&bvbits) = load_val<SR>(pr->B, t);
         }
@@ -1204,8 +1239,10 @@ __device__ __forceinline__ void load4(const T* __restrict__ p, T v[4]) {
 // whose arrays hold nnz_end entries (a quad past the end is read one by one).
 // f(valid, row, a, b) as in slab_walk, four times per window.
 template <class SR, bool NUM, class F>
-__device__ __forceinline__ void slab_walk_quads(const Items& it, const Prod* pr, int64_t bs, int64_t be, int64_t R0,
-                                                int64_t R1, int64_t m, int64_t nnz_end, RangeSmem* sc, F&& f) {
+__device__ __forceinline__ void slab_walk_quads(const Items& it, const Prod* pr, int64_t bs, int64_t be,
+                                                const int32_t* __restrict__ brow0,
+                                                const int32_t* __restrict__ brow1, int64_t nnz_end, RangeSmem* sc,
+                                                F&& f) {
     using T = typename SR::T;
     constexpr int NWARP = RT_BLOCK / 32;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1219,8 +1256,8 @@ __device__ __forceinline__ void slab_walk_quads(const Items& it, const Prod* pr,
             const int32_t k = __ldg(pr->B.ir + t);
             int64_t s, en;
             a_col(it, pr, t, k, s, en);
-            a = R0 == 0 ? s : s + lower_bound_rows(air + s, en - s, R0);
-            b = R1 == m ? en : s + lower_bound_rows(air + s, en - s, R1);
+            a = s + __ldg(brow0 + (t - bs));
+            b = s + __ldg(brow1 + (t - bs));
             nq = b > a ? (int)(((b - 1) >> 2) - (a >> 2) + 1) : 0;
             if constexpr (NUM) *reinterpret_cast<T*>(&bvbits) = load_val<SR>(pr->B, t);
         }
@@ -1314,8 +1351,10 @@ __global__ void __launch_bounds__(RT_BLOCK, 2) k_slab_sym(Items it, DenseWork dw
             const int lr = (int)(row - R0);
             if (ok && (unsigned)lr < (unsigned)span) atomicOr(&bitmap[lr >> 5], 1u << (lr & 31));
         };
-        if (quads_ok(pr)) slab_walk_quads<BOOL8, false>(it, pr, bs, be, R0, R1, m, pr->A.nnz, sc, mark);
-        else slab_walk<BOOL8, false>(it, pr, bs, be, R0, R1, m, sc, mark);
+        const int32_t* brow0 = dw.bnd + dw.bbase[d] + (int64_t)q * (be - bs);
+        const int32_t* brow1 = brow0 + (be - bs);
+        if (quads_ok(pr)) slab_walk_quads<BOOL8, false>(it, pr, bs, be, brow0, brow1, pr->A.nnz, sc, mark);
+        else slab_walk<BOOL8, false>(it, pr, bs, be, brow0, brow1, sc, mark);
         // count over contiguous word ranges, then store the row set
         const int wpt = (nw + RT_BLOCK - 1) / RT_BLOCK;
         const int w0 = min(tid * wpt, nw), w1 = min(w0 + wpt, nw);
@@ -1463,8 +1502,10 @@ __global__ void __launch_bounds__(RT_BLOCK, 2) k_slab_num(Items it, DenseWork dw
                 red_out<SR>(Cv, ob + rank, SR::mul(a, b));
             };
             const int64_t bs = __ldg(pr->B.cp + e.y), be = __ldg(pr->B.cp + e.y + 1);
-            if (quads_ok(pr)) slab_walk_quads<SR, true>(it, pr, bs, be, R0, R1, m, pr->A.nnz, sc, add);
-            else slab_walk<SR, true>(it, pr, bs, be, R0, R1, m, sc, add);
+            const int32_t* brow0 = dw.bnd + dw.bbase[d] + (int64_t)q * (be - bs);
+            const int32_t* brow1 = brow0 + (be - bs);
+            if (quads_ok(pr)) slab_walk_quads<SR, true>(it, pr, bs, be, brow0, brow1, pr->A.nnz, sc, add);
+            else slab_walk<SR, true>(it, pr, bs, be, brow0, brow1, sc, add);
         } else {
             __syncthreads();
         }
@@ -1487,6 +1528,8 @@ static void run_slabs(cudaStream_t st, const Items& it, const DenseWork& dw, boo
     if (dw.ndense <= 0) return;
     const int64_t nslab_max = dw.nslabs > 0 ? dw.nslabs : dw.ndense * MAX_PARTS;
     if (!numeric) {
+        k_slab_bounds<<<(int)std::min<int64_t>(nslab_max, sm_count() * 8), 256, 0, st>>>(it, dw);
+        note_launch();
         const size_t smem = RS_BYTES + (size_t)(dw.RB / 32) * 4;
         smem_at_least((const void*)k_slab_sym, smem);
         const int grid = (int)std::min<int64_t>(nslab_max, resident_grid((const void*)k_slab_sym, RT_BLOCK, smem));

@@ -63,6 +63,9 @@ struct DenseWork {
     int64_t store_cap = 0;                // entries of store
     unsigned long long* store_ctr = nullptr;
     const int* vals_zero = nullptr;       // boolean semiring: some operand value is false
+    int32_t* bnd = nullptr;               // slab boundaries: per long column, P + 1 rows of deg
+                                          // offsets into every A(:,k) (row P: its length)
+    const int64_t* bbase = nullptr;       // where each long column's boundary table starts
     int* err = nullptr;                   // nonzero: a capacity was exceeded
     int RB = 1 << 19;                     // most rows per slab
     // block mode (every A_i has at most BLOCK_TIER_MAX_ROWS rows): long columns
@@ -125,7 +128,8 @@ void launch_numeric_bins(cudaStream_t st, const Items& it, TierCfg cfg, const ui
 // most RB rows each; *store_bound accumulates the entries their row sets can need
 void launch_dense_items(cudaStream_t st, const Items& it, const int2* dense_list, int64_t ndense,
                         const int64_t* flops, int part_flops, int RB, int2* items, unsigned long long* nitems,
-                        int8_t* nparts, int32_t* sbase, unsigned long long* store_bound);
+                        int8_t* nparts, int32_t* sbase, unsigned long long* store_bound, int64_t* bbase,
+                        unsigned long long* bnd_total);
 // *flag = 1 when an operand of some product stores a false value (boolean semiring)
 void launch_false_values(cudaStream_t st, const Items& it, int* flag);
 // *flag = 1 when one of the n bytes at vals is 0 (vals == nullptr: nothing)
