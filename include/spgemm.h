@@ -102,7 +102,9 @@ typedef struct {
     int warp_max_flops;       /* columns with flops <= this use warp-wide hash tables  */
     int block_max_flops;      /* columns with flops <= this use CTA-wide hash tables;
                                  longer columns (the slab tier) are cut into row slabs,
-                                 each counted and then accumulated by one CTA          */
+                                 each counted and then accumulated by one CTA (at most
+                                 4096).  -1 (default) = automatic: 4096 for operands of
+                                 at most 32768 rows, 2048 for larger ones.            */
     int dense_part_flops;     /* slab tier: target flops per row slab of a long column
                                  (default 65536); a column whose B column is long gets
                                  fewer, larger slabs                                    */

@@ -111,7 +111,7 @@ void spgemm_opts_default(spgemm_opts_t* o) {
     o->summa_fused = 0;
     o->summa_merge_every = 0;
     o->warp_max_flops = 512;
-    o->block_max_flops = 4096;
+    o->block_max_flops = -1;
     o->dense_part_flops = DEFAULT_PART_FLOPS;
     o->range_slab_rows = 0;
     o->predictor_margin = 0.25f;
@@ -295,9 +295,13 @@ spgemm_status_t engine_setup(Engine* E, spgemm_ctx* ctx, spgemm_semiring_t sr, c
     E->sr = sr;
     E->opts = opts;
     E->cfg.warp_max = std::max(0, std::min(opts.warp_max_flops, 512));
-    E->cfg.block_max = std::max(E->cfg.warp_max, std::min(opts.block_max_flops, 4096));
     int64_t mmax = 32;
     for (auto& pr : prods) mmax = std::max<int64_t>(mmax, pr.A.m);
+    // automatic: operands of at most BLOCK_TIER_MAX_ROWS rows keep columns of up to 4096
+    // flops in warp groups of the block tier; larger operands send columns beyond 2048
+    // flops to the slab tier instead of the sorting CTA hash tables (measured best)
+    const int bm = opts.block_max_flops >= 0 ? opts.block_max_flops : (mmax <= BLOCK_TIER_MAX_ROWS ? 4096 : 2048);
+    E->cfg.block_max = std::max(E->cfg.warp_max, std::min(bm, 4096));
     {
         // symbolic slabs: at most MAX_PARTS per column, each within the shared-memory bitmap
         const int64_t cap = opts.range_slab_rows > 0

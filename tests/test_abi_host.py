@@ -81,7 +81,7 @@ def test_product_entry_points_check_their_handles(lib, ctx):
 def test_default_options():
     from paper_1006_2183_gb300 import spgemm as sp
     o = sp.default_opts()
-    assert (o.warp_max_flops, o.block_max_flops, o.dense_part_flops) == (512, 4096, 65536)
+    assert (o.warp_max_flops, o.block_max_flops, o.dense_part_flops) == (512, -1, 65536)
     assert (o.use_predictor, o.summa_fused, o.summa_merge_every, o.block_kernel, o.range_slab_rows) == (0, 0, 0, 0, 0)
 
 
