@@ -862,10 +862,10 @@ __global__ void __launch_bounds__(256) k_tiny(Items it, const int2* __restrict__
         } else {
             // exact mode: Coff are exact offsets; predicted mode (nnz_item set): capacity offsets
             const int64_t out0 = __ldg(Coff + u);
-            if (nnz_item) {
-                nnz_item[u] = m;
-                if (m > __ldg(Coff + u + 1) - out0) continue;   // overflow: redone in its exact place
-            }
+            if (nnz_item) nnz_item[u] = m;
+            // overflow (predicted mode): redone in its exact place; in exact mode the counts
+            // agree, and the check keeps an inconsistent input inside its column
+            if (m > __ldg(Coff + u + 1) - out0) continue;
             const int32_t rb = out_row_base(pr, e.y);
             for (int i = 0; i < m; ++i) {
                 Cir[out0 + i] = r[i] + rb;
