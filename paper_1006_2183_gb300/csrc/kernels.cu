@@ -958,6 +958,17 @@ __host__ __device__ __forceinline__ void slab_rows(int64_t m, int q, int P, int6
     R1 = q == P - 1 ? m : (((int64_t)(q + 1) * m / P) & ~int64_t(31));
 }
 
+// the most rows any of the P slabs over m rows holds
+__host__ __device__ __forceinline__ int64_t slab_max_rows(int64_t m, int P) {
+    int64_t mx = 0;
+    for (int q = 0; q < P; ++q) {
+        int64_t R0, R1;
+        slab_rows(m, q, P, R0, R1);
+        mx = R1 - R0 > mx ? R1 - R0 : mx;
+    }
+    return mx;
+}
+
 // Slabs of the long columns: P per column, items[sbase[d] + q] = (d, q); the
 // storage bound of the slab row sets, sum over columns of min(flops, words),
 // accumulates in *store_bound (a slab stores min(words, rows) 4-byte entries and
@@ -973,8 +984,10 @@ __global__ void k_dense_items(Items it, const int2* __restrict__ dlist, int64_t 
     const int64_t f = flops[__ldg(it.item_base + e.x) + e.y];
     const int64_t deg = __ldg(pr->B.cp + e.y + 1) - __ldg(pr->B.cp + e.y);
     const int64_t m = pr->A.m;
-    // slab rows stay <= RB: one slab when m fits, else cuts of at most RB - 32 rows plus alignment
-    const int64_t pmin = m <= RB ? 1 : ceil_div64(m, (int64_t)RB - 32);
+    // slab rows stay <= RB: the fewest slabs whose 32-aligned cuts all fit (the host
+    // sized RB so that MAX_PARTS slabs always do)
+    int64_t pmin = m <= RB ? 1 : ceil_div64(m, (int64_t)RB);
+    while (pmin < MAX_PARTS && slab_max_rows(m, (int)pmin) > RB) ++pmin;
     int64_t P = ceil_div64(f, part_flops);
     const int64_t pdeg = f / (32 * (deg > 0 ? deg : 1));   // about 32 products per (slab, B entry) at least
     P = P < pdeg ? P : pdeg;
@@ -1235,10 +1248,11 @@ __device__ __forceinline__ void load4(const T* __restrict__ p, T v[4]) {
 // slab_walk over aligned quads: a segment [a, b) of A(:,k) covers the quads
 // q = a/4 .. (b-1)/4, and each lane takes one quad per window, loading its four
 // rows with one 16-byte load (and its values with one or two) and masking the
-// positions outside [a, b).  Needs A.ir and A.num 16-byte aligned and A a CSC
-// whose arrays hold nnz_end entries (a quad past the end is read one by one).
+// positions outside [a, b).  U windows per step, every load issued before the
+// updates.  Needs A.ir and A.num 16-byte aligned and A a CSC whose arrays hold
+// nnz_end entries (a quad past the end is read one by one).
 // f(valid, row, a, b) as in slab_walk, four times per window.
-template <class SR, bool NUM, class F>
+template <class SR, bool NUM, int U, class F>
 __device__ __forceinline__ void slab_walk_quads(const Items& it, const Prod* pr, int64_t bs, int64_t be,
                                                 const int32_t* __restrict__ brow0,
                                                 const int32_t* __restrict__ brow1, int64_t nnz_end, RangeSmem* sc,
@@ -1273,41 +1287,55 @@ __device__ __forceinline__ void slab_walk_quads(const Items& it, const Prod* pr,
                 else hi = mid;
             }
             int o0 = lo;
-            for (int xw = xb; xw < xe; xw += 32) {
-                const int oi = warp_window_segment(sc->end, ns, xw, o0);
-                const bool ok = xw + lane < xe;
-                int32_t row[4] = {INT_MIN, INT_MIN, INT_MIN, INT_MIN};
-                T av[4] = {T(0), T(0), T(0), T(0)};
-                int64_t sa = 0, sb = 0, p0 = 0;
-                T bv = T(0);
-                if (ok) {
-                    sa = sc->start[oi];
-                    sb = sc->stop[oi];
-                    p0 = ((sa >> 2) + (xw + lane - (oi ? sc->end[oi - 1] : 0))) << 2;
-                    if (p0 + 4 <= nnz_end) {
-                        const int4 r = __ldg(reinterpret_cast<const int4*>(air + p0));
-                        row[0] = r.x;
-                        row[1] = r.y;
-                        row[2] = r.z;
-                        row[3] = r.w;
-                        if constexpr (NUM) {
-                            if (anum) load4<T>(anum + p0, av);
-                            else av[0] = av[1] = av[2] = av[3] = (T)SR::one();
-                        }
-                    } else {   // the array's last, partial quad
+            for (int x0 = xb; x0 < xe; x0 += 32 * U) {
+                int4 rq[U];
+                T av[U][4];
+                T bv[U];
+                unsigned vm[U];   // bit j: position p0 + j lies in the segment
 #pragma unroll
-                        for (int j = 0; j < 4; ++j)
-                            if (p0 + j < nnz_end) {
-                                row[j] = __ldg(air + p0 + j);
-                                if constexpr (NUM) av[j] = load_val<SR>(pr->A, p0 + j);
+                for (int uu = 0; uu < U; ++uu) {
+                    const int xw = x0 + 32 * uu;
+                    const int oi = warp_window_segment(sc->end, ns, xw, o0);
+                    rq[uu] = make_int4(INT_MIN, INT_MIN, INT_MIN, INT_MIN);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) av[uu][j] = T(0);
+                    bv[uu] = T(0);
+                    vm[uu] = 0u;
+                    if (xw + lane < xe) {
+                        const int64_t sa = sc->start[oi], sb = sc->stop[oi];
+                        const int64_t p0 = ((sa >> 2) + (xw + lane - (oi ? sc->end[oi - 1] : 0))) << 2;
+                        // sa - p0 is in [-inf, 3] and sb - p0 in [1, inf): the quad holds
+                        // positions lo .. hi-1 of the segment
+                        const int qlo = (int)max(sa - p0, (int64_t)0);
+                        const int qhi = (int)min(sb - p0, (int64_t)4);
+                        vm[uu] = (0xfu << qlo) & (0xfu >> (4 - qhi));
+                        if (p0 + 4 <= nnz_end) {
+                            rq[uu] = __ldg(reinterpret_cast<const int4*>(air + p0));
+                            if constexpr (NUM) {
+                                if (anum) load4<T>(anum + p0, av[uu]);
+                                else av[uu][0] = av[uu][1] = av[uu][2] = av[uu][3] = (T)SR::one();
                             }
+                        } else {   // the array's last, partial quad
+                            int32_t r4[4] = {INT_MIN, INT_MIN, INT_MIN, INT_MIN};
+#pragma unroll
+                            for (int j = 0; j < 4; ++j)
+                                if (p0 + j < nnz_end) {
+                                    r4[j] = __ldg(air + p0 + j);
+                                    if constexpr (NUM) av[uu][j] = load_val<SR>(pr->A, p0 + j);
+                                }
+                            rq[uu] = make_int4(r4[0], r4[1], r4[2], r4[3]);
+                        }
+                        if constexpr (NUM) bv[uu] = *reinterpret_cast<const T*>(&sc->bv[oi]);
                     }
-                    if constexpr (NUM) bv = *reinterpret_cast<const T*>(&sc->bv[oi]);
                 }
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const bool v = ok && p0 + j >= sa && p0 + j < sb;
-                    f(v, v ? row[j] : INT_MIN, av[j], bv);
+                for (int uu = 0; uu < U; ++uu) {
+                    const int32_t r4[4] = {rq[uu].x, rq[uu].y, rq[uu].z, rq[uu].w};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const bool v = (vm[uu] >> j) & 1u;
+                        f(v, v ? r4[j] : INT_MIN, av[uu][j], bv[uu]);
+                    }
                 }
             }
         }
@@ -1341,27 +1369,51 @@ __global__ void __launch_bounds__(RT_BLOCK, 2) k_slab_sym(Items it, DenseWork dw
         int64_t R0, R1;
         slab_rows(m, q, P, R0, R1);
         const int nw = (int)((R1 - R0 + 31) >> 5);
+        const int ng = (nw + 3) >> 2;   // groups of 4 words (the bitmap is padded to whole groups)
         const int64_t bs = __ldg(pr->B.cp + e.y), be = __ldg(pr->B.cp + e.y + 1);
-        for (int x = tid; x < nw; x += RT_BLOCK) bitmap[x] = 0u;
+        for (int g = tid; g < ng; g += RT_BLOCK) reinterpret_cast<uint4*>(bitmap)[g] = make_uint4(0u, 0u, 0u, 0u);
         __syncthreads();
         const int span = (int)(R1 - R0);
+        const int32_t r0 = (int32_t)R0;
         // one shared atomic per product: R-MAT rows of one window mostly fall in different
         // words, so folding lanes per word first (shuffles) measured slower
         auto mark = [&](bool ok, int32_t row, uint8_t, uint8_t) {
-            const int lr = (int)(row - R0);
+            const int lr = row - r0;
             if (ok && (unsigned)lr < (unsigned)span) atomicOr(&bitmap[lr >> 5], 1u << (lr & 31));
         };
         const int32_t* brow0 = dw.bnd + dw.bbase[d] + (int64_t)q * (be - bs);
         const int32_t* brow1 = brow0 + (be - bs);
-        if (quads_ok(pr)) slab_walk_quads<BOOL8, false>(it, pr, bs, be, brow0, brow1, pr->A.nnz, sc, mark);
+        if (quads_ok(pr)) slab_walk_quads<BOOL8, false, 2>(it, pr, bs, be, brow0, brow1, pr->A.nnz, sc, mark);
         else slab_walk<BOOL8, false>(it, pr, bs, be, brow0, brow1, sc, mark);
-        // count over contiguous word ranges, then store the row set
-        const int wpt = (nw + RT_BLOCK - 1) / RT_BLOCK;
-        const int w0 = min(tid * wpt, nw), w1 = min(w0 + wpt, nw);
+        // count per chunk of 32 groups (lane l reads group 32 c + l with one 16-byte load:
+        // no bank conflicts); a thread owns cpt consecutive chunks for the CTA scan
+        constexpr int NWARP = RT_BLOCK / 32;
+        const int lane = tid & 31, warp = tid >> 5;
+        const int nch = (ng + 31) >> 5;
+        const uint4* __restrict__ grp4 = reinterpret_cast<const uint4*>(bitmap);
+        int* s_cc = reinterpret_cast<int*>(sc->start);   // the walk's segment arrays are free now
+        for (int cc = warp; cc < nch; cc += NWARP) {
+            const int g = cc * 32 + lane;
+            int c = 0;
+            if (g < ng) {
+                const uint4 v = grp4[g];
+                c = __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+            }
+            c = __reduce_add_sync(0xffffffffu, c);
+            if (lane == 0) s_cc[cc] = c;
+        }
+        __syncthreads();
+        const int cpt = (nch + RT_BLOCK - 1) / RT_BLOCK;
+        const int c0 = min(tid * cpt, nch), c1 = min(c0 + cpt, nch);
         int cnt = 0;
-        for (int x = w0; x < w1; ++x) cnt += __popc(bitmap[x]);
+        for (int cc = c0; cc < c1; ++cc) cnt += s_cc[cc];
         int total;
-        const int excl = group_incl_scan<RT_BLOCK>(cnt, s_scan, total) - cnt;
+        int excl = group_incl_scan<RT_BLOCK>(cnt, s_scan, total) - cnt;
+        for (int cc = c0; cc < c1; ++cc) {
+            const int c = s_cc[cc];
+            s_cc[cc] = excl;   // rows before chunk cc
+            excl += c;
+        }
         const bool dense = total >= nw;
         const int64_t size = dense ? nw : total;
         if (tid == 0) {
@@ -1381,12 +1433,24 @@ __global__ void __launch_bounds__(RT_BLOCK, 2) k_slab_sym(Items it, DenseWork dw
             if (dense) {
                 for (int x = tid; x < nw; x += RT_BLOCK) __stcs(out + x, bitmap[x]);
             } else {
-                int r = excl;
-                for (int x = w0; x < w1; ++x) {
-                    uint32_t bits = bitmap[x];
-                    while (bits) {
-                        __stcs(out + r++, (uint32_t)(R0 + x * 32 + __ffs(bits) - 1));
-                        bits &= bits - 1;
+                // a warp per chunk: lanes write their group's rows at warp-scanned offsets,
+                // so the lanes of one store hit neighbouring addresses
+                for (int cc = warp; cc < nch; cc += NWARP) {
+                    const int g = cc * 32 + lane;
+                    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                    if (g < ng) v = grp4[g];
+                    const int c = __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+                    int r = s_cc[cc] + warp_incl_scan(c) - c;
+                    if (__ballot_sync(0xffffffffu, c != 0) == 0u) continue;
+                    const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+                    const uint32_t base = (uint32_t)(R0 + (int64_t)g * 128);
+#pragma unroll
+                    for (int y = 0; y < 4; ++y) {
+                        uint32_t bits = wv[y];
+                        while (bits) {
+                            __stcs(out + r++, base + 32 * y + __ffs(bits) - 1);
+                            bits &= bits - 1;
+                        }
                     }
                 }
             }
@@ -1450,34 +1514,76 @@ __global__ void __launch_bounds__(RT_BLOCK, 2) k_slab_num(Items it, DenseWork dw
             }
         }
         __syncthreads();
-        // 2. rows before every group: thread tid owns groups [g0, g1)
-        {
-            const int gpt = (ng + RT_BLOCK - 1) / RT_BLOCK;
-            const int g0 = min(tid * gpt, ng), g1 = min(g0 + gpt, ng);
+        // 2. rows before every group: a warp per chunk of 32 groups (lane l reads group
+        //    32 c + l: no bank conflicts), chunk totals scanned by the CTA, then added
+        constexpr int NWARP = RT_BLOCK / 32;
+        const int lane = tid & 31, warp = tid >> 5;
+        const int nch = (ng + 31) >> 5;
+        int* s_cc = reinterpret_cast<int*>(sc->start);   // free until the walk
+        for (int cc = warp; cc < nch; cc += NWARP) {
+            const int g = cc * 32 + lane;
             int c = 0;
-            for (int x = g0 * 4; x < g1 * 4; ++x) c += __popc(bitmap[x]);
+            if (g < ng) {
+                const uint4 grp = reinterpret_cast<const uint4*>(bitmap)[g];
+                c = __popc(grp.x) + __popc(grp.y) + __popc(grp.z) + __popc(grp.w);
+            }
+            const int inc = warp_incl_scan(c);
+            if (g < ng) gp[g] = inc - c;
+            if (lane == 31) s_cc[cc] = inc;
+        }
+        __syncthreads();
+        {
+            const int cpt = (nch + RT_BLOCK - 1) / RT_BLOCK;
+            const int c0 = min(tid * cpt, nch), c1 = min(c0 + cpt, nch);
+            int c = 0;
+            for (int cc = c0; cc < c1; ++cc) c += s_cc[cc];
             int total;
-            int r = group_incl_scan<RT_BLOCK>(c, s_scan, total) - c;
-            for (int g = g0; g < g1; ++g) {
-                gp[g] = r;
-                r += __popc(bitmap[4 * g]) + __popc(bitmap[4 * g + 1]) + __popc(bitmap[4 * g + 2]) +
-                     __popc(bitmap[4 * g + 3]);
+            int excl = group_incl_scan<RT_BLOCK>(c, s_scan, total) - c;
+            for (int cc = c0; cc < c1; ++cc) {
+                const int v = s_cc[cc];
+                s_cc[cc] = excl;
+                excl += v;
             }
         }
         __syncthreads();
-        // 3. C's rows of a bitmap slab (one group per thread: consecutive threads, consecutive ranks)
+        for (int g = tid; g < ng; g += RT_BLOCK) gp[g] += s_cc[g >> 5];
+        __syncthreads();
+        // 3. C's rows of a bitmap slab: a warp per chunk of 32 groups; lanes write their
+        //    group's rows from its rank base, or, for chunks of at least 16 rows a word,
+        //    the warp writes one word at a time (lane l: bit l), so that every store
+        //    covers neighbouring addresses
         if (dense) {
-            for (int g = tid; g < ng; g += RT_BLOCK) {
-                int r = gp[g];
-                const uint4 grp = reinterpret_cast<const uint4*>(bitmap)[g];
-                const uint32_t wv[4] = {grp.x, grp.y, grp.z, grp.w};
+            const uint4* __restrict__ grp4 = reinterpret_cast<const uint4*>(bitmap);
+            for (int cc = warp; cc < nch; cc += NWARP) {
+                const int g = cc * 32 + lane;
+                uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                if (g < ng) v = grp4[g];
+                const int c = __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+                const int tot = __reduce_add_sync(0xffffffffu, c);
+                if (tot == 0) continue;
+                int r = g < ng ? gp[g] : 0;
+                const int32_t base = (int32_t)(R0 + (int64_t)g * 128) + rb;
+                const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+                if (tot >= 2048) {
+                    for (int src = 0; src < 32; ++src) {
+                        int ry = __shfl_sync(0xffffffffu, r, src);
+                        const int32_t by = __shfl_sync(0xffffffffu, base, src);
 #pragma unroll
-                for (int y = 0; y < 4; ++y) {
-                    uint32_t bits = wv[y];
-                    const int32_t base = (int32_t)(R0 + (int64_t)(4 * g + y) * 32) + rb;
-                    while (bits) {
-                        __stcs(Cir + ob + r++, base + __ffs(bits) - 1);
-                        bits &= bits - 1;
+                        for (int y = 0; y < 4; ++y) {
+                            const uint32_t wy = __shfl_sync(0xffffffffu, wv[y], src);
+                            if ((wy >> lane) & 1u)
+                                __stcs(Cir + ob + ry + __popc(wy & ((1u << lane) - 1u)), by + 32 * y + lane);
+                            ry += __popc(wy);
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int y = 0; y < 4; ++y) {
+                        uint32_t bits = wv[y];
+                        while (bits) {
+                            __stcs(Cir + ob + r++, base + 32 * y + __ffs(bits) - 1);
+                            bits &= bits - 1;
+                        }
                     }
                 }
             }
@@ -1488,9 +1594,10 @@ __global__ void __launch_bounds__(RT_BLOCK, 2) k_slab_num(Items it, DenseWork dw
         // 5. every product, added at its row's rank
         if (walk) {
             const int span = (int)(R1 - R0);
+            const int32_t r0 = (int32_t)R0;
             auto add = [&](bool ok, int32_t row, T a, T b) {
                 if (!ok) return;
-                const int lr = (int)(row - R0);
+                const int lr = row - r0;
                 if ((unsigned)lr >= (unsigned)span) return;   // malformed input only
                 const int wd = lr >> 5, g = wd >> 2, y = wd & 3;
                 const uint4 grp = reinterpret_cast<const uint4*>(bitmap)[g];
@@ -1504,7 +1611,7 @@ __global__ void __launch_bounds__(RT_BLOCK, 2) k_slab_num(Items it, DenseWork dw
             const int64_t bs = __ldg(pr->B.cp + e.y), be = __ldg(pr->B.cp + e.y + 1);
             const int32_t* brow0 = dw.bnd + dw.bbase[d] + (int64_t)q * (be - bs);
             const int32_t* brow1 = brow0 + (be - bs);
-            if (quads_ok(pr)) slab_walk_quads<SR, true>(it, pr, bs, be, brow0, brow1, pr->A.nnz, sc, add);
+            if (quads_ok(pr)) slab_walk_quads<SR, true, 2>(it, pr, bs, be, brow0, brow1, pr->A.nnz, sc, add);
             else slab_walk<SR, true>(it, pr, bs, be, brow0, brow1, sc, add);
         } else {
             __syncthreads();
@@ -1530,7 +1637,7 @@ static void run_slabs(cudaStream_t st, const Items& it, const DenseWork& dw, boo
     if (!numeric) {
         k_slab_bounds<<<(int)std::min<int64_t>(nslab_max, sm_count() * 8), 256, 0, st>>>(it, dw);
         note_launch();
-        const size_t smem = RS_BYTES + (size_t)(dw.RB / 32) * 4;
+        const size_t smem = RS_BYTES + (size_t)(dw.RB / 128 + 1) * 16;
         smem_at_least((const void*)k_slab_sym, smem);
         const int grid = (int)std::min<int64_t>(nslab_max, resident_grid((const void*)k_slab_sym, RT_BLOCK, smem));
         k_slab_sym<<<grid, RT_BLOCK, smem, st>>>(it, dw);
