@@ -390,6 +390,8 @@ spgemm_status_t engine_setup(Engine* E, spgemm_ctx* ctx, spgemm_semiring_t sr, c
     E->it.acl = any_dcsc ? (int32_t*)(base + o_acl) : nullptr;
     E->it.max_m = 0;
     for (auto& pr : E->hprods) E->it.max_m = std::max<int64_t>(E->it.max_m, pr.A.m);
+    // operands of few rows: the sort tier takes the columns of 17 .. 128 products
+    E->cfg.sort_max = E->it.max_m <= BLOCK_TIER_MAX_ROWS ? 128 : 0;
     uint64_t* sketch = nullptr;
     int64_t* skbase = nullptr;
     PhaseTimer t_an(ctx, SPGEMM_PHASE_ANALYZE, sr);

@@ -317,6 +317,183 @@ __global__ void __launch_bounds__(BLOCK) k_block_tier(Items it, const int2* __re
     }
 }
 
+// ------------------------------------------------------------------ sort tier
+// Columns of at most N = 32 K products (bins 2, 3 and 4 when the tier configuration
+// bounds their flops, K = 1, 2 and 4), one warp each, in registers: slot i = 32 r + lane
+// receives product i keyed (row << 7) | i, a bitonic network across the warp sorts
+// the keys (the values follow through the slot index), a segmented scan combines
+// equal rows, and C's rows and values are written with coalesced stores.  There is
+// no bitmap to set up and clear, no shared memory and no atomic, which is what
+// dominates the block tier's cost on columns this short.
+
+// A lane's register shuffled up by d lanes, or from lane src (one-byte types through int).
+template <class V>
+__device__ __forceinline__ V shfl_v_up(V x, int d) {
+    if constexpr (sizeof(V) == 1) return (V)__shfl_up_sync(0xffffffffu, (int)x, d);
+    else return __shfl_up_sync(0xffffffffu, x, d);
+}
+
+template <class V>
+__device__ __forceinline__ V shfl_v(V x, int src) {
+    if constexpr (sizeof(V) == 1) return (V)__shfl_sync(0xffffffffu, (int)x, src);
+    else return __shfl_sync(0xffffffffu, x, src);
+}
+
+template <class SR, int K>
+__global__ void __launch_bounds__(256) k_sort_tier(Items it, const int2* __restrict__ list, int64_t count,
+                                                   int64_t* __restrict__ nnz_item, const int64_t* __restrict__ Coff,
+                                                   int32_t* __restrict__ Cir, typename SR::T* __restrict__ Cv,
+                                                   const int* __restrict__ vals_zero) {
+    using T = typename SR::T;
+    using Acc = typename SR::Acc;
+    constexpr int N = 32 * K;
+    constexpr uint32_t NONE = 0xffffffffu;
+    static_assert(K == 1 || K == 2 || K == 4, "slot index fits 7 bits; rows fit 25 bits");
+    const int lane = threadIdx.x & 31;
+    // boolean products whose operands hold no false value: every output value is true
+    const bool walk = SR::id != SPGEMM_OR_AND_BOOL || vals_zero == nullptr || *vals_zero != 0;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < count; w += nwarp) {
+        const int2 e = __ldg(list + w);
+        const Prod* pr = it.prods + e.x;
+        const int64_t u = __ldg(it.item_base + e.x) + e.y;
+        const int64_t bs = __ldg(pr->B.cp + e.y), be = __ldg(pr->B.cp + e.y + 1);
+        const int m = (int)pr->A.m;   // <= BLOCK_TIER_MAX_ROWS
+        uint32_t key[K];
+        Acc val[K];
+#pragma unroll
+        for (int r = 0; r < K; ++r) {
+            key[r] = NONE;
+            val[r] = SR::zero();
+        }
+        // 1. products into slots: the entries of B(:,j) 32 at a time, slot i holding
+        //    product i (the bin bounds the column's products by N)
+        int base = 0;
+        for (int64_t b0 = bs; b0 < be && base < N; b0 += 32) {
+            const int64_t t = b0 + lane;
+            int len = 0;
+            int64_t a0 = 0;
+            T bv = T(0);
+            if (t < be) {
+                const int32_t k = __ldg(pr->B.ir + t);
+                int64_t sa, ea;
+                a_col(it, pr, t, k, sa, ea);
+                a0 = sa;
+                len = (int)(ea - sa);
+                if (walk) bv = load_val<SR>(pr->B, t);
+            }
+            const int inc = warp_incl_scan(len);
+            const int tot = __shfl_sync(0xffffffffu, inc, 31);
+#pragma unroll
+            for (int r = 0; r < K; ++r) {
+                const int p = r * 32 + lane - base;   // the slot's product within this chunk
+                int src = 0;                          // entries that end at or before product p
+#pragma unroll
+                for (int st = 16; st > 0; st >>= 1)
+                    if (__shfl_sync(0xffffffffu, inc, src + st - 1) <= p) src += st;
+                const int ex = __shfl_sync(0xffffffffu, inc - len, src);
+                const int64_t as = __shfl_sync(0xffffffffu, a0, src);
+                const T bvs = shfl_v(bv, src);
+                if (p >= 0 && p < tot) {
+                    const int64_t pos = as + (p - ex);
+                    const int32_t row = __ldg(pr->A.ir + pos);
+                    if ((unsigned)row < (unsigned)m) {   // else malformed input: skipped
+                        key[r] = ((uint32_t)row << 7) | (uint32_t)(r * 32 + lane);
+                        val[r] = walk ? SR::mul(load_val<SR>(pr->A, pos), bvs) : SR::one();
+                    }
+                }
+            }
+            base += tot;
+        }
+        // 2. bitonic sort of the N keys (slot i = 32 r + lane; partner i ^ j)
+#pragma unroll
+        for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                uint32_t nk[K];
+#pragma unroll
+                for (int r = 0; r < K; ++r) {
+                    const int i = r * 32 + lane;
+                    const uint32_t kp = j >= 32 ? key[r ^ (j >> 5)] : __shfl_xor_sync(0xffffffffu, key[r], j);
+                    const bool take_min = ((i & k) == 0) == ((i & j) == 0);
+                    nk[r] = take_min ? min(key[r], kp) : max(key[r], kp);
+                }
+#pragma unroll
+                for (int r = 0; r < K; ++r) key[r] = nk[r];
+            }
+        }
+        // 3. every sorted key takes its slot's value; equal rows are combined by a
+        //    segmented scan (equal rows are adjacent), so a row's last slot holds its sum
+        Acc v[K];
+#pragma unroll
+        for (int r = 0; r < K; ++r) {
+            const int idx = (int)(key[r] & 127u);
+            Acc x = shfl_v(val[0], idx & 31);
+#pragma unroll
+            for (int q = 1; q < K; ++q) {
+                const Acc y = shfl_v(val[q], idx & 31);
+                x = (idx >> 5) == q ? y : x;
+            }
+            v[r] = x;
+        }
+#pragma unroll
+        for (int r = 0; r < K; ++r) {
+            const uint32_t rw = key[r] >> 7;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t rp = __shfl_up_sync(0xffffffffu, rw, d);
+                const Acc vp = shfl_v_up(v[r], d);
+                if (lane >= d && rp == rw) v[r] = SR::add(vp, v[r]);
+            }
+        }
+#pragma unroll
+        for (int r = 1; r < K; ++r) {   // a row whose slots continue from register r - 1 into r
+            const uint32_t cr = __shfl_sync(0xffffffffu, key[r - 1] >> 7, 31);
+            const Acc cv = shfl_v(v[r - 1], 31);
+            if (key[r] != NONE && (key[r] >> 7) == cr) v[r] = SR::add(cv, v[r]);
+        }
+        // 4. a row's last slot writes it: positions by ballots, coalesced stores
+        uint32_t tb[K];
+        int cnt = 0;
+#pragma unroll
+        for (int r = 0; r < K; ++r) {
+            const uint32_t rw = key[r] >> 7;
+            uint32_t nx = __shfl_down_sync(0xffffffffu, rw, 1);
+            const uint32_t first_next = __shfl_sync(0xffffffffu, key[r + 1 < K ? r + 1 : r] >> 7, 0);
+            if (lane == 31) nx = r + 1 < K ? first_next : NONE;
+            tb[r] = __ballot_sync(0xffffffffu, key[r] != NONE && nx != rw);
+            cnt += __popc(tb[r]);
+        }
+        const int64_t out0 = __ldg(Coff + u);
+        const int64_t capn = __ldg(Coff + u + 1) - out0;
+        if (nnz_item && lane == 0) nnz_item[u] = cnt;
+        // exact offsets always fit; with nnz_item a column that does not fit its slots
+        // is only counted
+        if (cnt <= capn) {
+            const int32_t rb = out_row_base(pr, e.y);
+            int before = 0;
+#pragma unroll
+            for (int r = 0; r < K; ++r) {
+                if ((tb[r] >> lane) & 1u) {
+                    const int pos = before + __popc(tb[r] & ((1u << lane) - 1u));
+                    __stcs(Cir + out0 + pos, (int32_t)(key[r] >> 7) + rb);
+                    Cv[out0 + pos] = SR::out(v[r]);
+                }
+                before += __popc(tb[r]);
+            }
+        }
+    }
+}
+
+template <class SR, int K>
+void run_sort(cudaStream_t st, const Items& it, const int2* list, int64_t count, int64_t* nnz_item,
+              const int64_t* Coff, int32_t* Cir, typename SR::T* Cv, const int* vals_zero) {
+    if (count <= 0) return;
+    const int grid = (int)std::min<int64_t>(ceil_div64(count, 8), (int64_t)sm_count() * 8);
+    k_sort_tier<SR, K><<<grid, 256, 0, st>>>(it, list, count, nnz_item, Coff, Cir, Cv, vals_zero);
+    note_launch();
+}
+
 template <class SR, int GS, int BLOCK>
 void run_bt(cudaStream_t st, const Items& it, const int2* list, int64_t count, int64_t* nnz_item, const int64_t* Coff,
             int32_t* Cir, typename SR::T* Cv, const int* vals_zero) {
@@ -364,9 +541,17 @@ void launch_block_tier(cudaStream_t st, const Items& it, const int2* list, const
                 b = e;
             }
         };
-        // one warp per column for the CTA-table bins too (cap <= 4096): without the CTA's
-        // barrier chain per column, measured faster than 256-thread groups
-        runs(BIN_WARP0, BIN_DENSE, [&](const int2* l, int64_t n) {
+        // bins 2, 3 and 4 (at most 32, 64 and 128 products per column here): the sort tier
+        run_sort<SR, 1>(st, it, list + bin_off[BIN_WARP0], bin_cnt[BIN_WARP0], nnz_item, Coff, Cir, Cv,
+                        dw.vals_zero);
+        run_sort<SR, 2>(st, it, list + bin_off[BIN_WARP0 + 1], bin_cnt[BIN_WARP0 + 1], nnz_item, Coff, Cir, Cv,
+                        dw.vals_zero);
+        run_sort<SR, 4>(st, it, list + bin_off[BIN_WARP0 + 2], bin_cnt[BIN_WARP0 + 2], nnz_item, Coff, Cir, Cv,
+                        dw.vals_zero);
+        // one warp per column for the other warp bins and the CTA-table bins too (cap <=
+        // 4096): without the CTA's barrier chain per column, measured faster than
+        // 256-thread groups
+        runs(BIN_WARP0 + 3, BIN_DENSE, [&](const int2* l, int64_t n) {
             run_bt<SR, 32, 256>(st, it, l, n, nnz_item, Coff, Cir, Cv, dw.vals_zero);
         });
     }

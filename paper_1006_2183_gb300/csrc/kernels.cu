@@ -62,13 +62,21 @@ static void smem_at_least(const void* fn, size_t bytes) {
 
 constexpr int WARP_BLOCK = 256;   // 8 warp groups per CTA
 
-__host__ __device__ __forceinline__ int bin_of(int64_t flops, int64_t cap, int warp_max, int block_max) {
+__host__ __device__ __forceinline__ int bin_of(int64_t flops, int64_t cap, int warp_max, int block_max,
+                                              int sort_max) {
     if (cap <= 0) return 0;
     if (flops <= TINY_MAX) return BIN_TINY;
     if (cap <= warp_max) {
+        // with sort_max, a column of more than sort_max products never lands in a bin
+        // whose table is for at most sort_max rows: bins 2 and 3 then also bound flops
+        int64_t c = cap;
+        if (sort_max > 0) {
+            const int64_t fl = flops < sort_max + 1 ? flops : sort_max + 1;
+            c = cap > fl ? cap : fl;
+        }
         int64_t t = WARP_TBL0;
         int b = BIN_WARP0;
-        while (t < 2 * cap) { t <<= 1; ++b; }
+        while (t < 2 * c) { t <<= 1; ++b; }
         return b;
     }
     if (cap <= block_max) {
@@ -149,7 +157,7 @@ __global__ void __launch_bounds__(256) k_analyze(Items it, TierCfg cfg, int64_t*
         flops[u] = f;
         if (it.nprod == 1) item_prod[u] = 0;
         int64_t cap = f < am ? f : am;
-        int b = bin_of(f, cap, cfg.warp_max, cfg.block_max);
+        int b = bin_of(f, cap, cfg.warp_max, cfg.block_max, cfg.sort_max);
         bin[u] = (uint8_t)b;
         atomicAdd(&s_cnt[b], 1ull);
         atomicAdd(&s_fl, (unsigned long long)f);
@@ -239,7 +247,7 @@ __global__ void k_numeric_bins(Items it, TierCfg cfg, const uint8_t* __restrict_
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < it.nitems; u += (int64_t)gridDim.x * blockDim.x) {
         const int b = bin[u];
         int nb = 0;
-        if (b >= BIN_TINY && b < BIN_DENSE) nb = bin_of(flops[u], nnz_item[u], cfg.warp_max, cfg.block_max);
+        if (b >= BIN_TINY && b < BIN_DENSE) nb = bin_of(flops[u], nnz_item[u], cfg.warp_max, cfg.block_max, cfg.sort_max);
         nbin[u] = (uint8_t)nb;
         if (nb) atomicAdd(&s_cnt[nb], 1ull);
     }

@@ -42,6 +42,8 @@ constexpr int DEFAULT_PART_FLOPS = 65536;
 struct TierCfg {
     int warp_max;     // cap <= warp_max -> warp tables (<= 512)
     int block_max;    // cap <= block_max -> CTA tables (<= 4096)
+    int sort_max = 0; // > 0 (operands of at most BLOCK_TIER_MAX_ROWS rows): bins 2, 3 and 4
+                      // hold only columns of at most 32, 64 and 128 products (the sort tier)
     int dense_rows;   // RB, most rows of one slab (bitmap bits in shared memory)
     int part_flops;   // target flops per slab of a long column
 };
