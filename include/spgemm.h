@@ -303,8 +303,11 @@ spgemm_status_t spgemm_batch_plan(spgemm_ctx_t ctx, int count, const spgemm_mat_
 spgemm_status_t spgemm_batch_execute(spgemm_plan_t plan);
 spgemm_status_t spgemm_batch_outputs(spgemm_plan_t plan, spgemm_mat_t* C);
 /* Autotuner: times the numeric phase of the batch for a small set of tier
- * thresholds (warp_max_flops, block_max_flops, dense_part_flops) and writes the
- * fastest into *opts.  When opts->use_predictor is set and the context holds
+ * thresholds (warp_max_flops, block_max_flops, dense_part_flops), then times
+ * whole spgemm_batch calls with the fastest of them and with the thresholds
+ * *opts came with, and writes the faster pair's thresholds into *opts (the
+ * thresholds also move work between the counting passes, which the numeric
+ * timing does not see).  When opts->use_predictor is set and the context holds
  * predictor parameters, it then times whole spgemm_batch calls with and
  * without the predictor (at the chosen thresholds) and leaves use_predictor at
  * 1 only if the predictor measured faster, so the tuned call never loses to

@@ -548,9 +548,20 @@ spgemm_status_t engine_symbolic(Engine* E) {
     SG_CUDA(ctx, cudaMemcpyAsync(nc, E->nctr, sizeof(nc), cudaMemcpyDeviceToHost, st));
     SG_CUDA(ctx, cudaMemcpyAsync(&nnz, E->Coff + U, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     SG_CUDA(ctx, cudaMemcpyAsync(&err, E->ctr + 2 * NBIN + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
+    // every product's first output, at the same synchronisation (batched calls)
+    std::shared_ptr<DevBuf> pob;
+    const int64_t np = E->it.nprod;
+    if (E->want_prod_off && np > 1) {
+        pob = ctx_buf(ctx, 8 * (np + 1));
+        if (!pob) return set_err(ctx, SPGEMM_ERR_OOM, "product offsets");
+        launch_gather_offsets(st, E->Coff, E->it.item_base, np, (int64_t*)pob->p);
+        E->prod_off.assign(np + 1, 0);
+        SG_CUDA(ctx, cudaMemcpyAsync(E->prod_off.data(), pob->p, 8 * (np + 1), cudaMemcpyDeviceToHost, st));
+    }
     SG_TRY(sync_ctx(ctx));
     if (err) return set_err(ctx, SPGEMM_ERR_INDEX_OVERFLOW, "slab tier capacity exceeded (code %d)", err);
     E->nnz_total = nnz;
+    if (E->want_prod_off && np <= 1) E->prod_off = {0, nnz};
     int64_t acc = 0;
     for (int b = 0; b < NBIN; ++b) {
         E->nbin_cnt[b] = (int64_t)nc[b];

@@ -15,12 +15,6 @@ using namespace sg;
 
 namespace {
 
-__global__ void k_gather_offsets(const int64_t* __restrict__ Coff, const int64_t* __restrict__ item_base, int64_t np,
-                                 int64_t* __restrict__ out) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= np; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = Coff[item_base[i]];
-}
-
 spgemm_status_t collect_prods(spgemm_ctx* ctx, int count, const spgemm_mat_t* A, const spgemm_mat_t* B,
                               spgemm_semiring_t sr, std::vector<Prod>* prods, std::vector<spgemm_mat_t>* convs,
                               bool check = false) {
@@ -63,6 +57,23 @@ spgemm_status_t finish_outputs(struct spgemm_plan* P) {
         P->colbase[i + 1] = P->colbase[i] + P->pn[i] + 1;
     }
     const int64_t total = P->colbase[np];
+    if ((int64_t)E.prod_off.size() == np + 1) {
+        // the symbolic pass returned where each product's output starts: no synchronisation
+        P->outoff = E.prod_off;
+        if (np == 1 && E.hprods[0].B.jc == nullptr) {
+            // one product with a CSC B: the item offsets are C's column pointers
+            P->out_cp = E.Coff_buf;
+            return SPGEMM_OK;
+        }
+        P->out_cp = ctx_buf(ctx, 8 * std::max<int64_t>(total, 1) + 8 * (np + 1));
+        if (!P->out_cp) return set_err(ctx, SPGEMM_ERR_OOM, "batch column pointers");
+        int64_t* cp = (int64_t*)P->out_cp->p;
+        int64_t* dcb = cp + std::max<int64_t>(total, 1);
+        SG_CUDA(ctx, cudaMemcpyAsync(dcb, P->colbase.data(), 8 * (np + 1), cudaMemcpyHostToDevice, ctx->stream));
+        launch_colptrs(ctx->stream, E.it, dcb, total, E.Coff, cp);
+        // P->colbase must outlive the copy: it lives with the plan
+        return SPGEMM_OK;
+    }
     P->out_cp = ctx_buf(ctx, 8 * std::max<int64_t>(total, 1) + 8 * (2 * np + 2));
     if (!P->out_cp) return set_err(ctx, SPGEMM_ERR_OOM, "batch column pointers");
     int64_t* cp = (int64_t*)P->out_cp->p;
@@ -70,8 +81,7 @@ spgemm_status_t finish_outputs(struct spgemm_plan* P) {
     int64_t* doff = dcb + (np + 1);
     SG_CUDA(ctx, cudaMemcpyAsync(dcb, P->colbase.data(), 8 * (np + 1), cudaMemcpyHostToDevice, ctx->stream));
     launch_colptrs(ctx->stream, E.it, dcb, total, E.Coff, cp);
-    k_gather_offsets<<<(int)ceil_div64(np + 1, 256), 256, 0, ctx->stream>>>(E.Coff, E.it.item_base, np, doff);
-    note_launch();
+    launch_gather_offsets(ctx->stream, E.Coff, E.it.item_base, np, doff);
     P->outoff.assign(np + 1, 0);
     SG_CUDA(ctx, cudaMemcpyAsync(P->outoff.data(), doff, 8 * (np + 1), cudaMemcpyDeviceToHost, ctx->stream));
     return sync_ctx(ctx);
@@ -99,6 +109,7 @@ spgemm_status_t batch_plan_build(spgemm_ctx* ctx, int count, const spgemm_mat_t*
     Engine& E = P->E;
     const bool learned = o.use_predictor && ctx->pred_ready && run_numeric;
     SG_TRY(engine_setup(&E, ctx, sr, o, prods, learned));
+    E.want_prod_off = true;
     if (learned) {
         SG_TRY(engine_numeric_predicted(&E, &P->out_r, &P->out_v));
     } else {
@@ -290,6 +301,22 @@ spgemm_status_t spgemm_autotune(spgemm_ctx_t ctx, int count, const spgemm_mat_t*
                 }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
+        {
+            // the grid above times the numeric pass alone; the thresholds also move work
+            // between the counting passes, so the pick must beat the caller's own
+            // thresholds as whole calls, or the caller's are kept
+            spgemm_opts_t o = *opts;
+            o.use_predictor = 0;
+            spgemm_status_t s0, s1;
+            const float t_given = time_batch_calls(ctx, count, A, B, sr, o, &s0);
+            SG_TRY(s0);
+            o.warp_max_flops = std::get<0>(pick);
+            o.block_max_flops = std::get<1>(pick);
+            o.dense_part_flops = std::get<2>(pick);
+            const float t_pick = time_batch_calls(ctx, count, A, B, sr, o, &s1);
+            SG_TRY(s1);
+            if (t_given <= t_pick) pick = {opts->warp_max_flops, opts->block_max_flops, opts->dense_part_flops, 0};
+        }
         if (try_pred) {
             // the predictor replaces the symbolic pass of the hash tiers but adds its own launches
             // and a move of C: keep it only where the whole batched call measured faster with it

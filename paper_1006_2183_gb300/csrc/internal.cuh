@@ -104,6 +104,8 @@ struct Engine {
     int64_t flops_total = 0;
     int64_t nnz_total = -1;
     bool symbolic_done = false;
+    bool want_prod_off = false;          // the symbolic pass also returns every product's first output
+    std::vector<int64_t> prod_off;       // entry (nprod + 1 values, filled with nnz_total)
     int64_t overflow_items = 0;
 };
 

@@ -1759,6 +1759,17 @@ __global__ void k_colptrs(Items it, const int64_t* __restrict__ colbase, int64_t
     }
 }
 
+__global__ void k_gather_offsets(const int64_t* __restrict__ Coff, const int64_t* __restrict__ item_base, int64_t np,
+                                 int64_t* __restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= np; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = Coff[item_base[i]];
+}
+
+void launch_gather_offsets(cudaStream_t st, const int64_t* Coff, const int64_t* item_base, int64_t np, int64_t* out) {
+    k_gather_offsets<<<(int)ceil_div64(np + 1, 256), 256, 0, st>>>(Coff, item_base, np, out);
+    note_launch();
+}
+
 void launch_colptrs(cudaStream_t st, const Items& it, const int64_t* colbase, int64_t total_cols, const int64_t* Coff,
                     int64_t* out) {
     if (total_cols <= 0) return;

@@ -164,6 +164,8 @@ void launch_sum_parts(cudaStream_t st, const Items& it, const DenseWork& dw, int
 // per-product column pointers from item offsets: out[colbase_i + j] for j in [0, n_i]
 void launch_colptrs(cudaStream_t st, const Items& it, const int64_t* colbase, int64_t total_cols, const int64_t* Coff,
                     int64_t* out);
+// out[i] = Coff[item_base[i]] for i in [0, np]: where each product's output starts
+void launch_gather_offsets(cudaStream_t st, const int64_t* Coff, const int64_t* item_base, int64_t np, int64_t* out);
 // out[0] = 0, out[i+1] = sum_{t <= i} in[t]; tmp needs scan_tmp_bytes(n)
 size_t scan_tmp_bytes(int64_t n);
 void launch_exclusive_scan(cudaStream_t st, const int64_t* in, int64_t n, int64_t* out, void* tmp);
