@@ -1,7 +1,8 @@
 """Parity of the sort tier (columns of 17 .. 128 products of operands with at most
-32,768 rows, sorted in the registers of one warp) with the oracle, at its edges:
+32,768 rows, sorted in the registers of one warp) with the oracle, at its edges and
+just beyond them (129 .. 256 products, the block tier):
 
-* every bin boundary (17, 32, 33, 64, 65, 128 products), each column exactly at it;
+* every bin boundary (17, 32, 33, 64, 65, 128, 129, 256 products), each column exactly at it;
 * columns whose products come from more than 32 entries of B (most of them hitting
   empty columns of A), so that the products arrive over several chunks of entries;
 * heavy duplication (every product of a column on one of three rows) and no
@@ -28,7 +29,7 @@ def ctx():
 
 
 def _operands(sr, seed):
-    """A (M x 600): columns 0..99 empty, 100..399 of 1..8 random rows, 400..499 of 1..4
+    """A (M x 600): columns 0..99 empty, 100..399 of 1..8 random rows, 400..499 of 1..3
     rows among {0, 1, 32767}, 500..599 of 1..8 rows in the top 64.  B (600 x n): one
     column per (target flops, style), built greedily from A's column lengths."""
     rng = np.random.default_rng(seed)
@@ -48,7 +49,7 @@ def _operands(sr, seed):
     np.cumsum(lens, out=colptr[1:])
     rowidx = np.concatenate(cols).astype(np.int32)
     bcols = []
-    for target in (17, 18, 31, 32, 33, 40, 63, 64, 65, 100, 127, 128):
+    for target in (17, 18, 31, 32, 33, 40, 63, 64, 65, 100, 127, 128, 129, 200, 255, 256):
         for style in ("plain", "many_empty", "dups", "top"):
             pool = {"plain": np.arange(100, 400), "many_empty": np.arange(100, 400),
                     "dups": np.arange(400, 500), "top": np.arange(500, 600)}[style]
@@ -85,7 +86,7 @@ def _operands(sr, seed):
 def test_sort_tier_edges_flat(ctx, sr):
     A, B = _operands(sr, 0x5A00 + sr)
     fl = oracle.flops_per_col(A, B)
-    assert fl.min() >= 17 and fl.max() <= 128 and (fl == 128).any() and (fl == 17).any()
+    assert fl.min() >= 17 and fl.max() <= 256 and (fl == 256).any() and (fl == 17).any()
     check_product(ctx, A, B, sr, what="sort tier columns")
 
 
