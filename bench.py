@@ -130,7 +130,13 @@ def learned_vs_plain(sp, ctx, steps: int, warmup: int, flush, c5=None) -> dict:
     import oracle
     train = _train_predictor(sp, ctx)
     out = {"predictor": train, "timing": f"CUDA events, median of {steps} after {warmup} warm-up runs, "
-                                          "L2 flushed before each"}
+                                          "L2 flushed before each",
+           "arms": {"plain": "one spgemm_multiply per product, in sequence",
+                    "batched": "one spgemm_batch call (one launch per tier over all products), no CUDA graph",
+                    "learned_batched": "spgemm_batch with the nnz predictor sizing the output, no CUDA graph",
+                    "auto": "spgemm_batch with the autotuner's thresholds and predictor choice, no CUDA graph",
+                    "graph_replay": "spgemm_batch_plan once, then one spgemm_batch_execute per call: the numeric "
+                                    "launches replayed from one CUDA graph (fixed structure)"}}
     work = {}
     pairs = gen.batch_pairs(512, 0x4004)
     As = [sp.Matrix.from_host(ctx, a, sp.PLUS_TIMES_I64) for a, _ in pairs]
