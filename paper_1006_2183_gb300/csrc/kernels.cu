@@ -697,7 +697,6 @@ __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK) k_bitcount(Items it, cons
         const Prod* pr = it.prods + e.x;
         const int64_t u = __ldg(it.item_base + e.x) + e.y;
         const int64_t bs = __ldg(pr->B.cp + e.y), be = __ldg(pr->B.cp + e.y + 1);
-        const int64_t mw = (pr->A.m + 31) >> 5;
         const uint32_t mrows = (uint32_t)(pr->A.m < (int64_t)bm_words * 32 ? pr->A.m : (int64_t)bm_words * 32);
         const int32_t* __restrict__ air = pr->A.ir;
         int c = 0;   // rows this lane marked first
