@@ -474,6 +474,7 @@ spgemm_status_t engine_setup(Engine* E, spgemm_ctx* ctx, spgemm_semiring_t sr, c
         size_t o_cnt = take(4 * ns1);
         size_t o_pref = take(4 * ns1);
         size_t o_soff = take(8 * ns1);
+        size_t o_rec = take(sizeof(SlabRec) * ns1);
         size_t o_store = take(4 * (size_t)std::max<int64_t>(dw.store_cap, 1));
         size_t o_bnd = take(4 * (size_t)std::max<unsigned long long>(hs[2], 1));
         auto sbuf = ctx_buf(ctx, off);
@@ -483,6 +484,7 @@ spgemm_status_t engine_setup(Engine* E, spgemm_ctx* ctx, spgemm_semiring_t sr, c
         dw.scount = (int32_t*)(sb + o_cnt);
         dw.spref = (int32_t*)(sb + o_pref);
         dw.soff = (int64_t*)(sb + o_soff);
+        dw.rec = (SlabRec*)(sb + o_rec);
         dw.store = (uint32_t*)(sb + o_store);
         dw.bnd = (int32_t*)(sb + o_bnd);
     }

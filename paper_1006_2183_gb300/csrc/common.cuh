@@ -267,6 +267,14 @@ __device__ __forceinline__ int warp_window_segment(const int* ends, int ns, int 
     return oi;
 }
 
+// Asynchronous 16-byte copy global -> shared (both 16-byte aligned), completed by
+// cp_async_wait_all in the issuing thread (then a barrier publishes it).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // C[pos] = C[pos] (+) v in global memory (an L2 reduction; the return value is unused).
 template <class SR>
 __device__ __forceinline__ void red_out(typename SR::T* Cv, int64_t pos, typename SR::Acc v) {

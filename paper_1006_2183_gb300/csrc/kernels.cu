@@ -1046,6 +1046,22 @@ __global__ void __launch_bounds__(256) k_slab_bounds(Items it, DenseWork dw) {
         const int64_t deg = be - bs;
         int32_t* __restrict__ row = dw.bnd + dw.bbase[d] + (int64_t)q * deg;
         const int32_t* __restrict__ air = pr->A.ir;
+        if (threadIdx.x == 0) {
+            SlabRec r;
+            r.prod = e.x;
+            r.col = e.y;
+            r.r0 = (int32_t)R0;
+            r.r1 = (int32_t)R1;
+            r.rb = out_row_base(pr, e.y);
+            r.cnt = 0;
+            r.bs = bs;
+            r.be = be;
+            r.bnd = dw.bbase[d] + (int64_t)q * deg;
+            r.u = __ldg(it.item_base + e.x) + e.y;
+            r.ob = 0;
+            r.soff = -1;
+            dw.rec[w] = r;
+        }
         for (int64_t t = threadIdx.x; t < deg; t += blockDim.x) {
             const int32_t k = __ldg(pr->B.ir + bs + t);
             int64_t s, en;
@@ -1364,20 +1380,25 @@ __global__ void __launch_bounds__(RT_BLOCK, 2) k_slab_sym(Items it, DenseWork dw
     uint32_t* bitmap = reinterpret_cast<uint32_t*>(smem + RS_BYTES);
     int* s_scan = sc->wc;
     __shared__ long long s_off;
+    __shared__ SlabRec s_rec[2];   // this slab's record and the next one's, in flight
+    constexpr int RC = sizeof(SlabRec) / 16;
     const int tid = threadIdx.x;
     const int64_t nsym = (int64_t)*dw.nitems;
-    for (int64_t w = blockIdx.x; w < nsym; w += gridDim.x) {
-        const int2 itm = dw.items[w];
-        const int d = itm.x, q = itm.y;
-        const int2 e = __ldg(dw.dlist + d);
-        const Prod* pr = it.prods + e.x;
-        const int P = dw.nparts[d];
-        const int64_t m = pr->A.m;
-        int64_t R0, R1;
-        slab_rows(m, q, P, R0, R1);
+    if (tid < RC && (int64_t)blockIdx.x < nsym)
+        cp_async16(reinterpret_cast<int4*>(&s_rec[0]) + tid, reinterpret_cast<const int4*>(dw.rec + blockIdx.x) + tid);
+    int k = 0;
+    for (int64_t w = blockIdx.x; w < nsym; w += gridDim.x, k ^= 1) {
+        if (tid < RC) cp_async_wait_all();
+        __syncthreads();   // s_rec[k] is slab w's record; s_rec[k ^ 1] is free
+        if (tid < RC && w + gridDim.x < nsym)
+            cp_async16(reinterpret_cast<int4*>(&s_rec[k ^ 1]) + tid,
+                       reinterpret_cast<const int4*>(dw.rec + w + gridDim.x) + tid);
+        const SlabRec& rc = s_rec[k];
+        const Prod* pr = it.prods + rc.prod;
+        const int64_t R0 = rc.r0, R1 = rc.r1;
         const int nw = (int)((R1 - R0 + 31) >> 5);
         const int ng = (nw + 3) >> 2;   // groups of 4 words (the bitmap is padded to whole groups)
-        const int64_t bs = __ldg(pr->B.cp + e.y), be = __ldg(pr->B.cp + e.y + 1);
+        const int64_t bs = rc.bs, be = rc.be;
         for (int g = tid; g < ng; g += RT_BLOCK) reinterpret_cast<uint4*>(bitmap)[g] = make_uint4(0u, 0u, 0u, 0u);
         __syncthreads();
         const int span = (int)(R1 - R0);
@@ -1388,7 +1409,7 @@ __global__ void __launch_bounds__(RT_BLOCK, 2) k_slab_sym(Items it, DenseWork dw
             const int lr = row - r0;
             if (ok && (unsigned)lr < (unsigned)span) atomicOr(&bitmap[lr >> 5], 1u << (lr & 31));
         };
-        const int32_t* brow0 = dw.bnd + dw.bbase[d] + (int64_t)q * (be - bs);
+        const int32_t* brow0 = dw.bnd + rc.bnd;
         const int32_t* brow1 = brow0 + (be - bs);
         if (quads_ok(pr)) slab_walk_quads<BOOL8, false, 2>(it, pr, bs, be, brow0, brow1, pr->A.nnz, sc, mark);
         else slab_walk<BOOL8, false>(it, pr, bs, be, brow0, brow1, sc, mark);
@@ -1431,6 +1452,8 @@ __global__ void __launch_bounds__(RT_BLOCK, 2) k_slab_sym(Items it, DenseWork dw
             }
             dw.soff[w] = off;
             dw.scount[w] = total;
+            dw.rec[w].soff = off;
+            dw.rec[w].cnt = total;
             s_off = off;
         }
         __syncthreads();
@@ -1481,25 +1504,29 @@ __global__ void __launch_bounds__(RT_BLOCK, 2) k_slab_num(Items it, DenseWork dw
     const bool walk = SR::id != SPGEMM_OR_AND_BOOL || dw.vals_zero == nullptr || *dw.vals_zero != 0;
     const T init = walk ? SR::out(SR::zero()) : T(1);
     const int64_t nsym = (int64_t)*dw.nitems;
-    for (int64_t w = blockIdx.x; w < nsym; w += gridDim.x) {
-        const int cnt = dw.scount[w];
+    __shared__ SlabRec s_rec[2];   // this slab's record and the next one's, in flight
+    constexpr int RC = sizeof(SlabRec) / 16;
+    if (tid < RC && (int64_t)blockIdx.x < nsym)
+        cp_async16(reinterpret_cast<int4*>(&s_rec[0]) + tid, reinterpret_cast<const int4*>(dw.rec + blockIdx.x) + tid);
+    int kb = 0;
+    for (int64_t w = blockIdx.x; w < nsym; w += gridDim.x, kb ^= 1) {
+        if (tid < RC) cp_async_wait_all();
+        __syncthreads();   // s_rec[kb] is slab w's record; s_rec[kb ^ 1] is free
+        if (tid < RC && w + gridDim.x < nsym)
+            cp_async16(reinterpret_cast<int4*>(&s_rec[kb ^ 1]) + tid,
+                       reinterpret_cast<const int4*>(dw.rec + w + gridDim.x) + tid);
+        const SlabRec& rc = s_rec[kb];
+        const int cnt = rc.cnt;
         // the same for every thread of the CTA; a row set that found no room (possible
         // only with malformed input, reported by the symbolic pass) is skipped
-        if (cnt == 0 || dw.soff[w] < 0) continue;
-        const int2 itm = dw.items[w];
-        const int d = itm.x, q = itm.y;
-        const int2 e = __ldg(dw.dlist + d);
-        const Prod* pr = it.prods + e.x;
-        const int P = dw.nparts[d];
-        const int64_t m = pr->A.m;
-        int64_t R0, R1;
-        slab_rows(m, q, P, R0, R1);
+        if (cnt == 0 || rc.soff < 0) continue;
+        const Prod* pr = it.prods + rc.prod;
+        const int64_t R0 = rc.r0, R1 = rc.r1;
         const int nw = (int)((R1 - R0 + 31) >> 5);
         const int ng = (nw + 3) >> 2;
-        const int64_t u = __ldg(it.item_base + e.x) + e.y;
-        const int32_t rb = out_row_base(pr, e.y);
-        const int64_t ob = __ldg(Coff + u) + dw.spref[w];
-        const uint32_t* __restrict__ rs = dw.store + dw.soff[w];
+        const int32_t rb = rc.rb;
+        const int64_t ob = rc.ob;
+        const uint32_t* __restrict__ rs = dw.store + rc.soff;
         const bool dense = cnt >= nw;
         // Streaming data (the stored row sets, read once; C's rows, written once) use
         // evict-first loads and stores, so that the slab's value region, zeroed below and
@@ -1615,8 +1642,8 @@ __global__ void __launch_bounds__(RT_BLOCK, 2) k_slab_num(Items it, DenseWork dw
                                  (y > 1 ? __popc(grp.y) : 0) + (y > 2 ? __popc(grp.z) : 0);
                 red_out<SR>(Cv, ob + rank, SR::mul(a, b));
             };
-            const int64_t bs = __ldg(pr->B.cp + e.y), be = __ldg(pr->B.cp + e.y + 1);
-            const int32_t* brow0 = dw.bnd + dw.bbase[d] + (int64_t)q * (be - bs);
+            const int64_t bs = rc.bs, be = rc.be;
+            const int32_t* brow0 = dw.bnd + rc.bnd;
             const int32_t* brow1 = brow0 + (be - bs);
             if (quads_ok(pr)) slab_walk_quads<SR, true, 2>(it, pr, bs, be, brow0, brow1, pr->A.nnz, sc, add);
             else slab_walk<SR, true>(it, pr, bs, be, brow0, brow1, sc, add);
@@ -1624,6 +1651,13 @@ __global__ void __launch_bounds__(RT_BLOCK, 2) k_slab_num(Items it, DenseWork dw
             __syncthreads();
         }
     }
+}
+
+// Completes the slab records for the numeric pass: where each slab's rows start in C.
+__global__ void k_slab_fin(DenseWork dw, const int64_t* __restrict__ Coff) {
+    const int64_t nsym = (int64_t)*dw.nitems;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nsym; w += (int64_t)gridDim.x * blockDim.x)
+        dw.rec[w].ob = __ldg(Coff + dw.rec[w].u) + dw.spref[w];
 }
 
 // CTAs per SM the kernel can keep resident with `smem` bytes, times the SM count
@@ -1649,6 +1683,8 @@ static void run_slabs(cudaStream_t st, const Items& it, const DenseWork& dw, boo
         const int grid = (int)std::min<int64_t>(nslab_max, resident_grid((const void*)k_slab_sym, RT_BLOCK, smem));
         k_slab_sym<<<grid, RT_BLOCK, smem, st>>>(it, dw);
     } else {
+        k_slab_fin<<<(int)std::min<int64_t>(ceil_div64(nslab_max, 256), sm_count() * 8), 256, 0, st>>>(dw, Coff);
+        note_launch();
         const size_t smem = RS_BYTES + (size_t)(dw.RB / 128 + 1) * 16 + (size_t)(dw.RB / 128 + 1) * 4;
         smem_at_least((const void*)k_slab_num<SR>, smem);
         const int grid = (int)std::min<int64_t>(nslab_max, resident_grid((const void*)k_slab_num<SR>, RT_BLOCK, smem));

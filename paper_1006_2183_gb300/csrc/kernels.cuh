@@ -48,6 +48,23 @@ struct TierCfg {
     int part_flops;   // target flops per slab of a long column
 };
 
+// Everything a pass needs about slab s before its work starts, written by the
+// boundary pre-pass (and, for the numeric pass, completed once C's offsets are
+// known): the passes copy the next slab's record into shared memory while the
+// current slab runs, so a slab starts without a chain of dependent loads.
+struct __align__(16) SlabRec {
+    int32_t prod, col;   // the long column: product and stored column of B
+    int32_t r0, r1;      // rows [r0, r1) of the slab
+    int32_t rb;          // output row base of the column
+    int32_t cnt;         // rows of the slab's row set (counting pass)
+    int64_t bs, be;      // B(:,j) is entries [bs, be)
+    int64_t bnd;         // this slab's row of the boundary table in `bnd`
+    int64_t u;           // item index of the column
+    int64_t ob;          // where the slab's rows start in C (numeric pass)
+    int64_t soff;        // where its row set is stored (< 0: none)
+};
+static_assert(sizeof(SlabRec) == 80, "five 16-byte chunks");
+
 // State of the slab tier shared by its kernels.  Slab s = sbase[d] + q is slab q
 // of long column d (position d in the dense list); items[s] = (d, q).
 struct DenseWork {
@@ -68,6 +85,7 @@ struct DenseWork {
     int32_t* bnd = nullptr;               // slab boundaries: per long column, P + 1 rows of deg
                                           // offsets into every A(:,k) (row P: its length)
     const int64_t* bbase = nullptr;       // where each long column's boundary table starts
+    SlabRec* rec = nullptr;               // per slab: its record
     int* err = nullptr;                   // nonzero: a capacity was exceeded
     int RB = 1 << 19;                     // most rows per slab
     // block mode (every A_i has at most BLOCK_TIER_MAX_ROWS rows): long columns
