@@ -1009,8 +1009,9 @@ __global__ void k_dense_items(Items it, const int2* __restrict__ dlist, int64_t 
         words += (R1 - R0 + 31) >> 5;
     }
     atomicAdd(store_bound, (unsigned long long)(f < words ? f : words));
-    // boundary table: P + 1 rows of deg positions (where each slab starts in every A(:,k))
-    bbase[d] = (int64_t)atomicAdd(bnd_total, (unsigned long long)((P + 1) * deg));
+    // boundary table: P + 1 rows of deg positions (where each slab starts in every A(:,k)),
+    // then two rows with where every A(:,k) starts (low and high 32 bits)
+    bbase[d] = (int64_t)atomicAdd(bnd_total, (unsigned long long)((P + 3) * deg));
     unsigned long long base = atomicAdd(nitems, (unsigned long long)P);
     sbase[d] = (int32_t)base;
     for (int q = 0; q < P; ++q) items[base + q] = make_int2((int)d, q);
@@ -1060,6 +1061,7 @@ __global__ void __launch_bounds__(256) k_slab_bounds(Items it, DenseWork dw) {
             r.u = __ldg(it.item_base + e.x) + e.y;
             r.ob = 0;
             r.soff = -1;
+            r.sab = dw.bbase[d] + (int64_t)(P + 1) * deg;
             dw.rec[w] = r;
         }
         for (int64_t t = threadIdx.x; t < deg; t += blockDim.x) {
@@ -1068,6 +1070,11 @@ __global__ void __launch_bounds__(256) k_slab_bounds(Items it, DenseWork dw) {
             a_col(it, pr, bs + t, k, s, en);
             row[t] = q == 0 ? 0 : lower_bound_rows(air + s, en - s, R0);
             if (q == P - 1) row[t + deg] = (int32_t)(en - s);
+            if (q == 0) {   // where A(:,k) starts, for the passes' segment arithmetic
+                int32_t* sr = dw.bnd + dw.bbase[d] + (int64_t)(P + 1) * deg;
+                sr[t] = (int32_t)(uint32_t)s;
+                sr[t + deg] = (int32_t)(s >> 32);
+            }
         }
     }
 }
@@ -1176,6 +1183,12 @@ __device__ __forceinline__ void rt_compact(RangeSmem* sc, bool active, int len, 
     __syncthreads();
 }
 
+// Where A(:,k) starts for entry i of B(:,j) (deg entries): two int32 rows of the
+// column's boundary table, low and high 32 bits, written by the boundary pre-pass.
+__device__ __forceinline__ int64_t seg_start(const int32_t* __restrict__ sab, int64_t i, int64_t deg) {
+    return (int64_t)(uint32_t)__ldg(sab + i) | ((int64_t)__ldg(sab + deg + i) << 32);
+}
+
 // Flattened walk over the products of rows [R0, R1) of column bs..be of B: B's
 // entries in chunks of RT_BLOCK; per entry the part of A(:,k) inside the rows
 // (two binary searches), compacted into segments; each warp takes a contiguous
@@ -1186,7 +1199,7 @@ __device__ __forceinline__ void rt_compact(RangeSmem* sc, bool active, int len, 
 template <class SR, bool NUM, class F>
 __device__ __forceinline__ void slab_walk(const Items& it, const Prod* pr, int64_t bs, int64_t be,
                                           const int32_t* __restrict__ brow0, const int32_t* __restrict__ brow1,
-                                          RangeSmem* sc, F&& f) {
+                                          const int32_t* __restrict__ sab, RangeSmem* sc, F&& f) {
     using T = typename SR::T;
     constexpr int U = 4, NWARP = RT_BLOCK / 32;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1196,9 +1209,7 @@ __device__ __forceinline__ void slab_walk(const Items& it, const Prod* pr, int64
         int len = 0;
         int64_t a = 0, bvbits = 0;
         if (t < be) {
-            const int32_t k = __ldg(pr->B.ir + t);
-            int64_t s, en;
-            a_col(it, pr, t, k, s, en);
+            const int64_t s = seg_start(sab, t - bs, be - bs);
             a = s + __ldg(brow0 + (t - bs));
             const int64_t b = s + __ldg(brow1 + (t - bs));
             len = (int)(b - a);
@@ -1278,8 +1289,8 @@ __device__ __forceinline__ void load4(const T* __restrict__ p, T v[4]) {
 template <class SR, bool NUM, int U, class F>
 __device__ __forceinline__ void slab_walk_quads(const Items& it, const Prod* pr, int64_t bs, int64_t be,
                                                 const int32_t* __restrict__ brow0,
-                                                const int32_t* __restrict__ brow1, int64_t nnz_end, RangeSmem* sc,
-                                                F&& f) {
+                                                const int32_t* __restrict__ brow1, const int32_t* __restrict__ sab,
+                                                int64_t nnz_end, RangeSmem* sc, F&& f) {
     using T = typename SR::T;
     constexpr int NWARP = RT_BLOCK / 32;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1290,9 +1301,7 @@ __device__ __forceinline__ void slab_walk_quads(const Items& it, const Prod* pr,
         int nq = 0;
         int64_t a = 0, b = 0, bvbits = 0;
         if (t < be) {
-            const int32_t k = __ldg(pr->B.ir + t);
-            int64_t s, en;
-            a_col(it, pr, t, k, s, en);
+            const int64_t s = seg_start(sab, t - bs, be - bs);
             a = s + __ldg(brow0 + (t - bs));
             b = s + __ldg(brow1 + (t - bs));
             nq = b > a ? (int)(((b - 1) >> 2) - (a >> 2) + 1) : 0;
@@ -1411,8 +1420,9 @@ __global__ void __launch_bounds__(RT_BLOCK, 2) k_slab_sym(Items it, DenseWork dw
         };
         const int32_t* brow0 = dw.bnd + rc.bnd;
         const int32_t* brow1 = brow0 + (be - bs);
-        if (quads_ok(pr)) slab_walk_quads<BOOL8, false, 2>(it, pr, bs, be, brow0, brow1, pr->A.nnz, sc, mark);
-        else slab_walk<BOOL8, false>(it, pr, bs, be, brow0, brow1, sc, mark);
+        const int32_t* sab = dw.bnd + rc.sab;
+        if (quads_ok(pr)) slab_walk_quads<BOOL8, false, 2>(it, pr, bs, be, brow0, brow1, sab, pr->A.nnz, sc, mark);
+        else slab_walk<BOOL8, false>(it, pr, bs, be, brow0, brow1, sab, sc, mark);
         // count per chunk of 32 groups (lane l reads group 32 c + l with one 16-byte load:
         // no bank conflicts); a thread owns cpt consecutive chunks for the CTA scan
         constexpr int NWARP = RT_BLOCK / 32;
@@ -1645,8 +1655,9 @@ __global__ void __launch_bounds__(RT_BLOCK, 2) k_slab_num(Items it, DenseWork dw
             const int64_t bs = rc.bs, be = rc.be;
             const int32_t* brow0 = dw.bnd + rc.bnd;
             const int32_t* brow1 = brow0 + (be - bs);
-            if (quads_ok(pr)) slab_walk_quads<SR, true, 2>(it, pr, bs, be, brow0, brow1, pr->A.nnz, sc, add);
-            else slab_walk<SR, true>(it, pr, bs, be, brow0, brow1, sc, add);
+            const int32_t* sab = dw.bnd + rc.sab;
+            if (quads_ok(pr)) slab_walk_quads<SR, true, 2>(it, pr, bs, be, brow0, brow1, sab, pr->A.nnz, sc, add);
+            else slab_walk<SR, true>(it, pr, bs, be, brow0, brow1, sab, sc, add);
         } else {
             __syncthreads();
         }

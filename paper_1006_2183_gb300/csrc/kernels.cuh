@@ -62,6 +62,7 @@ struct __align__(16) SlabRec {
     int64_t u;           // item index of the column
     int64_t ob;          // where the slab's rows start in C (numeric pass)
     int64_t soff;        // where its row set is stored (< 0: none)
+    int64_t sab;         // the column's rows P + 1 and P + 2 of `bnd`: where each A(:,k) starts
 };
 static_assert(sizeof(SlabRec) == 80, "five 16-byte chunks");
 
@@ -82,8 +83,9 @@ struct DenseWork {
     int64_t store_cap = 0;                // entries of store
     unsigned long long* store_ctr = nullptr;
     const int* vals_zero = nullptr;       // boolean semiring: some operand value is false
-    int32_t* bnd = nullptr;               // slab boundaries: per long column, P + 1 rows of deg
-                                          // offsets into every A(:,k) (row P: its length)
+    int32_t* bnd = nullptr;               // slab boundaries: per long column, P + 3 rows of deg:
+                                          // offsets into every A(:,k) (row P: its length),
+                                          // then where A(:,k) starts (low, high 32 bits)
     const int64_t* bbase = nullptr;       // where each long column's boundary table starts
     SlabRec* rec = nullptr;               // per slab: its record
     int* err = nullptr;                   // nonzero: a capacity was exceeded
