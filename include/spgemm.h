@@ -104,7 +104,7 @@ typedef struct {
                                  longer columns (the slab tier) are cut into row slabs,
                                  each counted and then accumulated by one CTA (at most
                                  4096).  -1 (default) = automatic: 4096 for operands of
-                                 at most 32768 rows, 2048 for larger ones.            */
+                                 at most 32768 rows, 1024 for larger ones.            */
     int dense_part_flops;     /* slab tier: target flops per row slab of a long column
                                  (default 65536); a column whose B column is long gets
                                  fewer, larger slabs                                    */

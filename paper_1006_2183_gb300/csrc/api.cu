@@ -298,9 +298,10 @@ spgemm_status_t engine_setup(Engine* E, spgemm_ctx* ctx, spgemm_semiring_t sr, c
     int64_t mmax = 32;
     for (auto& pr : prods) mmax = std::max<int64_t>(mmax, pr.A.m);
     // automatic: operands of at most BLOCK_TIER_MAX_ROWS rows keep columns of up to 4096
-    // flops in warp groups of the block tier; larger operands send columns beyond 2048
-    // flops to the slab tier instead of the sorting CTA hash tables (measured best)
-    const int bm = opts.block_max_flops >= 0 ? opts.block_max_flops : (mmax <= BLOCK_TIER_MAX_ROWS ? 4096 : 2048);
+    // flops in warp groups of the block tier; larger operands send columns beyond 1024
+    // flops to the slab tier instead of the sorting CTA hash tables (measured best: R-MAT
+    // 20 flat FP64 + bool 165.7 / 161.9 / 163.7 ms at 2048 / 1024 / 768)
+    const int bm = opts.block_max_flops >= 0 ? opts.block_max_flops : (mmax <= BLOCK_TIER_MAX_ROWS ? 4096 : 1024);
     E->cfg.block_max = std::max(E->cfg.warp_max, std::min(bm, 4096));
     {
         // symbolic slabs: at most MAX_PARTS per column, each within the shared-memory bitmap
