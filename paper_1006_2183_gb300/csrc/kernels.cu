@@ -153,14 +153,24 @@ __global__ void __launch_bounds__(256) k_analyze(Items it, TierCfg cfg, int64_t*
         mx = om > mx ? om : mx;
         sk |= __shfl_xor_sync(0xffffffffu, sk, o, LPI);
     }
-    if (u < it.nitems && sub == 0) {
+    const bool has = u < it.nitems && sub == 0;
+    const int64_t cap = f < am ? f : am;
+    const int b = has ? bin_of(f, cap, cfg.warp_max, cfg.block_max, cfg.sort_max) : -1;
+    {
+        // per-bin counts and total flops, one shared atomic per bin per warp (every
+        // item of a CTA adding to the same few counters serialises on them)
+        const unsigned peers = __match_any_sync(0xffffffffu, b);
+        const int lane = threadIdx.x & 31;
+        if (has && lane == __ffs(peers) - 1) atomicAdd(&s_cnt[b], (unsigned long long)__popc(peers));
+        unsigned long long fs = has ? (unsigned long long)f : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) fs += __shfl_xor_sync(0xffffffffu, fs, o);
+        if (lane == 0 && fs) atomicAdd(&s_fl, fs);
+    }
+    if (has) {
         flops[u] = f;
         if (it.nprod == 1) item_prod[u] = 0;
-        int64_t cap = f < am ? f : am;
-        int b = bin_of(f, cap, cfg.warp_max, cfg.block_max, cfg.sort_max);
         bin[u] = (uint8_t)b;
-        atomicAdd(&s_cnt[b], 1ull);
-        atomicAdd(&s_fl, (unsigned long long)f);
         if (maxlen) maxlen[u] = mx;
         if (feat) {
             // predictor inputs (definitions in predictor.cu)
