@@ -133,7 +133,14 @@ void spgemm_opts_default(spgemm_opts_t* opts);
 
 /* ---------------------------------------------------------------- context */
 /* stream: a cudaStream_t (NULL = legacy default stream).  alloc/free may be NULL,
- * in which case cudaMallocAsync/cudaFreeAsync on the stream are used. */
+ * in which case cudaMallocAsync/cudaFreeAsync on the stream are used.
+ * Where a call waits for the device (the counts behind C's size, flags), it reads
+ * those few bytes through mapped pinned host memory written by a kernel on the
+ * context's stream, not with a device-to-host cudaMemcpy: such a copy waits behind
+ * every bulk device-to-host copy already queued on the copy engine, the caller's
+ * included, so a caller may copy one result back on another stream while the next
+ * product runs.  The context holds that buffer (64 KiB or more) until
+ * spgemm_ctx_destroy. */
 spgemm_status_t spgemm_ctx_create(spgemm_ctx_t* ctx, void* cuda_stream, spgemm_alloc_fn alloc,
                                   spgemm_free_fn free_fn, void* alloc_user);
 spgemm_status_t spgemm_ctx_destroy(spgemm_ctx_t ctx);

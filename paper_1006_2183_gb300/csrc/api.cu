@@ -16,6 +16,11 @@ spgemm_status_t set_err(spgemm_ctx* ctx, spgemm_status_t s, const char* fmt, ...
         vsnprintf(buf, sizeof buf, fmt, ap);
         va_end(ap);
         ctx->err = buf;
+        if (s != SPGEMM_OK) {
+            // queued reads whose destinations the failing call is about to abandon
+            ctx->rb_pending.clear();
+            ctx->rb_used = 0;
+        }
     }
     return s;
 }
@@ -61,8 +66,63 @@ size_t sr_size(spgemm_semiring_t sr) {
 }
 
 spgemm_status_t sync_ctx(spgemm_ctx* ctx) {
-    SG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    const cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess) {
+        for (const auto& r : ctx->rb_pending) std::memcpy(r.dst, ctx->rb_host + r.off, r.bytes);
+    }
+    ctx->rb_pending.clear();
+    ctx->rb_used = 0;
+    SG_CUDA(ctx, e);
     SG_CUDA(ctx, cudaGetLastError());
+    return SPGEMM_OK;
+}
+
+namespace {
+// dst (mapped host memory) <- src (device), 8 bytes per thread when both are aligned
+__global__ void k_read_back(unsigned char* __restrict__ dst, const unsigned char* __restrict__ src, size_t bytes) {
+    const size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x, step = (size_t)gridDim.x * blockDim.x;
+    if ((((uintptr_t)src | (uintptr_t)dst | bytes) & 7) == 0) {
+        for (size_t i = i0; i < bytes / 8; i += step)
+            reinterpret_cast<unsigned long long*>(dst)[i] = reinterpret_cast<const unsigned long long*>(src)[i];
+    } else {
+        for (size_t i = i0; i < bytes; i += step) dst[i] = src[i];
+    }
+}
+}  // namespace
+
+spgemm_status_t read_back(spgemm_ctx* ctx, void* dst, const void* src, size_t bytes) {
+    if (bytes == 0) return SPGEMM_OK;
+    size_t off = (ctx->rb_used + 15) / 16 * 16;
+    if (off + bytes > ctx->rb_cap) {
+        if (!ctx->rb_pending.empty()) SG_TRY(sync_ctx(ctx));   // completes the queued reads first
+        off = 0;
+        if (bytes > ctx->rb_cap) {
+            if (ctx->rb_host) {
+                cudaStreamSynchronize(ctx->stream);   // no read still writes into the old buffer
+                cudaFreeHost(ctx->rb_host);
+            }
+            ctx->rb_host = ctx->rb_dev = nullptr;
+            ctx->rb_cap = 0;
+            const size_t cap = std::max<size_t>((bytes + 4095) / 4096 * 4096, 64 * 1024);
+            void* h = nullptr;
+            SG_CUDA(ctx, cudaHostAlloc(&h, cap, cudaHostAllocMapped));
+            void* d = nullptr;
+            const cudaError_t e = cudaHostGetDevicePointer(&d, h, 0);
+            if (e != cudaSuccess) {
+                cudaFreeHost(h);
+                return check_cuda(ctx, e, "mapped read-back buffer");
+            }
+            ctx->rb_host = (unsigned char*)h;
+            ctx->rb_dev = (unsigned char*)d;
+            ctx->rb_cap = cap;
+        }
+    }
+    const int grid = (int)std::min<size_t>((bytes + 2047) / 2048, 256);
+    k_read_back<<<grid, 256, 0, ctx->stream>>>(ctx->rb_dev + off, (const unsigned char*)src, bytes);
+    note_launch();
+    SG_CUDA(ctx, cudaGetLastError());
+    ctx->rb_pending.push_back({dst, off, bytes});
+    ctx->rb_used = off + bytes;
     return SPGEMM_OK;
 }
 
@@ -134,6 +194,8 @@ spgemm_status_t spgemm_ctx_create(spgemm_ctx_t* out, void* stream, spgemm_alloc_
 
 spgemm_status_t spgemm_ctx_set_stream(spgemm_ctx_t ctx, void* stream) {
     if (!ctx) return SPGEMM_ERR_INVALID_ARG;
+    // a read left in flight by a failed call still writes the mapped buffer on the old stream
+    if (ctx->rb_host && ctx->stream != (cudaStream_t)stream) cudaStreamSynchronize(ctx->stream);
     ctx->stream = (cudaStream_t)stream;
     return SPGEMM_OK;
 }
@@ -145,6 +207,7 @@ spgemm_status_t spgemm_ctx_destroy(spgemm_ctx_t ctx) {
     ctx_free(ctx, ctx->adam_v);
     ctx_free(ctx, ctx->grad);
     cudaStreamSynchronize(ctx->stream);
+    if (ctx->rb_host) cudaFreeHost(ctx->rb_host);
     delete ctx;
     return SPGEMM_OK;
 }
@@ -412,8 +475,8 @@ spgemm_status_t engine_setup(Engine* E, spgemm_ctx* ctx, spgemm_semiring_t sr, c
     launch_analyze(st, E->it, E->cfg, E->flops, E->bin, E->item_prod, E->ctr, E->ctr + 2 * NBIN, sketch, skbase,
                    E->feat, E->maxlen);
     unsigned long long hc[NBIN + 1];
-    SG_CUDA(ctx, cudaMemcpyAsync(hc, E->ctr, sizeof(unsigned long long) * NBIN, cudaMemcpyDeviceToHost, st));
-    SG_CUDA(ctx, cudaMemcpyAsync(hc + NBIN, E->ctr + 2 * NBIN, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    SG_TRY(read_back(ctx, hc, E->ctr, sizeof(unsigned long long) * NBIN));
+    SG_TRY(read_back(ctx, hc + NBIN, E->ctr + 2 * NBIN, sizeof(unsigned long long)));
     SG_TRY(sync_ctx(ctx));
     int64_t acc = 0;
     for (int b = 0; b < NBIN; ++b) {
@@ -464,9 +527,9 @@ spgemm_status_t engine_setup(Engine* E, spgemm_ctx* ctx, spgemm_semiring_t sr, c
                            E->ctr + 2 * NBIN + 1, (int8_t*)dw.nparts, (int32_t*)dw.sbase, store_bound,
                            (int64_t*)dw.bbase, bnd_total);
         unsigned long long hs[3] = {0, 0, 0};
-        SG_CUDA(ctx, cudaMemcpyAsync(&hs[0], E->ctr + 2 * NBIN + 1, 8, cudaMemcpyDeviceToHost, st));
-        SG_CUDA(ctx, cudaMemcpyAsync(&hs[1], store_bound, 8, cudaMemcpyDeviceToHost, st));
-        SG_CUDA(ctx, cudaMemcpyAsync(&hs[2], bnd_total, 8, cudaMemcpyDeviceToHost, st));
+        SG_TRY(read_back(ctx, &hs[0], E->ctr + 2 * NBIN + 1, 8));
+        SG_TRY(read_back(ctx, &hs[1], store_bound, 8));
+        SG_TRY(read_back(ctx, &hs[2], bnd_total, 8));
         SG_TRY(sync_ctx(ctx));
         dw.nslabs = (int64_t)hs[0];
         dw.store_cap = (int64_t)hs[1];
@@ -548,9 +611,9 @@ spgemm_status_t engine_symbolic(Engine* E) {
         SG_CUDA(ctx, cudaMemsetAsync(E->nctr, 0, 8 * 2 * NBIN, st));
         launch_numeric_bins(st, E->it, E->cfg, E->bin, E->flops, E->nnz_item, E->nbin, E->nctr);
     }
-    SG_CUDA(ctx, cudaMemcpyAsync(nc, E->nctr, sizeof(nc), cudaMemcpyDeviceToHost, st));
-    SG_CUDA(ctx, cudaMemcpyAsync(&nnz, E->Coff + U, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    SG_CUDA(ctx, cudaMemcpyAsync(&err, E->ctr + 2 * NBIN + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SG_TRY(read_back(ctx, nc, E->nctr, sizeof(nc)));
+    SG_TRY(read_back(ctx, &nnz, E->Coff + U, sizeof(int64_t)));
+    SG_TRY(read_back(ctx, &err, E->ctr + 2 * NBIN + 3, sizeof(int)));
     // every product's first output, at the same synchronisation (batched calls)
     std::shared_ptr<DevBuf> pob;
     const int64_t np = E->it.nprod;
@@ -559,7 +622,7 @@ spgemm_status_t engine_symbolic(Engine* E) {
         if (!pob) return set_err(ctx, SPGEMM_ERR_OOM, "product offsets");
         launch_gather_offsets(st, E->Coff, E->it.item_base, np, (int64_t*)pob->p);
         E->prod_off.assign(np + 1, 0);
-        SG_CUDA(ctx, cudaMemcpyAsync(E->prod_off.data(), pob->p, 8 * (np + 1), cudaMemcpyDeviceToHost, st));
+        SG_TRY(read_back(ctx, E->prod_off.data(), pob->p, 8 * (np + 1)));
     }
     SG_TRY(sync_ctx(ctx));
     if (err) return set_err(ctx, SPGEMM_ERR_INDEX_OVERFLOW, "slab tier capacity exceeded (code %d)", err);
@@ -714,7 +777,7 @@ spgemm_status_t spgemm_plan_tier_stats(spgemm_plan_t P, int64_t* cols4, int64_t*
     launch_tier_stats(ctx->stream, P->E.it, P->E.bin, P->E.item_prod, P->E.flops, P->E.nnz_item,
                       (unsigned long long*)buf->p);
     unsigned long long h[16];
-    SG_CUDA(ctx, cudaMemcpyAsync(h, buf->p, 128, cudaMemcpyDeviceToHost, ctx->stream));
+    SG_TRY(read_back(ctx, h, buf->p, 128));
     SG_TRY(sync_ctx(ctx));
     for (int t = 0; t < 4; ++t) {
         if (cols4) cols4[t] = (int64_t)h[t];

@@ -83,7 +83,7 @@ spgemm_status_t finish_outputs(struct spgemm_plan* P) {
     launch_colptrs(ctx->stream, E.it, dcb, total, E.Coff, cp);
     launch_gather_offsets(ctx->stream, E.Coff, E.it.item_base, np, doff);
     P->outoff.assign(np + 1, 0);
-    SG_CUDA(ctx, cudaMemcpyAsync(P->outoff.data(), doff, 8 * (np + 1), cudaMemcpyDeviceToHost, ctx->stream));
+    SG_TRY(read_back(ctx, P->outoff.data(), doff, 8 * (np + 1)));
     return sync_ctx(ctx);
 }
 

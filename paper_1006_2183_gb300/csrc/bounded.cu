@@ -92,8 +92,8 @@ spgemm_status_t engine_numeric_bounded(Engine* E, std::shared_ptr<DevBuf>* rbuf,
             note_launch();
         }
         launch_exclusive_scan(st, cap, U, cap_off, stmp);
-        SG_CUDA(ctx, cudaMemcpyAsync(&total, cap_off + U, 8, cudaMemcpyDeviceToHost, st));
-        SG_CUDA(ctx, cudaMemcpyAsync(&err, E->ctr + 2 * NBIN + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
+        SG_TRY(read_back(ctx, &total, cap_off + U, 8));
+        SG_TRY(read_back(ctx, &err, E->ctr + 2 * NBIN + 3, sizeof(int)));
         SG_TRY(sync_ctx(ctx));
     }
     if (err) return set_err(ctx, SPGEMM_ERR_INDEX_OVERFLOW, "slab tier capacity exceeded (code %d)", err);
@@ -116,7 +116,7 @@ spgemm_status_t engine_numeric_bounded(Engine* E, std::shared_ptr<DevBuf>* rbuf,
         auto sb = ctx_buf(ctx, 8 * (U1 + 1));
         if (!sb) return set_err(ctx, SPGEMM_ERR_OOM, "entry count");
         launch_exclusive_scan(st, E->nnz_item, U, (int64_t*)sb->p, stmp);
-        SG_CUDA(ctx, cudaMemcpyAsync(&nnz, (int64_t*)sb->p + U, 8, cudaMemcpyDeviceToHost, st));
+        SG_TRY(read_back(ctx, &nnz, (int64_t*)sb->p + U, 8));
         SG_TRY(sync_ctx(ctx));
     }
     SG_CUDA(ctx, cudaGetLastError());

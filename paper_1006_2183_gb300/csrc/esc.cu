@@ -166,7 +166,7 @@ spgemm_status_t esc_run(Engine* E, std::shared_ptr<DevBuf>* rbuf_out, std::share
     int64_t* F = (int64_t*)Fb->p;
     launch_exclusive_scan(st, E->flops, U, F, F + (U + 1));
     int64_t Ttot = 0;
-    SG_CUDA(ctx, cudaMemcpyAsync(&Ttot, F + U, 8, cudaMemcpyDeviceToHost, st));
+    SG_TRY(read_back(ctx, &Ttot, F + U, 8));
     SG_TRY(sync_ctx(ctx));
     // chunks of consecutive items holding about ESC_CHUNK products each
     const int64_t nc = std::max<int64_t>(1, ceil_div64(Ttot, ESC_CHUNK));
@@ -176,10 +176,10 @@ spgemm_status_t esc_run(Engine* E, std::shared_ptr<DevBuf>* rbuf_out, std::share
         if (!bb) return set_err(ctx, SPGEMM_ERR_OOM, "chunk bounds");
         k_esc_bounds<<<grid_esc(nc + 1), 256, 0, st>>>(F, U, ESC_CHUNK, nc, (int64_t*)bb->p);
         note_launch();
-        SG_CUDA(ctx, cudaMemcpyAsync(hb.data(), bb->p, 8 * (nc + 1), cudaMemcpyDeviceToHost, st));
+        SG_TRY(read_back(ctx, hb.data(), bb->p, 8 * (nc + 1)));
         SG_TRY(sync_ctx(ctx));
         for (int64_t c = 0; c <= nc; ++c)
-            SG_CUDA(ctx, cudaMemcpyAsync(&hf[c], F + hb[c], 8, cudaMemcpyDeviceToHost, st));
+            SG_TRY(read_back(ctx, &hf[c], F + hb[c], 8));
         SG_TRY(sync_ctx(ctx));
     }
     int64_t tmax = 1;
@@ -241,7 +241,7 @@ spgemm_status_t esc_run(Engine* E, std::shared_ptr<DevBuf>* rbuf_out, std::share
             note_launch();
         }
         launch_exclusive_scan(st, flag, Tc, opos, stmp);
-        SG_CUDA(ctx, cudaMemcpyAsync(&nc_nnz, opos + Tc, 8, cudaMemcpyDeviceToHost, st));
+        SG_TRY(read_back(ctx, &nc_nnz, opos + Tc, 8));
         SG_TRY(sync_ctx(ctx));
         auto rb = ctx_buf(ctx, 4 * std::max<int64_t>(nc_nnz, 1));
         auto vb = ctx_buf(ctx, sizeof(T) * std::max<int64_t>(nc_nnz, 1));

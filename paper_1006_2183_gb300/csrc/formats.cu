@@ -241,11 +241,11 @@ spgemm_status_t check_handles(spgemm_ctx* ctx, const std::vector<spgemm_mat*>& m
         k_validate_many<<<grid_for(hb[nh] * 32), 256, 0, st>>>(dd, db, nh, dbad);
         note_launch();
     }
-    SG_CUDA(ctx, cudaMemcpyAsync(hbad.data(), dbad, 4 * nh, cudaMemcpyDeviceToHost, st));
+    SG_TRY(read_back(ctx, hbad.data(), dbad, 4 * nh));
     // a matrix without columns: its (single) column pointer must be 0 and nnz 0
     std::vector<int64_t> c0(nh, 0);
     for (int h = 0; h < nh; ++h)
-        if (hb[h + 1] == hb[h]) SG_CUDA(ctx, cudaMemcpyAsync(&c0[h], todo[h]->cp, 8, cudaMemcpyDeviceToHost, st));
+        if (hb[h + 1] == hb[h]) SG_TRY(read_back(ctx, &c0[h], todo[h]->cp, 8));
     SG_TRY(sync_ctx(ctx));
     static const char* why[] = {"", "colptr[0] != 0", "colptr[n] != nnz", "colptr not monotone",
                                 "row index out of range", "rows not strictly ascending in a column"};
@@ -374,7 +374,7 @@ spgemm_status_t make_dcsc(spgemm_ctx* ctx, const spgemm_mat* M, bool with_aux, s
         k_nonempty<<<grid_for(n), 256, 0, st>>>(M->cp, n, flag);
         note_launch();
         launch_exclusive_scan(st, flag, n, pos, stmp);
-        SG_CUDA(ctx, cudaMemcpyAsync(&nzc, pos + n, 8, cudaMemcpyDeviceToHost, st));
+        SG_TRY(read_back(ctx, &nzc, pos + n, 8));
         SG_TRY(sync_ctx(ctx));
     }
     const int64_t chunk = n == 0 ? 1 : (nzc > 0 ? ceil_div64(n, nzc) : n);
@@ -489,7 +489,7 @@ static spgemm_status_t check_perm(spgemm_ctx* ctx, const int32_t* perm, int64_t 
     k_perm_check<<<grid_for(n), 256, 0, st>>>(cnt, n, bad);
     note_launch(2);
     int h = 0;
-    SG_CUDA(ctx, cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SG_TRY(read_back(ctx, &h, bad, sizeof(int)));
     SG_TRY(sync_ctx(ctx));
     if (h) return set_err(ctx, SPGEMM_ERR_INVALID_ARG, "%s is not a permutation of 0..%lld", what, (long long)(n - 1));
     return SPGEMM_OK;
@@ -648,12 +648,12 @@ spgemm_status_t spgemm_mat_validate(spgemm_mat_t M) {
         note_launch();
     } else {
         int64_t c0 = -1;
-        SG_CUDA(ctx, cudaMemcpyAsync(&c0, M->cp, 8, cudaMemcpyDeviceToHost, ctx->stream));
+        SG_TRY(read_back(ctx, &c0, M->cp, 8));
         SG_TRY(sync_ctx(ctx));
         if (c0 != 0 || M->nnz != 0) h = 1;
     }
     if (sn > 0) {
-        SG_CUDA(ctx, cudaMemcpyAsync(&h, flag->p, 4, cudaMemcpyDeviceToHost, ctx->stream));
+        SG_TRY(read_back(ctx, &h, flag->p, 4));
         SG_TRY(sync_ctx(ctx));
     }
     static const char* why[] = {"", "colptr[0] != 0", "colptr[n] != nnz", "colptr not monotone",

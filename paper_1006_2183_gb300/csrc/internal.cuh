@@ -37,6 +37,15 @@ struct spgemm_ctx {
     // statistics of the last SUMMA call
     std::vector<int64_t> summa_stage_flops;
     int64_t summa_nonempty = 0;
+    // Small device -> host reads (counts, offsets, flags) are written by a kernel into
+    // mapped pinned memory and copied out on the host at the next sync_ctx: a
+    // cudaMemcpyAsync device -> host would wait behind every bulk device -> host copy
+    // already queued on the copy engine (from any stream, the caller's included).
+    unsigned char* rb_host = nullptr;   // cudaHostAlloc(..., cudaHostAllocMapped)
+    unsigned char* rb_dev = nullptr;    // its device address
+    size_t rb_cap = 0, rb_used = 0;
+    struct Readback { void* dst; size_t off, bytes; };
+    std::vector<Readback> rb_pending;
 };
 
 // Shared ownership of an allocation (batch outputs share one buffer).
@@ -155,6 +164,9 @@ size_t sr_size(spgemm_semiring_t sr);
 sg::DMat dmat_of(const spgemm_mat* M);
 spgemm_status_t check_cuda(spgemm_ctx* ctx, cudaError_t e, const char* what);
 spgemm_status_t sync_ctx(spgemm_ctx* ctx);
+// Queues a read of `bytes` at device address src into host memory dst, on the context
+// stream; dst holds the bytes after the next sync_ctx (not before).
+spgemm_status_t read_back(spgemm_ctx* ctx, void* dst, const void* src, size_t bytes);
 
 // formats.cu
 // Checks, in one launch and one synchronisation, every handle of `mats` that is a

@@ -276,7 +276,7 @@ spgemm_status_t engine_numeric_predicted(Engine* E, std::shared_ptr<DevBuf>* rbu
             note_launch();
         }
         launch_exclusive_scan(st, cap, U, cap_off, E->scan_tmp);
-        SG_CUDA(ctx, cudaMemcpyAsync(&total_cap, cap_off + U, 8, cudaMemcpyDeviceToHost, st));
+        SG_TRY(read_back(ctx, &total_cap, cap_off + U, 8));
         SG_TRY(sync_ctx(ctx));
     }
     auto trb = ctx_buf(ctx, 4 * (size_t)std::max<int64_t>(total_cap, 1));
@@ -319,8 +319,8 @@ spgemm_status_t engine_numeric_predicted(Engine* E, std::shared_ptr<DevBuf>* rbu
                                                         E->bin_off_dev, octr, olist);
             note_launch();
         }
-        SG_CUDA(ctx, cudaMemcpyAsync(&nnz, E->Coff + U, 8, cudaMemcpyDeviceToHost, st));
-        SG_CUDA(ctx, cudaMemcpyAsync(ocnt, octr, 8 * NBIN, cudaMemcpyDeviceToHost, st));
+        SG_TRY(read_back(ctx, &nnz, E->Coff + U, 8));
+        SG_TRY(read_back(ctx, ocnt, octr, 8 * NBIN));
         SG_TRY(sync_ctx(ctx));
     }
     E->nnz_total = nnz;
@@ -378,7 +378,7 @@ spgemm_status_t spgemm_predictor_set(spgemm_ctx_t ctx, const float* params) {
 spgemm_status_t spgemm_predictor_get(spgemm_ctx_t ctx, float* params) {
     if (!ctx || !params) return SPGEMM_ERR_INVALID_ARG;
     if (!ctx->pred_ready) return set_err(ctx, SPGEMM_ERR_STATE, "predictor parameters are not set");
-    SG_CUDA(ctx, cudaMemcpyAsync(params, ctx->pred, 4 * NP, cudaMemcpyDeviceToHost, ctx->stream));
+    SG_TRY(read_back(ctx, params, ctx->pred, 4 * NP));
     return sync_ctx(ctx);
 }
 
@@ -411,9 +411,9 @@ spgemm_status_t spgemm_predictor_train_step(spgemm_ctx_t ctx, const float* X, co
     SG_CUDA(ctx, cudaMemsetAsync(ctx->grad, 0, 4 * (NP + 1), st));
     k_mlp_grad<<<gridp(N), 256, 0, st>>>(ctx->pred, X, y, N, ctx->grad, ctx->grad + NP);
     note_launch();
-    if (grad_host) SG_CUDA(ctx, cudaMemcpyAsync(grad_host, ctx->grad, 4 * NP, cudaMemcpyDeviceToHost, st));
+    if (grad_host) SG_TRY(read_back(ctx, grad_host, ctx->grad, 4 * NP));
     float l = 0.f;
-    SG_CUDA(ctx, cudaMemcpyAsync(&l, ctx->grad + NP, 4, cudaMemcpyDeviceToHost, st));
+    SG_TRY(read_back(ctx, &l, ctx->grad + NP, 4));
     ctx->adam_t += 1;
     k_adam<<<(NP + 255) / 256, 256, 0, st>>>(ctx->pred, ctx->grad, ctx->adam_m, ctx->adam_v, ctx->adam_t, lr);
     note_launch();

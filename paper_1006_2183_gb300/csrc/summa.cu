@@ -284,7 +284,7 @@ spgemm_status_t partition(spgemm_ctx* ctx, const DMat& M, size_t w, int g, Block
         k_block_counts<<<(int)ceil_div64(nblk, 256), 256, 0, st>>>(sk, nnz, pos, nblk, bcnt, bcnt + nblk);
         note_launch(2);
         std::vector<unsigned long long> hc(2 * nblk + 1);
-        SG_CUDA(ctx, cudaMemcpyAsync(hc.data(), bcnt, 16 * nblk + 8, cudaMemcpyDeviceToHost, st));
+        SG_TRY(read_back(ctx, hc.data(), bcnt, 16 * nblk + 8));
         SG_TRY(sync_ctx(ctx));
         if (hc[2 * nblk])
             return set_err(ctx, SPGEMM_ERR_BAD_FORMAT, "partition: %llu row indices outside [0, %lld)",
@@ -470,7 +470,7 @@ spgemm_status_t stage_products(spgemm_ctx* ctx, spgemm_semiring_t sr, const spge
     k_prod_flops<<<gridn(ceil_div64(G->U, PF_RUN)), 256, 0, ctx->stream>>>(E.it, E.item_prod, E.flops, (unsigned long long*)pf->p);
     note_launch();
     std::vector<unsigned long long> hpf(grp.size());
-    SG_CUDA(ctx, cudaMemcpyAsync(hpf.data(), pf->p, 8 * grp.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    SG_TRY(read_back(ctx, hpf.data(), pf->p, 8 * grp.size()));
     SG_TRY(sync_ctx(ctx));
     for (size_t i = 0; i < grp.size(); ++i) ctx->summa_stage_flops[grp[i].tag] += (int64_t)hpf[i];
     return SPGEMM_OK;
@@ -632,7 +632,7 @@ spgemm_status_t summa_run(spgemm_ctx_t ctx, spgemm_ctx_t mctx, spgemm_mat_t A, s
         launch_any_false(ctx->stream, A->num, A->nnz, (int*)fb->p);
         launch_any_false(ctx->stream, B->num, B->nnz, (int*)fb->p);
         int hf = 0;
-        SG_CUDA(ctx, cudaMemcpyAsync(&hf, fb->p, 4, cudaMemcpyDeviceToHost, ctx->stream));
+        SG_TRY(read_back(ctx, &hf, fb->p, 4));
         SG_TRY(sync_ctx(ctx));
         ctx->bool_hint = hf ? 1 : 0;
         if (mctx) mctx->bool_hint = ctx->bool_hint;
@@ -804,7 +804,7 @@ spgemm_status_t spgemm_summa_block_flops(spgemm_ctx_t ctx, spgemm_mat_t A, spgem
     k_prod_flops<<<gridn(ceil_div64(E.it.nitems, PF_RUN)), 256, 0, ctx->stream>>>(E.it, E.item_prod, E.flops, (unsigned long long*)pf->p);
     note_launch();
     std::vector<unsigned long long> h(all.size());
-    SG_CUDA(ctx, cudaMemcpyAsync(h.data(), pf->p, 8 * all.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    SG_TRY(read_back(ctx, h.data(), pf->p, 8 * all.size()));
     SG_TRY(sync_ctx(ctx));
     for (size_t i = 0; i < all.size(); ++i) flops[slot[i]] = (int64_t)h[i];
     return SPGEMM_OK;
