@@ -690,13 +690,17 @@ def e2e_leg(sp, ctx, W, steps, warmup, flush, world):
     out_v = _t.empty(nzmax * 8, dtype=_t.uint8).pin_memory()   # viewed per semiring
     d2h = sum((A64.n + 1) * 8 + nz * (4 + SR_WIDTH[sr]) for (kind, sr), nz in W["nnz_seen"].items())
     side = _t.cuda.Stream()
+    # the copies back are the longer part: start them as early as possible (the flat
+    # products first, the smaller boolean result leading) and end the step on a short
+    # one (the boolean SUMMA result last)
+    order = sorted(products, key=lambda p: (p[0] != "flat", (p[1] == sp.OR_AND_BOOL) != (p[0] == "flat")))
     et = []
     for it in range(warmup + steps):
         flush.fill_(1.0)
         _t.cuda.synchronize()
         t0 = time.perf_counter()
         inflight = []   # (copy finished, what the copy still reads)
-        for (kind, sr) in products:
+        for (kind, sr) in order:
             cp, ir, v = (x.to(dev, non_blocking=True) for x in pinned[sr])
             M = sp.Matrix.csc(ctx, A64.m, A64.n, cp, ir, v, sr)
             C, plan = run_product(kind, sr, M)

@@ -132,18 +132,44 @@ __global__ void __launch_bounds__(256) k_analyze(Items it, TierCfg cfg, int64_t*
         am = pr->A.m;
         const uint64_t* skp = sketch ? sketch + sketch_base[prod] : nullptr;
         const int64_t b0 = it.acs ? pr->bnz_base - __ldg(pr->B.cp) : 0;
-        for (int64_t t = bs + sub; t < be; t += LPI) {
-            int32_t k = __ldg(pr->B.ir + t);
-            int64_t cs, ce;
-            col_range(pr->A, k, cs, ce);
-            long long len = ce - cs;
-            if (it.acs) {   // fill the A-column cache for the later passes
-                it.acs[b0 + t] = cs;
-                it.acl[b0 + t] = (int32_t)len;
+        if constexpr (LPI == 1) {
+            // two entries of B(:,j) at a time, each step of their A-column lookups issued
+            // for both before either is used (a lookup is a chain of dependent loads: B's
+            // row, then AUX, then JC, then CP)
+            const DMat& A = pr->A;
+            for (int64_t t0 = bs; t0 < be; t0 += 2) {
+                int32_t k[2];
+#pragma unroll
+                for (int i = 0; i < 2; ++i) k[i] = t0 + i < be ? __ldg(pr->B.ir + t0 + i) : -1;
+                int64_t cs[2], ce[2];
+                col_range2(A, k, cs, ce);
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    if (t0 + i >= be) break;
+                    const long long len = ce[i] - cs[i];
+                    if (it.acs) {   // fill the A-column cache for the later passes
+                        it.acs[b0 + t0 + i] = cs[i];
+                        it.acl[b0 + t0 + i] = (int32_t)len;
+                    }
+                    f += len;
+                    mx = len > mx ? len : mx;
+                    if (skp && k[i] >= 0 && k[i] < A.n) sk |= __ldg(skp + k[i]);
+                }
             }
-            f += len;
-            mx = len > mx ? len : mx;
-            if (skp && k >= 0 && k < pr->A.n) sk |= __ldg(skp + k);
+        } else {
+            for (int64_t t = bs + sub; t < be; t += LPI) {
+                int32_t k = __ldg(pr->B.ir + t);
+                int64_t cs, ce;
+                col_range(pr->A, k, cs, ce);
+                long long len = ce - cs;
+                if (it.acs) {   // fill the A-column cache for the later passes
+                    it.acs[b0 + t] = cs;
+                    it.acl[b0 + t] = (int32_t)len;
+                }
+                f += len;
+                mx = len > mx ? len : mx;
+                if (skp && k >= 0 && k < pr->A.n) sk |= __ldg(skp + k);
+            }
         }
     }
 #pragma unroll

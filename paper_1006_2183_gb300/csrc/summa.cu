@@ -140,21 +140,34 @@ __global__ void k_block_aux(int nblk, const int64_t* __restrict__ boff, const in
 
 // Output column of every item: col_base + JC[p] of the product's B.
 __global__ void k_item_outcol(Items it, const int32_t* __restrict__ item_prod, int g, uint32_t* __restrict__ oc,
-                              uint32_t* __restrict__ pay, int64_t ofs) {
+                              int64_t ofs) {
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < it.nitems; u += (int64_t)gridDim.x * blockDim.x) {
         const int prod = item_prod[u];
         const Prod* pr = it.prods + prod;
         const int64_t p = u - it.item_base[prod];
         const int64_t j = pr->B.jc ? pr->B.jc[p] : p;
         oc[ofs + u] = (uint32_t)((pr->col_base + j) * g + pr->blk);
-        pay[ofs + u] = (uint32_t)(ofs + u);
     }
 }
 
-__global__ void k_iota_cols(uint32_t* oc, uint32_t* pay, int64_t n) {
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+__global__ void k_iota_cols(uint32_t* oc, int64_t n) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
         oc[j] = (uint32_t)j;
-        pay[j] = (uint32_t)j;
+}
+
+// The selector's rows for one run of merge inputs [u0, u0 + cnt) whose output columns
+// oc[u] are all different (the accumulated columns, or the partial columns of one
+// stage): each input takes the next free slot of its column.  The runs are filled in
+// input order, one launch after another, so every column lists its inputs in input
+// order, the order a stable sort by output column gives.
+__global__ void k_sel_fill(const uint32_t* __restrict__ oc, int64_t u0, int64_t cnt, int64_t* __restrict__ cur,
+                           int32_t* __restrict__ sir) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t u = u0 + i;
+        const uint32_t t = oc[u];
+        const int64_t pos = cur[t];
+        sir[pos] = (int32_t)u;
+        cur[t] = pos + 1;
     }
 }
 
@@ -167,11 +180,6 @@ __global__ void k_every_gth(const int64_t* __restrict__ Coff, int64_t n, int g, 
 __global__ void k_hist_u32(const uint32_t* __restrict__ k, int64_t n, int64_t* __restrict__ cnt) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         atomicAdd(reinterpret_cast<unsigned long long*>(cnt + k[i]), 1ull);
-}
-
-__global__ void k_u32_to_i32(const uint32_t* __restrict__ in, int64_t n, int32_t* __restrict__ out) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = (int32_t)in[i];
 }
 
 __global__ void k_add_offset(const int64_t* __restrict__ in, int64_t n, int64_t add, int64_t* __restrict__ out) {
@@ -246,7 +254,7 @@ spgemm_status_t partition(spgemm_ctx* ctx, const DMat& M, size_t w, int g, Block
     };
     size_t o_k0 = take(4 * nz1), o_v0 = take(4 * nz1), o_k1 = take(4 * nz1), o_v1 = take(4 * nz1);
     size_t o_col = take(4 * nz1), o_lcol = take(4 * nz1), o_flag = take(8 * nz1), o_pos = take(8 * (nz1 + 1));
-    size_t o_cnt = take(8 * (2 * nblk + 1)), o_boff = take(8 * (nblk + 1)), o_jcb = take(8 * (nblk + 1));
+    size_t o_cnt = take(8 * (2 * nblk + 1));
     size_t o_rs = take(radix_tmp_bytes(nz1)), o_sc = take(scan_tmp_bytes(std::max<int64_t>(nz1, nblk)));
     auto tmp = ctx_buf(ctx, off);
     if (!tmp) return set_err(ctx, SPGEMM_ERR_OOM, "partition temporaries");
@@ -258,8 +266,6 @@ spgemm_status_t partition(spgemm_ctx* ctx, const DMat& M, size_t w, int g, Block
     int64_t* flag = (int64_t*)(t + o_flag);
     int64_t* pos = (int64_t*)(t + o_pos);
     unsigned long long* bcnt = (unsigned long long*)(t + o_cnt);   // bnnz[nblk], bnzc[nblk], bad rows
-    int64_t* boff = (int64_t*)(t + o_boff);
-    int64_t* jcbase = (int64_t*)(t + o_jcb);
     SG_CUDA(ctx, cudaMemsetAsync(bcnt, 0, 16 * nblk + 8, st));
     std::vector<int64_t> hnnz(nblk, 0), hnzc(nblk, 0);
     if (nnz > 0) {
@@ -364,11 +370,13 @@ bool bounded_fits(const Engine& E) {
 
 // Merges the partial columns P (local rows < mb; column u goes to merge column
 // oc[u] = j * g + I) into the mb x (n g) matrix of merge columns, or, when
-// `final`, into C (m x n, global rows I * mb + local row).
+// `final`, into C (m x n, global rows I * mb + local row).  `runs` cover [0, ncols)
+// in order, each a range of inputs whose merge columns are all different.
 spgemm_status_t merge_columns(spgemm_ctx* ctx, spgemm_semiring_t sr, const spgemm_opts_t& opts, int64_t m,
                               int64_t mb, int64_t n0, int g, bool final, int64_t ncols, const int64_t* Pcp,
-                              const int64_t* Pce, const int32_t* Pir, const void* Pv, int64_t pnnz, uint32_t* oc,
-                              uint32_t* pay, spgemm_mat_t* C) {
+                              const int64_t* Pce, const int32_t* Pir, const void* Pv, int64_t pnnz,
+                              const uint32_t* oc, const std::vector<std::pair<int64_t, int64_t>>& runs,
+                              spgemm_mat_t* C) {
     cudaStream_t st = ctx->stream;
     PhaseTimer tm(ctx, SPGEMM_PHASE_MERGE, sr);
     const int64_t n = n0 * g;   // merge columns
@@ -379,27 +387,30 @@ spgemm_status_t merge_columns(spgemm_ctx* ctx, spgemm_semiring_t sr, const spgem
         off += (bytes + 255) / 256 * 256;
         return o;
     };
-    size_t o_k1 = take(4 * nc1), o_v1 = take(4 * nc1), o_cnt = take(8 * (n + 1)), o_rs = take(radix_tmp_bytes(nc1)),
-           o_sc = take(scan_tmp_bytes(std::max<int64_t>(n, 1)));
+    size_t o_cnt = take(8 * (n + 1)), o_sc = take(scan_tmp_bytes(std::max<int64_t>(n, 1)));
     auto tmp = ctx_buf(ctx, off);
     auto scp = ctx_buf(ctx, 8 * (n + 1));
     auto sir = ctx_buf(ctx, 4 * nc1);
     if (!tmp || !scp || !sir) return set_err(ctx, SPGEMM_ERR_OOM, "merge selector");
     char* t = (char*)tmp->p;
-    int bits = 0;
-    while (bits < 32 && (int64_t(1) << bits) < std::max<int64_t>(n, 1)) ++bits;
-    bool second = false;
-    radix_sort_pairs(st, oc, pay, (uint32_t*)(t + o_k1), (uint32_t*)(t + o_v1), ncols, bits, t + o_rs, &second);
-    const uint32_t* sk = second ? (uint32_t*)(t + o_k1) : oc;
-    const uint32_t* sv = second ? (uint32_t*)(t + o_v1) : pay;
+    // the selector S in CSC: inputs per merge column (a count and a scan), then every
+    // input placed at the next free slot of its column, run after run
     int64_t* cnt = (int64_t*)(t + o_cnt);
     SG_CUDA(ctx, cudaMemsetAsync(cnt, 0, 8 * (n + 1), st));
     if (ncols > 0) {
-        k_hist_u32<<<gridn(ncols), 256, 0, st>>>(sk, ncols, cnt);
-        k_u32_to_i32<<<gridn(ncols), 256, 0, st>>>(sv, ncols, (int32_t*)sir->p);
-        note_launch(2);
+        k_hist_u32<<<gridn(ncols), 256, 0, st>>>(oc, ncols, cnt);
+        note_launch();
     }
     launch_exclusive_scan(st, cnt, n, (int64_t*)scp->p, t + o_sc);
+    if (ncols > 0) {
+        SG_CUDA(ctx, cudaMemcpyAsync(cnt, scp->p, 8 * n, cudaMemcpyDeviceToDevice, st));
+        for (const auto& r : runs) {
+            if (r.second <= r.first) continue;
+            k_sel_fill<<<gridn(r.second - r.first), 256, 0, st>>>(oc, r.first, r.second - r.first, cnt,
+                                                                  (int32_t*)sir->p);
+            note_launch();
+        }
+    }
     // C = P * S
     Prod pr;
     pr.A = csc_view(mb, ncols, pnnz, Pcp, Pir, Pv);
@@ -489,10 +500,9 @@ spgemm_status_t merge_group(spgemm_ctx* mctx, spgemm_semiring_t sr, const spgemm
     const int64_t ncols = nacc + U;
     const int64_t pnz = accnz + pn;
     cudaStream_t stq = mctx->stream;
-    auto ocb = ctx_buf(mctx, 8 * std::max<int64_t>(ncols, 1));
+    auto ocb = ctx_buf(mctx, 4 * std::max<int64_t>(ncols, 1));
     if (!ocb) return set_err(mctx, SPGEMM_ERR_OOM, "merge keys");
     uint32_t* oc = (uint32_t*)ocb->p;
-    uint32_t* pay = oc + std::max<int64_t>(ncols, 1);
     std::shared_ptr<DevBuf> pcp, pir, pv;
     const int64_t* Pcp;
     const int32_t* Pir;
@@ -532,15 +542,25 @@ spgemm_status_t merge_group(spgemm_ctx* mctx, spgemm_semiring_t sr, const spgemm
         Pir = (const int32_t*)pir->p;
         Pv = pv->p;
     }
+    // runs of inputs whose merge columns differ: the accumulated columns, then the
+    // partial columns of each stage (one per merge column at most; items are stage-major)
+    std::vector<std::pair<int64_t, int64_t>> runs;
     if (acc) {
-        k_iota_cols<<<gridn(nacc), 256, 0, stq>>>(oc, pay, nacc);
+        k_iota_cols<<<gridn(nacc), 256, 0, stq>>>(oc, nacc);
         note_launch();
+        runs.push_back({0, nacc});
     }
     if (U > 0) {
-        k_item_outcol<<<gridn(U), 256, 0, stq>>>(E.it, E.item_prod, g, oc, pay, nacc);
+        k_item_outcol<<<gridn(U), 256, 0, stq>>>(E.it, E.item_prod, g, oc, nacc);
         note_launch();
+        for (size_t i = 0; i < E.hprods.size();) {
+            size_t j = i;
+            while (j < E.hprods.size() && E.hprods[j].tag == E.hprods[i].tag) ++j;
+            runs.push_back({nacc + E.hitem_base[i], nacc + E.hitem_base[j]});
+            i = j;
+        }
     }
-    return merge_columns(mctx, sr, o, m, mb, n, g, G.final, ncols, Pcp, Pce, Pir, Pv, pnz, oc, pay, Cn);
+    return merge_columns(mctx, sr, o, m, mb, n, g, G.final, ncols, Pcp, Pce, Pir, Pv, pnz, oc, runs, Cn);
 }
 
 // Hand-over between the products (calling thread, ctx's stream) and the merges
