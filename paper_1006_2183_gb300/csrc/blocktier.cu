@@ -178,8 +178,12 @@ __device__ __forceinline__ int row_word(bool ok, int32_t r, int m) { return ok &
 // offsets are exact.  With nnz_item the column's count is recorded there and the
 // column is written only when it fits its capacity Coff[u+1] - Coff[u] (the
 // predicted and the upper-bound layouts).
+// The 512-thread form is held to 32 registers, so that four CTAs (64 warps) stay resident
+// per SM: its time is the walk of L2 reductions, which more warps keep in flight.  In the
+// FP64 32 x 32 SUMMA at R-MAT scale 20, two CTAs per SM (59 registers) took 3.4 ms longer
+// in the stage products and 7.8 ms longer in the merge; three CTAs took 0.4 and 2.0 ms longer.
 template <class SR, int GS, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_block_tier(Items it, const int2* __restrict__ list, int64_t count,
+__global__ void __launch_bounds__(BLOCK, BLOCK == 512 ? 4 : 1) k_block_tier(Items it, const int2* __restrict__ list, int64_t count,
                                                      int64_t* __restrict__ nnz_item, const int64_t* __restrict__ Coff,
                                                      int32_t* __restrict__ Cir, typename SR::T* __restrict__ Cv,
                                                      const int* __restrict__ vals_zero) {
